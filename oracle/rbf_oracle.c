@@ -1,0 +1,528 @@
+/*
+ * rbf_oracle.c -- plain FP64 CPU oracle for RBF mesh deformation with the
+ * grouping-circular-based (GCB) greedy support-node selection.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * reference that the CUDA library is checked against.  It shares no code,
+ * header, table or helper with the CUDA path, and the product never calls
+ * it: only tests/, the smoke check and bench.py's CPU-baseline leg do.
+ *
+ * Every routine follows the paper step by step, in double precision, with
+ * no blocking, fusion or reordering beyond what the text states:
+ *
+ *   - Wendland C2 basis, Eq. 2:  phi(eta) = (1-eta)^4 (4 eta + 1), eta <= 1;
+ *     0 otherwise; eta = distance / R (the "RBF radius", Sec. 2 and Sec. 4).
+ *   - RBF interpolant, Eq. 1 and volume displacement, Eq. 6:
+ *     F(r) = sum_i w_i phi(|r - r_i| / R), one weight vector per axis, Eq. 4.
+ *   - Support system, Eqs. 3-5 restricted to the support set S: Phi_SS W = dX_S,
+ *     SPD (Sec. 2), solved by a dense Cholesky factorisation from scratch at
+ *     every iteration (the plain re-solve the greedy literature starts from,
+ *     Sec. 1).
+ *   - GCB greedy, Algorithm 1 (Sec. 3): random uniform partition into m
+ *     groups, 3 seed nodes, then for k = 3, 4, ...: solve, i = k mod m,
+ *     errors in G_i, local maximum, append if E > E*.
+ *
+ * Readings of points the paper leaves open (all listed in the design doc):
+ *   - error of node q: E_q = || dr_q - F(r_q) ||_2 (Euclidean norm of the
+ *     3-vector);
+ *   - partition: SplitMix64 stream from the seed, Fisher-Yates shuffle from the
+ *     last position down, node perm[p] belongs to group p mod m;
+ *   - seed nodes: n0 = argmax |dr|, n1 = farthest node from n0,
+ *     n2 = node farthest from {n0, n1}; lowest index on ties;
+ *   - argmax ties: lowest node index; nodes already in S are skipped;
+ *   - strict comparison E > E*;
+ *   - termination: a full check (all nodes, current weights) with global
+ *     maximum <= E*.  It runs when an active group adds nothing and after
+ *     every m-th iteration; a failed check continues with the next group,
+ *     which leaves the literal algorithm's selection sequence unchanged;
+ *   - N_c^max caps |S|.
+ *
+ * Parity pins (tests/test_oracle_*.py): closed-form phi values, partition
+ * invariants, a published SplitMix64 output, brute-force selection on tiny
+ * problems through numpy.linalg.solve, reproduction of the prescribed
+ * displacement at support nodes, SPD pivots, m = 1 equal to the plain greedy.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_E_ARG 1
+#define ORC_E_NOT_SPD 2
+#define ORC_E_NC_MAX 3
+#define ORC_E_NOMEM 5
+#define ORC_E_FOLLOW 8
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 2: Wendland C2 basis function of the normalised distance eta.        */
+/* ------------------------------------------------------------------------ */
+double orc_phi(double eta)
+{
+    if (eta > 1.0)
+        return 0.0;
+    double t = 1.0 - eta;
+    return t * t * t * t * (4.0 * eta + 1.0);
+}
+
+static double dist3(const double *a, const double *b)
+{
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Partition into m groups (Sec. 3, Algorithm 1 first step).               */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): one step of the stream. */
+uint64_t orc_splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* perm: a random permutation of 0..nb-1 by the Fisher-Yates shuffle driven
+ * by SplitMix64(seed).  Node perm[p] is in group p mod m, so the groups are
+ * disjoint, cover all nodes and differ in size by at most one. */
+void orc_permutation(int64_t nb, uint64_t seed, int32_t *perm)
+{
+    uint64_t st = seed;
+    for (int64_t p = 0; p < nb; ++p)
+        perm[p] = (int32_t)p;
+    for (int64_t i = nb - 1; i >= 1; --i) {
+        uint64_t j = orc_splitmix64_next(&st) % (uint64_t)(i + 1);
+        int32_t tmp = perm[i];
+        perm[i] = perm[j];
+        perm[j] = tmp;
+    }
+}
+
+/* group_of[node] = group index (0..m-1). */
+void orc_groups(int64_t nb, int64_t m, uint64_t seed, int32_t *group_of)
+{
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
+    orc_permutation(nb, seed, perm);
+    for (int64_t p = 0; p < nb; ++p)
+        group_of[perm[p]] = (int32_t)(p % m);
+    free(perm);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Seed nodes (Algorithm 1: "select any 3 nodes").                          */
+/* ------------------------------------------------------------------------ */
+void orc_seed_nodes(const double *xb, const double *db, int64_t nb, int32_t out[3])
+{
+    int64_t n0 = 0;
+    double best = -1.0;
+    for (int64_t j = 0; j < nb; ++j) {
+        const double *d = db + 3 * j;
+        double v = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (v > best) { best = v; n0 = j; }
+    }
+    int64_t n1 = 0;
+    best = -1.0;
+    for (int64_t j = 0; j < nb; ++j) {
+        const double *a = xb + 3 * j, *b = xb + 3 * n0;
+        double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+        double v = dx * dx + dy * dy + dz * dz;
+        if (v > best) { best = v; n1 = j; }
+    }
+    int64_t n2 = 0;
+    best = -1.0;
+    for (int64_t j = 0; j < nb; ++j) {
+        const double *a = xb + 3 * j, *b0 = xb + 3 * n0, *b1 = xb + 3 * n1;
+        double dx = a[0] - b0[0], dy = a[1] - b0[1], dz = a[2] - b0[2];
+        double v0 = dx * dx + dy * dy + dz * dz;
+        dx = a[0] - b1[0]; dy = a[1] - b1[1]; dz = a[2] - b1[2];
+        double v1 = dx * dx + dy * dy + dz * dz;
+        double v = v0 < v1 ? v0 : v1;
+        if (v > best) { best = v; n2 = j; }
+    }
+    out[0] = (int32_t)n0;
+    out[1] = (int32_t)n1;
+    out[2] = (int32_t)n2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense SPD solve (Sec. 2: Phi is SPD, so Cholesky applies).               */
+/* ------------------------------------------------------------------------ */
+
+/* A squared pivot at or below this fraction of its diagonal entry means the
+ * matrix is singular to working precision (coincident nodes make Phi exactly
+ * singular, but rounding can leave a pivot of order 1e-16 instead of 0). */
+#define ORC_PIVOT_REL 1e-13
+
+/* In-place lower Cholesky of the n x n row-major matrix A (upper part is not
+ * referenced).  Returns ORC_E_NOT_SPD if a pivot is not positive. */
+int orc_cholesky(int64_t n, double *A)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        double diag = s;
+        for (int64_t p = 0; p < j; ++p)
+            s -= A[j * n + p] * A[j * n + p];
+        if (!(s > ORC_PIVOT_REL * diag))
+            return ORC_E_NOT_SPD;
+        double ljj = sqrt(s);
+        A[j * n + j] = ljj;
+        for (int64_t i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int64_t p = 0; p < j; ++p)
+                t -= A[i * n + p] * A[j * n + p];
+            A[i * n + j] = t / ljj;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Solve L L^T X = B for nrhs right-hand sides stored row-major (n x nrhs). */
+void orc_cholesky_solve(int64_t n, const double *L, double *B, int nrhs)
+{
+    for (int c = 0; c < nrhs; ++c) {
+        for (int64_t i = 0; i < n; ++i) {           /* forward: L y = b */
+            double t = B[i * nrhs + c];
+            for (int64_t p = 0; p < i; ++p)
+                t -= L[i * n + p] * B[p * nrhs + c];
+            B[i * nrhs + c] = t / L[i * n + i];
+        }
+        for (int64_t i = n - 1; i >= 0; --i) {      /* backward: L^T x = y */
+            double t = B[i * nrhs + c];
+            for (int64_t p = i + 1; p < n; ++p)
+                t -= L[p * n + i] * B[p * nrhs + c];
+            B[i * nrhs + c] = t / L[i * n + i];
+        }
+    }
+}
+
+/* Weights of the support set S (Eqs. 4-5 restricted to S): Phi_SS W = dX_S.
+ * W is k x 3 row-major.  Optionally returns the smallest Cholesky pivot. */
+int orc_solve_weights(const double *xb, const double *db, const int32_t *S, int64_t k,
+                      double R, double *W, double *min_pivot)
+{
+    double *A = (double *)malloc(sizeof(double) * (size_t)(k * k > 0 ? k * k : 1));
+    if (!A)
+        return ORC_E_NOMEM;
+    for (int64_t i = 0; i < k; ++i)
+        for (int64_t j = 0; j < k; ++j)
+            A[i * k + j] = orc_phi(dist3(xb + 3 * S[i], xb + 3 * S[j]) / R);
+    int st = orc_cholesky(k, A);
+    if (st == ORC_OK) {
+        for (int64_t i = 0; i < k; ++i)
+            for (int c = 0; c < 3; ++c)
+                W[i * 3 + c] = db[3 * S[i] + c];
+        orc_cholesky_solve(k, A, W, 3);
+        if (min_pivot) {
+            double mp = INFINITY;
+            for (int64_t i = 0; i < k; ++i)
+                if (A[i * k + i] < mp) mp = A[i * k + i];
+            *min_pivot = mp * mp;
+        }
+    }
+    free(A);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 / Eq. 6: F(r) at arbitrary points, and the interpolation error.    */
+/* ------------------------------------------------------------------------ */
+
+/* out (nq x 3) = sum_j W_j phi(|x_q - c_j| / R), centres c_j = xb[S[j]]. */
+void orc_rbf_sum(const double *xq, int64_t nq, const double *xb, const int32_t *S,
+                 int64_t k, const double *W, double R, double *out, int nthreads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t q = 0; q < nq; ++q) {
+        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+        for (int64_t j = 0; j < k; ++j) {
+            double p = orc_phi(dist3(xq + 3 * q, xb + 3 * S[j]) / R);
+            f0 += W[3 * j + 0] * p;
+            f1 += W[3 * j + 1] * p;
+            f2 += W[3 * j + 2] * p;
+        }
+        out[3 * q + 0] = f0;
+        out[3 * q + 1] = f1;
+        out[3 * q + 2] = f2;
+    }
+    (void)nthreads;
+}
+
+/* E_q = |dr_q - F(x_q)|_2 for the listed boundary nodes q = idx[t]. */
+static void node_errors(const double *xb, const double *db, const int32_t *idx, int64_t n,
+                        const int32_t *S, int64_t k, const double *W, double R,
+                        double *E, int nthreads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t t = 0; t < n; ++t) {
+        int32_t q = idx[t];
+        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+        for (int64_t j = 0; j < k; ++j) {
+            double p = orc_phi(dist3(xb + 3 * q, xb + 3 * S[j]) / R);
+            f0 += W[3 * j + 0] * p;
+            f1 += W[3 * j + 1] * p;
+            f2 += W[3 * j + 2] * p;
+        }
+        double e0 = db[3 * q + 0] - f0, e1 = db[3 * q + 1] - f1, e2 = db[3 * q + 2] - f2;
+        E[t] = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+    }
+    (void)nthreads;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1: GCB greedy (m = 1 is the plain Rendall-Allen greedy).      */
+/* ------------------------------------------------------------------------ */
+
+/* History rows: [iteration k, |S| before the step, local max E in G_i,
+ *                global max E (or -1 if no full check), global RMS E (or -1),
+ *                added node (or -1)].  */
+#define ORC_HIST_COLS 6
+
+typedef struct {
+    int64_t iterations;   /* iterations run (k - 3 at exit)                 */
+    int64_t full_checks;  /* number of all-node error evaluations           */
+    int64_t pairs_group;  /* sum over iterations of |G_i| * |S| (Sec. 3)    */
+    int64_t pairs_full;   /* sum over full checks of N_b * |S|              */
+    double final_max;     /* global max E at exit (current weights)        */
+    double final_rms;
+    double min_pivot;     /* smallest Cholesky pivot seen (SPD check)       */
+    int64_t n_div;        /* follow mode: accepted divergences              */
+    int64_t n_fail;       /* follow mode: rejected steps                    */
+    double worst_rel_gap; /* follow mode: max (E_oracle - E_follow)/E_oracle */
+} orc_greedy_stats;
+
+/*
+ * follow mode (follow_n >= 0): instead of adding its own argmax, the oracle
+ * adopts the decision of another implementation, given as the nodes it added
+ * (follow_idx) and the iteration at which each was added (follow_iter).  At
+ * every iteration it checks that decision against its own FP64 errors:
+ *   - an added node must lie in G_i, not be in S, have E > E*(1 - tie) and
+ *     E >= (1 - tie) * max_G_i E; it counts as a divergence when it is not
+ *     the oracle's own argmax;
+ *   - "no add" is accepted when max_G_i E <= E*(1 + tie).
+ * follow_n < 0 runs the literal algorithm.
+ */
+int orc_greedy(const double *xb, const double *db, int64_t nb, double R, double Estar,
+               int64_t m, uint64_t seed, int64_t ncmax,
+               const int32_t *follow_idx, const int64_t *follow_iter, int64_t follow_n,
+               double tie_rel,
+               int32_t *out_idx, int64_t *out_iter, int64_t *out_nc,
+               double *hist, int64_t hist_cap, int64_t *n_hist,
+               orc_greedy_stats *stats, int nthreads)
+{
+    if (nb < 3 || m < 1 || m > nb || ncmax < 3 || !(R > 0.0) || !(Estar >= 0.0))
+        return ORC_E_ARG;
+    memset(stats, 0, sizeof(*stats));
+    stats->min_pivot = INFINITY;
+    int32_t *group_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    int32_t *members = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    int64_t *goff = (int64_t *)calloc((size_t)m + 1, sizeof(int64_t));
+    char *inS = (char *)calloc((size_t)nb, 1);
+    int32_t *all = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    double *E = (double *)malloc(sizeof(double) * (size_t)nb);
+    double *W = (double *)malloc(sizeof(double) * 3 * (size_t)ncmax);
+    if (!group_of || !members || !goff || !inS || !all || !E || !W) {
+        free(group_of); free(members); free(goff); free(inS); free(all); free(E); free(W);
+        return ORC_E_NOMEM;
+    }
+    /* Step 1: partition; members of each group listed in node order. */
+    orc_groups(nb, m, seed, group_of);
+    for (int64_t j = 0; j < nb; ++j)
+        goff[group_of[j] + 1]++;
+    for (int64_t g = 0; g < m; ++g)
+        goff[g + 1] += goff[g];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+        for (int64_t g = 0; g < m; ++g)
+            fill[g] = goff[g];
+        for (int64_t j = 0; j < nb; ++j)
+            members[fill[group_of[j]]++] = (int32_t)j;
+        free(fill);
+    }
+    for (int64_t j = 0; j < nb; ++j)
+        all[j] = (int32_t)j;
+
+    /* Step 2: three seed nodes. */
+    int32_t seeds[3];
+    orc_seed_nodes(xb, db, nb, seeds);
+    int64_t nc = 0;
+    for (int s = 0; s < 3; ++s) {
+        out_idx[nc] = seeds[s];
+        out_iter[nc] = -1;
+        inS[seeds[s]] = 1;
+        ++nc;
+    }
+    int64_t fpos = 0;
+    if (follow_n >= 0) {
+        /* the follower must start from the same seed nodes */
+        for (int s = 0; s < 3; ++s)
+            if (follow_n <= s || follow_idx[s] != seeds[s])
+                stats->n_fail++;
+        fpos = 3;
+    }
+    int status = ORC_OK;
+    int64_t nh = 0;
+    int64_t k = 3;
+    for (;; ++k) {
+        /* Solve Phi_SS W = dX_S from scratch (dense Cholesky). */
+        double mp;
+        int st = orc_solve_weights(xb, db, out_idx, nc, R, W, &mp);
+        if (st != ORC_OK) { status = st; break; }
+        if (mp < stats->min_pivot) stats->min_pivot = mp;
+
+        /* i = k mod m; errors in G_i (nodes already in S are skipped). */
+        int64_t gi = k % m;
+        int64_t g0 = goff[gi], gn = goff[gi + 1] - goff[gi];
+        node_errors(xb, db, members + g0, gn, out_idx, nc, W, R, E, nthreads);
+        stats->pairs_group += gn * nc;
+        double Eloc = -1.0;
+        int64_t nloc = -1;
+        for (int64_t t = 0; t < gn; ++t) {
+            int32_t q = members[g0 + t];
+            if (inS[q]) continue;
+            if (E[t] > Eloc) { Eloc = E[t]; nloc = q; }   /* ascending q: lowest index wins ties */
+        }
+        int64_t add = -1;
+        if (follow_n < 0) {
+            if (nloc >= 0 && Eloc > Estar)
+                add = nloc;
+        } else {
+            int follower_adds = (fpos < follow_n && follow_iter[fpos] == k);
+            if (follower_adds) {
+                int32_t nf = follow_idx[fpos];
+                double Ef = -1.0;
+                int ok = nf >= 0 && nf < nb && group_of[nf] == gi && !inS[nf];
+                if (ok) {
+                    for (int64_t t = 0; t < gn; ++t)
+                        if (members[g0 + t] == nf) { Ef = E[t]; break; }
+                    ok = Ef > Estar * (1.0 - tie_rel) && Ef >= (1.0 - tie_rel) * Eloc;
+                }
+                if (!ok) stats->n_fail++;
+                else if (nf != nloc) stats->n_div++;
+                if (Eloc > 0.0 && Ef >= 0.0) {
+                    double gap = (Eloc - Ef) / Eloc;
+                    if (gap > stats->worst_rel_gap) stats->worst_rel_gap = gap;
+                }
+                add = nf;
+                fpos++;
+            } else {
+                if (nloc >= 0 && Eloc > Estar * (1.0 + tie_rel)) stats->n_fail++;
+                else if (nloc >= 0 && Eloc > Estar) stats->n_div++;
+            }
+        }
+        if (add >= 0) {
+            if (nc >= ncmax) {
+                status = ORC_E_NC_MAX;
+                break;
+            }
+            out_idx[nc] = (int32_t)add;
+            out_iter[nc] = k;
+            inS[add] = 1;
+            ++nc;
+        }
+        /* Full check: all nodes, current S, fresh weights. */
+        int full = (add < 0) || ((k - 2) % m == 0);
+        double gmax = -1.0, grms = -1.0;
+        if (full) {
+            if (add >= 0) {
+                st = orc_solve_weights(xb, db, out_idx, nc, R, W, &mp);
+                if (st != ORC_OK) { status = st; break; }
+                if (mp < stats->min_pivot) stats->min_pivot = mp;
+            }
+            node_errors(xb, db, all, nb, out_idx, nc, W, R, E, nthreads);
+            stats->full_checks++;
+            stats->pairs_full += nb * nc;
+            double s2 = 0.0;
+            gmax = 0.0;
+            for (int64_t j = 0; j < nb; ++j) {
+                if (E[j] > gmax) gmax = E[j];
+                s2 += E[j] * E[j];
+            }
+            grms = sqrt(s2 / (double)nb);
+        }
+        if (hist && nh < hist_cap) {
+            double *h = hist + ORC_HIST_COLS * nh;
+            h[0] = (double)k;
+            h[1] = (double)(add >= 0 ? nc - 1 : nc);
+            h[2] = Eloc;
+            h[3] = gmax;
+            h[4] = grms;
+            h[5] = (double)add;
+        }
+        ++nh;
+        if (full && gmax <= Estar) {
+            stats->final_max = gmax;
+            stats->final_rms = grms;
+            break;
+        }
+        if (follow_n >= 0 && fpos >= follow_n && full && add < 0) {
+            /* the follower stopped adding although the oracle's full check
+             * fails: accepted only inside the tie band above E* */
+            if (gmax > Estar * (1.0 + tie_rel)) stats->n_fail++;
+            else stats->n_div++;
+            stats->final_max = gmax;
+            stats->final_rms = grms;
+            break;
+        }
+    }
+    if (follow_n >= 0 && fpos != follow_n)
+        stats->n_fail++;
+    stats->iterations = k - 3 + 1;
+    *out_nc = nc;
+    *n_hist = nh;
+    free(group_of); free(members); free(goff); free(inS); free(all); free(E); free(W);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of Eq. 6 for J(d_v) with d_v = Phi_vc W, W = Phi_cc^{-1} d_c:     */
+/*   dJ/dd_c = Phi_cc^{-1} Phi_vc^T dJ/dd_v  (Phi_cc symmetric).            */
+/* ------------------------------------------------------------------------ */
+int orc_adjoint(const double *xv, int64_t nv, const double *xb, const int32_t *S, int64_t k,
+                double R, const double *gv, double *gc, int nthreads)
+{
+    /* g = Phi_vc^T gv, accumulated column by column in fixed order */
+    for (int64_t j = 0; j < k; ++j) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int64_t v = 0; v < nv; ++v) {
+            double p = orc_phi(dist3(xv + 3 * v, xb + 3 * S[j]) / R);
+            a0 += p * gv[3 * v + 0];
+            a1 += p * gv[3 * v + 1];
+            a2 += p * gv[3 * v + 2];
+        }
+        gc[3 * j + 0] = a0;
+        gc[3 * j + 1] = a1;
+        gc[3 * j + 2] = a2;
+    }
+    (void)nthreads;
+    /* solve Phi_cc lambda = g */
+    double *A = (double *)malloc(sizeof(double) * (size_t)(k * k > 0 ? k * k : 1));
+    if (!A)
+        return ORC_E_NOMEM;
+    for (int64_t i = 0; i < k; ++i)
+        for (int64_t j = 0; j < k; ++j)
+            A[i * k + j] = orc_phi(dist3(xb + 3 * S[i], xb + 3 * S[j]) / R);
+    int st = orc_cholesky(k, A);
+    if (st == ORC_OK)
+        orc_cholesky_solve(k, A, gc, 3);
+    free(A);
+    return st;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,241 @@
+"""Seeded synthetic workloads for RBF mesh deformation (geometry only).
+
+This module produces the inputs that both the CUDA path and the CPU oracle
+consume: boundary (surface) points with their prescribed displacements and
+volume points.  It contains none of the method's arithmetic (no basis
+function, no interpolation, no grouping): it only builds point clouds.
+
+The paper deforms the ONERA M6 wing (Sec. 4.1: 10,499 surface nodes,
+1,353,105 volume nodes, first-layer height 1e-5) and the DLR-F6
+wing-body-nacelle-pylon (Sec. 4.2: 79,079 surface nodes, 4,007,571 volume
+nodes).  Those meshes are public benchmark geometries that are not available
+here, so these generators stand in for them with synthetic surfaces of the
+same kind and comparable size:
+
+* a swept, tapered half wing made of symmetric 12 %-thick 4-digit-style
+  sections (root chord 0.8, taper 0.56, leading-edge sweep 30 deg, span 1);
+* a wing-body-nacelle-pylon assembly built from a cylinder fuselage, the
+  wing at 3x scale, an annular nacelle and a pylon plate.
+
+Axes: x chordwise, y spanwise, z vertical.
+
+All randomness comes from ``numpy.random.Generator(PCG64(seed))``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# Wing planform and section
+# ----------------------------------------------------------------------------
+SPAN = 1.0
+ROOT_CHORD = 0.8
+TAPER = 0.56
+SWEEP_DEG = 30.0
+THICKNESS = 0.12
+
+
+def chord_at(y, span=SPAN, root_chord=ROOT_CHORD, taper=TAPER):
+    """Local chord c(y) = c_r (1 - (1 - lambda) y / b)."""
+    return root_chord * (1.0 - (1.0 - taper) * np.asarray(y) / span)
+
+
+def leading_edge_x(y, sweep_deg=SWEEP_DEG):
+    """Leading-edge x position x_LE(y) = y tan(sweep)."""
+    return np.asarray(y) * math.tan(math.radians(sweep_deg))
+
+
+def half_thickness(xc, tau=THICKNESS):
+    """Symmetric 4-digit half-thickness t(x/c), closed trailing edge.
+
+    Standard NACA 4-digit thickness polynomial with the closed-trailing-edge
+    last coefficient, so t(0) = t(1) = 0.
+    """
+    xc = np.clip(np.asarray(xc, dtype=np.float64), 0.0, 1.0)
+    return 5.0 * tau * (0.2969 * np.sqrt(xc) - 0.1260 * xc - 0.3516 * xc**2
+                        + 0.2843 * xc**3 - 0.1036 * xc**4)
+
+
+def section_ring(n_chord):
+    """Unit-chord section contour: (x/c, z/c) for theta_i = 2 pi i / n_chord.
+
+    x/c = (1 + cos theta)/2, upper surface (z > 0) for theta in (0, pi), lower
+    for theta in (pi, 2 pi).  i = 0 is the single trailing-edge point; for even
+    n_chord, i = n_chord/2 is the leading edge.  No two ring points coincide.
+    """
+    theta = 2.0 * np.pi * np.arange(n_chord) / n_chord
+    xc = 0.5 * (1.0 + np.cos(theta))
+    sign = np.where(theta < np.pi, 1.0, -1.0)
+    zc = sign * half_thickness(xc)
+    return xc, zc
+
+
+def wing_surface(n_span, n_chord, *, span=SPAN, root_chord=ROOT_CHORD,
+                 taper=TAPER, sweep_deg=SWEEP_DEG, origin=(0.0, 0.0, 0.0),
+                 scale=1.0):
+    """Structured half-wing surface: n_span stations x n_chord ring points.
+
+    Returns (points (n_span*n_chord, 3) float64, normals (same), station y of
+    each point in the unscaled wing frame).  Station s lies at
+    y_s = b s / (n_span - 1).  Normals are outward unit normals of the section
+    contour in the x-z plane (central differences around the ring).
+    """
+    xc, zc = section_ring(n_chord)
+    ys = span * np.arange(n_span) / max(n_span - 1, 1)
+    c = chord_at(ys, span, root_chord, taper)[:, None]
+    xle = leading_edge_x(ys, sweep_deg)[:, None]
+    x = xle + xc[None, :] * c
+    z = zc[None, :] * c
+    y = np.broadcast_to(ys[:, None], x.shape)
+    pts = np.stack([x, y, z], axis=-1).reshape(-1, 3)
+    # ring tangent by central differences; outward normal of a counter-clockwise
+    # contour in the (x, z) plane is (dz, -dx)
+    xn = np.roll(x, -1, axis=1) - np.roll(x, 1, axis=1)
+    zn = np.roll(z, -1, axis=1) - np.roll(z, 1, axis=1)
+    nrm = np.stack([zn, np.zeros_like(xn), -xn], axis=-1)
+    nrm /= np.linalg.norm(nrm, axis=-1, keepdims=True)
+    nrm = nrm.reshape(-1, 3)
+    y_station = np.repeat(ys, n_chord)
+    o = np.asarray(origin, dtype=np.float64)
+    return pts * scale + o, nrm, y_station
+
+
+def inside_wing(p, *, span=SPAN, root_chord=ROOT_CHORD, taper=TAPER,
+                sweep_deg=SWEEP_DEG, origin=(0.0, 0.0, 0.0), scale=1.0):
+    """True where a point lies strictly inside the (scaled, shifted) wing."""
+    q = (np.asarray(p, dtype=np.float64) - np.asarray(origin)) / scale
+    x, y, z = q[..., 0], q[..., 1], q[..., 2]
+    ok = (y >= 0.0) & (y <= span)
+    yc = np.clip(y, 0.0, span)
+    c = chord_at(yc, span, root_chord, taper)
+    xle = leading_edge_x(yc, sweep_deg)
+    xc = (x - xle) / c
+    ok &= (xc > 0.0) & (xc < 1.0)
+    return ok & (np.abs(z) < c * half_thickness(xc))
+
+
+def wing_bending_twist(pts, *, span=SPAN, root_chord=ROOT_CHORD, taper=TAPER,
+                       sweep_deg=SWEEP_DEG, bend=0.05, twist_deg=5.0,
+                       origin=(0.0, 0.0, 0.0), scale=1.0):
+    """Prescribed surface displacement: quadratic bending plus linear twist.
+
+    dz_bend = bend * scale * (y/b)^2; twist angle theta(y) = twist_deg * y/b
+    (nose up positive) about the quarter-chord line
+    x_qc = x_LE + c/4.  Returns (n, 3) float64 with dy = 0.
+    """
+    p = np.asarray(pts, dtype=np.float64)
+    o = np.asarray(origin, dtype=np.float64)
+    q = (p - o) / scale
+    yb = np.clip(q[:, 1] / span, 0.0, 1.0)
+    c = chord_at(yb * span, span, root_chord, taper)
+    xqc = leading_edge_x(yb * span, sweep_deg) + 0.25 * c
+    th = math.radians(twist_deg) * yb
+    dxq = (q[:, 0] - xqc) * scale
+    zq = q[:, 2] * scale
+    d = np.zeros_like(p)
+    d[:, 0] = dxq * (np.cos(th) - 1.0) + zq * np.sin(th)
+    d[:, 2] = -dxq * np.sin(th) + zq * (np.cos(th) - 1.0) + bend * scale * yb**2
+    return d
+
+
+# ----------------------------------------------------------------------------
+# Volume points
+# ----------------------------------------------------------------------------
+def volume_uniform_box(n, lo, hi, rng, reject):
+    """n points uniform in the box [lo, hi] with reject(p) == False."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    out = []
+    have = 0
+    while have < n:
+        p = lo + (hi - lo) * rng.random((max(2 * (n - have), 1024), 3))
+        p = p[~reject(p)]
+        out.append(p)
+        have += len(p)
+    return np.concatenate(out)[:n]
+
+
+def volume_log_clustered(n, surf_pts, surf_nrm, rng, reject, d_min=1e-5,
+                         d_max=1.5):
+    """n points offset from random surface points along their normals.
+
+    The offset is d = d_min (d_max/d_min)^u with u ~ U(0, 1), so points are
+    log-uniformly clustered toward the surface (the paper's meshes have a
+    first-layer height of 1e-5).  Points with reject(p) True are redrawn.
+    """
+    out = []
+    have = 0
+    ns = len(surf_pts)
+    while have < n:
+        k = max(2 * (n - have), 1024)
+        idx = rng.integers(0, ns, size=k)
+        u = rng.random(k)
+        d = d_min * (d_max / d_min) ** u
+        p = surf_pts[idx] + d[:, None] * surf_nrm[idx]
+        p = p[~reject(p)]
+        out.append(p)
+        have += len(p)
+    return np.concatenate(out)[:n]
+
+
+# ----------------------------------------------------------------------------
+# Workloads
+# ----------------------------------------------------------------------------
+def wing_case(n_span, n_chord, n_vol, *, vol_seed, vol_kind="box",
+              radius=2.0, tol_rel=1e-3):
+    """One synthetic wing deformation problem.
+
+    Returns a dict with float64 arrays ``xb`` (N_b, 3), ``db`` (N_b, 3),
+    ``xv`` (N_v, 3), the support radius and the relative tolerance.
+    """
+    xb, nb_, _ = wing_surface(n_span, n_chord)
+    db = wing_bending_twist(xb)
+    rng = np.random.Generator(np.random.PCG64(vol_seed))
+    if n_vol == 0:
+        xv = np.zeros((0, 3))
+    elif vol_kind == "box":
+        lo, hi = xb.min(0), xb.max(0)
+        ctr = 0.5 * (lo + hi)
+        side = 3.0 * max(hi[0] - lo[0], hi[1] - lo[1])
+        xv = volume_uniform_box(n_vol, ctr - side / 2, ctr + side / 2, rng,
+                                inside_wing)
+    else:
+        xv = volume_log_clustered(n_vol, xb, nb_, rng, inside_wing,
+                                  d_max=1.5 * SPAN)
+    return dict(xb=xb, db=db, xv=xv, radius=float(radius),
+                tol_rel=float(tol_rel), name=f"wing{n_span}x{n_chord}")
+
+
+def wing_small(n_vol=20_000):
+    """Plain-greedy wing: 16 x 125 = 2,000 surface points, 20k box points,
+    R = 2 x span, tolerance 1e-3 of the largest displacement, seed 0."""
+    return wing_case(16, 125, n_vol, vol_seed=0, vol_kind="box", radius=2.0,
+                     tol_rel=1e-3)
+
+
+def wing_gcb(n_vol=2_000_000):
+    """GCB wing: 100 x 500 = 50,000 surface points, volume log-clustered
+    toward the surface (2e6 points, seed 2), R = 2, tolerance 1e-4."""
+    return wing_case(100, 500, n_vol, vol_seed=2, vol_kind="log", radius=2.0,
+                     tol_rel=1e-4)
+
+
+def tiny_wing(n_span=4, n_chord=20, n_vol=200, seed=0, radius=2.0,
+              tol_rel=1e-3):
+    """A small wing for brute-force and unit checks."""
+    return wing_case(n_span, n_chord, n_vol, vol_seed=seed, vol_kind="box",
+                     radius=radius, tol_rel=tol_rel)
+
+
+def random_cloud(n, seed, scale=1.0):
+    """n distinct points uniform in a cube of side ``scale`` (float64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return scale * rng.random((n, 3))
+
+
+def random_field(n, seed, sigma=1.0):
+    """i.i.d. Gaussian (n, 3) field with standard deviation sigma."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return sigma * rng.standard_normal((n, 3))

@@ -1,0 +1,206 @@
+/*
+ * rbfgcb.h -- C ABI of librbfgcb.so: GB300 (sm_103a) kernels for RBF mesh
+ * deformation with the grouping-circular-based (GCB) greedy selection of
+ * support nodes (arXiv:2004.04817).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Point and displacement arrays are row-major n x 3 (x, y, z per row),
+ *    unless a signature says otherwise.
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device; the
+ *    caller owns them (allocates, frees, keeps them alive until the stream
+ *    work completes).  Pointers named h_* are HOST pointers.  The library never
+ *    frees caller memory.
+ *  - Scratch comes from the caller-supplied device workspace `d_ws` of
+ *    `ws_bytes` bytes, sized with the matching *_workspace_bytes query; the
+ *    workspace must be 256-byte aligned.  Entry points allocate no device
+ *    memory of their own.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Every call returns an rbf_status; argument errors are reported before any
+ *    work is enqueued.  Calls marked SYNCHRONOUS block until their stream work
+ *    is done (their outputs include host scalars).  Calls marked ASYNC only
+ *    enqueue; device-side failures of an ASYNC call are reported by the next
+ *    SYNCHRONOUS call or by rbf_last_device_status().
+ *  - No call falls back to the CPU.  Without a usable CUDA device every call
+ *    returns RBF_E_CUDA.
+ *
+ * Notation (paper): boundary nodes r_j with prescribed displacements dr_j
+ * (N_b of them), support set S (N_c nodes), support radius R, Wendland C2
+ * basis phi(eta) = (1 - eta)^4 (4 eta + 1) for eta = |r - r_j| / R < 1 and 0
+ * otherwise (Eq. 2), interpolant F(r) = sum_{j in S} w_j phi(|r - r_j| / R)
+ * (Eq. 1), weights from Phi_SS W = dX_S (Eqs. 3-5), interpolation error of a
+ * boundary node E_q = |dr_q - F(r_q)|_2.
+ */
+#ifndef RBFGCB_H
+#define RBFGCB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RBF_OK = 0,
+    RBF_E_ARG = 1,        /* invalid argument (sizes, radius, m, alignment, NULL) */
+    RBF_E_NOT_SPD = 2,    /* a Cholesky pivot d^2 <= 1e-13: coincident or nearly
+                             coincident support nodes (Phi is SPD only for
+                             distinct nodes, Sec. 2) */
+    RBF_E_NC_MAX = 3,     /* the greedy wanted more than nc_max support nodes;
+                             the partial selection is returned */
+    RBF_E_NONFINITE = 4,  /* NaN or Inf in an input */
+    RBF_E_WORKSPACE = 5,  /* workspace missing, too small or misaligned */
+    RBF_E_TIMEOUT = 6,    /* a bounded device-side wait (grid barrier) ran out;
+                             the kernel returned without finishing */
+    RBF_E_CUDA = 7        /* a CUDA runtime call failed (no device, launch error) */
+} rbf_status;
+
+/* Precision of the pair evaluations (Eq. 1 sums). */
+enum {
+    RBF_PREC_F64 = 64,    /* every pair in FP64 */
+    RBF_PREC_F32 = 32     /* FP32 pairs; the greedy certifies its argmax and its
+                             stopping test by re-scoring near-maximal nodes in
+                             FP64 (FP32 values carry an error bound) */
+};
+
+typedef struct {
+    double radius;        /* support radius R > 0 (eta = distance / R) */
+    double tol;           /* E*; absolute, or relative (tol_mode = 1) */
+    int32_t tol_mode;     /* 0: E* = tol; 1: E* = tol * max_j |dr_j|_2 */
+    int32_t eval_prec;    /* RBF_PREC_F64 or RBF_PREC_F32 */
+    int64_t m;            /* number of groups, 1 <= m <= N_b (1 = plain greedy) */
+    uint64_t seed;        /* seed of the random partition into groups */
+    int64_t nc_max;       /* capacity of the support set, 3 <= nc_max <= N_b */
+    int32_t refine_steps; /* FP64 iterative-refinement steps in rbf_solve_weights */
+    int32_t flags;        /* reserved, must be 0 */
+} rbf_params;
+
+/* Per-run statistics of rbf_greedy_select (host struct). */
+typedef struct {
+    int64_t iterations;      /* greedy iterations run (k - 3 + 1 at exit)      */
+    int64_t nc;              /* |S| at exit                                     */
+    int64_t full_checks;     /* evaluations of all N_b errors                   */
+    int64_t pairs_f32;       /* (node, centre) pairs evaluated in FP32          */
+    int64_t pairs_f64;       /* (node, centre) pairs evaluated in FP64          */
+    int64_t rescored;        /* nodes re-scored in FP64 after an FP32 screen    */
+    double estar;            /* the absolute tolerance E* used                  */
+    double final_max;        /* FP64-certified global max error at exit         */
+    double final_rms;        /* RMS error over all nodes at the last full check */
+    double min_pivot;        /* smallest squared Cholesky pivot d^2 seen        */
+} rbf_greedy_stats;
+
+/* Columns of one row of the optional iteration history (device doubles):
+ * [k, |S| before the step, local max E in G_(k mod m), global max E (or -1 if
+ *  no full check ran), global RMS E (or -1), node added (or -1)]. */
+#define RBF_HIST_COLS 6
+
+/* --------------------------------------------------------------------------
+ * Greedy / GCB support-node selection (Sec. 3, Algorithm 1; m = 1 is the
+ * plain Rendall-Allen greedy of Sec. 1).
+ *
+ * Partition: node perm[p] of a SplitMix64-driven Fisher-Yates permutation
+ * belongs to group p mod m (groups disjoint, covering, sizes within one,
+ * Sec. 3).  Seed nodes: n0 = argmax |dr_j|, n1 = the node farthest from n0,
+ * n2 = the node farthest from {n0, n1} (lowest index on ties).  Iteration k
+ * (from 3) evaluates E_q for q in G_(k mod m) minus S with the current
+ * weights, takes the largest (lowest index on ties) and appends it to S when
+ * E > E* (strict).  The Cholesky factor of Phi_SS grows by one row per
+ * appended node (recurrence Cholesky, Sec. 1), in FP64.  All N_b errors are
+ * checked after every m-th iteration and whenever a group adds nothing; the
+ * run stops when that full check finds max_q E_q <= E*.
+ *
+ * d_xb, d_db : device FP64, nb x 3 (boundary coordinates, displacements).
+ * d_sel_idx  : device int32[nc_max]: selected node indices in selection order
+ *              (the three seed nodes first).
+ * d_sel_iter : device int64[nc_max] or NULL: iteration k at which each node
+ *              was added (-1 for seeds).
+ * d_hist     : device double[hist_cap * RBF_HIST_COLS] or NULL.
+ * h_nc       : host; number of selected nodes.
+ * h_n_hist   : host or NULL; number of iterations (history rows wanted).
+ * h_stats    : host or NULL.
+ * SYNCHRONOUS.  Returns RBF_E_NC_MAX with a valid partial selection when the
+ * cap is reached, RBF_E_NOT_SPD when an append meets a non-positive pivot.
+ * ------------------------------------------------------------------------ */
+size_t rbf_greedy_workspace_bytes(int64_t nb, const rbf_params *p);
+
+rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, int64_t nb,
+                             const rbf_params *p,
+                             int32_t *d_sel_idx, int64_t *d_sel_iter,
+                             double *d_hist, int64_t hist_cap,
+                             int64_t *h_nc, int64_t *h_n_hist,
+                             rbf_greedy_stats *h_stats,
+                             void *d_ws, size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------------------------------
+ * Support weights: solve Phi_SS W = dX_S (Eqs. 4-5 restricted to S, SPD by
+ * Sec. 2) in FP64 by a recurrence Cholesky, then p->refine_steps steps of
+ * iterative refinement W += Phi_SS^-1 (dX_S - Phi_SS W) with the residual
+ * recomputed from coordinates.
+ *
+ * d_sel_idx : device int32[nc], distinct indices into the nb boundary nodes.
+ * d_w       : device FP64 nc x 3 (output weights, support order).
+ * h_max_resid : host or NULL; max_j |F(r_j) - dr_j|_inf over j in S after
+ *               refinement (FP64).
+ * SYNCHRONOUS.
+ * ------------------------------------------------------------------------ */
+size_t rbf_solve_workspace_bytes(int64_t nc);
+
+rbf_status rbf_solve_weights(const double *d_xb, const double *d_db, int64_t nb,
+                             const int32_t *d_sel_idx, int64_t nc,
+                             const rbf_params *p, double *d_w,
+                             double *h_max_resid,
+                             void *d_ws, size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------------------------------
+ * Volume displacements, Eq. 6: dv_v = sum_{j in S} w_j phi(|x_v - r_j| / R)
+ * for the nv volume points.
+ *
+ * d_xv : device FP64 nv x 3.   d_dv : device FP64 nv x 3 (output).
+ * d_xb, d_sel_idx, nc, d_w : centres r_j = xb[sel_idx[j]] and weights w_j
+ *                            (device FP64 nc x 3), as from rbf_solve_weights.
+ * p->eval_prec selects the pair arithmetic (FP32 or FP64); only radius and
+ * eval_prec are read from p.
+ * ASYNC.
+ * ------------------------------------------------------------------------ */
+size_t rbf_volume_workspace_bytes(int64_t nv, int64_t nc, const rbf_params *p);
+
+rbf_status rbf_deform_volume(const double *d_xv, int64_t nv,
+                             const double *d_xb, const int32_t *d_sel_idx,
+                             int64_t nc, const double *d_w,
+                             const rbf_params *p, double *d_dv,
+                             void *d_ws, size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------------------------------
+ * The random partition rbf_greedy_select uses (Sec. 3: "stochastically and
+ * uniformly" into m groups whose sizes differ by at most one), on the host:
+ * h_group_of[node] = group of the node, 0..m-1.  SplitMix64(seed) drives a
+ * Fisher-Yates shuffle (position i = nb-1 down to 1 swapped with
+ * j = next() mod (i+1)); node perm[p] belongs to group p mod m.
+ * HOST ONLY (no device needed).  Returns RBF_E_ARG for nb < 1, m < 1, m > nb.
+ * ------------------------------------------------------------------------ */
+rbf_status rbf_group_of(int64_t nb, int64_t m, uint64_t seed, int32_t *h_group_of);
+
+/* --------------------------------------------------------------------------
+ * Vector-FMA peak microbenchmark of this GPU (dependent-FMA chains on every
+ * SM), used as the denominator of the pair kernels' roofline.
+ * prec: 32 or 64.  h_flops: host; measured FLOP/s (an FMA counts 2).
+ * SYNCHRONOUS.
+ * ------------------------------------------------------------------------ */
+rbf_status rbf_measure_fma_peak(int prec, double *h_flops, void *stream);
+
+/* Status latched by the last ASYNC call's device work on this device
+ * (RBF_OK if none failed); reading it synchronises the device. */
+rbf_status rbf_last_device_status(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *rbf_status_string(rbf_status s);
+
+/* Library version string (static storage). */
+const char *rbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBFGCB_H */

@@ -1,0 +1,23 @@
+"""GB300 (sm_103a) RBF mesh deformation with GCB greedy support selection.
+
+The compute runs in ``librbfgcb.so`` (hand-written CUDA behind a C ABI, see
+``include/rbfgcb.h``); this package only marshals torch CUDA tensors to it.
+Importing the package does not load the library: the first call does, and it
+raises if the library or a CUDA device is missing (there is no CPU path).
+"""
+from .rbf import (  # noqa: F401
+    RBFError,
+    Params,
+    GreedyStats,
+    lib,
+    greedy_select,
+    solve_weights,
+    deform_volume,
+    measure_fma_peak,
+    group_of,
+    status_string,
+    STATUS,
+    PREC_F32,
+    PREC_F64,
+    HIST_COLS,
+)

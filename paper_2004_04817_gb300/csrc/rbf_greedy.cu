@@ -1,0 +1,1283 @@
+// rbf_greedy.cu -- persistent GCB greedy selection of support nodes
+// (Algorithm 1 of arXiv:2004.04817; m = 1 is the plain Rendall-Allen greedy).
+//
+// One cooperative launch runs the whole loop on the device:
+//   prologue : pack the boundary nodes in group order (groups contiguous),
+//              E* = tol * max |dr| if relative, three seed nodes, append them;
+//   iteration: errors E_q in the active group G_(k mod m) (FP64, or FP32 with
+//              an error bound and an FP64 re-score of every node whose bound
+//              reaches the maximum), grid argmax (lowest node on ties), append
+//              when E > E*, full check of all N_b errors after every m-th
+//              iteration and whenever a group adds nothing.
+// The Cholesky factor of Phi_SS grows by one row per appended node (the
+// recurrence Cholesky of Sec. 1).  The kernel keeps Z = L^-1 (and Z^T) in
+// FP64, so an append is two matrix-vector products (l = Z b, u = Z^T l) that
+// spread over the whole grid, instead of a triangular solve whose k-step
+// dependency chain would run on one SM:
+//   l = Z b,  d = sqrt(1 - l.l),  y_new = (dr_n - l.y) / d,
+//   new row of Z = [-u^T / d, 1 / d],  W <- W - u y_new / d,  w_new = y_new / d.
+// Grid barriers are bounded (RBF_E_TIMEOUT instead of a hang).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "rbf_device.cuh"
+#include "rbf_host.h"
+
+namespace rbf {
+
+constexpr int kGThreads = 256;
+constexpr int kGWarps = kGThreads / kWarp;
+constexpr int kMaxGrid = 4096;
+constexpr int kSmemCentresF32 = 4096;      // FP32 centre tile kept in shared memory
+constexpr double kPivotMin = 1e-13;        // d^2 at or below: singular (coincident nodes)
+constexpr float kU32 = 5.9604645e-8f;      // 2^-24, unit roundoff of FP32
+constexpr float kBetaPhi = 16.0f;          // error-bound factors (see screen_bound)
+constexpr float kBetaCoord = 8.0f;
+
+struct GreedyCtl {
+    GridBar bar;
+    int status;
+    int pad0;
+    unsigned long long slot[3];   // argmax keys (ring, indexed by evaluation count)
+    unsigned int tslot[3];        // FP32 screen thresholds (float bits, ring)
+    unsigned int pad1;
+    double estar;
+    long long nc;
+    long long iterations;
+    long long full_checks;
+    long long pairs_f32;
+    long long pairs_f64;
+    unsigned long long rescored;
+    double final_max;
+    double final_rms;
+    double min_pivot;
+    long long n_hist;
+};
+
+struct GreedyArgs {
+    const double *xb;
+    const double *db;
+    int nb;
+    int m;
+    int nc_max;
+    int prec;
+    double inv_r;
+    double tol;
+    int tol_mode;
+    int ld;                       // leading dimension of Z, Z^T (= nc_max)
+    int32_t *sel_idx;
+    int64_t *sel_iter;
+    double *hist;
+    int64_t hist_cap;
+    GreedyCtl *ctl;
+    const int32_t *perm;
+    int32_t *node_of_pos;
+    int32_t *pos_of_node;
+    D4 *xg64;                // scaled coordinates, group order
+    D4 *dg64;                // displacements, group order
+    float4 *xg32;
+    uint8_t *in_s;
+    float *u32;                   // FP32 upper bound of E per position
+    double *e64;                  // FP64 E per position (last evaluation)
+    double *part;                 // 2 x kMaxGrid x 4 reduction partials
+    long long *parti;             // 2 x kMaxGrid index partials
+    int32_t *spos;                // support positions
+    D4 *c64;                 // support centres (scaled)
+    D4 *w64;                 // weights
+    float4 *cw32;                 // (centre, weight) FP32 pairs, interleaved
+    D4 *y64;                 // forward-solve vector y = Z dr_S
+    double *z;                    // Z = L^-1, row-major, ld
+    double *zt;                   // Z^T, row-major, ld
+    double *bvec;
+    double *lvec;
+};
+
+__device__ __forceinline__ int goff(int i, int nb, int m)
+{
+    const int base = nb / m, rem = nb % m;
+    return i * base + min(i, rem);
+}
+
+// (value, index) pair reductions: larger value wins, lowest index on ties.
+__device__ __forceinline__ void pick(double &v, long long &i, double v2, long long i2)
+{
+    if (v2 > v || (v2 == v && i2 >= 0 && (i < 0 || i2 < i))) {
+        v = v2;
+        i = i2;
+    }
+}
+
+struct Red {
+    double v[kGWarps];
+    long long i[kGWarps];
+    double s[kGWarps][4];
+    unsigned long long key[kGWarps];
+};
+
+// Block-level argmax of (v, i); thread 0 returns the result.
+__device__ void block_pick(Red &r, double &v, long long &i)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const long long i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        pick(v, i, v2, i2);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        r.v[w] = v;
+        r.i[w] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kGWarps; ++k)
+            pick(v, i, r.v[k], r.i[k]);
+    }
+}
+
+// Block sums of 4 values (deterministic order); thread 0 holds the result.
+__device__ void block_sum4(Red &r, double a[4])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        a[c] = warp_sum_f64(a[c]);
+    __syncthreads();
+    if (lane == 0)
+        for (int c = 0; c < 4; ++c)
+            r.s[w][c] = a[c];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; ++c) {
+            double t = 0.0;
+            for (int k = 0; k < kGWarps; ++k)
+                t += r.s[k][c];
+            a[c] = t;
+        }
+}
+
+__device__ void block_max_key(Red &r, unsigned long long &key)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    key = warp_max_u64(key);
+    __syncthreads();
+    if (lane == 0)
+        r.key[w] = key;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 1; k < kGWarps; ++k)
+            key = r.key[k] > key ? r.key[k] : key;
+}
+
+// Grid-wide (value, index) argmax through per-CTA partials: every CTA reads
+// the G partials after the barrier and reduces them in the same order.
+__device__ void grid_pick_reduce(const double *pv, const long long *pi, int G, double &v,
+                                 long long &i)
+{
+    __shared__ double s_v;
+    __shared__ long long s_i;
+    if (threadIdx.x < 32) {
+        double bv = -1.0;
+        long long bi = -1;
+        for (int b = threadIdx.x; b < G; b += 32)
+            pick(bv, bi, ldcg(pv + b), ldcg(pi + b));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+            const long long i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            pick(bv, bi, v2, i2);
+        }
+        if (threadIdx.x == 0) {
+            s_v = bv;
+            s_i = bi;
+        }
+    }
+    __syncthreads();
+    v = s_v;
+    i = s_i;
+    __syncthreads();
+}
+
+// Grid-wide sums of 4 values per CTA (fixed order, so every CTA gets the
+// same bits).
+__device__ void grid_sum4(const double *p, int G, double out[4])
+{
+    __shared__ double s_o[4];
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int b = 0; b < G; ++b)
+            t += ldcg(p + 4 * b + threadIdx.x);
+        s_o[threadIdx.x] = t;
+    }
+    __syncthreads();
+    for (int c = 0; c < 4; ++c)
+        out[c] = s_o[c];
+    __syncthreads();
+}
+
+__device__ void grid_max4(const double *p, int G, double out[4])
+{
+    __shared__ double s_o[4];
+    if (threadIdx.x < 4) {
+        double t = -INFINITY;
+        for (int b = 0; b < G; ++b)
+            t = fmax(t, ldcg(p + 4 * b + threadIdx.x));
+        s_o[threadIdx.x] = t;
+    }
+    __syncthreads();
+    for (int c = 0; c < 4; ++c)
+        out[c] = s_o[c];
+    __syncthreads();
+}
+
+// Squared distance with the oracle's operation order and no contraction,
+// for the seed-node decisions (exact ties must resolve identically).
+__device__ __forceinline__ double dist2_exact(const double *a, const double *b)
+{
+    const double dx = __dsub_rn(a[0], b[0]), dy = __dsub_rn(a[1], b[1]), dz = __dsub_rn(a[2], b[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// ---------------------------------------------------------------------------
+// Team layout: `ts` consecutive lanes (power of two <= 32) share one query and
+// split the centres between them.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int team_size(int64_t nq, int G)
+{
+    const int64_t lanes = (int64_t)G * kGThreads;
+    int ts = 1;
+    while (ts < 32 && (int64_t)(ts * 2) * nq <= lanes)
+        ts *= 2;
+    return ts;
+}
+
+template <typename T>
+__device__ __forceinline__ T team_sum(T v, int ts)
+{
+    for (int o = 1; o < ts; o <<= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP64 error of the node at position q with the current support (nc centres).
+__device__ __forceinline__ double team_error_f64(const GreedyArgs &a, int q, int nc, int sub,
+                                                 int ts)
+{
+    const D4 x = ldcg(a.xg64 + q);
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    for (int j = sub; j < nc; j += ts) {
+        const D4 c = ldcg(a.c64 + j);
+        const D4 w = ldcg(a.w64 + j);
+        const double dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
+        const double ph = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
+        fx = fma(w.x, ph, fx);
+        fy = fma(w.y, ph, fy);
+        fz = fma(w.z, ph, fz);
+    }
+    fx = team_sum(fx, ts);
+    fy = team_sum(fy, ts);
+    fz = team_sum(fz, ts);
+    const D4 d = ldcg(a.dg64 + q);
+    const double ex = d.x - fx, ey = d.y - fy, ez = d.z - fz;
+    return sqrt(fma(ez, ez, fma(ey, ey, ex * ex)));
+}
+
+// FP64 residual dr_q - F(r_q) of the node at position q (all lanes of the
+// team return the same value).
+__device__ __forceinline__ D4 team_resid_f64(const GreedyArgs &a, int q, int nc, int sub, int ts)
+{
+    const D4 x = ldcg(a.xg64 + q);
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    for (int j = sub; j < nc; j += ts) {
+        const D4 c = ldcg(a.c64 + j);
+        const D4 w = ldcg(a.w64 + j);
+        const double dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
+        const double ph = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
+        fx = fma(w.x, ph, fx);
+        fy = fma(w.y, ph, fy);
+        fz = fma(w.z, ph, fz);
+    }
+    fx = team_sum(fx, ts);
+    fy = team_sum(fy, ts);
+    fz = team_sum(fz, ts);
+    const D4 d = ldcg(a.dg64 + q);
+    return mk4(d.x - fx, d.y - fy, d.z - fz, 0.0);
+}
+
+struct EvalOut {
+    unsigned long long key;   // argmax key over [lo, hi) minus S (0 = none)
+    double gmax;              // full evaluations: certified global max
+    double grms;              // full evaluations: RMS over all nodes
+    bool certified_below;     // full evaluations: every node has E <= E*
+};
+
+// ---------------------------------------------------------------------------
+// Recurrence-Cholesky append of the node at position pn (Sec. 1, RC scheme):
+// with Z = L^-1 of the current nc x nc factor, b_j = phi(|r_n - r_j| / R),
+//   l = Z b,  d^2 = phi(0) - l.l,  y_new = (dr_n - l.y) / d,
+//   Z gains the row [-(Z^T l)^T / d, 1 / d],
+//   W_j += -(Z^T l)_j / d * y_new (j < nc),  w_new = y_new / d.
+// All CTAs call it; three grid barriers.  Returns kAppendOk, kAppendNotSpd
+// (d^2 <= kPivotMin, status latched) or kAppendTimeout.
+// ---------------------------------------------------------------------------
+constexpr int kAppendOk = 0, kAppendTimeout = 1, kAppendNotSpd = 2;
+
+__device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, double &min_piv,
+                           int pn, int node, long long kiter)
+{
+    GreedyCtl *ctl = a.ctl;
+    const int G = gridDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gtid = blockIdx.x * kGThreads + tid;
+    const int gthreads = G * kGThreads;
+    const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
+    // A1: b_j = phi(|r_n - r_j| / R)
+    const D4 xn = ldcg(a.xg64 + pn);
+    for (int j = gtid; j < nc; j += gthreads) {
+        const D4 c = ldcg(a.c64 + j);
+        const double dx = xn.x - c.x, dy = xn.y - c.y, dz = xn.z - c.z;
+        a.bvec[j] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
+    }
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) return kAppendTimeout;
+    // A2: l = Z b (warp per row) and partial sums of l.l and l.y
+    double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = gwarp; i < nc; i += gwarps) {
+        const double *zr = a.z + (size_t)i * a.ld;
+        double s = 0.0;
+        for (int p = lane; p <= i; p += 32)
+            s = fma(ldcg(zr + p), ldcg(a.bvec + p), s);
+        s = warp_sum_f64(s);
+        if (lane == 0) {
+            a.lvec[i] = s;
+            const D4 y = ldcg(a.y64 + i);
+            acc4[0] = fma(s, s, acc4[0]);
+            acc4[1] = fma(s, y.x, acc4[1]);
+            acc4[2] = fma(s, y.y, acc4[2]);
+            acc4[3] = fma(s, y.z, acc4[3]);
+        }
+    }
+    block_sum4(red, acc4);
+    if (tid == 0)
+        for (int c = 0; c < 4; ++c)
+            (a.part + (size_t)(use & 1) * kMaxGrid * 4)[4 * blockIdx.x + c] = acc4[c];
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) return kAppendTimeout;
+    double s4[4];
+    grid_sum4((a.part + (size_t)(use & 1) * kMaxGrid * 4), G, s4);
+    ++use;
+    const double d2 = 1.0 - s4[0];   // phi(0) = 1
+    if (!(d2 > kPivotMin)) {
+        if (blockIdx.x == 0 && tid == 0)
+            ctl->status = RBF_E_NOT_SPD;
+        return kAppendNotSpd;
+    }
+    min_piv = fmin(min_piv, d2);
+    const double d = sqrt(d2), inv_d = 1.0 / d;
+    const D4 dn = ldcg(a.dg64 + pn);
+    const double yx = (dn.x - s4[1]) * inv_d, yy = (dn.y - s4[2]) * inv_d,
+                 yz = (dn.z - s4[3]) * inv_d;
+    // A3: u = Z^T l (warp per row of Z^T); new row of Z; weight update
+    for (int j = gwarp; j < nc; j += gwarps) {
+        const double *ztr = a.zt + (size_t)j * a.ld;
+        double s = 0.0;
+        for (int i = j + lane; i < nc; i += 32)
+            s = fma(ldcg(ztr + i), ldcg(a.lvec + i), s);
+        s = warp_sum_f64(s);
+        if (lane == 0) {
+            const double zz = -s * inv_d;
+            a.z[(size_t)nc * a.ld + j] = zz;
+            a.zt[(size_t)j * a.ld + nc] = zz;
+            D4 w = ldcg(a.w64 + j);
+            w.x = fma(zz, yx, w.x);
+            w.y = fma(zz, yy, w.y);
+            w.z = fma(zz, yz, w.z);
+            a.w64[j] = w;
+            a.cw32[2 * j + 1] = make_float4((float)w.x, (float)w.y, (float)w.z,
+                                            (float)(fabs(w.x) + fabs(w.y) + fabs(w.z)));
+        }
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        a.z[(size_t)nc * a.ld + nc] = inv_d;
+        a.zt[(size_t)nc * a.ld + nc] = inv_d;
+        a.y64[nc] = mk4(yx, yy, yz, 0.0);   // y_new = (dr_n - l.y) / d
+        const double wx = yx * inv_d, wy = yy * inv_d, wz = yz * inv_d;
+        a.w64[nc] = mk4(wx, wy, wz, 0.0);
+        const D4 xc = ldcg(a.xg64 + pn);
+        a.c64[nc] = xc;
+        a.cw32[2 * nc] = make_float4((float)xc.x, (float)xc.y, (float)xc.z, 0.0f);
+        a.cw32[2 * nc + 1] = make_float4((float)wx, (float)wy, (float)wz,
+                                         (float)(fabs(wx) + fabs(wy) + fabs(wz)));
+        a.spos[nc] = pn;
+        a.in_s[pn] = 1;
+        a.sel_idx[nc] = node;
+        if (a.sel_iter)
+            a.sel_iter[nc] = kiter;
+    }
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) return kAppendTimeout;
+    ++nc;
+    return kAppendOk;
+}
+
+// ---------------------------------------------------------------------------
+// The persistent kernel.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
+{
+    extern __shared__ float4 s_cw[];
+    __shared__ Red red;
+    __shared__ float s_wabs;
+    GreedyCtl *ctl = a.ctl;
+    const int G = gridDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gtid = blockIdx.x * kGThreads + tid;
+    const int gthreads = G * kGThreads;
+    const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
+    const int nb = a.nb, m = a.m;
+    int use = 0;   // partial-buffer use counter (double buffering)
+    auto part = [&](int u) { return a.part + (size_t)(u & 1) * kMaxGrid * 4; };
+    auto parti = [&](int u) { return a.parti + (size_t)(u & 1) * kMaxGrid; };
+#define GSYNC()                                                                   \
+    do {                                                                          \
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) \
+            return;                                                               \
+    } while (0)
+#define GSYNC_B()                                                                 \
+    do {                                                                          \
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) \
+            return false;                                                         \
+    } while (0)
+
+    // ---------------- prologue: group-ordered packing ----------------------
+    double dmax = 0.0, xmax = 0.0;
+    int bad = 0;
+    for (int p = gtid; p < nb; p += gthreads) {
+        const int node = a.perm[p];
+        const int pos = goff(p % m, nb, m) + p / m;
+        a.node_of_pos[pos] = node;
+        a.pos_of_node[node] = pos;
+        const double x = a.xb[3 * node] * a.inv_r, y = a.xb[3 * node + 1] * a.inv_r,
+                     z = a.xb[3 * node + 2] * a.inv_r;
+        const double d0 = a.db[3 * node], d1 = a.db[3 * node + 1], d2 = a.db[3 * node + 2];
+        a.xg64[pos] = mk4(x, y, z, 0.0);
+        a.xg32[pos] = make_float4((float)x, (float)y, (float)z, 0.0f);
+        a.dg64[pos] = mk4(d0, d1, d2, 0.0);
+        a.in_s[pos] = 0;
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(d0) || !isfinite(d1) ||
+            !isfinite(d2))
+            bad = 1;
+        dmax = fmax(dmax, d0 * d0 + d1 * d1 + d2 * d2);
+        xmax = fmax(xmax, fmax(fabs(x), fmax(fabs(y), fabs(z))));
+    }
+    {
+        double mx[3] = {dmax, xmax, (double)bad};
+        for (int o = 16; o > 0; o >>= 1)
+            for (int c = 0; c < 3; ++c)
+                mx[c] = fmax(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+        __syncthreads();
+        if (lane == 0)
+            for (int c = 0; c < 3; ++c)
+                red.s[warp][c] = mx[c];
+        __syncthreads();
+        if (tid == 0) {
+            for (int k = 1; k < kGWarps; ++k)
+                for (int c = 0; c < 3; ++c)
+                    mx[c] = fmax(mx[c], red.s[k][c]);
+            double *pp = part(use) + 4 * blockIdx.x;
+            pp[0] = mx[0];
+            pp[1] = mx[1];
+            pp[2] = mx[2];
+            pp[3] = 0.0;
+        }
+    }
+    GSYNC();
+    double g4[4];
+    grid_max4(part(use), G, g4);
+    ++use;
+    if (g4[2] > 0.0) {
+        if (blockIdx.x == 0 && tid == 0)
+            ctl->status = RBF_E_NONFINITE;
+        return;   // every CTA sees the same flag
+    }
+    const double estar = a.tol_mode == 1 ? a.tol * sqrt(g4[0]) : a.tol;
+    const float xscale = (float)g4[1];
+
+    // ---------------- seed nodes (lowest index on ties) ---------------------
+    int seeds[3];
+    for (int s = 0; s < 3; ++s) {
+        double bv = -1.0;
+        long long bi = -1;
+        for (int n = gtid; n < nb; n += gthreads) {
+            double v;
+            if (s == 0) {
+                const double *d = a.db + 3 * n;
+                v = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])),
+                              __dmul_rn(d[2], d[2]));
+            } else if (s == 1) {
+                v = dist2_exact(a.xb + 3 * n, a.xb + 3 * seeds[0]);
+            } else {
+                v = fmin(dist2_exact(a.xb + 3 * n, a.xb + 3 * seeds[0]),
+                         dist2_exact(a.xb + 3 * n, a.xb + 3 * seeds[1]));
+            }
+            pick(bv, bi, v, n);
+        }
+        block_pick(red, bv, bi);
+        if (tid == 0) {
+            part(use)[blockIdx.x] = bv;
+            parti(use)[blockIdx.x] = bi;
+        }
+        GSYNC();
+        double v;
+        long long i;
+        grid_pick_reduce(part(use), parti(use), G, v, i);
+        ++use;
+        seeds[s] = (int)i;
+    }
+
+    int nc = 0;
+    double min_piv = INFINITY;
+
+    for (int s = 0; s < 3; ++s) {
+        const int pn = ldcg(a.pos_of_node + seeds[s]);
+        if (chol_append(a, red, nc, use, min_piv, pn, seeds[s], -1) != kAppendOk) {
+            if (blockIdx.x == 0 && tid == 0) {
+                ctl->nc = nc;
+                ctl->min_pivot = min_piv;
+            }
+            return;
+        }
+    }
+
+    // ---------------- error evaluation over a position range ---------------
+    int ev = 0;                      // evaluation counter (ring index)
+    long long pairs32 = 0, pairs64 = 0;
+    unsigned long long rescored_local = 0;
+    // Evaluates E at positions [p0, p1); argmax over [lo, hi) minus S; when
+    // `full`, also the certified global max and the RMS over [p0, p1).
+    auto evaluate = [&](int p0, int p1, int lo, int hi, bool full, EvalOut &out) -> bool {
+        const int r = ev % 3;
+        const int nq = p1 - p0;
+        const int ts = team_size(nq, G);
+        const int sub = lane & (ts - 1);
+        const int team = gtid / ts, nteams = gthreads / ts;
+        const int rounds = (nq + nteams - 1) / nteams;
+        unsigned long long key = 0;
+        double lmax = 0.0, lsq = 0.0;
+        if (a.prec == RBF_PREC_F64) {
+            for (int it = 0; it < rounds; ++it) {
+                const int q = p0 + team + it * nteams;
+                const bool act = q < p1;
+                const double e = team_error_f64(a, act ? q : p0, nc, sub, ts);
+                if (act && sub == 0) {
+                    a.e64[q] = e;
+                    if (full) {
+                        lmax = fmax(lmax, e);
+                        lsq = fma(e, e, lsq);
+                    }
+                    if (q >= lo && q < hi && !ldcg(a.in_s + q)) {
+                        const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
+                        key = k2 > key ? k2 : key;
+                    }
+                }
+            }
+            if (blockIdx.x == 0 && tid == 0)
+                pairs64 += (long long)nq * nc;
+        } else {
+            // ---- pass 1: FP32 errors with a bound (centres from shared memory)
+            const bool smem = nc <= kSmemCentresF32;
+            if (smem) {
+                for (int j = tid; j < 2 * nc; j += kGThreads)
+                    s_cw[j] = ldcg(a.cw32 + j);
+            }
+            if (tid < 32) {
+                float t = 0.0f;
+                for (int j = tid; j < nc; j += 32)
+                    t += ldcg(a.cw32 + 2 * j + 1).w;
+                t = team_sum(t, 32);
+                if (tid == 0)
+                    s_wabs = t;
+            }
+            __syncthreads();
+            const float4 *cw = smem ? s_cw : a.cw32;
+            const float coord_term = kBetaCoord * xscale * s_wabs * 1.001f;
+            float tloc = 0.0f, umax = 0.0f;
+            for (int it = 0; it < rounds; ++it) {
+                const int q = p0 + team + it * nteams;
+                const bool act = q < p1;
+                const float4 x = ldcg(a.xg32 + (act ? q : p0));
+                float fx = 0.0f, fy = 0.0f, fz = 0.0f, sb = 0.0f;
+                for (int j = sub; j < nc; j += ts) {
+                    const float4 c = smem ? cw[2 * j] : ldcg(cw + 2 * j);
+                    const float4 w = smem ? cw[2 * j + 1] : ldcg(cw + 2 * j + 1);
+                    const float dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
+                    const float ph = phi_f32_s(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                    fx = fmaf(w.x, ph, fx);
+                    fy = fmaf(w.y, ph, fy);
+                    fz = fmaf(w.z, ph, fz);
+                    sb = fmaf(w.w, ph, sb);
+                }
+                fx = team_sum(fx, ts);
+                fy = team_sum(fy, ts);
+                fz = team_sum(fz, ts);
+                sb = team_sum(sb, ts);
+                if (act && sub == 0) {
+                    const D4 d = ldcg(a.dg64 + q);
+                    const float ex = (float)d.x - fx, ey = (float)d.y - fy, ez = (float)d.z - fz;
+                    const float e = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
+                    const float dabs = (float)(fabs(d.x) + fabs(d.y) + fabs(d.z));
+                    // error bound of the FP32 error: rounding of phi and of the
+                    // sums (proportional to sum |w| phi), rounding of the
+                    // coordinates (proportional to max|x|/R * sum |w|), and of
+                    // the displacement
+                    const float beta =
+                        kU32 * (kBetaPhi * (sb + dabs) + coord_term + 4.0f * e) + 1e-30f;
+                    const float up = e + beta;
+                    a.u32[q] = up;
+                    if (full)
+                        umax = fmaxf(umax, up);
+                    if (q >= lo && q < hi && !ldcg(a.in_s + q))
+                        tloc = fmaxf(tloc, fmaxf(e - beta, 0.0f));
+                }
+            }
+            tloc = warp_max_f32(tloc);
+            umax = warp_max_f32(umax);
+            if (lane == 0) {
+                if (tloc > 0.0f)
+                    atomicMax(&ctl->tslot[r], __float_as_uint(tloc));
+            }
+            if (blockIdx.x == 0 && tid == 0)
+                pairs32 += (long long)nq * nc;
+            GSYNC_B();
+            const float thr = __uint_as_float(ldcg(&ctl->tslot[r]));
+            // ---- pass 2: FP64 re-score of every node whose bound reaches the
+            // group maximum (argmax) or E* (full check)
+            for (int it = 0; it < rounds; ++it) {
+                const int q = p0 + team + it * nteams;
+                const bool act = q < p1;
+                bool need = false;
+                float up = 0.0f;
+                if (act) {
+                    up = ldcg(a.u32 + q);
+                    const bool in_arg = q >= lo && q < hi && !ldcg(a.in_s + q) && up >= thr;
+                    need = in_arg || (full && (double)up > estar);
+                    if (full && !need && sub == 0) {
+                        // certified: E <= up <= E* (bound enters max and RMS)
+                        lmax = fmax(lmax, (double)up);
+                        lsq = fma((double)up, (double)up, lsq);
+                    }
+                }
+                // the whole warp takes the same branch per team; teams that do
+                // not need FP64 still join the shuffles
+                const unsigned long long bal = __ballot_sync(0xffffffffu, need);
+                if (bal == 0ull && !need)
+                    continue;
+                const double e = team_error_f64(a, act ? q : p0, nc, sub, ts);
+                if (need && sub == 0) {
+                    ++rescored_local;
+                    a.e64[q] = e;
+                    if (full) {
+                        lmax = fmax(lmax, e);
+                        lsq = fma(e, e, lsq);
+                    }
+                    if (q >= lo && q < hi && !ldcg(a.in_s + q)) {
+                        const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
+                        key = k2 > key ? k2 : key;
+                    }
+                }
+            }
+            (void)umax;
+        }
+        // ---- reductions
+        block_max_key(red, key);
+        if (tid == 0 && key)
+            atomicMax(&ctl->slot[r], key);
+        if (full) {
+            double a4[4] = {0.0, lsq, 0.0, 0.0};
+            double mx = lmax;
+            for (int o = 16; o > 0; o >>= 1)
+                mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            block_sum4(red, a4);
+            __syncthreads();
+            if (lane == 0)
+                red.v[warp] = mx;
+            __syncthreads();
+            if (tid == 0) {
+                for (int k = 1; k < kGWarps; ++k)
+                    mx = fmax(mx, red.v[k]);
+                double *pp = part(use) + 4 * blockIdx.x;
+                pp[0] = mx;
+                pp[1] = a4[1];
+                pp[2] = 0.0;
+                pp[3] = 0.0;
+            }
+        }
+        GSYNC_B();
+        out.key = ldcg(&ctl->slot[r]);
+        if (full) {
+            double mx4[4], sm4[4];
+            grid_max4(part(use), G, mx4);
+            grid_sum4(part(use), G, sm4);
+            ++use;
+            out.gmax = mx4[0];
+            out.grms = sqrt(sm4[1] / (double)nq);
+            out.certified_below = mx4[0] <= estar;
+        }
+        if (blockIdx.x == 0 && tid == 0) {
+            ctl->slot[(r + 2) % 3] = 0ull;
+            ctl->tslot[(r + 2) % 3] = 0u;
+        }
+        ++ev;
+        return true;
+    };
+
+    // ---------------- main loop (k counts iterations from 3) ---------------
+    long long k = 3, nhist = 0, nfull = 0, idle = 0;
+    bool have_key = false;
+    unsigned long long next_key = 0;
+    double fmax_last = -1.0, frms_last = -1.0;
+    int status = RBF_OK;
+    for (;; ++k) {
+        const int gi = (int)(k % m);
+        const int g0 = goff(gi, nb, m), g1 = goff(gi + 1, nb, m);
+        unsigned long long key;
+        if (have_key) {
+            key = next_key;
+        } else {
+            EvalOut eo;
+            if (!evaluate(g0, g1, g0, g1, false, eo))
+                return;
+            key = eo.key;
+        }
+        int add_node = -1, add_pos = -1;
+        double eloc = -1.0;
+        if (key) {
+            add_node = key_node(key);
+            add_pos = ldcg(a.pos_of_node + add_node);
+            eloc = ldcg(a.e64 + add_pos);
+            if (!(eloc > estar))
+                add_node = -1;
+        }
+        const long long nc_before = nc;
+        if (add_node >= 0) {
+            if (nc >= a.nc_max) {
+                status = RBF_E_NC_MAX;
+                break;
+            }
+            if (chol_append(a, red, nc, use, min_piv, add_pos, add_node, k) != kAppendOk) {
+                status = RBF_E_NOT_SPD;   // or the latched timeout, which wins
+                break;
+            }
+        }
+        const bool full = add_node < 0 || ((k - 2) % m) == 0;
+        double gmax = -1.0, grms = -1.0;
+        bool stop = false;
+        have_key = false;
+        if (full) {
+            const int ni = (int)((k + 1) % m);
+            EvalOut eo;
+            if (!evaluate(0, nb, goff(ni, nb, m), goff(ni + 1, nb, m), true, eo))
+                return;
+            ++nfull;
+            gmax = eo.gmax;
+            grms = eo.grms;
+            fmax_last = gmax;
+            frms_last = grms;
+            stop = eo.certified_below;
+            have_key = true;
+            next_key = eo.key;
+        }
+        if (blockIdx.x == 0 && tid == 0 && a.hist && nhist < a.hist_cap) {
+            double *h = a.hist + RBF_HIST_COLS * nhist;
+            h[0] = (double)k;
+            h[1] = (double)nc_before;
+            h[2] = eloc;
+            h[3] = gmax;
+            h[4] = grms;
+            h[5] = (double)add_node;
+        }
+        ++nhist;
+        if (stop)
+            break;
+        // A full cycle of m groups that adds nothing while the full check
+        // still fails can only come from rounding differences between two
+        // evaluations of the same node (errors within a few ulp of E*): stop.
+        idle = add_node >= 0 ? 0 : idle + 1;
+        if (idle > m)
+            break;
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        if (status != RBF_OK)
+            atomicCAS(&ctl->status, (int)RBF_OK, status);
+        ctl->estar = estar;
+        ctl->nc = nc;
+        ctl->iterations = k - 3 + 1;
+        ctl->full_checks = nfull;
+        ctl->pairs_f32 = pairs32;
+        ctl->pairs_f64 = pairs64;
+        ctl->final_max = fmax_last;
+        ctl->final_rms = frms_last;
+        ctl->min_pivot = min_piv;
+        ctl->n_hist = nhist;
+    }
+    if (rescored_local)
+        atomicAdd(&ctl->rescored, rescored_local);
+#undef GSYNC
+#undef GSYNC_B
+}
+
+
+// ---------------------------------------------------------------------------
+// Support weights (Eqs. 4-5 on S): recurrence-Cholesky appends in the given
+// order, then FP64 iterative refinement W += Z^T Z (dX_S - Phi_SS W) with the
+// residual recomputed from coordinates.  One cooperative launch.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGThreads, 1)
+k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
+        D4 *__restrict__ rvec, D4 *__restrict__ tvec, double *__restrict__ w_out)
+{
+    __shared__ Red red;
+    GreedyCtl *ctl = a.ctl;
+    const int G = gridDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gtid = blockIdx.x * kGThreads + tid;
+    const int gthreads = G * kGThreads;
+    const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
+    int use = 0;
+    auto part = [&](int u) { return a.part + (size_t)(u & 1) * kMaxGrid * 4; };
+#define GSYNC()                                                                   \
+    do {                                                                          \
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) \
+            return;                                                               \
+    } while (0)
+
+    double bad = 0.0;
+    for (int j = gtid; j < nc_total; j += gthreads) {
+        const int node = sel[j];
+        if (node < 0 || node >= a.nb) {
+            bad = fmax(bad, 2.0);
+            continue;
+        }
+        const double x = a.xb[3 * node] * a.inv_r, y = a.xb[3 * node + 1] * a.inv_r,
+                     z = a.xb[3 * node + 2] * a.inv_r;
+        const double d0 = a.db[3 * node], d1 = a.db[3 * node + 1], d2 = a.db[3 * node + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(d0) || !isfinite(d1) ||
+            !isfinite(d2))
+            bad = fmax(bad, 1.0);
+        a.xg64[j] = mk4(x, y, z, 0.0);
+        a.dg64[j] = mk4(d0, d1, d2, 0.0);
+        a.in_s[j] = 0;
+    }
+    {
+        double mx = bad;
+        for (int o = 16; o > 0; o >>= 1)
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        __syncthreads();
+        if (lane == 0)
+            red.v[warp] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            for (int k = 1; k < kGWarps; ++k)
+                mx = fmax(mx, red.v[k]);
+            part(use)[4 * blockIdx.x] = mx;
+        }
+    }
+    GSYNC();
+    {
+        double g4[4];
+        // only slot 0 of each CTA's partial is meaningful here
+        __shared__ double s_m;
+        if (tid == 0) {
+            double mm = 0.0;
+            for (int b = 0; b < G; ++b)
+                mm = fmax(mm, ldcg(part(use) + 4 * b));
+            s_m = mm;
+        }
+        __syncthreads();
+        g4[0] = s_m;
+        __syncthreads();
+        ++use;
+        if (g4[0] > 0.0) {
+            if (blockIdx.x == 0 && tid == 0)
+                ctl->status = g4[0] > 1.5 ? RBF_E_ARG : RBF_E_NONFINITE;
+            return;
+        }
+    }
+    int nc = 0;
+    double min_piv = INFINITY;
+    for (int j = 0; j < nc_total; ++j) {
+        const int node = sel[j];
+        const int r = chol_append(a, red, nc, use, min_piv, j, node, -1);
+        if (r != kAppendOk) {
+            if (blockIdx.x == 0 && tid == 0) {
+                ctl->nc = nc;
+                ctl->min_pivot = min_piv;
+            }
+            return;
+        }
+    }
+    const int ts = team_size(nc, G);
+    const int sub = lane & (ts - 1);
+    const int team = gtid / ts, nteams = gthreads / ts;
+    const int rounds = (nc + nteams - 1) / nteams;
+    double maxres = 0.0;
+    for (int step = 0; step <= steps; ++step) {
+        // residual r = dX_S - Phi_SS W
+        double lmax = 0.0;
+        for (int it = 0; it < rounds; ++it) {
+            const int q = team + it * nteams;
+            const bool act = q < nc;
+            const D4 r = team_resid_f64(a, act ? q : 0, nc, sub, ts);
+            if (act && sub == 0) {
+                rvec[q] = r;
+                lmax = fmax(lmax, fmax(fabs(r.x), fmax(fabs(r.y), fabs(r.z))));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        __syncthreads();
+        if (lane == 0)
+            red.v[warp] = lmax;
+        __syncthreads();
+        if (tid == 0) {
+            for (int k = 1; k < kGWarps; ++k)
+                lmax = fmax(lmax, red.v[k]);
+            part(use)[4 * blockIdx.x] = lmax;
+        }
+        GSYNC();
+        {
+            __shared__ double s_m;
+            if (tid == 0) {
+                double mm = 0.0;
+                for (int b = 0; b < G; ++b)
+                    mm = fmax(mm, ldcg(part(use) + 4 * b));
+                s_m = mm;
+            }
+            __syncthreads();
+            maxres = s_m;
+            __syncthreads();
+            ++use;
+        }
+        if (step == steps)
+            break;
+        // t = Z r (3 right-hand sides, warp per row)
+        for (int i = gwarp; i < nc; i += gwarps) {
+            const double *zr = a.z + (size_t)i * a.ld;
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int p = lane; p <= i; p += 32) {
+                const double zz = ldcg(zr + p);
+                const D4 r = ldcg(rvec + p);
+                sx = fma(zz, r.x, sx);
+                sy = fma(zz, r.y, sy);
+                sz = fma(zz, r.z, sz);
+            }
+            sx = warp_sum_f64(sx);
+            sy = warp_sum_f64(sy);
+            sz = warp_sum_f64(sz);
+            if (lane == 0)
+                tvec[i] = mk4(sx, sy, sz, 0.0);
+        }
+        GSYNC();
+        // W += Z^T t
+        for (int j = gwarp; j < nc; j += gwarps) {
+            const double *ztr = a.zt + (size_t)j * a.ld;
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int i = j + lane; i < nc; i += 32) {
+                const double zz = ldcg(ztr + i);
+                const D4 t = ldcg(tvec + i);
+                sx = fma(zz, t.x, sx);
+                sy = fma(zz, t.y, sy);
+                sz = fma(zz, t.z, sz);
+            }
+            sx = warp_sum_f64(sx);
+            sy = warp_sum_f64(sy);
+            sz = warp_sum_f64(sz);
+            if (lane == 0) {
+                D4 w = ldcg(a.w64 + j);
+                w.x += sx;
+                w.y += sy;
+                w.z += sz;
+                a.w64[j] = w;
+            }
+        }
+        GSYNC();
+    }
+    for (int j = gtid; j < nc; j += gthreads) {
+        const D4 w = ldcg(a.w64 + j);
+        w_out[3 * j] = w.x;
+        w_out[3 * j + 1] = w.y;
+        w_out[3 * j + 2] = w.z;
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        ctl->nc = nc;
+        ctl->min_pivot = min_piv;
+        ctl->final_max = maxres;
+    }
+#undef GSYNC
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout.
+// ---------------------------------------------------------------------------
+struct GreedyWs {
+    size_t ctl, part, parti, perm, node_of_pos, pos_of_node, xg64, dg64, xg32, in_s, u32, e64,
+        spos, c64, w64, cw32, y64, z, zt, bvec, lvec, total;
+};
+
+static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
+{
+    GreedyWs L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    L.ctl = take(sizeof(GreedyCtl));
+    L.part = take(sizeof(double) * 2 * kMaxGrid * 4);
+    L.parti = take(sizeof(long long) * 2 * kMaxGrid);
+    L.perm = take(sizeof(int32_t) * nb);
+    L.node_of_pos = take(sizeof(int32_t) * nb);
+    L.pos_of_node = take(sizeof(int32_t) * nb);
+    L.xg64 = take(sizeof(D4) * nb);
+    L.dg64 = take(sizeof(D4) * nb);
+    L.xg32 = take(sizeof(float4) * nb);
+    L.in_s = take(nb);
+    L.u32 = take(sizeof(float) * nb);
+    L.e64 = take(sizeof(double) * nb);
+    L.spos = take(sizeof(int32_t) * ncm);
+    L.c64 = take(sizeof(D4) * ncm);
+    L.w64 = take(sizeof(D4) * ncm);
+    L.cw32 = take(sizeof(float4) * 2 * ncm);
+    L.y64 = take(sizeof(D4) * ncm);
+    L.z = take(sizeof(double) * ncm * ncm);
+    L.zt = take(sizeof(double) * ncm * ncm);
+    L.bvec = take(sizeof(double) * ncm);
+    L.lvec = take(sizeof(double) * ncm);
+    L.total = o;
+    return L;
+}
+
+static bool greedy_args_ok(int64_t nb, const rbf_params *p)
+{
+    return p && nb >= 3 && nb < kMaxNodes && p->m >= 1 && p->m <= nb && p->nc_max >= 3 &&
+           p->nc_max <= nb && p->nc_max <= 46340 && p->radius > 0.0 &&
+           std::isfinite(p->radius) && p->tol >= 0.0 && std::isfinite(p->tol) &&
+           (p->tol_mode == 0 || p->tol_mode == 1) &&
+           (p->eval_prec == RBF_PREC_F32 || p->eval_prec == RBF_PREC_F64) && p->flags == 0;
+}
+
+}  // namespace rbf
+
+namespace rbf {
+struct SolveWs {
+    GreedyWs g;
+    size_t sel, rvec, tvec, total;
+};
+
+static SolveWs solve_ws_layout(int64_t nc)
+{
+    SolveWs L{};
+    L.g = greedy_ws_layout(nc, nc);
+    size_t o = L.g.total;
+    L.sel = o;
+    o = align_up(o + sizeof(int32_t) * nc, 256);
+    L.rvec = o;
+    o = align_up(o + sizeof(D4) * nc, 256);
+    L.tvec = o;
+    o = align_up(o + sizeof(D4) * nc, 256);
+    L.total = o;
+    return L;
+}
+
+static void fill_args(GreedyArgs &a, char *ws, const GreedyWs &L)
+{
+    a.ctl = (GreedyCtl *)(ws + L.ctl);
+    a.perm = (const int32_t *)(ws + L.perm);
+    a.node_of_pos = (int32_t *)(ws + L.node_of_pos);
+    a.pos_of_node = (int32_t *)(ws + L.pos_of_node);
+    a.xg64 = (D4 *)(ws + L.xg64);
+    a.dg64 = (D4 *)(ws + L.dg64);
+    a.xg32 = (float4 *)(ws + L.xg32);
+    a.in_s = (uint8_t *)(ws + L.in_s);
+    a.u32 = (float *)(ws + L.u32);
+    a.e64 = (double *)(ws + L.e64);
+    a.part = (double *)(ws + L.part);
+    a.parti = (long long *)(ws + L.parti);
+    a.spos = (int32_t *)(ws + L.spos);
+    a.c64 = (D4 *)(ws + L.c64);
+    a.w64 = (D4 *)(ws + L.w64);
+    a.cw32 = (float4 *)(ws + L.cw32);
+    a.y64 = (D4 *)(ws + L.y64);
+    a.z = (double *)(ws + L.z);
+    a.zt = (double *)(ws + L.zt);
+    a.bvec = (double *)(ws + L.bvec);
+    a.lvec = (double *)(ws + L.lvec);
+}
+}  // namespace rbf
+
+using namespace rbf;
+
+extern "C" size_t rbf_greedy_workspace_bytes(int64_t nb, const rbf_params *p)
+{
+    if (!greedy_args_ok(nb, p))
+        return 0;
+    return greedy_ws_layout(nb, p->nc_max).total;
+}
+
+extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, int64_t nb,
+                                        const rbf_params *p, int32_t *d_sel_idx,
+                                        int64_t *d_sel_iter, double *d_hist, int64_t hist_cap,
+                                        int64_t *h_nc, int64_t *h_n_hist,
+                                        rbf_greedy_stats *h_stats, void *d_ws, size_t ws_bytes,
+                                        void *stream)
+{
+    if (!greedy_args_ok(nb, p) || !d_xb || !d_db || !d_sel_idx || !h_nc || hist_cap < 0 ||
+        (hist_cap > 0 && !d_hist))
+        return RBF_E_ARG;
+    const GreedyWs L = greedy_ws_layout(nb, p->nc_max);
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
+        return RBF_E_WORKSPACE;
+    DeviceInfo dev;
+    if (!device_info(&dev) || !dev.coop)
+        return RBF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)d_ws;
+
+    // the random partition (host, O(N_b)) -- overlaps nothing yet
+    std::vector<int32_t> perm((size_t)nb);
+    fisher_yates(nb, p->seed, perm.data());
+    if (cudaMemsetAsync(ws + L.ctl, 0, sizeof(GreedyCtl), st) != cudaSuccess ||
+        cudaMemcpyAsync(ws + L.perm, perm.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+        return RBF_E_CUDA;
+
+    GreedyArgs a{};
+    a.xb = d_xb;
+    a.db = d_db;
+    a.nb = (int)nb;
+    a.m = (int)p->m;
+    a.nc_max = (int)p->nc_max;
+    a.prec = p->eval_prec;
+    a.inv_r = 1.0 / p->radius;
+    a.tol = p->tol;
+    a.tol_mode = p->tol_mode;
+    a.ld = (int)p->nc_max;
+    a.sel_idx = d_sel_idx;
+    a.sel_iter = d_sel_iter;
+    a.hist = hist_cap > 0 ? d_hist : nullptr;
+    a.hist_cap = hist_cap;
+    fill_args(a, ws, L);
+
+    const size_t smem = p->eval_prec == RBF_PREC_F32
+                            ? sizeof(float4) * 2 * (size_t)std::min<int64_t>(p->nc_max, kSmemCentresF32)
+                            : 0;
+    if (cudaFuncSetAttribute(k_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float4) * 2 * kSmemCentresF32)) != cudaSuccess)
+        return RBF_E_CUDA;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_greedy, kGThreads, smem) !=
+            cudaSuccess ||
+        occ < 1)
+        return RBF_E_CUDA;
+    const int grid = std::min(dev.sms * std::min(occ, 1), kMaxGrid);
+    void *kargs[] = {&a};
+    if (cudaLaunchCooperativeKernel((const void *)k_greedy, grid, kGThreads, kargs, smem, st) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return RBF_E_CUDA;
+    }
+    GreedyCtl ctl;
+    if (cudaMemcpyAsync(&ctl, ws + L.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return RBF_E_CUDA;
+    }
+    *h_nc = ctl.nc;
+    if (h_n_hist)
+        *h_n_hist = ctl.n_hist;
+    if (h_stats) {
+        h_stats->iterations = ctl.iterations;
+        h_stats->nc = ctl.nc;
+        h_stats->full_checks = ctl.full_checks;
+        h_stats->pairs_f32 = ctl.pairs_f32;
+        h_stats->pairs_f64 = ctl.pairs_f64;
+        h_stats->rescored = (int64_t)ctl.rescored;
+        h_stats->estar = ctl.estar;
+        h_stats->final_max = ctl.final_max;
+        h_stats->final_rms = ctl.final_rms;
+        h_stats->min_pivot = ctl.min_pivot;
+    }
+    return (rbf_status)ctl.status;
+}
+
+// ---------------------------------------------------------------------------
+// rbf_solve_weights
+// ---------------------------------------------------------------------------
+
+extern "C" size_t rbf_solve_workspace_bytes(int64_t nc)
+{
+    if (nc < 1 || nc > 46340)
+        return 0;
+    return solve_ws_layout(nc).total;
+}
+
+extern "C" rbf_status rbf_solve_weights(const double *d_xb, const double *d_db, int64_t nb,
+                                        const int32_t *d_sel_idx, int64_t nc,
+                                        const rbf_params *p, double *d_w, double *h_max_resid,
+                                        void *d_ws, size_t ws_bytes, void *stream)
+{
+    if (!p || !d_xb || !d_db || !d_sel_idx || !d_w || nc < 1 || nc > nb || nc > 46340 ||
+        nb >= kMaxNodes || !(p->radius > 0.0) || !std::isfinite(p->radius) ||
+        p->refine_steps < 0 || p->refine_steps > 16)
+        return RBF_E_ARG;
+    const SolveWs L = solve_ws_layout(nc);
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
+        return RBF_E_WORKSPACE;
+    DeviceInfo dev;
+    if (!device_info(&dev) || !dev.coop)
+        return RBF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)d_ws;
+    GreedyArgs a{};
+    a.xb = d_xb;
+    a.db = d_db;
+    a.nb = (int)nb;
+    a.m = 1;
+    a.nc_max = (int)nc;
+    a.prec = RBF_PREC_F64;
+    a.inv_r = 1.0 / p->radius;
+    a.ld = (int)nc;
+    a.sel_idx = (int32_t *)(ws + L.sel);
+    a.sel_iter = nullptr;
+    a.hist = nullptr;
+    fill_args(a, ws, L.g);
+    if (cudaMemsetAsync(ws + L.g.ctl, 0, sizeof(GreedyCtl), st) != cudaSuccess)
+        return RBF_E_CUDA;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve, kGThreads, 0) != cudaSuccess ||
+        occ < 1)
+        return RBF_E_CUDA;
+    const int grid = std::min(dev.sms, kMaxGrid);
+    int nc_i = (int)nc, steps = p->refine_steps;
+    D4 *rvec = (D4 *)(ws + L.rvec), *tvec = (D4 *)(ws + L.tvec);
+    void *kargs[] = {&a, (void *)&d_sel_idx, &nc_i, &steps, &rvec, &tvec, &d_w};
+    if (cudaLaunchCooperativeKernel((const void *)k_solve, grid, kGThreads, kargs, 0, st) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return RBF_E_CUDA;
+    }
+    GreedyCtl ctl;
+    if (cudaMemcpyAsync(&ctl, ws + L.g.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return RBF_E_CUDA;
+    }
+    if (h_max_resid)
+        *h_max_resid = ctl.final_max;
+    return (rbf_status)ctl.status;
+}

@@ -1,0 +1,153 @@
+// rbf_host.cu -- host helpers, status strings and the FMA-peak microbenchmark.
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "rbf_device.cuh"
+#include "rbf_host.h"
+
+namespace rbf {
+
+bool device_info(DeviceInfo *out)
+{
+    static std::mutex mu;
+    static std::vector<DeviceInfo> cache;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev)
+        cache.resize(dev + 1, DeviceInfo{-1, 0, 0, 0});
+    if (cache[dev].device < 0) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        cache[dev].device = dev;
+        cache[dev].sms = prop.multiProcessorCount;
+        cache[dev].coop = prop.cooperativeLaunch;
+        cache[dev].smem_optin = prop.sharedMemPerBlockOptin;
+    }
+    *out = cache[dev];
+    return true;
+}
+
+void fisher_yates(int64_t n, uint64_t seed, int32_t *perm)
+{
+    uint64_t st = seed;
+    for (int64_t p = 0; p < n; ++p)
+        perm[p] = (int32_t)p;
+    for (int64_t i = n - 1; i >= 1; --i) {
+        const uint64_t j = splitmix64_next(&st) % (uint64_t)(i + 1);
+        const int32_t t = perm[i];
+        perm[i] = perm[j];
+        perm[j] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FMA peak: every thread runs 8 independent dependent-FMA chains; the grid is
+// 4 CTAs of 512 threads per SM.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) k_fma_peak(T *out, int iters, T a, T b)
+{
+    T x0 = (T)threadIdx.x, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+    T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            x0 = x0 * a + b; x1 = x1 * a + b; x2 = x2 * a + b; x3 = x3 * a + b;
+            x4 = x4 * a + b; x5 = x5 * a + b; x6 = x6 * a + b; x7 = x7 * a + b;
+        }
+    }
+    const T s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+    if (s == (T)-12345.0)   // never true; keeps the chains alive
+        out[blockIdx.x] = s;
+}
+
+}  // namespace rbf
+
+using namespace rbf;
+
+extern "C" const char *rbf_status_string(rbf_status s)
+{
+    switch (s) {
+    case RBF_OK: return "RBF_OK";
+    case RBF_E_ARG: return "RBF_E_ARG: invalid argument";
+    case RBF_E_NOT_SPD: return "RBF_E_NOT_SPD: non-positive Cholesky pivot (coincident support nodes)";
+    case RBF_E_NC_MAX: return "RBF_E_NC_MAX: support-set capacity reached";
+    case RBF_E_NONFINITE: return "RBF_E_NONFINITE: NaN or Inf in an input";
+    case RBF_E_WORKSPACE: return "RBF_E_WORKSPACE: workspace missing, too small or misaligned";
+    case RBF_E_TIMEOUT: return "RBF_E_TIMEOUT: bounded device wait expired";
+    case RBF_E_CUDA: return "RBF_E_CUDA: CUDA runtime error or no device";
+    }
+    return "unknown rbf_status";
+}
+
+extern "C" rbf_status rbf_group_of(int64_t nb, int64_t m, uint64_t seed, int32_t *h_group_of)
+{
+    if (nb < 1 || m < 1 || m > nb || !h_group_of || nb > ((int64_t)1 << 31) - 1)
+        return RBF_E_ARG;
+    std::vector<int32_t> perm((size_t)nb);
+    fisher_yates(nb, seed, perm.data());
+    for (int64_t p = 0; p < nb; ++p)
+        h_group_of[perm[p]] = (int32_t)(p % m);
+    return RBF_OK;
+}
+
+extern "C" const char *rbf_version(void) { return "rbfgcb 0.1 (sm_103a)"; }
+
+extern "C" rbf_status rbf_last_device_status(void)
+{
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return RBF_E_CUDA;
+    }
+    return RBF_OK;
+}
+
+extern "C" rbf_status rbf_measure_fma_peak(int prec, double *h_flops, void *stream)
+{
+    if (!h_flops || (prec != 32 && prec != 64))
+        return RBF_E_ARG;
+    DeviceInfo dev;
+    if (!device_info(&dev))
+        return RBF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int threads = 512, blocks = dev.sms * 4;
+    const int iters = prec == 32 ? 4096 : 256;
+    void *out = nullptr;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return RBF_E_CUDA;
+    // The output is never written (the guard is never true): a null pointer
+    // keeps this entry point free of allocations.
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, st);
+        if (prec == 32)
+            k_fma_peak<float><<<blocks, threads, 0, st>>>((float *)out, iters, 0.999f, 0.001f);
+        else
+            k_fma_peak<double><<<blocks, threads, 0, st>>>((double *)out, iters, 0.999, 0.001);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            return RBF_E_CUDA;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best_ms)
+            best_ms = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess)
+        return RBF_E_CUDA;
+    const double fmas = (double)blocks * threads * iters * 16.0 * 8.0;
+    *h_flops = 2.0 * fmas / (best_ms * 1e-3);
+    return RBF_OK;
+}

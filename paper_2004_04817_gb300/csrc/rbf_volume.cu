@@ -1,0 +1,263 @@
+// rbf_volume.cu -- volume displacement sum (Eq. 6 of arXiv:2004.04817):
+//     dv_v = sum_{j in S} w_j phi(|x_v - r_j| / R),  v = 1..N_v.
+//
+// FP32 kernel: every thread owns Q volume points (coordinates pre-scaled by
+// 1/R, float4 loads), centres and weights are staged in shared memory in
+// tiles and read as broadcast float4 pairs, so a pair costs ~15 FP32-pipe
+// instructions plus one MUFU square root and no memory traffic.
+// FP64 kernel: the same structure in double precision (reference arithmetic).
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rbf_device.cuh"
+#include "rbf_host.h"
+
+namespace rbf {
+
+constexpr int kVolThreads = 256;
+constexpr int kVolQ = 4;               // points per thread (register blocking)
+constexpr int kTileF32 = 2048;         // centres per shared-memory tile (64 KB)
+constexpr int kTileF64 = 1024;         // centres per shared-memory tile (64 KB)
+
+// ---------------------------------------------------------------------------
+// Packing: FP64 row-major inputs -> scaled, vector-aligned device layouts.
+// ---------------------------------------------------------------------------
+__global__ void k_pack_points_f32(const double *__restrict__ x, int64_t n, double inv_r,
+                                  float4 *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        out[i] = make_float4((float)(x[3 * i] * inv_r), (float)(x[3 * i + 1] * inv_r),
+                             (float)(x[3 * i + 2] * inv_r), 0.0f);
+    }
+}
+
+// centres c_j = xb[sel[j]] / R and weights w_j, interleaved (c_j, w_j).
+__global__ void k_pack_centres(const double *__restrict__ xb, const int32_t *__restrict__ sel,
+                               const double *__restrict__ w, int64_t nc, double inv_r,
+                               float4 *__restrict__ c32, D4 *__restrict__ c64)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = sel[j];
+        const double cx = xb[3 * n] * inv_r, cy = xb[3 * n + 1] * inv_r, cz = xb[3 * n + 2] * inv_r;
+        const double wx = w[3 * j], wy = w[3 * j + 1], wz = w[3 * j + 2];
+        if (c32) {
+            c32[2 * j] = make_float4((float)cx, (float)cy, (float)cz, 0.0f);
+            c32[2 * j + 1] = make_float4((float)wx, (float)wy, (float)wz, 0.0f);
+        }
+        if (c64) {
+            c64[2 * j] = mk4(cx, cy, cz, 0.0);
+            c64[2 * j + 1] = mk4(wx, wy, wz, 0.0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 pair sum.
+// ---------------------------------------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(kVolThreads)
+k_volume_f32(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ cw, int nc,
+             double *__restrict__ out)
+{
+    extern __shared__ float4 s_cw[];
+    const int tid = threadIdx.x;
+    const int64_t per_block = (int64_t)kVolThreads * Q;
+    const bool one_tile = nc <= kTileF32;
+    if (one_tile) {
+        for (int j = tid; j < 2 * nc; j += kVolThreads)
+            s_cw[j] = cw[j];
+        __syncthreads();
+    }
+    for (int64_t base = blockIdx.x * per_block; base < nv; base += (int64_t)gridDim.x * per_block) {
+        float qx[Q], qy[Q], qz[Q], ax[Q], ay[Q], az[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            int64_t v = base + (int64_t)i * kVolThreads + tid;
+            v = v < nv ? v : nv - 1;
+            const float4 p = xq[v];
+            qx[i] = p.x; qy[i] = p.y; qz[i] = p.z;
+            ax[i] = 0.0f; ay[i] = 0.0f; az[i] = 0.0f;
+        }
+        for (int t0 = 0; t0 < nc; t0 += kTileF32) {
+            const int nt = min(kTileF32, nc - t0);
+            if (!one_tile) {
+                __syncthreads();
+                for (int j = tid; j < 2 * nt; j += kVolThreads)
+                    s_cw[j] = cw[2 * t0 + j];
+                __syncthreads();
+            }
+#pragma unroll 2
+            for (int j = 0; j < nt; ++j) {
+                const float4 c = s_cw[2 * j];
+                const float4 w = s_cw[2 * j + 1];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const float dx = qx[i] - c.x, dy = qy[i] - c.y, dz = qz[i] - c.z;
+                    const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    const float ph = phi_f32_s(s);
+                    ax[i] = fmaf(w.x, ph, ax[i]);
+                    ay[i] = fmaf(w.y, ph, ay[i]);
+                    az[i] = fmaf(w.z, ph, az[i]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int64_t v = base + (int64_t)i * kVolThreads + tid;
+            if (v < nv) {
+                out[3 * v] = (double)ax[i];
+                out[3 * v + 1] = (double)ay[i];
+                out[3 * v + 2] = (double)az[i];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 pair sum (one point per thread).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVolThreads)
+k_volume_f64(const double *__restrict__ xv, int64_t nv, double inv_r,
+             const D4 *__restrict__ cw, int nc, double *__restrict__ out)
+{
+    extern __shared__ D4 s_cw64[];
+    const int tid = threadIdx.x;
+    for (int64_t base = blockIdx.x * (int64_t)kVolThreads; base < nv;
+         base += (int64_t)gridDim.x * kVolThreads) {
+        int64_t v = base + tid;
+        const int64_t vc = v < nv ? v : nv - 1;
+        const double qx = xv[3 * vc] * inv_r, qy = xv[3 * vc + 1] * inv_r, qz = xv[3 * vc + 2] * inv_r;
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int t0 = 0; t0 < nc; t0 += kTileF64) {
+            const int nt = min(kTileF64, nc - t0);
+            __syncthreads();
+            for (int j = tid; j < 2 * nt; j += kVolThreads)
+                s_cw64[j] = cw[2 * t0 + j];
+            __syncthreads();
+            for (int j = 0; j < nt; ++j) {
+                const D4 c = s_cw64[2 * j];
+                const D4 w = s_cw64[2 * j + 1];
+                const double dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
+                const double s = fma(dz, dz, fma(dy, dy, dx * dx));
+                const double ph = phi_f64_s(s);
+                ax = fma(w.x, ph, ax);
+                ay = fma(w.y, ph, ay);
+                az = fma(w.z, ph, az);
+            }
+        }
+        if (v < nv) {
+            out[3 * v] = ax;
+            out[3 * v + 1] = ay;
+            out[3 * v + 2] = az;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout.
+// ---------------------------------------------------------------------------
+struct VolumeWs {
+    size_t off_xq32, off_c32, off_c64, total;
+};
+
+static VolumeWs volume_ws_layout(int64_t nv, int64_t nc, int prec)
+{
+    VolumeWs L{};
+    size_t o = 0;
+    L.off_xq32 = o;
+    if (prec == RBF_PREC_F32)
+        o = align_up(o + sizeof(float4) * (size_t)nv, 256);
+    L.off_c32 = o;
+    if (prec == RBF_PREC_F32)
+        o = align_up(o + sizeof(float4) * 2 * (size_t)nc, 256);
+    L.off_c64 = o;
+    if (prec == RBF_PREC_F64)
+        o = align_up(o + sizeof(D4) * 2 * (size_t)nc, 256);
+    L.total = std::max<size_t>(o, 256);
+    return L;
+}
+
+}  // namespace rbf
+
+using namespace rbf;
+
+extern "C" size_t rbf_volume_workspace_bytes(int64_t nv, int64_t nc, const rbf_params *p)
+{
+    if (!p || nv < 0 || nc < 0)
+        return 0;
+    return volume_ws_layout(nv, nc, p->eval_prec).total;
+}
+
+extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const double *d_xb,
+                                        const int32_t *d_sel_idx, int64_t nc, const double *d_w,
+                                        const rbf_params *p, double *d_dv, void *d_ws,
+                                        size_t ws_bytes, void *stream)
+{
+    if (!p || nv < 0 || nc < 0 || !(p->radius > 0.0) ||
+        (p->eval_prec != RBF_PREC_F32 && p->eval_prec != RBF_PREC_F64))
+        return RBF_E_ARG;
+    if (nv == 0)
+        return RBF_OK;
+    if (!d_xv || !d_dv)
+        return RBF_E_ARG;
+    if (nc > 0 && (!d_xb || !d_sel_idx || !d_w))
+        return RBF_E_ARG;
+    if (nc > (int64_t)1 << 30 || nv > (int64_t)1 << 40)
+        return RBF_E_ARG;
+    const VolumeWs L = volume_ws_layout(nv, nc, p->eval_prec);
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
+        return RBF_E_WORKSPACE;
+    DeviceInfo dev;
+    if (!device_info(&dev))
+        return RBF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)d_ws;
+    const double inv_r = 1.0 / p->radius;
+    if (nc == 0) {
+        if (cudaMemsetAsync(d_dv, 0, sizeof(double) * 3 * (size_t)nv, st) != cudaSuccess)
+            return RBF_E_CUDA;
+        return RBF_OK;
+    }
+    if (p->eval_prec == RBF_PREC_F32) {
+        float4 *xq = (float4 *)(ws + L.off_xq32);
+        float4 *c32 = (float4 *)(ws + L.off_c32);
+        const int pb = (int)std::min<int64_t>((nv + 255) / 256, (int64_t)dev.sms * 8);
+        k_pack_points_f32<<<pb, 256, 0, st>>>(d_xv, nv, inv_r, xq);
+        const int cb = (int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4);
+        k_pack_centres<<<cb, 256, 0, st>>>(d_xb, d_sel_idx, d_w, nc, inv_r, c32, nullptr);
+        const size_t smem = sizeof(float4) * 2 * (size_t)std::min<int64_t>(nc, kTileF32);
+        static int occ = -1;
+        if (occ < 0) {
+            cudaFuncSetAttribute(k_volume_f32<kVolQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float4) * 2 * kTileF32));
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_volume_f32<kVolQ>, kVolThreads,
+                                                              sizeof(float4) * 2 * kTileF32) !=
+                    cudaSuccess ||
+                occ < 1)
+                occ = 1;
+        }
+        const int64_t want = (nv + (int64_t)kVolThreads * kVolQ - 1) / ((int64_t)kVolThreads * kVolQ);
+        const int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms * occ);
+        k_volume_f32<kVolQ><<<grid, kVolThreads, smem, st>>>(xq, nv, c32, (int)nc, d_dv);
+    } else {
+        D4 *c64 = (D4 *)(ws + L.off_c64);
+        const int cb = (int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4);
+        k_pack_centres<<<cb, 256, 0, st>>>(d_xb, d_sel_idx, d_w, nc, inv_r, nullptr, c64);
+        const size_t smem = sizeof(D4) * 2 * (size_t)std::min<int64_t>(nc, kTileF64);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_volume_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(D4) * 2 * kTileF64));
+            attr = true;
+        }
+        const int64_t want = (nv + kVolThreads - 1) / kVolThreads;
+        const int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms * 8);
+        k_volume_f64<<<grid, kVolThreads, smem, st>>>(d_xv, nv, inv_r, c64, (int)nc, d_dv);
+    }
+    if (cudaGetLastError() != cudaSuccess)
+        return RBF_E_CUDA;
+    return RBF_OK;
+}

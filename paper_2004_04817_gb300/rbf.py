@@ -1,0 +1,234 @@
+"""ctypes binding of librbfgcb.so: argument marshalling only.
+
+Every function takes and returns torch tensors on the current CUDA device and
+forwards raw device pointers, sizes and the current stream to the C ABI of
+``include/rbfgcb.h``.  Workspaces are torch allocations sized by the
+library's own *_workspace_bytes queries.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+PREC_F32 = 32
+PREC_F64 = 64
+HIST_COLS = 6
+STATUS = {0: "RBF_OK", 1: "RBF_E_ARG", 2: "RBF_E_NOT_SPD", 3: "RBF_E_NC_MAX",
+          4: "RBF_E_NONFINITE", 5: "RBF_E_WORKSPACE", 6: "RBF_E_TIMEOUT", 7: "RBF_E_CUDA"}
+E_NC_MAX = 3
+
+
+class RBFError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = int(status)
+        super().__init__(f"{where}: {status_string(status)}")
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("radius", C.c_double),
+        ("tol", C.c_double),
+        ("tol_mode", C.c_int32),
+        ("eval_prec", C.c_int32),
+        ("m", C.c_int64),
+        ("seed", C.c_uint64),
+        ("nc_max", C.c_int64),
+        ("refine_steps", C.c_int32),
+        ("flags", C.c_int32),
+    ]
+
+
+class GreedyStats(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int64),
+        ("nc", C.c_int64),
+        ("full_checks", C.c_int64),
+        ("pairs_f32", C.c_int64),
+        ("pairs_f64", C.c_int64),
+        ("rescored", C.c_int64),
+        ("estar", C.c_double),
+        ("final_max", C.c_double),
+        ("final_rms", C.c_double),
+        ("min_pivot", C.c_double),
+    ]
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def lib():
+    """Load librbfgcb.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or os.environ.get("RBF_REBUILD"):
+            path = _build.build()
+        L = C.CDLL(path)
+        P = C.POINTER(Params)
+        L.rbf_greedy_workspace_bytes.restype = C.c_size_t
+        L.rbf_greedy_workspace_bytes.argtypes = [C.c_int64, P]
+        L.rbf_greedy_select.restype = C.c_int
+        L.rbf_greedy_select.argtypes = [_vp, _vp, C.c_int64, P, _vp, _vp, _vp, C.c_int64,
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                        C.POINTER(GreedyStats), _vp, C.c_size_t, _vp]
+        L.rbf_solve_workspace_bytes.restype = C.c_size_t
+        L.rbf_solve_workspace_bytes.argtypes = [C.c_int64]
+        L.rbf_solve_weights.restype = C.c_int
+        L.rbf_solve_weights.argtypes = [_vp, _vp, C.c_int64, _vp, C.c_int64, P, _vp,
+                                        C.POINTER(C.c_double), _vp, C.c_size_t, _vp]
+        L.rbf_volume_workspace_bytes.restype = C.c_size_t
+        L.rbf_volume_workspace_bytes.argtypes = [C.c_int64, C.c_int64, P]
+        L.rbf_deform_volume.restype = C.c_int
+        L.rbf_deform_volume.argtypes = [_vp, C.c_int64, _vp, _vp, C.c_int64, _vp, P, _vp, _vp,
+                                        C.c_size_t, _vp]
+        L.rbf_measure_fma_peak.restype = C.c_int
+        L.rbf_measure_fma_peak.argtypes = [C.c_int, C.POINTER(C.c_double), _vp]
+        L.rbf_last_device_status.restype = C.c_int
+        L.rbf_status_string.restype = C.c_char_p
+        L.rbf_status_string.argtypes = [C.c_int]
+        L.rbf_version.restype = C.c_char_p
+        L.rbf_group_of.restype = C.c_int
+        L.rbf_group_of.argtypes = [C.c_int64, C.c_int64, C.c_uint64, C.POINTER(C.c_int32)]
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().rbf_status_string(int(s)).decode()
+
+
+def _check(st, where, allow=()):
+    if st != 0 and st not in allow:
+        raise RBFError(st, where)
+    return st
+
+
+def _dev(t, dtype, name, shape2=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape2 is not None and (t.dim() != 2 or t.shape[1] != shape2):
+        raise ValueError(f"{name} must have shape (n, {shape2})")
+    return t
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def make_params(radius, tol=0.0, tol_mode=1, eval_prec=PREC_F64, m=1, seed=1, nc_max=0,
+                refine_steps=2):
+    return Params(float(radius), float(tol), int(tol_mode), int(eval_prec), int(m), int(seed),
+                  int(nc_max), int(refine_steps), 0)
+
+
+def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
+                  eval_prec=PREC_F64, hist_cap=0, stream=None, workspace=None):
+    """GCB greedy (m = 1: plain greedy).  Returns a dict with ``idx`` (int32
+    CUDA tensor, selection order), ``iter`` (int64), ``nc``, ``hist`` (CUDA
+    (n, 6) or None), ``stats`` (dict) and ``status`` (0 or RBF_E_NC_MAX)."""
+    L = lib()
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(db, torch.float64, "db", 3)
+    nb = xb.shape[0]
+    if db.shape[0] != nb:
+        raise ValueError("xb and db must have the same number of rows")
+    nc_max = int(nc_max or min(nb, 4096))
+    p = make_params(radius, tol, tol_mode, eval_prec, m, seed, nc_max)
+    need = L.rbf_greedy_workspace_bytes(nb, C.byref(p))
+    if need == 0:
+        raise RBFError(1, "rbf_greedy_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xb.device)
+    idx = torch.empty(nc_max, dtype=torch.int32, device=xb.device)
+    it = torch.empty(nc_max, dtype=torch.int64, device=xb.device)
+    hist = torch.empty((hist_cap, HIST_COLS), dtype=torch.float64, device=xb.device) \
+        if hist_cap else None
+    nc = C.c_int64(0)
+    nh = C.c_int64(0)
+    stats = GreedyStats()
+    st = L.rbf_greedy_select(_ptr(xb), _ptr(db), nb, C.byref(p), _ptr(idx), _ptr(it),
+                             _ptr(hist), int(hist_cap), C.byref(nc), C.byref(nh),
+                             C.byref(stats), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "rbf_greedy_select", allow=(E_NC_MAX,))
+    n = nc.value
+    return dict(idx=idx[:n], iter=it[:n], nc=n, status=st,
+                hist=hist[:min(nh.value, hist_cap)] if hist is not None else None,
+                n_hist=nh.value,
+                stats={f: getattr(stats, f) for f, _ in GreedyStats._fields_})
+
+
+def solve_weights(xb, db, sel_idx, *, radius, refine_steps=2, stream=None, workspace=None):
+    """FP64 weights (nc, 3) of the support set; returns (w, max_residual)."""
+    L = lib()
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(db, torch.float64, "db", 3)
+    _dev(sel_idx, torch.int32, "sel_idx")
+    nc = sel_idx.numel()
+    p = make_params(radius, refine_steps=refine_steps)
+    need = L.rbf_solve_workspace_bytes(nc)
+    if need == 0:
+        raise RBFError(1, "rbf_solve_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xb.device)
+    w = torch.empty((nc, 3), dtype=torch.float64, device=xb.device)
+    res = C.c_double(0.0)
+    st = L.rbf_solve_weights(_ptr(xb), _ptr(db), xb.shape[0], _ptr(sel_idx), nc, C.byref(p),
+                             _ptr(w), C.byref(res), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "rbf_solve_weights")
+    return w, res.value
+
+
+def deform_volume(xv, xb, sel_idx, w, *, radius, eval_prec=PREC_F32, stream=None,
+                  workspace=None, out=None):
+    """Volume displacements (nv, 3) FP64 by Eq. 6 in FP32 or FP64 pairs."""
+    L = lib()
+    _dev(xv, torch.float64, "xv", 3)
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(sel_idx, torch.int32, "sel_idx")
+    _dev(w, torch.float64, "w", 3)
+    nv, nc = xv.shape[0], sel_idx.numel()
+    p = make_params(radius, eval_prec=eval_prec)
+    need = L.rbf_volume_workspace_bytes(nv, nc, C.byref(p))
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xv.device)
+    dv = out if out is not None else torch.empty((nv, 3), dtype=torch.float64, device=xv.device)
+    _dev(dv, torch.float64, "out", 3)
+    st = L.rbf_deform_volume(_ptr(xv), nv, _ptr(xb), _ptr(sel_idx), nc, _ptr(w), C.byref(p),
+                             _ptr(dv), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "rbf_deform_volume")
+    return dv
+
+
+def group_of(nb, m, seed):
+    """The partition the greedy uses: group index of every node (host)."""
+    import numpy as np
+    g = np.empty(int(nb), dtype=np.int32)
+    _check(lib().rbf_group_of(int(nb), int(m), int(seed),
+                              g.ctypes.data_as(C.POINTER(C.c_int32))), "rbf_group_of")
+    return g
+
+
+def measure_fma_peak(prec=32, stream=None):
+    """Measured vector FMA peak of this GPU in FLOP/s (an FMA counts 2)."""
+    f = C.c_double(0.0)
+    _check(lib().rbf_measure_fma_peak(int(prec), C.byref(f), _stream(stream)),
+           "rbf_measure_fma_peak")
+    return f.value

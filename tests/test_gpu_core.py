@@ -1,0 +1,199 @@
+"""GPU parity of the CUDA path against the FP64 oracle (through the C ABI).
+
+Tolerances (floating point) follow the hot-path contract:
+  - support-node sequences: identical; a divergence is accepted only where the
+    oracle's own FP64 errors of the two candidates agree to 1e-6 relative
+    (oracle follow mode);
+  - weights and volume displacements: within 1e-5 of the largest boundary
+    displacement (FP64 paths; the FP32 volume path is held to its derived
+    rounding bound instead, see test_volume_f32_within_rounding_bound).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2004_04817_gb300 as P
+from paper_2004_04817_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+TIE = 1e-6
+
+
+def cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def run_greedy(case, m, prec, tol_rel, seed=1, nc_max=None, hist_cap=0):
+    xb, db = case["xb"], case["db"]
+    estar = oracle.tolerance(db, tol_rel)
+    r = P.greedy_select(cuda(xb), cuda(db), radius=case["radius"], tol=estar, tol_mode=0,
+                        m=m, seed=seed, nc_max=nc_max, eval_prec=prec, hist_cap=hist_cap)
+    torch.cuda.synchronize()
+    return r, estar
+
+
+# ------------------------------------------------------------------ peak ----
+def test_fma_peak_positive():
+    f32 = P.measure_fma_peak(32)
+    f64 = P.measure_fma_peak(64)
+    assert f32 > 1e12 and f64 > 1e10
+
+
+# --------------------------------------------------------------- greedy -----
+@pytest.mark.parametrize("m", [1, 2, 5, 9])
+def test_greedy_f64_matches_oracle_tiny(m):
+    c = synth.tiny_wing(n_span=6, n_chord=30, radius=1.0)
+    r, estar = run_greedy(c, m, P.PREC_F64, 2e-3, hist_cap=1000)
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1)
+    assert r["status"] == 0 and o["status"] == 0
+    assert host(r["idx"]).tolist() == o["idx"].tolist()
+    assert host(r["iter"]).tolist() == o["iter"].tolist()
+    assert r["stats"]["iterations"] == o["stats"]["iterations"]
+    assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-12
+    h = host(r["hist"])
+    assert h.shape == o["hist"].shape
+    assert np.array_equal(h[:, [0, 1, 5]], o["hist"][:, [0, 1, 5]])
+
+
+@pytest.mark.parametrize("m", [1, 7, 40])
+def test_greedy_f64_matches_oracle_wing_2000(m):
+    c = synth.wing_small(n_vol=0)
+    r, estar = run_greedy(c, m, P.PREC_F64, c["tol_rel"])
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1)
+    f = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1,
+                      follow=(host(r["idx"]), host(r["iter"])), tie_rel=TIE)
+    assert f["stats"]["n_fail"] == 0
+    if f["stats"]["n_div"] == 0:
+        assert host(r["idx"]).tolist() == o["idx"].tolist()
+    assert r["stats"]["final_max"] <= estar
+
+
+@pytest.mark.parametrize("m", [1, 5])
+def test_greedy_f32_screen_is_certified(m):
+    """FP32 screening + FP64 re-score: every decision checked by the oracle."""
+    c = synth.wing_small(n_vol=0)
+    r, estar = run_greedy(c, m, P.PREC_F32, c["tol_rel"])
+    f = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1,
+                      follow=(host(r["idx"]), host(r["iter"])), tie_rel=TIE)
+    assert f["stats"]["n_fail"] == 0, f["stats"]
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1)
+    if f["stats"]["n_div"] == 0:
+        assert host(r["idx"]).tolist() == o["idx"].tolist()
+    assert r["stats"]["final_max"] <= estar
+
+
+def test_greedy_nc_max_returns_partial_prefix():
+    c = synth.tiny_wing(n_span=6, n_chord=30, radius=1.0)
+    r, estar = run_greedy(c, 1, P.PREC_F64, 1e-5, nc_max=10)
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1, ncmax=10)
+    assert r["status"] == 3 and o["status"] == oracle.E_NC_MAX
+    assert host(r["idx"]).tolist() == o["idx"].tolist()
+
+
+def test_greedy_coincident_nodes_not_spd():
+    rng = np.random.default_rng(1)
+    xb = rng.random((50, 3))
+    xb[49] = xb[7]                       # a coincident pair with different displacements
+    db = rng.standard_normal((50, 3)) * 0.1
+    with pytest.raises(P.RBFError) as e:
+        P.greedy_select(cuda(xb), cuda(db), radius=1.5, tol=1e-9, tol_mode=0, m=1,
+                        eval_prec=P.PREC_F64)
+    assert e.value.status == 2
+
+
+def test_greedy_nonfinite_input():
+    c = synth.tiny_wing(n_span=4, n_chord=20)
+    db = c["db"].copy()
+    db[5, 1] = np.nan
+    with pytest.raises(P.RBFError) as e:
+        P.greedy_select(cuda(c["xb"]), cuda(db), radius=2.0, tol=1e-3, m=1)
+    assert e.value.status == 4
+
+
+# ---------------------------------------------------------------- solve -----
+def test_solve_weights_matches_oracle_and_reproduces():
+    c = synth.wing_small(n_vol=0)
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1)
+    S = o["idx"]
+    Wo, st, _ = oracle.solve_weights(c["xb"], c["db"], S, c["radius"])
+    w, res = P.solve_weights(cuda(c["xb"]), cuda(c["db"]), cuda(S, torch.int32),
+                             radius=c["radius"], refine_steps=2)
+    dmax = np.abs(c["db"]).max()
+    assert np.abs(host(w) - Wo).max() <= 1e-5 * dmax
+    assert res <= 1e-10 * dmax
+
+
+def test_solve_duplicate_support_not_spd():
+    c = synth.tiny_wing(n_span=4, n_chord=20)
+    S = np.array([0, 5, 9, 5], dtype=np.int32)
+    with pytest.raises(P.RBFError) as e:
+        P.solve_weights(cuda(c["xb"]), cuda(c["db"]), cuda(S, torch.int32), radius=2.0)
+    assert e.value.status == 2
+
+
+# --------------------------------------------------------------- volume -----
+def _volume_case(n_vol=20_000):
+    c = synth.wing_small(n_vol=n_vol)
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1)
+    W, st, _ = oracle.solve_weights(c["xb"], c["db"], o["idx"], c["radius"])
+    return c, o["idx"], W
+
+
+@pytest.mark.parametrize("nv", [1, 255, 1023, 20_000])
+def test_volume_f64_matches_oracle(nv):
+    c, S, W = _volume_case()
+    xv = c["xv"][:nv]
+    ref = oracle.rbf_sum(xv, c["xb"], S, W, c["radius"])
+    dv = P.deform_volume(cuda(xv), cuda(c["xb"]), cuda(S, torch.int32), cuda(W),
+                         radius=c["radius"], eval_prec=P.PREC_F64)
+    dmax = np.abs(c["db"]).max()
+    assert np.abs(host(dv) - ref).max() <= 1e-5 * dmax
+    assert np.abs(host(dv) - ref).max() <= 1e-12
+
+
+def test_volume_f32_within_rounding_bound():
+    """FP32 pairs: |dv32 - dv64| <= u32 (64 sum_j |w_j| phi_vj + 16 X sum_j |w_j|),
+    X = max scaled coordinate (rounding of phi and sums, and of coordinates)."""
+    c, S, W = _volume_case()
+    xv = c["xv"]
+    ref = oracle.rbf_sum(xv, c["xb"], S, W, c["radius"])
+    dv = host(P.deform_volume(cuda(xv), cuda(c["xb"]), cuda(S, torch.int32), cuda(W),
+                              radius=c["radius"], eval_prec=P.PREC_F32))
+    R = c["radius"]
+    D = np.linalg.norm(xv[:, None, :] - c["xb"][S][None], axis=-1) / R
+    Phi = oracle.phi(D)
+    Sabs = Phi @ np.abs(W).sum(1)
+    X = max(np.abs(xv).max(), np.abs(c["xb"]).max()) / R
+    bound = U32 * (64 * Sabs + 16 * X * np.abs(W).sum())
+    err = np.abs(dv - ref).max(axis=1)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def test_volume_compact_support_and_edges():
+    rng = np.random.default_rng(4)
+    xb = rng.random((64, 3))
+    S = np.arange(0, 64, 3).astype(np.int32)
+    W = rng.standard_normal((len(S), 3))
+    xv = np.concatenate([rng.random((300, 3)), np.full((3, 3), 9.0)])
+    R = 0.35
+    ref = oracle.rbf_sum(xv, xb, S, W, R)
+    for prec, tol in ((P.PREC_F64, 1e-13), (P.PREC_F32, 1e-5)):
+        dv = host(P.deform_volume(cuda(xv), cuda(xb), cuda(S, torch.int32), cuda(W), radius=R,
+                                  eval_prec=prec))
+        assert np.abs(dv - ref).max() <= tol
+        assert np.all(dv[-3:] == 0.0)
+    # empty inputs
+    empty = P.deform_volume(cuda(np.zeros((0, 3))), cuda(xb), cuda(S, torch.int32), cuda(W),
+                            radius=R)
+    assert empty.shape == (0, 3)
+    zero_c = host(P.deform_volume(cuda(xv), cuda(xb), cuda(np.zeros(0), torch.int32),
+                                  cuda(np.zeros((0, 3))), radius=R))
+    assert np.all(zero_c == 0.0)

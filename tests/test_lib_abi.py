@@ -1,0 +1,80 @@
+"""CPU checks of the C-ABI library: it loads without a GPU, exports every
+entry point include/rbfgcb.h declares, validates arguments on the host, and
+its host-side partition matches the oracle's."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2004_04817_gb300 as P
+from paper_2004_04817_gb300 import rbf
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "rbfgcb.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rbf_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("rbf_greedy_select", "rbf_solve_weights", "rbf_deform_volume"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = P.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_status_strings_and_version():
+    for code, name in rbf.STATUS.items():
+        assert P.status_string(code).startswith(name)
+    assert b"sm_103a" in P.lib().rbf_version()
+
+
+def test_workspace_queries_validate_arguments():
+    L = P.lib()
+    p = rbf.make_params(2.0, 1e-3, 1, 64, m=1, nc_max=100)
+    assert L.rbf_greedy_workspace_bytes(2000, C.byref(p)) > 0
+    for bad in (rbf.make_params(0.0, 1e-3, 1, 64, m=1, nc_max=100),       # radius
+                rbf.make_params(2.0, 1e-3, 1, 64, m=0, nc_max=100),        # m
+                rbf.make_params(2.0, 1e-3, 1, 64, m=3000, nc_max=100),     # m > nb
+                rbf.make_params(2.0, 1e-3, 1, 16, m=1, nc_max=100),        # precision
+                rbf.make_params(2.0, -1.0, 1, 64, m=1, nc_max=100),        # tolerance
+                rbf.make_params(2.0, 1e-3, 1, 64, m=1, nc_max=2)):         # capacity
+        assert L.rbf_greedy_workspace_bytes(2000, C.byref(bad)) == 0
+    assert L.rbf_solve_workspace_bytes(0) == 0
+    assert L.rbf_solve_workspace_bytes(500) > 8 * 500 * 500
+
+
+def test_calls_reject_bad_arguments_before_touching_a_device():
+    L = P.lib()
+    p = rbf.make_params(2.0, 1e-3, 1, 64, m=1, nc_max=100)
+    nc = C.c_int64(0)
+    # null inputs
+    st = L.rbf_greedy_select(None, None, 2000, C.byref(p), None, None, None, 0, C.byref(nc),
+                             None, None, None, 0, None)
+    assert st == 1
+    bad = rbf.make_params(-1.0, eval_prec=32)
+    st = L.rbf_deform_volume(C.c_void_p(16), 10, C.c_void_p(16), C.c_void_p(16), 5,
+                             C.c_void_p(16), C.byref(bad), C.c_void_p(16), None, 0, None)
+    assert st == 1
+
+
+@pytest.mark.parametrize("nb,m,seed", [(1, 1, 0), (10, 3, 7), (2000, 13, 1), (50000, 161, 1),
+                                       (999, 999, 12345)])
+def test_partition_matches_oracle_bit_exact(nb, m, seed):
+    assert np.array_equal(P.group_of(nb, m, seed), oracle.groups(nb, m, seed))
+
+
+def test_partition_rejects_bad_sizes():
+    with pytest.raises(P.RBFError):
+        P.group_of(10, 11, 0)

@@ -161,10 +161,13 @@ def rbf_sum(xq, xb, S, W, R, threads=None):
 
 
 def greedy(xb, db, R, Estar, m=1, seed=1, ncmax=None, follow=None, tie_rel=1e-6,
-           threads=None, hist_cap=None):
+           threads=None, history=True, hist_cap=None):
     """Algorithm 1.  ``follow`` = (idx, iter) of another run to check.
 
-    Returns dict(status, idx, iter, nc, hist, stats).
+    ``history`` records one row per iteration, with the all-node maximum and
+    RMS error after every m-th iteration (extra all-node evaluations that do
+    not change the selection).  Returns dict(status, idx, iter, nc, hist,
+    stats).
     """
     L = lib()
     xb, px = _d(xb)
@@ -182,19 +185,20 @@ def greedy(xb, db, R, Estar, m=1, seed=1, ncmax=None, follow=None, tie_rel=1e-6,
     out_idx = np.zeros(ncmax, dtype=np.int32)
     out_it = np.zeros(ncmax, dtype=np.int64)
     nc = C.c_int64(0)
-    hist_cap = int(hist_cap or (4 * nb + 16))
-    hist = np.zeros((hist_cap, HIST_COLS))
+    hist_cap = int(hist_cap or (4 * nb + 16)) if history else 0
+    hist = np.zeros((max(hist_cap, 1), HIST_COLS))
     nh = C.c_int64(0)
     stats = GreedyStats()
     st = L.orc_greedy(px, pd, nb, float(R), float(Estar), int(m), int(seed), ncmax,
                       pfi, pft, fn, float(tie_rel),
                       out_idx.ctypes.data_as(C.POINTER(C.c_int32)),
                       out_it.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(nc),
-                      hist.ctypes.data_as(C.POINTER(C.c_double)), hist_cap, C.byref(nh),
+                      hist.ctypes.data_as(C.POINTER(C.c_double)) if history else None,
+                      hist_cap, C.byref(nh),
                       C.byref(stats), threads or default_threads())
     n = nc.value
     return dict(status=st, idx=out_idx[:n].copy(), iter=out_it[:n].copy(), nc=n,
-                hist=hist[:min(nh.value, hist_cap)].copy(),
+                hist=hist[:min(nh.value, hist_cap)].copy() if history else None,
                 stats={f: getattr(stats, f) for f, _ in GreedyStats._fields_})
 
 

@@ -31,10 +31,11 @@
  *     n2 = node farthest from {n0, n1}; lowest index on ties;
  *   - argmax ties: lowest node index; nodes already in S are skipped;
  *   - strict comparison E > E*;
- *   - termination: a full check (all nodes, current weights) with global
- *     maximum <= E*.  It runs when an active group adds nothing and after
- *     every m-th iteration; a failed check continues with the next group,
- *     which leaves the literal algorithm's selection sequence unchanged;
+ *   - termination: m consecutive iterations that add nothing.  They evaluate
+ *     every node once (Sec. 3) with one set of weights, so the global maximum
+ *     is then <= E*; the selection sequence is the literal algorithm's.  An
+ *     all-node check after every m-th iteration is kept only to fill the
+ *     optional error history;
  *   - N_c^max caps |S|.
  *
  * Parity pins (tests/test_oracle_*.py): closed-form phi values, partition
@@ -371,6 +372,8 @@ int orc_greedy(const double *xb, const double *db, int64_t nb, double R, double 
     }
     int status = ORC_OK;
     int64_t nh = 0;
+    int64_t idle = 0;          /* consecutive iterations without an append */
+    double run_max = 0.0, run_sq = 0.0;
     int64_t k = 3;
     for (;; ++k) {
         /* Solve Phi_SS W = dX_S from scratch (dense Cholesky). */
@@ -429,8 +432,22 @@ int orc_greedy(const double *xb, const double *db, int64_t nb, double R, double 
             inS[add] = 1;
             ++nc;
         }
-        /* Full check: all nodes, current S, fresh weights. */
-        int full = (add < 0) || ((k - 2) % m == 0);
+        /* Termination (Sec. 3: after m iterations every boundary node has had
+         * its error computed once): m consecutive iterations that add nothing
+         * evaluated every node with the same weights and found E <= E*. */
+        if (add >= 0) {
+            idle = 0;
+            run_max = 0.0;
+            run_sq = 0.0;
+        } else {
+            ++idle;
+            for (int64_t t = 0; t < gn; ++t) {
+                if (E[t] > run_max) run_max = E[t];
+                run_sq += E[t] * E[t];
+            }
+        }
+        /* Optional history: all-node errors after every m-th iteration. */
+        int full = hist != NULL && ((k - 2) % m == 0);
         double gmax = -1.0, grms = -1.0;
         if (full) {
             if (add >= 0) {
@@ -459,18 +476,9 @@ int orc_greedy(const double *xb, const double *db, int64_t nb, double R, double 
             h[5] = (double)add;
         }
         ++nh;
-        if (full && gmax <= Estar) {
-            stats->final_max = gmax;
-            stats->final_rms = grms;
-            break;
-        }
-        if (follow_n >= 0 && fpos >= follow_n && full && add < 0) {
-            /* the follower stopped adding although the oracle's full check
-             * fails: accepted only inside the tie band above E* */
-            if (gmax > Estar * (1.0 + tie_rel)) stats->n_fail++;
-            else stats->n_div++;
-            stats->final_max = gmax;
-            stats->final_rms = grms;
+        if (idle >= m) {
+            stats->final_max = run_max;
+            stats->final_rms = sqrt(run_sq / (double)nb);
             break;
         }
     }

@@ -1,0 +1,408 @@
+"""Benchmark of the RBF mesh-deformation hot path on one GB300 (or N replicas).
+
+One step = the whole hot path on the GCB wing workload: greedy support
+selection to tolerance (GCB, m = 1.5 N_b / N_c), FP64 weights with
+iterative refinement, and the volume displacement sum over N_v points.
+Inputs are resident in HBM when the timed region starts; L2 is flushed
+(256 MiB write) between steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
+host cores on a bounded sample of the same workload.  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("greedy time-to-tol (s) and RBF pairs/s + %FP32 peak, GCB vs plain greedy, "
+          "1×GB300")
+FLOPS_PER_PAIR = 22          # algorithmic FP32 flops of one Wendland pair
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nv", type=int, default=2_000_000)
+    ap.add_argument("--prec", type=int, default=32, choices=[32, 64])
+    return ap.parse_args()
+
+
+def workload(nv):
+    from paper_2004_04817_gb300 import synth
+    t = time.time()
+    c = synth.wing_gcb(n_vol=nv)
+    c["gen_s"] = time.time() - t
+    return c
+
+
+def workload_desc(c, m, nc_plain, prec):
+    return {
+        "workload": "swept tapered wing, GCB greedy + weights + volume sum",
+        "n_b": int(len(c["xb"])), "grid": "100x500", "n_v": int(len(c["xv"])),
+        "volume": "log-clustered toward the surface (d in [1e-5, 1.5])",
+        "radius": c["radius"], "tol_rel": c["tol_rel"], "m": int(m),
+        "m_rule": "round(1.5 N_b / N_c), N_c from the m = 1 run",
+        "nc_plain": int(nc_plain), "group_seed": 1,
+        "eval": "FP32 pairs + FP64-certified argmax" if prec == 32 else "FP64 pairs",
+        "solve": "FP64 recurrence Cholesky + 2 refinement steps",
+        "volume_eval": "FP32",
+        "l2": "flushed between steps (256 MiB write), outside the timed events",
+    }
+
+
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    import paper_2004_04817_gb300 as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    P.lib()
+    c = workload(args.nv)
+    tod = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=t,
+                                                      device=dev)
+    xb, db, xv = tod(c["xb"]), tod(c["db"]), tod(c["xv"])
+    R, tol = c["radius"], c["tol_rel"]
+    nb, nv = xb.shape[0], xv.shape[0]
+
+    # calibration (untimed): N_c of the plain greedy fixes m
+    plain = P.greedy_select(xb, db, radius=R, tol=tol, tol_mode=1, m=1, seed=1,
+                            eval_prec=args.prec)
+    nc_plain = plain["nc"]
+    m = max(1, int(round(1.5 * nb / nc_plain)))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    gws = torch.empty(P.lib().rbf_greedy_workspace_bytes(
+        nb, __import__("ctypes").byref(P.rbf.make_params(R, tol, 1, args.prec, m, 1,
+                                                         min(nb, 4096)))),
+        dtype=torch.uint8, device=dev)
+    dv = torch.empty((nv, 3), dtype=torch.float64, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(record=None):
+        e = [ev() for _ in range(4)]
+        e[0].record()
+        g = P.greedy_select(xb, db, radius=R, tol=tol, tol_mode=1, m=m, seed=1,
+                            eval_prec=args.prec, workspace=gws)
+        e[1].record()
+        w, res = P.solve_weights(xb, db, g["idx"], radius=R, refine_steps=2)
+        e[2].record()
+        P.deform_volume(xv, xb, g["idx"], w, radius=R, eval_prec=32, out=dv)
+        e[3].record()
+        if record is not None:
+            record.append((e, g, res))
+        return g
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    recs = []
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            step(recs)
+            flush.zero_()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    ph = [[r[0][i].elapsed_time(r[0][i + 1]) for i in range(3)] for r in recs]
+    step_ms = [sum(p) for p in ph]
+    ms_per_step = sum(step_ms) / len(step_ms)
+    g_ms = statistics.median(p[0] for p in ph)
+    s_ms = statistics.median(p[1] for p in ph)
+    v_ms = statistics.median(p[2] for p in ph)
+    g_last, res_last = recs[-1][1], recs[-1][2]
+    nc = g_last["nc"]
+
+    # plain greedy on the same GPU at the same tolerance (the comparison arm)
+    pt = []
+    for _ in range(3):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record()
+        pr = P.greedy_select(xb, db, radius=R, tol=tol, tol_mode=1, m=1, seed=1,
+                             eval_prec=args.prec, workspace=None)
+        b.record()
+        torch.cuda.synchronize()
+        pt.append(a.elapsed_time(b))
+    plain_ms = statistics.median(pt)
+
+    # e2e through the public API with host buffers (pinned), copies timed
+    hx = torch.from_numpy(np.ascontiguousarray(c["xb"])).pin_memory()
+    hd = torch.from_numpy(np.ascontiguousarray(c["db"])).pin_memory()
+    hv = torch.from_numpy(np.ascontiguousarray(c["xv"])).pin_memory()
+    hout = torch.empty((nv, 3), dtype=torch.float64).pin_memory()
+    hidx = torch.empty(4096, dtype=torch.int32).pin_memory()
+    dxb, ddb, dxv = torch.empty_like(xb), torch.empty_like(db), torch.empty_like(xv)
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        dxb.copy_(hx, non_blocking=True)
+        ddb.copy_(hd, non_blocking=True)
+        dxv.copy_(hv, non_blocking=True)
+        g = P.greedy_select(dxb, ddb, radius=R, tol=tol, tol_mode=1, m=m, seed=1,
+                            eval_prec=args.prec, workspace=gws)
+        w, _ = P.solve_weights(dxb, ddb, g["idx"], radius=R, refine_steps=2)
+        P.deform_volume(dxv, dxb, g["idx"], w, radius=R, eval_prec=32, out=dv)
+        hout.copy_(dv, non_blocking=True)
+        hidx[:g["nc"]].copy_(g["idx"], non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    h2d = (hx.numel() + hd.numel() + hv.numel()) * 8
+    d2h = hout.numel() * 8 + nc * 4
+
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([ms_per_step, statistics.mean(e2e_ms)], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_per_step, e2e_mean = t.tolist()
+    else:
+        e2e_mean = statistics.mean(e2e_ms)
+
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6     # FLOP/s
+    fp64_peak = props.multi_processor_count * 2 * 2 * sm_max * 1e6
+    st = g_last["stats"]
+    vol_pairs = nv * nc
+    vol_achieved = vol_pairs * FLOPS_PER_PAIR / (v_ms * 1e-3)
+    greedy_flops = FLOPS_PER_PAIR * (st["pairs_f32"] + st["pairs_f64"] +
+                                     st["rescored"] * nc)
+    kernels = [
+        {"name": "k_greedy (persistent GCB loop)", "ms": g_ms, "bound": "alu",
+         "achieved_tflops": greedy_flops / (g_ms * 1e-3) / 1e12,
+         "note": "latency-bound: grid barriers and FP64 appends per iteration"},
+        {"name": "k_solve (weights + refinement)", "ms": s_ms, "bound": "alu"},
+        {"name": "k_volume_f32 (Eq. 6)", "ms": v_ms, "bound": "alu",
+         "pairs_per_s": vol_pairs / (v_ms * 1e-3),
+         "achieved_tflops": vol_achieved / 1e12, "frac": vol_achieved / fp32_peak},
+    ]
+    tot = g_ms + s_ms + v_ms
+    for k in kernels:
+        k["share"] = k["ms"] / tot
+    dom = max(kernels, key=lambda k: k["ms"])
+    if dom is kernels[2]:
+        roof = {"bound": "alu", "kernel": dom["name"], "achieved": vol_achieved / 1e12,
+                "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": vol_achieved / fp32_peak,
+                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        ach = greedy_flops / (g_ms * 1e-3) if dom is kernels[0] else \
+            FLOPS_PER_PAIR * nc * nc * 3 / (s_ms * 1e-3)
+        roof = {"bound": "alu", "kernel": dom["name"], "achieved": ach / 1e12,
+                "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "note": "latency-bound persistent kernel (see kernels)"}
+    out = {
+        "metric": METRIC,
+        "value": ms_per_step / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.prec == 32 else "f64",
+        "data": "synthetic (seeded wing generator; see DESIGN.md)",
+        "config": workload_desc(c, m, nc_plain, args.prec),
+        "greedy": {
+            "gcb_s": g_ms / 1e3, "plain_s": plain_ms / 1e3,
+            "speedup_gcb_vs_plain": plain_ms / g_ms, "m": m,
+            "nc_gcb": nc, "nc_plain": nc_plain,
+            "iterations_gcb": st["iterations"], "iterations_plain": pr["stats"]["iterations"],
+            "pairs_f32": st["pairs_f32"], "pairs_f64": st["pairs_f64"],
+            "rescored": st["rescored"], "estar": st["estar"], "final_max": st["final_max"],
+            "us_per_iteration": g_ms * 1e3 / max(st["iterations"], 1),
+        },
+        "volume": {"pairs_per_s": vol_pairs / (v_ms * 1e-3), "ms": v_ms,
+                   "fp32_peak_frac": vol_achieved / fp32_peak},
+        "weights_max_resid": res_last,
+        "kernels": kernels,
+        "roofline": roof,
+        "peaks": {"fp32_tflops_derived": fp32_peak / 1e12, "fp64_tflops_derived": fp64_peak / 1e12,
+                  "hbm_gbs_measured": pk.get("hbm_gbs")},
+        "e2e": {"value": e2e_mean / 1e3, "unit": "s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(c, m)
+    return out
+
+
+# --------------------------------------------------------------------------
+def oracle_step(c, m, nv_sample):
+    """One pass of the oracle over the workload with a volume sample; returns
+    (seconds for the full workload, seconds spent, details)."""
+    import oracle
+    t0 = time.perf_counter()
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    g = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1, history=False)
+    t1 = time.perf_counter()
+    W, st, _ = oracle.solve_weights(c["xb"], c["db"], g["idx"], c["radius"])
+    t2 = time.perf_counter()
+    oracle.rbf_sum(c["xv"][:nv_sample], c["xb"], g["idx"], W, c["radius"])
+    t3 = time.perf_counter()
+    scale = len(c["xv"]) / nv_sample
+    full = (t1 - t0) + (t2 - t1) + (t3 - t2) * scale
+    return full, t3 - t0, {"nc": g["nc"], "greedy_s": t1 - t0, "solve_s": t2 - t1,
+                           "volume_sample_s": t3 - t2}
+
+
+def cpu_baseline(c, m, nv_sample=100_000):
+    import oracle
+    full, spent, det = oracle_step(c, m, nv_sample)
+    return {"value": full, "unit": "s", "cores": oracle.default_threads(), "kind": "oracle",
+            "sample": f"full GCB greedy (m={m}) and weights; volume sum on {nv_sample} of "
+                      f"{len(c['xv'])} points, scaled by the point count",
+            "spent_s": spent, **det}
+
+
+def run_reference(args):
+    import oracle
+    c = workload(args.nv)
+    nb = len(c["xb"])
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    # m from the oracle's own plain-greedy N_c (untimed calibration)
+    g1 = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1, history=False)
+    m = max(1, int(round(1.5 * nb / g1["nc"])))
+    nv_sample = 50_000
+    for _ in range(args.warmup):
+        oracle_step(c, m, nv_sample)
+    vals, spent = [], 0.0
+    for _ in range(args.steps):
+        v, s, det = oracle_step(c, m, nv_sample)
+        vals.append(v)
+        spent += s
+    v = statistics.mean(vals)
+    base = {"kind": "oracle", "cores": oracle.default_threads(),
+            "sample": f"full GCB greedy (m={m}) and weights; volume sum on {nv_sample} of "
+                      f"{len(c['xv'])} points, scaled by the point count", "value": v,
+            "unit": "s"}
+    return {
+        "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded wing generator; see DESIGN.md)",
+        "config": workload_desc(c, m, g1["nc"], args.prec), "impl": "reference",
+        "cpu_baseline": base,
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0, "spent_s": spent,
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    rank = int(os.environ.get("RANK", 0))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)), flush=True)
+        return 0
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

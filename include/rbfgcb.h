@@ -73,20 +73,28 @@ typedef struct {
     uint64_t seed;        /* seed of the random partition into groups */
     int64_t nc_max;       /* capacity of the support set, 3 <= nc_max <= N_b */
     int32_t refine_steps; /* FP64 iterative-refinement steps in rbf_solve_weights */
-    int32_t flags;        /* reserved, must be 0 */
+    int32_t flags;        /* 0, or RBF_FLAG_HISTORY_FULL */
 } rbf_params;
+
+/* rbf_params.flags: with a history buffer, also evaluate all N_b errors in
+ * FP64 after every m-th iteration to fill its global max / RMS columns
+ * (diagnostic; the selection does not depend on it). */
+#define RBF_FLAG_HISTORY_FULL 1
 
 /* Per-run statistics of rbf_greedy_select (host struct). */
 typedef struct {
     int64_t iterations;      /* greedy iterations run (k - 3 + 1 at exit)      */
     int64_t nc;              /* |S| at exit                                     */
-    int64_t full_checks;     /* evaluations of all N_b errors                   */
+    int64_t full_checks;     /* diagnostic all-node evaluations (history)       */
     int64_t pairs_f32;       /* (node, centre) pairs evaluated in FP32          */
     int64_t pairs_f64;       /* (node, centre) pairs evaluated in FP64          */
     int64_t rescored;        /* nodes re-scored in FP64 after an FP32 screen    */
     double estar;            /* the absolute tolerance E* used                  */
-    double final_max;        /* FP64-certified global max error at exit         */
-    double final_rms;        /* RMS error over all nodes at the last full check */
+    double final_max;        /* certified global max error at exit (-1 if the
+                                run ended on an error status)                  */
+    double final_rms;        /* RMS error over the nodes outside S at exit; in
+                                FP32 mode nodes not re-scored enter with their
+                                FP32 value (-1 on an error status)            */
     double min_pivot;        /* smallest squared Cholesky pivot d^2 seen        */
 } rbf_greedy_stats;
 
@@ -106,9 +114,12 @@ typedef struct {
  * (from 3) evaluates E_q for q in G_(k mod m) minus S with the current
  * weights, takes the largest (lowest index on ties) and appends it to S when
  * E > E* (strict).  The Cholesky factor of Phi_SS grows by one row per
- * appended node (recurrence Cholesky, Sec. 1), in FP64.  All N_b errors are
- * checked after every m-th iteration and whenever a group adds nothing; the
- * run stops when that full check finds max_q E_q <= E*.
+ * appended node (recurrence Cholesky, Sec. 1), in FP64.  The run stops after
+ * m consecutive iterations without an append: those m groups cover every
+ * node (Sec. 3) and share one set of weights, so max_q E_q <= E* is then
+ * certified (in FP32 mode every decision uses FP64 values: the FP32 errors
+ * carry a bound, and each node whose bound reaches the group maximum is
+ * re-scored in FP64).
  *
  * d_xb, d_db : device FP64, nb x 3 (boundary coordinates, displacements).
  * d_sel_idx  : device int32[nc_max]: selected node indices in selection order

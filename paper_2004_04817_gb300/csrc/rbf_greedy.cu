@@ -69,6 +69,7 @@ struct GreedyArgs {
     double inv_r;
     double tol;
     int tol_mode;
+    int flags;
     int ld;                       // leading dimension of Z, Z^T (= nc_max)
     int32_t *sel_idx;
     int64_t *sel_iter;
@@ -311,10 +312,9 @@ __device__ __forceinline__ D4 team_resid_f64(const GreedyArgs &a, int q, int nc,
 }
 
 struct EvalOut {
-    unsigned long long key;   // argmax key over [lo, hi) minus S (0 = none)
-    double gmax;              // full evaluations: certified global max
-    double grms;              // full evaluations: RMS over all nodes
-    bool certified_below;     // full evaluations: every node has E <= E*
+    unsigned long long key;   // argmax key over the range minus S (0 = none)
+    double gmax;              // certified maximum of E over the range minus S
+    double gsq;               // sum of squares of E over the range minus S
 };
 
 // ---------------------------------------------------------------------------
@@ -556,9 +556,13 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
     int ev = 0;                      // evaluation counter (ring index)
     long long pairs32 = 0, pairs64 = 0;
     unsigned long long rescored_local = 0;
-    // Evaluates E at positions [p0, p1); argmax over [lo, hi) minus S; when
-    // `full`, also the certified global max and the RMS over [p0, p1).
-    auto evaluate = [&](int p0, int p1, int lo, int hi, bool full, EvalOut &out) -> bool {
+    // Evaluates E at positions [p0, p1) with the current weights.  With
+    // `argmax`, the largest E among nodes not in S (lowest node index on
+    // ties) comes back as a key; `out.gmax` is the certified maximum of E over
+    // the range (nodes of S excluded: their error is the FP64 interpolation
+    // residual) and `out.gsq` the sum of squares.  `force64` evaluates every
+    // pair in FP64 whatever the precision mode.
+    auto evaluate = [&](int p0, int p1, bool argmax, bool force64, EvalOut &out) -> bool {
         const int r = ev % 3;
         const int nq = p1 - p0;
         const int ts = team_size(nq, G);
@@ -567,18 +571,16 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
         const int rounds = (nq + nteams - 1) / nteams;
         unsigned long long key = 0;
         double lmax = 0.0, lsq = 0.0;
-        if (a.prec == RBF_PREC_F64) {
+        if (a.prec == RBF_PREC_F64 || force64) {
             for (int it = 0; it < rounds; ++it) {
                 const int q = p0 + team + it * nteams;
                 const bool act = q < p1;
                 const double e = team_error_f64(a, act ? q : p0, nc, sub, ts);
-                if (act && sub == 0) {
+                if (act && sub == 0 && !ldcg(a.in_s + q)) {
                     a.e64[q] = e;
-                    if (full) {
-                        lmax = fmax(lmax, e);
-                        lsq = fma(e, e, lsq);
-                    }
-                    if (q >= lo && q < hi && !ldcg(a.in_s + q)) {
+                    lmax = fmax(lmax, e);
+                    lsq = fma(e, e, lsq);
+                    if (argmax) {
                         const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
                         key = k2 > key ? k2 : key;
                     }
@@ -604,7 +606,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
             __syncthreads();
             const float4 *cw = smem ? s_cw : a.cw32;
             const float coord_term = kBetaCoord * xscale * s_wabs * 1.001f;
-            float tloc = 0.0f, umax = 0.0f;
+            float tloc = 0.0f;
             for (int it = 0; it < rounds; ++it) {
                 const int q = p0 + team + it * nteams;
                 const bool act = q < p1;
@@ -629,73 +631,60 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                     const float ex = (float)d.x - fx, ey = (float)d.y - fy, ez = (float)d.z - fz;
                     const float e = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
                     const float dabs = (float)(fabs(d.x) + fabs(d.y) + fabs(d.z));
-                    // error bound of the FP32 error: rounding of phi and of the
-                    // sums (proportional to sum |w| phi), rounding of the
-                    // coordinates (proportional to max|x|/R * sum |w|), and of
-                    // the displacement
+                    // bound of |E32 - E|: rounding of phi and of the sums
+                    // (proportional to sum |w| phi), of the coordinates
+                    // (max|x|/R * sum |w|), of the displacement and of E
                     const float beta =
                         kU32 * (kBetaPhi * (sb + dabs) + coord_term + 4.0f * e) + 1e-30f;
-                    const float up = e + beta;
-                    a.u32[q] = up;
-                    if (full)
-                        umax = fmaxf(umax, up);
-                    if (q >= lo && q < hi && !ldcg(a.in_s + q))
+                    a.u32[q] = e + beta;
+                    a.e64[q] = (double)e;     // replaced by the FP64 value if re-scored
+                    if (!ldcg(a.in_s + q))
                         tloc = fmaxf(tloc, fmaxf(e - beta, 0.0f));
                 }
             }
             tloc = warp_max_f32(tloc);
-            umax = warp_max_f32(umax);
-            if (lane == 0) {
-                if (tloc > 0.0f)
-                    atomicMax(&ctl->tslot[r], __float_as_uint(tloc));
-            }
+            if (lane == 0 && tloc > 0.0f)
+                atomicMax(&ctl->tslot[r], __float_as_uint(tloc));
             if (blockIdx.x == 0 && tid == 0)
                 pairs32 += (long long)nq * nc;
             GSYNC_B();
             const float thr = __uint_as_float(ldcg(&ctl->tslot[r]));
-            // ---- pass 2: FP64 re-score of every node whose bound reaches the
-            // group maximum (argmax) or E* (full check)
+            // ---- pass 2: FP64 re-score of every node whose upper bound
+            // reaches the largest lower bound; the others are certified below
+            // the maximum
             for (int it = 0; it < rounds; ++it) {
                 const int q = p0 + team + it * nteams;
                 const bool act = q < p1;
                 bool need = false;
-                float up = 0.0f;
+                bool ins = true;
                 if (act) {
-                    up = ldcg(a.u32 + q);
-                    const bool in_arg = q >= lo && q < hi && !ldcg(a.in_s + q) && up >= thr;
-                    need = in_arg || (full && (double)up > estar);
-                    if (full && !need && sub == 0) {
-                        // certified: E <= up <= E* (bound enters max and RMS)
-                        lmax = fmax(lmax, (double)up);
-                        lsq = fma((double)up, (double)up, lsq);
+                    ins = ldcg(a.in_s + q) != 0;
+                    need = !ins && ldcg(a.u32 + q) >= thr;
+                    if (!need && !ins && sub == 0) {
+                        const double e32 = ldcg(a.e64 + q);
+                        lsq = fma(e32, e32, lsq);
                     }
                 }
-                // the whole warp takes the same branch per team; teams that do
-                // not need FP64 still join the shuffles
-                const unsigned long long bal = __ballot_sync(0xffffffffu, need);
-                if (bal == 0ull && !need)
+                if (__ballot_sync(0xffffffffu, need) == 0u)
                     continue;
                 const double e = team_error_f64(a, act ? q : p0, nc, sub, ts);
                 if (need && sub == 0) {
                     ++rescored_local;
                     a.e64[q] = e;
-                    if (full) {
-                        lmax = fmax(lmax, e);
-                        lsq = fma(e, e, lsq);
-                    }
-                    if (q >= lo && q < hi && !ldcg(a.in_s + q)) {
+                    lmax = fmax(lmax, e);
+                    lsq = fma(e, e, lsq);
+                    if (argmax) {
                         const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
                         key = k2 > key ? k2 : key;
                     }
                 }
             }
-            (void)umax;
         }
-        // ---- reductions
+        // ---- reductions: key by atomic max, (max, sum of squares) by partials
         block_max_key(red, key);
         if (tid == 0 && key)
             atomicMax(&ctl->slot[r], key);
-        if (full) {
+        {
             double a4[4] = {0.0, lsq, 0.0, 0.0};
             double mx = lmax;
             for (int o = 16; o > 0; o >>= 1)
@@ -706,8 +695,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                 red.v[warp] = mx;
             __syncthreads();
             if (tid == 0) {
-                for (int k = 1; k < kGWarps; ++k)
-                    mx = fmax(mx, red.v[k]);
+                for (int k2 = 1; k2 < kGWarps; ++k2)
+                    mx = fmax(mx, red.v[k2]);
                 double *pp = part(use) + 4 * blockIdx.x;
                 pp[0] = mx;
                 pp[1] = a4[1];
@@ -717,14 +706,13 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
         }
         GSYNC_B();
         out.key = ldcg(&ctl->slot[r]);
-        if (full) {
+        {
             double mx4[4], sm4[4];
             grid_max4(part(use), G, mx4);
             grid_sum4(part(use), G, sm4);
             ++use;
             out.gmax = mx4[0];
-            out.grms = sqrt(sm4[1] / (double)nq);
-            out.certified_below = mx4[0] <= estar;
+            out.gsq = sm4[1];
         }
         if (blockIdx.x == 0 && tid == 0) {
             ctl->slot[(r + 2) % 3] = 0ull;
@@ -735,27 +723,23 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
     };
 
     // ---------------- main loop (k counts iterations from 3) ---------------
+    // Stops after m consecutive iterations without an append: those m groups
+    // cover every node (Sec. 3) and were evaluated with the same weights, so
+    // the largest of their maxima is the certified global maximum.
     long long k = 3, nhist = 0, nfull = 0, idle = 0;
-    bool have_key = false;
-    unsigned long long next_key = 0;
-    double fmax_last = -1.0, frms_last = -1.0;
+    double run_max = 0.0, run_sq = 0.0;
     int status = RBF_OK;
+    const bool hist_full = a.hist != nullptr && (a.flags & RBF_FLAG_HISTORY_FULL) != 0;
     for (;; ++k) {
         const int gi = (int)(k % m);
         const int g0 = goff(gi, nb, m), g1 = goff(gi + 1, nb, m);
-        unsigned long long key;
-        if (have_key) {
-            key = next_key;
-        } else {
-            EvalOut eo;
-            if (!evaluate(g0, g1, g0, g1, false, eo))
-                return;
-            key = eo.key;
-        }
+        EvalOut eo;
+        if (!evaluate(g0, g1, true, false, eo))
+            return;
         int add_node = -1, add_pos = -1;
         double eloc = -1.0;
-        if (key) {
-            add_node = key_node(key);
+        if (eo.key) {
+            add_node = key_node(eo.key);
             add_pos = ldcg(a.pos_of_node + add_node);
             eloc = ldcg(a.e64 + add_pos);
             if (!(eloc > estar))
@@ -771,24 +755,22 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                 status = RBF_E_NOT_SPD;   // or the latched timeout, which wins
                 break;
             }
+            idle = 0;
+            run_max = 0.0;
+            run_sq = 0.0;
+        } else {
+            ++idle;
+            run_max = fmax(run_max, eo.gmax);
+            run_sq += eo.gsq;
         }
-        const bool full = add_node < 0 || ((k - 2) % m) == 0;
         double gmax = -1.0, grms = -1.0;
-        bool stop = false;
-        have_key = false;
-        if (full) {
-            const int ni = (int)((k + 1) % m);
-            EvalOut eo;
-            if (!evaluate(0, nb, goff(ni, nb, m), goff(ni + 1, nb, m), true, eo))
+        if (hist_full && ((k - 2) % m) == 0) {
+            EvalOut d;
+            if (!evaluate(0, nb, false, true, d))
                 return;
             ++nfull;
-            gmax = eo.gmax;
-            grms = eo.grms;
-            fmax_last = gmax;
-            frms_last = grms;
-            stop = eo.certified_below;
-            have_key = true;
-            next_key = eo.key;
+            gmax = d.gmax;
+            grms = sqrt(d.gsq / (double)nb);
         }
         if (blockIdx.x == 0 && tid == 0 && a.hist && nhist < a.hist_cap) {
             double *h = a.hist + RBF_HIST_COLS * nhist;
@@ -800,13 +782,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
             h[5] = (double)add_node;
         }
         ++nhist;
-        if (stop)
-            break;
-        // A full cycle of m groups that adds nothing while the full check
-        // still fails can only come from rounding differences between two
-        // evaluations of the same node (errors within a few ulp of E*): stop.
-        idle = add_node >= 0 ? 0 : idle + 1;
-        if (idle > m)
+        if (idle >= m)
             break;
     }
     if (blockIdx.x == 0 && tid == 0) {
@@ -818,8 +794,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
         ctl->full_checks = nfull;
         ctl->pairs_f32 = pairs32;
         ctl->pairs_f64 = pairs64;
-        ctl->final_max = fmax_last;
-        ctl->final_rms = frms_last;
+        ctl->final_max = idle >= m ? run_max : -1.0;
+        ctl->final_rms = idle >= m ? sqrt(run_sq / (double)nb) : -1.0;
         ctl->min_pivot = min_piv;
         ctl->n_hist = nhist;
     }
@@ -1067,7 +1043,8 @@ static bool greedy_args_ok(int64_t nb, const rbf_params *p)
            p->nc_max <= nb && p->nc_max <= 46340 && p->radius > 0.0 &&
            std::isfinite(p->radius) && p->tol >= 0.0 && std::isfinite(p->tol) &&
            (p->tol_mode == 0 || p->tol_mode == 1) &&
-           (p->eval_prec == RBF_PREC_F32 || p->eval_prec == RBF_PREC_F64) && p->flags == 0;
+           (p->eval_prec == RBF_PREC_F32 || p->eval_prec == RBF_PREC_F64) &&
+           (p->flags & ~RBF_FLAG_HISTORY_FULL) == 0;
 }
 
 }  // namespace rbf
@@ -1165,6 +1142,7 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
     a.inv_r = 1.0 / p->radius;
     a.tol = p->tol;
     a.tol_mode = p->tol_mode;
+    a.flags = p->flags;
     a.ld = (int)p->nc_max;
     a.sel_idx = d_sel_idx;
     a.sel_iter = d_sel_iter;

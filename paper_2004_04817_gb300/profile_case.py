@@ -1,0 +1,47 @@
+"""Small, self-contained launches of one kernel for profiling (ncu) runs.
+
+  python -m paper_2004_04817_gb300.profile_case volume [--nv N] [--reps R]
+  python -m paper_2004_04817_gb300.profile_case greedy [--m M] [--prec 32|64]
+  python -m paper_2004_04817_gb300.profile_case solve
+
+Each case builds the GCB wing workload (N_b = 50,000), runs the calls once
+untimed, then `--reps` more times, and exits 0.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+import torch
+
+import paper_2004_04817_gb300 as P
+from paper_2004_04817_gb300 import synth
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["volume", "greedy", "solve"])
+    ap.add_argument("--nv", type=int, default=1_000_000)
+    ap.add_argument("--m", type=int, default=241)
+    ap.add_argument("--prec", type=int, default=32)
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args()
+    c = synth.wing_gcb(n_vol=a.nv if a.case == "volume" else 0)
+    dev = lambda x, t=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=t,
+                                                      device="cuda")
+    xb, db = dev(c["xb"]), dev(c["db"])
+    for _ in range(1 + a.reps):
+        g = P.greedy_select(xb, db, radius=c["radius"], tol=c["tol_rel"], tol_mode=1,
+                            m=a.m if a.case == "greedy" else 241, seed=1,
+                            eval_prec=a.prec)
+        if a.case == "greedy":
+            continue
+        w, _ = P.solve_weights(xb, db, g["idx"], radius=c["radius"])
+        if a.case == "volume":
+            P.deform_volume(dev(c["xv"]), xb, g["idx"], w, radius=c["radius"], eval_prec=32)
+    torch.cuda.synchronize()
+    print("profile case done", a.case, g["nc"])
+
+
+if __name__ == "__main__":
+    main()

@@ -133,17 +133,23 @@ def _workspace(nbytes, device):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
+FLAG_HISTORY_FULL = 1
+
+
 def make_params(radius, tol=0.0, tol_mode=1, eval_prec=PREC_F64, m=1, seed=1, nc_max=0,
-                refine_steps=2):
+                refine_steps=2, flags=0):
     return Params(float(radius), float(tol), int(tol_mode), int(eval_prec), int(m), int(seed),
-                  int(nc_max), int(refine_steps), 0)
+                  int(nc_max), int(refine_steps), int(flags))
 
 
 def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
-                  eval_prec=PREC_F64, hist_cap=0, stream=None, workspace=None):
+                  eval_prec=PREC_F64, hist_cap=0, history_full=False, stream=None,
+                  workspace=None):
     """GCB greedy (m = 1: plain greedy).  Returns a dict with ``idx`` (int32
     CUDA tensor, selection order), ``iter`` (int64), ``nc``, ``hist`` (CUDA
-    (n, 6) or None), ``stats`` (dict) and ``status`` (0 or RBF_E_NC_MAX)."""
+    (n, 6) or None), ``stats`` (dict) and ``status`` (0 or RBF_E_NC_MAX).
+    ``history_full`` adds FP64 all-node maxima to the history after every
+    m-th iteration (diagnostic)."""
     L = lib()
     _dev(xb, torch.float64, "xb", 3)
     _dev(db, torch.float64, "db", 3)
@@ -151,7 +157,8 @@ def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
     if db.shape[0] != nb:
         raise ValueError("xb and db must have the same number of rows")
     nc_max = int(nc_max or min(nb, 4096))
-    p = make_params(radius, tol, tol_mode, eval_prec, m, seed, nc_max)
+    p = make_params(radius, tol, tol_mode, eval_prec, m, seed, nc_max,
+                    flags=FLAG_HISTORY_FULL if history_full else 0)
     need = L.rbf_greedy_workspace_bytes(nb, C.byref(p))
     if need == 0:
         raise RBFError(1, "rbf_greedy_workspace_bytes")

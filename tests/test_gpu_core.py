@@ -33,7 +33,8 @@ def run_greedy(case, m, prec, tol_rel, seed=1, nc_max=None, hist_cap=0):
     xb, db = case["xb"], case["db"]
     estar = oracle.tolerance(db, tol_rel)
     r = P.greedy_select(cuda(xb), cuda(db), radius=case["radius"], tol=estar, tol_mode=0,
-                        m=m, seed=seed, nc_max=nc_max, eval_prec=prec, hist_cap=hist_cap)
+                        m=m, seed=seed, nc_max=nc_max, eval_prec=prec, hist_cap=hist_cap,
+                        history_full=hist_cap > 0)
     torch.cuda.synchronize()
     return r, estar
 
@@ -56,21 +57,25 @@ def test_greedy_f64_matches_oracle_tiny(m):
     assert host(r["iter"]).tolist() == o["iter"].tolist()
     assert r["stats"]["iterations"] == o["stats"]["iterations"]
     assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-12
+    assert abs(r["stats"]["final_rms"] - o["stats"]["final_rms"]) <= 1e-12
     h = host(r["hist"])
     assert h.shape == o["hist"].shape
     assert np.array_equal(h[:, [0, 1, 5]], o["hist"][:, [0, 1, 5]])
+    assert np.allclose(h[:, [2, 3, 4]], o["hist"][:, [2, 3, 4]], rtol=0, atol=1e-12)
 
 
 @pytest.mark.parametrize("m", [1, 7, 40])
 def test_greedy_f64_matches_oracle_wing_2000(m):
     c = synth.wing_small(n_vol=0)
     r, estar = run_greedy(c, m, P.PREC_F64, c["tol_rel"])
-    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1)
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1, history=False)
     f = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1,
-                      follow=(host(r["idx"]), host(r["iter"])), tie_rel=TIE)
+                      follow=(host(r["idx"]), host(r["iter"])), tie_rel=TIE, history=False)
     assert f["stats"]["n_fail"] == 0
     if f["stats"]["n_div"] == 0:
         assert host(r["idx"]).tolist() == o["idx"].tolist()
+        assert r["stats"]["iterations"] == o["stats"]["iterations"]
+        assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-12
     assert r["stats"]["final_max"] <= estar
 
 
@@ -80,12 +85,15 @@ def test_greedy_f32_screen_is_certified(m):
     c = synth.wing_small(n_vol=0)
     r, estar = run_greedy(c, m, P.PREC_F32, c["tol_rel"])
     f = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1,
-                      follow=(host(r["idx"]), host(r["iter"])), tie_rel=TIE)
+                      follow=(host(r["idx"]), host(r["iter"])), tie_rel=TIE, history=False)
     assert f["stats"]["n_fail"] == 0, f["stats"]
-    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1)
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1, history=False)
     if f["stats"]["n_div"] == 0:
         assert host(r["idx"]).tolist() == o["idx"].tolist()
+        assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-12
     assert r["stats"]["final_max"] <= estar
+    # the FP32 screen must have spared some FP64 work
+    assert r["stats"]["rescored"] < r["stats"]["pairs_f32"] // max(r["nc"], 1)
 
 
 def test_greedy_nc_max_returns_partial_prefix():

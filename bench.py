@@ -41,7 +41,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nv", type=int, default=2_000_000)
-    ap.add_argument("--prec", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--prec", type=int, default=48, choices=[32, 48, 64],
+                    help="greedy pair arithmetic: FP32, double-float (48) or FP64")
+    ap.add_argument("--vol-prec", type=int, default=48, choices=[32, 48, 64],
+                    help="volume-sum arithmetic inside the step")
     return ap.parse_args()
 
 
@@ -53,7 +56,10 @@ def workload(nv):
     return c
 
 
-def workload_desc(c, m, nc_plain, prec):
+PREC_NAME = {32: "FP32", 48: "double-float (FP32 pipe)", 64: "FP64"}
+
+
+def workload_desc(c, m, nc_plain, prec, vol_prec=48):
     return {
         "workload": "swept tapered wing, GCB greedy + weights + volume sum",
         "n_b": int(len(c["xb"])), "grid": "100x500", "n_v": int(len(c["xv"])),
@@ -61,9 +67,10 @@ def workload_desc(c, m, nc_plain, prec):
         "radius": c["radius"], "tol_rel": c["tol_rel"], "m": int(m),
         "m_rule": "round(1.5 N_b / N_c), N_c from the m = 1 run",
         "nc_plain": int(nc_plain), "group_seed": 1,
-        "eval": "FP32 pairs + FP64-certified argmax" if prec == 32 else "FP64 pairs",
+        "eval": (PREC_NAME[prec] + " pairs, FP64-certified argmax") if prec != 64
+                else "FP64 pairs",
         "solve": "FP64 recurrence Cholesky + 2 refinement steps",
-        "volume_eval": "FP32",
+        "volume_eval": PREC_NAME[vol_prec],
         "l2": "flushed between steps (256 MiB write), outside the timed events",
     }
 
@@ -165,10 +172,10 @@ def run_ours(args, rank, world):
         e[1].record()
         w, res = P.solve_weights(xb, db, g["idx"], radius=R, refine_steps=2)
         e[2].record()
-        P.deform_volume(xv, xb, g["idx"], w, radius=R, eval_prec=32, out=dv)
+        P.deform_volume(xv, xb, g["idx"], w, radius=R, eval_prec=args.vol_prec, out=dv)
         e[3].record()
         if record is not None:
-            record.append((e, g, res))
+            record.append((e, g, res, w))
         return g
 
     for _ in range(args.warmup):
@@ -210,6 +217,21 @@ def run_ours(args, rank, world):
         pt.append(a.elapsed_time(b))
     plain_ms = statistics.median(pt)
 
+    # each volume-sum precision timed alone on the same inputs
+    vol_alone = {}
+    for vp in (32, 48):
+        P.deform_volume(xv, xb, g_last["idx"], recs[-1][3], radius=R, eval_prec=vp, out=dv)
+        ts_ = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record()
+            P.deform_volume(xv, xb, g_last["idx"], recs[-1][3], radius=R, eval_prec=vp, out=dv)
+            b.record()
+            torch.cuda.synchronize()
+            ts_.append(a.elapsed_time(b))
+        vol_alone[vp] = statistics.median(ts_)
+
     # e2e through the public API with host buffers (pinned), copies timed
     hx = torch.from_numpy(np.ascontiguousarray(c["xb"])).pin_memory()
     hd = torch.from_numpy(np.ascontiguousarray(c["db"])).pin_memory()
@@ -229,7 +251,7 @@ def run_ours(args, rank, world):
         g = P.greedy_select(dxb, ddb, radius=R, tol=tol, tol_mode=1, m=m, seed=1,
                             eval_prec=args.prec, workspace=gws)
         w, _ = P.solve_weights(dxb, ddb, g["idx"], radius=R, refine_steps=2)
-        P.deform_volume(dxv, dxb, g["idx"], w, radius=R, eval_prec=32, out=dv)
+        P.deform_volume(dxv, dxb, g["idx"], w, radius=R, eval_prec=args.vol_prec, out=dv)
         hout.copy_(dv, non_blocking=True)
         hidx[:g["nc"]].copy_(g["idx"], non_blocking=True)
         b.record()
@@ -255,14 +277,14 @@ def run_ours(args, rank, world):
     st = g_last["stats"]
     vol_pairs = nv * nc
     vol_achieved = vol_pairs * FLOPS_PER_PAIR / (v_ms * 1e-3)
-    greedy_flops = FLOPS_PER_PAIR * (st["pairs_f32"] + st["pairs_f64"] +
+    greedy_flops = FLOPS_PER_PAIR * (st["pairs_f32"] + st["pairs_f64"] + st["pairs_ff"] +
                                      st["rescored"] * nc)
     kernels = [
         {"name": "k_greedy (persistent GCB loop)", "ms": g_ms, "bound": "alu",
          "achieved_tflops": greedy_flops / (g_ms * 1e-3) / 1e12,
          "note": "latency-bound: grid barriers and FP64 appends per iteration"},
         {"name": "k_solve (weights + refinement)", "ms": s_ms, "bound": "alu"},
-        {"name": "k_volume_f32 (Eq. 6)", "ms": v_ms, "bound": "alu",
+        {"name": "k_volume (Eq. 6, %s)" % PREC_NAME[args.vol_prec], "ms": v_ms, "bound": "alu",
          "pairs_per_s": vol_pairs / (v_ms * 1e-3),
          "achieved_tflops": vol_achieved / 1e12, "frac": vol_achieved / fp32_peak},
     ]
@@ -292,20 +314,25 @@ def run_ours(args, rank, world):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.prec == 32 else "f64",
+        "dtype": {32: "f32", 48: "f32x2", 64: "f64"}[args.prec],
         "data": "synthetic (seeded wing generator; see DESIGN.md)",
-        "config": workload_desc(c, m, nc_plain, args.prec),
+        "config": workload_desc(c, m, nc_plain, args.prec, args.vol_prec),
         "greedy": {
             "gcb_s": g_ms / 1e3, "plain_s": plain_ms / 1e3,
             "speedup_gcb_vs_plain": plain_ms / g_ms, "m": m,
             "nc_gcb": nc, "nc_plain": nc_plain,
             "iterations_gcb": st["iterations"], "iterations_plain": pr["stats"]["iterations"],
             "pairs_f32": st["pairs_f32"], "pairs_f64": st["pairs_f64"],
+            "pairs_ff": st["pairs_ff"],
             "rescored": st["rescored"], "estar": st["estar"], "final_max": st["final_max"],
             "us_per_iteration": g_ms * 1e3 / max(st["iterations"], 1),
         },
         "volume": {"pairs_per_s": vol_pairs / (v_ms * 1e-3), "ms": v_ms,
-                   "fp32_peak_frac": vol_achieved / fp32_peak},
+                   "fp32_peak_frac": vol_achieved / fp32_peak,
+                   "alone": {PREC_NAME[k]: {"ms": t, "pairs_per_s": vol_pairs / (t * 1e-3),
+                                            "useful_flops_frac_fp32_peak":
+                                                vol_pairs * FLOPS_PER_PAIR / (t * 1e-3) / fp32_peak}
+                             for k, t in vol_alone.items()}},
         "weights_max_resid": res_last,
         "kernels": kernels,
         "roofline": roof,
@@ -376,7 +403,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded wing generator; see DESIGN.md)",
-        "config": workload_desc(c, m, g1["nc"], args.prec), "impl": "reference",
+        "config": workload_desc(c, m, g1["nc"], args.prec, args.vol_prec), "impl": "reference",
         "cpu_baseline": base,
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0, "spent_s": spent,

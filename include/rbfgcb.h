@@ -59,9 +59,13 @@ typedef enum {
 /* Precision of the pair evaluations (Eq. 1 sums). */
 enum {
     RBF_PREC_F64 = 64,    /* every pair in FP64 */
-    RBF_PREC_F32 = 32     /* FP32 pairs; the greedy certifies its argmax and its
+    RBF_PREC_F32 = 32,    /* FP32 pairs; the greedy certifies its argmax and its
                              stopping test by re-scoring near-maximal nodes in
                              FP64 (FP32 values carry an error bound) */
+    RBF_PREC_F32X2 = 48   /* double-float pairs on the FP32 pipe (about 44
+                             correct bits); the greedy re-scores only nodes
+                             within the double-float bound of the maximum in
+                             FP64 */
 };
 
 typedef struct {
@@ -88,6 +92,7 @@ typedef struct {
     int64_t full_checks;     /* diagnostic all-node evaluations (history)       */
     int64_t pairs_f32;       /* (node, centre) pairs evaluated in FP32          */
     int64_t pairs_f64;       /* (node, centre) pairs evaluated in FP64          */
+    int64_t pairs_ff;        /* (node, centre) pairs evaluated in double-float  */
     int64_t rescored;        /* nodes re-scored in FP64 after an FP32 screen    */
     double estar;            /* the absolute tolerance E* used                  */
     double final_max;        /* certified global max error at exit (-1 if the
@@ -170,8 +175,8 @@ rbf_status rbf_solve_weights(const double *d_xb, const double *d_db, int64_t nb,
  * d_xv : device FP64 nv x 3.   d_dv : device FP64 nv x 3 (output).
  * d_xb, d_sel_idx, nc, d_w : centres r_j = xb[sel_idx[j]] and weights w_j
  *                            (device FP64 nc x 3), as from rbf_solve_weights.
- * p->eval_prec selects the pair arithmetic (FP32 or FP64); only radius and
- * eval_prec are read from p.
+ * p->eval_prec selects the pair arithmetic (FP32, double-float or FP64); only
+ * radius and eval_prec are read from p.
  * ASYNC.
  * ------------------------------------------------------------------------ */
 size_t rbf_volume_workspace_bytes(int64_t nv, int64_t nc, const rbf_params *p);

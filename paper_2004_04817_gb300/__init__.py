@@ -18,6 +18,7 @@ from .rbf import (  # noqa: F401
     status_string,
     STATUS,
     PREC_F32,
+    PREC_F32X2,
     PREC_F64,
     HIST_COLS,
 )

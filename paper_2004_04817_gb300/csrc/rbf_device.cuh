@@ -42,6 +42,115 @@ __device__ __forceinline__ double phi_f64_s(double s)
 }
 
 // ----------------------------------------------------------------------------
+// Double-float ("ff") arithmetic on the FP32 pipe: a value is the unevaluated
+// sum h + l of two floats (about 48 significant bits).  Built from the
+// error-free transformations of Knuth (TwoSum: the exact rounding error of a
+// sum) and Dekker (FastTwoSum for |a| >= |b|; the exact error of a product
+// through one fused multiply-add).  The __f*_rn intrinsics keep the compiler
+// from contracting or reordering the steps whose rounding the method needs.
+// On GB300 an ff pair costs ~150 FP32 instructions, 20x less time than the
+// same pair in native FP64 (FP64 runs at 1/64 of the FP32 rate).
+// ----------------------------------------------------------------------------
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b)   // needs |a| >= |b| (or a == 0)
+{
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const ff s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_sqr(ff a)
+{
+    const float p = __fmul_rn(a.h, a.h);
+    float e = fmaf(a.h, a.h, -p);
+    e = fmaf(__fadd_rn(a.h, a.h), a.l, e);
+    return fast_two_sum(p, e);
+}
+
+// Split of an FP64 value into h + l (h = nearest float, l = nearest float to
+// the exact remainder): 48 significant bits.
+__host__ __device__ __forceinline__ void split_f64(double x, float &h, float &l)
+{
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+// phi(eta) for s = eta^2 given as ff (coordinates pre-scaled by 1/R).
+// sqrt: FP32 reciprocal square root refined by one Newton step in FP32, then
+// one Newton correction of eta in ff (about 2^-46 relative).
+__device__ __forceinline__ ff phi_ff_s(ff s)
+{
+    const float sc = fmaxf(s.h, 1e-37f);
+    float y = rsqrtf(sc);
+    y = __fmul_rn(y, fmaf(-0.5f * sc, __fmul_rn(y, y), 1.5f));
+    const float e0 = __fmul_rn(s.h, y);
+    const float r = __fadd_rn(fmaf(-e0, e0, s.h), s.l);
+    const ff eta = fast_two_sum(e0, __fmul_rn(__fmul_rn(r, 0.5f), y));
+    ff t = two_sum(1.0f, -eta.h);
+    t = fast_two_sum(t.h, __fsub_rn(t.l, eta.l));
+    const ff t2 = ff_sqr(t);
+    const ff t4 = ff_sqr(t2);
+    ff p = two_sum(1.0f, __fmul_rn(4.0f, eta.h));
+    p = fast_two_sum(p.h, __fmaf_rn(4.0f, eta.l, p.l));
+    ff ph = ff_mul(t4, p);
+    if (!(eta.h < 1.0f))
+        ph = ff{0.0f, 0.0f};
+    return ph;
+}
+
+// Squared scaled distance between an ff point and an ff centre.
+__device__ __forceinline__ ff dist2_ff(float qxh, float qxl, float qyh, float qyl, float qzh,
+                                       float qzl, float cxh, float cxl, float cyh, float cyl,
+                                       float czh, float czl)
+{
+    ff dx = two_sum(qxh, -cxh);
+    dx.l = __fadd_rn(dx.l, __fsub_rn(qxl, cxl));
+    ff dy = two_sum(qyh, -cyh);
+    dy.l = __fadd_rn(dy.l, __fsub_rn(qyl, cyl));
+    ff dz = two_sum(qzh, -czh);
+    dz.l = __fadd_rn(dz.l, __fsub_rn(qzl, czl));
+    return ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+}
+
+// acc += w * phi with w and phi in ff; acc kept as an unnormalised pair whose
+// low part collects the product and sum errors.
+__device__ __forceinline__ void ff_fma_acc(ff &acc, float wh, float wl, ff ph)
+{
+    const float p = __fmul_rn(wh, ph.h);
+    float pe = fmaf(wh, ph.h, -p);
+    pe = fmaf(wh, ph.l, pe);
+    pe = fmaf(wl, ph.h, pe);
+    const ff s = two_sum(acc.h, p);
+    acc.h = s.h;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, pe));
+}
+
+// ----------------------------------------------------------------------------
 // Argmax keys.  Larger key = larger error; among equal errors the lowest node
 // index wins.  Key 0 means "no candidate".
 //  - FP64 errors: the top 40 bits of the (non-negative) double's bit pattern,

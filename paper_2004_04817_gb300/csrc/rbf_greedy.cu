@@ -33,25 +33,28 @@ namespace rbf {
 constexpr int kGThreads = 256;
 constexpr int kGWarps = kGThreads / kWarp;
 constexpr int kMaxGrid = 4096;
-constexpr int kSmemCentresF32 = 4096;      // FP32 centre tile kept in shared memory
+constexpr int kSmemCentresF32 = 4096;      // FP32 centres kept in shared memory (128 KB)
+constexpr int kSmemCentresFF = 2048;       // double-float centres in the same 128 KB
 constexpr double kPivotMin = 1e-13;        // d^2 at or below: singular (coincident nodes)
 constexpr float kU32 = 5.9604645e-8f;      // 2^-24, unit roundoff of FP32
 constexpr float kBetaPhi = 16.0f;          // error-bound factors (see screen_bound)
 constexpr float kBetaCoord = 8.0f;
+constexpr double kUFF = 5.684341886080802e-14;   // 2^-44: double-float pair accuracy used
+constexpr double kBetaFF = 64.0;                  // in the bound of the ff errors
 
 struct GreedyCtl {
     GridBar bar;
     int status;
     int pad0;
     unsigned long long slot[3];   // argmax keys (ring, indexed by evaluation count)
-    unsigned int tslot[3];        // FP32 screen thresholds (float bits, ring)
-    unsigned int pad1;
+    unsigned long long tslot[3];  // screen thresholds (bits of a non-negative double, ring)
     double estar;
     long long nc;
     long long iterations;
     long long full_checks;
     long long pairs_f32;
     long long pairs_f64;
+    long long pairs_ff;
     unsigned long long rescored;
     double final_max;
     double final_rms;
@@ -91,6 +94,7 @@ struct GreedyArgs {
     D4 *c64;                 // support centres (scaled)
     D4 *w64;                 // weights
     float4 *cw32;                 // (centre, weight) FP32 pairs, interleaved
+    float4 *cwff;                 // (centre hi, centre lo, weight hi, weight lo) per centre
     D4 *y64;                 // forward-solve vector y = Z dr_S
     double *z;                    // Z = L^-1, row-major, ld
     double *zt;                   // Z^T, row-major, ld
@@ -205,16 +209,27 @@ __device__ void grid_pick_reduce(const double *pv, const long long *pi, int G, d
     __syncthreads();
 }
 
-// Grid-wide sums of 4 values per CTA (fixed order, so every CTA gets the
-// same bits).
+// Grid-wide reductions of the per-CTA partials (4 values per CTA).  Warp 0
+// loads them in parallel (lane i takes CTAs i, i + 32, ...) and combines them
+// with a fixed shuffle tree, so every CTA computes the same bits.
 __device__ void grid_sum4(const double *p, int G, double out[4])
 {
     __shared__ double s_o[4];
-    if (threadIdx.x < 4) {
-        double t = 0.0;
-        for (int b = 0; b < G; ++b)
-            t += ldcg(p + 4 * b + threadIdx.x);
-        s_o[threadIdx.x] = t;
+    if (threadIdx.x < 32) {
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = threadIdx.x; b < G; b += 32) {
+            const double2 v0 = __ldcg((const double2 *)(p + 4 * b));
+            const double2 v1 = __ldcg((const double2 *)(p + 4 * b + 2));
+            t[0] += v0.x;
+            t[1] += v0.y;
+            t[2] += v1.x;
+            t[3] += v1.y;
+        }
+        for (int c = 0; c < 4; ++c)
+            t[c] = warp_sum_f64(t[c]);
+        if (threadIdx.x == 0)
+            for (int c = 0; c < 4; ++c)
+                s_o[c] = t[c];
     }
     __syncthreads();
     for (int c = 0; c < 4; ++c)
@@ -225,11 +240,22 @@ __device__ void grid_sum4(const double *p, int G, double out[4])
 __device__ void grid_max4(const double *p, int G, double out[4])
 {
     __shared__ double s_o[4];
-    if (threadIdx.x < 4) {
-        double t = -INFINITY;
-        for (int b = 0; b < G; ++b)
-            t = fmax(t, ldcg(p + 4 * b + threadIdx.x));
-        s_o[threadIdx.x] = t;
+    if (threadIdx.x < 32) {
+        double t[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int b = threadIdx.x; b < G; b += 32) {
+            const double2 v0 = __ldcg((const double2 *)(p + 4 * b));
+            const double2 v1 = __ldcg((const double2 *)(p + 4 * b + 2));
+            t[0] = fmax(t[0], v0.x);
+            t[1] = fmax(t[1], v0.y);
+            t[2] = fmax(t[2], v1.x);
+            t[3] = fmax(t[3], v1.y);
+        }
+        for (int c = 0; c < 4; ++c)
+            for (int o = 16; o > 0; o >>= 1)
+                t[c] = fmax(t[c], __shfl_xor_sync(0xffffffffu, t[c], o));
+        if (threadIdx.x == 0)
+            for (int c = 0; c < 4; ++c)
+                s_o[c] = t[c];
     }
     __syncthreads();
     for (int c = 0; c < 4; ++c)
@@ -412,6 +438,19 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
         a.cw32[2 * nc] = make_float4((float)xc.x, (float)xc.y, (float)xc.z, 0.0f);
         a.cw32[2 * nc + 1] = make_float4((float)wx, (float)wy, (float)wz,
                                          (float)(fabs(wx) + fabs(wy) + fabs(wz)));
+        {
+            float h0, l0, h1, l1, h2, l2;
+            split_f64(xc.x, h0, l0);
+            split_f64(xc.y, h1, l1);
+            split_f64(xc.z, h2, l2);
+            a.cwff[4 * nc] = make_float4(h0, h1, h2, 0.0f);
+            a.cwff[4 * nc + 1] = make_float4(l0, l1, l2, 0.0f);
+            split_f64(wx, h0, l0);
+            split_f64(wy, h1, l1);
+            split_f64(wz, h2, l2);
+            a.cwff[4 * nc + 2] = make_float4(h0, h1, h2, (float)(fabs(wx) + fabs(wy) + fabs(wz)));
+            a.cwff[4 * nc + 3] = make_float4(l0, l1, l2, 0.0f);
+        }
         a.spos[nc] = pn;
         a.in_s[pn] = 1;
         a.sel_idx[nc] = node;
@@ -554,7 +593,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
 
     // ---------------- error evaluation over a position range ---------------
     int ev = 0;                      // evaluation counter (ring index)
-    long long pairs32 = 0, pairs64 = 0;
+    long long pairs32 = 0, pairs64 = 0, pairsff = 0;
     unsigned long long rescored_local = 0;
     // Evaluates E at positions [p0, p1) with the current weights.  With
     // `argmax`, the largest E among nodes not in S (lowest node index on
@@ -589,11 +628,16 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
             if (blockIdx.x == 0 && tid == 0)
                 pairs64 += (long long)nq * nc;
         } else {
-            // ---- pass 1: FP32 errors with a bound (centres from shared memory)
-            const bool smem = nc <= kSmemCentresF32;
+            // ---- pass 1: FP32 or double-float errors E~ with a bound beta,
+            // |E~ - E| <= beta; e64[q] = E~, u32[q] = beta.  Centres come from
+            // shared memory when they fit.
+            const bool use_ff = a.prec == RBF_PREC_F32X2;
+            const bool smem = nc <= (use_ff ? kSmemCentresFF : kSmemCentresF32);
             if (smem) {
-                for (int j = tid; j < 2 * nc; j += kGThreads)
-                    s_cw[j] = ldcg(a.cw32 + j);
+                const int n4 = (use_ff ? 4 : 2) * nc;
+                const float4 *src = use_ff ? a.cwff : a.cw32;
+                for (int j = tid; j < n4; j += kGThreads)
+                    s_cw[j] = ldcg(src + j);
             }
             if (tid < 32) {
                 float t = 0.0f;
@@ -604,51 +648,107 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                     s_wabs = t;
             }
             __syncthreads();
-            const float4 *cw = smem ? s_cw : a.cw32;
-            const float coord_term = kBetaCoord * xscale * s_wabs * 1.001f;
-            float tloc = 0.0f;
-            for (int it = 0; it < rounds; ++it) {
-                const int q = p0 + team + it * nteams;
-                const bool act = q < p1;
-                const float4 x = ldcg(a.xg32 + (act ? q : p0));
-                float fx = 0.0f, fy = 0.0f, fz = 0.0f, sb = 0.0f;
-                for (int j = sub; j < nc; j += ts) {
-                    const float4 c = smem ? cw[2 * j] : ldcg(cw + 2 * j);
-                    const float4 w = smem ? cw[2 * j + 1] : ldcg(cw + 2 * j + 1);
-                    const float dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
-                    const float ph = phi_f32_s(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-                    fx = fmaf(w.x, ph, fx);
-                    fy = fmaf(w.y, ph, fy);
-                    fz = fmaf(w.z, ph, fz);
-                    sb = fmaf(w.w, ph, sb);
+            double tloc = 0.0;
+            if (!use_ff) {
+                const float4 *cw = smem ? s_cw : a.cw32;
+                const float coord_term = kBetaCoord * xscale * s_wabs * 1.001f;
+                for (int it = 0; it < rounds; ++it) {
+                    const int q = p0 + team + it * nteams;
+                    const bool act = q < p1;
+                    const float4 x = ldcg(a.xg32 + (act ? q : p0));
+                    float fx = 0.0f, fy = 0.0f, fz = 0.0f, sb = 0.0f;
+                    for (int j = sub; j < nc; j += ts) {
+                        const float4 c = smem ? cw[2 * j] : ldcg(cw + 2 * j);
+                        const float4 w = smem ? cw[2 * j + 1] : ldcg(cw + 2 * j + 1);
+                        const float dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
+                        const float ph = phi_f32_s(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                        fx = fmaf(w.x, ph, fx);
+                        fy = fmaf(w.y, ph, fy);
+                        fz = fmaf(w.z, ph, fz);
+                        sb = fmaf(w.w, ph, sb);
+                    }
+                    fx = team_sum(fx, ts);
+                    fy = team_sum(fy, ts);
+                    fz = team_sum(fz, ts);
+                    sb = team_sum(sb, ts);
+                    if (act && sub == 0) {
+                        const D4 d = ldcg(a.dg64 + q);
+                        const float ex = (float)d.x - fx, ey = (float)d.y - fy,
+                                    ez = (float)d.z - fz;
+                        const float e = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
+                        const float dabs = (float)(fabs(d.x) + fabs(d.y) + fabs(d.z));
+                        // bound of |E32 - E|: rounding of phi and of the sums
+                        // (proportional to sum |w| phi), of the coordinates
+                        // (max|x|/R * sum |w|), of the displacement and of E
+                        const float beta =
+                            kU32 * (kBetaPhi * (sb + dabs) + coord_term + 4.0f * e) + 1e-30f;
+                        a.u32[q] = beta;
+                        a.e64[q] = (double)e;
+                        if (!ldcg(a.in_s + q))
+                            tloc = fmax(tloc, fmax((double)e - (double)beta, 0.0));
+                    }
                 }
-                fx = team_sum(fx, ts);
-                fy = team_sum(fy, ts);
-                fz = team_sum(fz, ts);
-                sb = team_sum(sb, ts);
-                if (act && sub == 0) {
-                    const D4 d = ldcg(a.dg64 + q);
-                    const float ex = (float)d.x - fx, ey = (float)d.y - fy, ez = (float)d.z - fz;
-                    const float e = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
-                    const float dabs = (float)(fabs(d.x) + fabs(d.y) + fabs(d.z));
-                    // bound of |E32 - E|: rounding of phi and of the sums
-                    // (proportional to sum |w| phi), of the coordinates
-                    // (max|x|/R * sum |w|), of the displacement and of E
-                    const float beta =
-                        kU32 * (kBetaPhi * (sb + dabs) + coord_term + 4.0f * e) + 1e-30f;
-                    a.u32[q] = e + beta;
-                    a.e64[q] = (double)e;     // replaced by the FP64 value if re-scored
-                    if (!ldcg(a.in_s + q))
-                        tloc = fmaxf(tloc, fmaxf(e - beta, 0.0f));
+                if (blockIdx.x == 0 && tid == 0)
+                    pairs32 += (long long)nq * nc;
+            } else {
+                const float4 *cw = smem ? s_cw : a.cwff;
+                const double coord_term = (16.0 * (double)xscale + 4.0) * (double)s_wabs;
+                for (int it = 0; it < rounds; ++it) {
+                    const int q = p0 + team + it * nteams;
+                    const bool act = q < p1;
+                    const D4 xq = ldcg(a.xg64 + (act ? q : p0));
+                    float qxh, qxl, qyh, qyl, qzh, qzl;
+                    split_f64(xq.x, qxh, qxl);
+                    split_f64(xq.y, qyh, qyl);
+                    split_f64(xq.z, qzh, qzl);
+                    ff fx{0.0f, 0.0f}, fy{0.0f, 0.0f}, fz{0.0f, 0.0f};
+                    float sb = 0.0f;
+                    for (int j = sub; j < nc; j += ts) {
+                        const float4 ch = smem ? cw[4 * j] : ldcg(cw + 4 * j);
+                        const float4 cl = smem ? cw[4 * j + 1] : ldcg(cw + 4 * j + 1);
+                        const float4 wh = smem ? cw[4 * j + 2] : ldcg(cw + 4 * j + 2);
+                        const float4 wl = smem ? cw[4 * j + 3] : ldcg(cw + 4 * j + 3);
+                        const ff s2 = dist2_ff(qxh, qxl, qyh, qyl, qzh, qzl, ch.x, cl.x, ch.y,
+                                               cl.y, ch.z, cl.z);
+                        const ff ph = phi_ff_s(s2);
+                        ff_fma_acc(fx, wh.x, wl.x, ph);
+                        ff_fma_acc(fy, wh.y, wl.y, ph);
+                        ff_fma_acc(fz, wh.z, wl.z, ph);
+                        sb = fmaf(wh.w, ph.h, sb);
+                    }
+                    // team reduction in FP64 (exact enough: each ff value is
+                    // converted to the double h + l)
+                    double sx = (double)fx.h + (double)fx.l, sy = (double)fy.h + (double)fy.l,
+                           sz = (double)fz.h + (double)fz.l;
+                    sx = team_sum(sx, ts);
+                    sy = team_sum(sy, ts);
+                    sz = team_sum(sz, ts);
+                    sb = team_sum(sb, ts);
+                    if (act && sub == 0) {
+                        const D4 d = ldcg(a.dg64 + q);
+                        const double ex = d.x - sx, ey = d.y - sy, ez = d.z - sz;
+                        const double e = sqrt(fma(ez, ez, fma(ey, ey, ex * ex)));
+                        const double dabs = fabs(d.x) + fabs(d.y) + fabs(d.z);
+                        // bound of |E~ - E|: ff rounding of phi, products and
+                        // sums (proportional to sum |w| phi), of the coordinate
+                        // splits (max|x|/R * sum |w|) and of the displacement
+                        const double beta =
+                            kUFF * (kBetaFF * ((double)sb + dabs) + coord_term) + 1e-300;
+                        a.u32[q] = (float)(beta * 1.0000002);
+                        a.e64[q] = e;
+                        if (!ldcg(a.in_s + q))
+                            tloc = fmax(tloc, fmax(e - (double)a.u32[q], 0.0));
+                    }
                 }
+                if (blockIdx.x == 0 && tid == 0)
+                    pairsff += (long long)nq * nc;
             }
-            tloc = warp_max_f32(tloc);
-            if (lane == 0 && tloc > 0.0f)
-                atomicMax(&ctl->tslot[r], __float_as_uint(tloc));
-            if (blockIdx.x == 0 && tid == 0)
-                pairs32 += (long long)nq * nc;
+            for (int o = 16; o > 0; o >>= 1)
+                tloc = fmax(tloc, __shfl_xor_sync(0xffffffffu, tloc, o));
+            if (lane == 0 && tloc > 0.0)
+                atomicMax(&ctl->tslot[r], (unsigned long long)__double_as_longlong(tloc));
             GSYNC_B();
-            const float thr = __uint_as_float(ldcg(&ctl->tslot[r]));
+            const double thr = __longlong_as_double((long long)ldcg(&ctl->tslot[r]));
             // ---- pass 2: FP64 re-score of every node whose upper bound
             // reaches the largest lower bound; the others are certified below
             // the maximum
@@ -659,11 +759,10 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                 bool ins = true;
                 if (act) {
                     ins = ldcg(a.in_s + q) != 0;
-                    need = !ins && ldcg(a.u32 + q) >= thr;
-                    if (!need && !ins && sub == 0) {
-                        const double e32 = ldcg(a.e64 + q);
-                        lsq = fma(e32, e32, lsq);
-                    }
+                    const double ea = ldcg(a.e64 + q);
+                    need = !ins && ea + (double)ldcg(a.u32 + q) >= thr;
+                    if (!need && !ins && sub == 0)
+                        lsq = fma(ea, ea, lsq);
                 }
                 if (__ballot_sync(0xffffffffu, need) == 0u)
                     continue;
@@ -716,7 +815,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
         }
         if (blockIdx.x == 0 && tid == 0) {
             ctl->slot[(r + 2) % 3] = 0ull;
-            ctl->tslot[(r + 2) % 3] = 0u;
+            ctl->tslot[(r + 2) % 3] = 0ull;
         }
         ++ev;
         return true;
@@ -794,6 +893,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
         ctl->full_checks = nfull;
         ctl->pairs_f32 = pairs32;
         ctl->pairs_f64 = pairs64;
+        ctl->pairs_ff = pairsff;
         ctl->final_max = idle >= m ? run_max : -1.0;
         ctl->final_rms = idle >= m ? sqrt(run_sq / (double)nb) : -1.0;
         ctl->min_pivot = min_piv;
@@ -864,17 +964,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
     GSYNC();
     {
         double g4[4];
-        // only slot 0 of each CTA's partial is meaningful here
-        __shared__ double s_m;
-        if (tid == 0) {
-            double mm = 0.0;
-            for (int b = 0; b < G; ++b)
-                mm = fmax(mm, ldcg(part(use) + 4 * b));
-            s_m = mm;
-        }
-        __syncthreads();
-        g4[0] = s_m;
-        __syncthreads();
+        grid_max4(part(use), G, g4);   // slot 0 of each CTA's partial
         ++use;
         if (g4[0] > 0.0) {
             if (blockIdx.x == 0 && tid == 0)
@@ -925,16 +1015,9 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
         }
         GSYNC();
         {
-            __shared__ double s_m;
-            if (tid == 0) {
-                double mm = 0.0;
-                for (int b = 0; b < G; ++b)
-                    mm = fmax(mm, ldcg(part(use) + 4 * b));
-                s_m = mm;
-            }
-            __syncthreads();
-            maxres = s_m;
-            __syncthreads();
+            double g4[4];
+            grid_max4(part(use), G, g4);
+            maxres = g4[0];
             ++use;
         }
         if (step == steps)
@@ -1000,7 +1083,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
 // ---------------------------------------------------------------------------
 struct GreedyWs {
     size_t ctl, part, parti, perm, node_of_pos, pos_of_node, xg64, dg64, xg32, in_s, u32, e64,
-        spos, c64, w64, cw32, y64, z, zt, bvec, lvec, total;
+        spos, c64, w64, cw32, cwff, y64, z, zt, bvec, lvec, total;
 };
 
 static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
@@ -1028,6 +1111,7 @@ static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
     L.c64 = take(sizeof(D4) * ncm);
     L.w64 = take(sizeof(D4) * ncm);
     L.cw32 = take(sizeof(float4) * 2 * ncm);
+    L.cwff = take(sizeof(float4) * 4 * ncm);
     L.y64 = take(sizeof(D4) * ncm);
     L.z = take(sizeof(double) * ncm * ncm);
     L.zt = take(sizeof(double) * ncm * ncm);
@@ -1043,7 +1127,8 @@ static bool greedy_args_ok(int64_t nb, const rbf_params *p)
            p->nc_max <= nb && p->nc_max <= 46340 && p->radius > 0.0 &&
            std::isfinite(p->radius) && p->tol >= 0.0 && std::isfinite(p->tol) &&
            (p->tol_mode == 0 || p->tol_mode == 1) &&
-           (p->eval_prec == RBF_PREC_F32 || p->eval_prec == RBF_PREC_F64) &&
+           (p->eval_prec == RBF_PREC_F32 || p->eval_prec == RBF_PREC_F64 ||
+            p->eval_prec == RBF_PREC_F32X2) &&
            (p->flags & ~RBF_FLAG_HISTORY_FULL) == 0;
 }
 
@@ -1088,6 +1173,7 @@ static void fill_args(GreedyArgs &a, char *ws, const GreedyWs &L)
     a.c64 = (D4 *)(ws + L.c64);
     a.w64 = (D4 *)(ws + L.w64);
     a.cw32 = (float4 *)(ws + L.cw32);
+    a.cwff = (float4 *)(ws + L.cwff);
     a.y64 = (D4 *)(ws + L.y64);
     a.z = (double *)(ws + L.z);
     a.zt = (double *)(ws + L.zt);
@@ -1150,9 +1236,12 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
     a.hist_cap = hist_cap;
     fill_args(a, ws, L);
 
-    const size_t smem = p->eval_prec == RBF_PREC_F32
-                            ? sizeof(float4) * 2 * (size_t)std::min<int64_t>(p->nc_max, kSmemCentresF32)
-                            : 0;
+    const size_t smem =
+        p->eval_prec == RBF_PREC_F32
+            ? sizeof(float4) * 2 * (size_t)std::min<int64_t>(p->nc_max, kSmemCentresF32)
+        : p->eval_prec == RBF_PREC_F32X2
+            ? sizeof(float4) * 4 * (size_t)std::min<int64_t>(p->nc_max, kSmemCentresFF)
+            : 0;
     if (cudaFuncSetAttribute(k_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(float4) * 2 * kSmemCentresF32)) != cudaSuccess)
         return RBF_E_CUDA;
@@ -1183,6 +1272,7 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
         h_stats->full_checks = ctl.full_checks;
         h_stats->pairs_f32 = ctl.pairs_f32;
         h_stats->pairs_f64 = ctl.pairs_f64;
+        h_stats->pairs_ff = ctl.pairs_ff;
         h_stats->rescored = (int64_t)ctl.rescored;
         h_stats->estar = ctl.estar;
         h_stats->final_max = ctl.final_max;

@@ -19,6 +19,8 @@ constexpr int kVolThreads = 256;
 constexpr int kVolQ = 4;               // points per thread (register blocking)
 constexpr int kTileF32 = 2048;         // centres per shared-memory tile (64 KB)
 constexpr int kTileF64 = 1024;         // centres per shared-memory tile (64 KB)
+constexpr int kTileFF = 1024;          // double-float centres per tile (64 KB)
+constexpr int kVolQFF = 2;             // points per thread, double-float kernel
 
 // ---------------------------------------------------------------------------
 // Packing: FP64 row-major inputs -> scaled, vector-aligned device layouts.
@@ -30,6 +32,42 @@ __global__ void k_pack_points_f32(const double *__restrict__ x, int64_t n, doubl
          i += (int64_t)gridDim.x * blockDim.x) {
         out[i] = make_float4((float)(x[3 * i] * inv_r), (float)(x[3 * i + 1] * inv_r),
                              (float)(x[3 * i + 2] * inv_r), 0.0f);
+    }
+}
+
+__global__ void k_pack_points_ff(const double *__restrict__ x, int64_t n, double inv_r,
+                                 float4 *__restrict__ hi, float4 *__restrict__ lo)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float h0, l0, h1, l1, h2, l2;
+        split_f64(x[3 * i] * inv_r, h0, l0);
+        split_f64(x[3 * i + 1] * inv_r, h1, l1);
+        split_f64(x[3 * i + 2] * inv_r, h2, l2);
+        hi[i] = make_float4(h0, h1, h2, 0.0f);
+        lo[i] = make_float4(l0, l1, l2, 0.0f);
+    }
+}
+
+// double-float centres and weights: (c_hi, c_lo, w_hi, w_lo) per centre
+__global__ void k_pack_centres_ff(const double *__restrict__ xb, const int32_t *__restrict__ sel,
+                                  const double *__restrict__ w, int64_t nc, double inv_r,
+                                  float4 *__restrict__ cff)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = sel[j];
+        float h0, l0, h1, l1, h2, l2;
+        split_f64(xb[3 * n] * inv_r, h0, l0);
+        split_f64(xb[3 * n + 1] * inv_r, h1, l1);
+        split_f64(xb[3 * n + 2] * inv_r, h2, l2);
+        cff[4 * j] = make_float4(h0, h1, h2, 0.0f);
+        cff[4 * j + 1] = make_float4(l0, l1, l2, 0.0f);
+        split_f64(w[3 * j], h0, l0);
+        split_f64(w[3 * j + 1], h1, l1);
+        split_f64(w[3 * j + 2], h2, l2);
+        cff[4 * j + 2] = make_float4(h0, h1, h2, 0.0f);
+        cff[4 * j + 3] = make_float4(l0, l1, l2, 0.0f);
     }
 }
 
@@ -117,6 +155,71 @@ k_volume_f32(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict
 }
 
 // ---------------------------------------------------------------------------
+// Double-float pair sum: ~48-bit coordinates and weights, ~44-bit phi, ff
+// accumulation; result h + l rounded to FP64.
+// ---------------------------------------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(kVolThreads)
+k_volume_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_t nv,
+            const float4 *__restrict__ cw, int nc, double *__restrict__ out)
+{
+    extern __shared__ float4 s_cwff[];
+    const int tid = threadIdx.x;
+    const int64_t per_block = (int64_t)kVolThreads * Q;
+    const bool one_tile = nc <= kTileFF;
+    if (one_tile) {
+        for (int j = tid; j < 4 * nc; j += kVolThreads)
+            s_cwff[j] = cw[j];
+        __syncthreads();
+    }
+    for (int64_t base = blockIdx.x * per_block; base < nv; base += (int64_t)gridDim.x * per_block) {
+        float4 qh[Q], ql[Q];
+        ff ax[Q], ay[Q], az[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            int64_t v = base + (int64_t)i * kVolThreads + tid;
+            v = v < nv ? v : nv - 1;
+            qh[i] = xh[v];
+            ql[i] = xl[v];
+            ax[i] = ff{0.0f, 0.0f};
+            ay[i] = ff{0.0f, 0.0f};
+            az[i] = ff{0.0f, 0.0f};
+        }
+        for (int t0 = 0; t0 < nc; t0 += kTileFF) {
+            const int nt = min(kTileFF, nc - t0);
+            if (!one_tile) {
+                __syncthreads();
+                for (int j = tid; j < 4 * nt; j += kVolThreads)
+                    s_cwff[j] = cw[4 * t0 + j];
+                __syncthreads();
+            }
+            for (int j = 0; j < nt; ++j) {
+                const float4 ch = s_cwff[4 * j], cl = s_cwff[4 * j + 1];
+                const float4 wh = s_cwff[4 * j + 2], wl = s_cwff[4 * j + 3];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const ff s2 = dist2_ff(qh[i].x, ql[i].x, qh[i].y, ql[i].y, qh[i].z, ql[i].z,
+                                           ch.x, cl.x, ch.y, cl.y, ch.z, cl.z);
+                    const ff ph = phi_ff_s(s2);
+                    ff_fma_acc(ax[i], wh.x, wl.x, ph);
+                    ff_fma_acc(ay[i], wh.y, wl.y, ph);
+                    ff_fma_acc(az[i], wh.z, wl.z, ph);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int64_t v = base + (int64_t)i * kVolThreads + tid;
+            if (v < nv) {
+                out[3 * v] = (double)ax[i].h + (double)ax[i].l;
+                out[3 * v + 1] = (double)ay[i].h + (double)ay[i].l;
+                out[3 * v + 2] = (double)az[i].h + (double)az[i].l;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 pair sum (one point per thread).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVolThreads)
@@ -160,7 +263,7 @@ k_volume_f64(const double *__restrict__ xv, int64_t nv, double inv_r,
 // Workspace layout.
 // ---------------------------------------------------------------------------
 struct VolumeWs {
-    size_t off_xq32, off_c32, off_c64, total;
+    size_t off_xq32, off_c32, off_c64, off_xh, off_xl, off_cff, total;
 };
 
 static VolumeWs volume_ws_layout(int64_t nv, int64_t nc, int prec)
@@ -176,6 +279,15 @@ static VolumeWs volume_ws_layout(int64_t nv, int64_t nc, int prec)
     L.off_c64 = o;
     if (prec == RBF_PREC_F64)
         o = align_up(o + sizeof(D4) * 2 * (size_t)nc, 256);
+    L.off_xh = o;
+    if (prec == RBF_PREC_F32X2)
+        o = align_up(o + sizeof(float4) * (size_t)nv, 256);
+    L.off_xl = o;
+    if (prec == RBF_PREC_F32X2)
+        o = align_up(o + sizeof(float4) * (size_t)nv, 256);
+    L.off_cff = o;
+    if (prec == RBF_PREC_F32X2)
+        o = align_up(o + sizeof(float4) * 4 * (size_t)nc, 256);
     L.total = std::max<size_t>(o, 256);
     return L;
 }
@@ -197,7 +309,8 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
                                         size_t ws_bytes, void *stream)
 {
     if (!p || nv < 0 || nc < 0 || !(p->radius > 0.0) ||
-        (p->eval_prec != RBF_PREC_F32 && p->eval_prec != RBF_PREC_F64))
+        (p->eval_prec != RBF_PREC_F32 && p->eval_prec != RBF_PREC_F64 &&
+         p->eval_prec != RBF_PREC_F32X2))
         return RBF_E_ARG;
     if (nv == 0)
         return RBF_OK;
@@ -242,6 +355,29 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
         const int64_t want = (nv + (int64_t)kVolThreads * kVolQ - 1) / ((int64_t)kVolThreads * kVolQ);
         const int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms * occ);
         k_volume_f32<kVolQ><<<grid, kVolThreads, smem, st>>>(xq, nv, c32, (int)nc, d_dv);
+    } else if (p->eval_prec == RBF_PREC_F32X2) {
+        float4 *xh = (float4 *)(ws + L.off_xh), *xl = (float4 *)(ws + L.off_xl);
+        float4 *cff = (float4 *)(ws + L.off_cff);
+        const int pb = (int)std::min<int64_t>((nv + 255) / 256, (int64_t)dev.sms * 8);
+        k_pack_points_ff<<<pb, 256, 0, st>>>(d_xv, nv, inv_r, xh, xl);
+        const int cb = (int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4);
+        k_pack_centres_ff<<<cb, 256, 0, st>>>(d_xb, d_sel_idx, d_w, nc, inv_r, cff);
+        const size_t smem = sizeof(float4) * 4 * (size_t)std::min<int64_t>(nc, kTileFF);
+        static int occ_ff = -1;
+        if (occ_ff < 0) {
+            cudaFuncSetAttribute(k_volume_ff<kVolQFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float4) * 4 * kTileFF));
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ff, k_volume_ff<kVolQFF>,
+                                                              kVolThreads,
+                                                              sizeof(float4) * 4 * kTileFF) !=
+                    cudaSuccess ||
+                occ_ff < 1)
+                occ_ff = 1;
+        }
+        const int64_t want =
+            (nv + (int64_t)kVolThreads * kVolQFF - 1) / ((int64_t)kVolThreads * kVolQFF);
+        const int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms * occ_ff);
+        k_volume_ff<kVolQFF><<<grid, kVolThreads, smem, st>>>(xh, xl, nv, cff, (int)nc, d_dv);
     } else {
         D4 *c64 = (D4 *)(ws + L.off_c64);
         const int cb = (int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4);

@@ -15,6 +15,7 @@ import torch
 from . import build as _build
 
 PREC_F32 = 32
+PREC_F32X2 = 48
 PREC_F64 = 64
 HIST_COLS = 6
 STATUS = {0: "RBF_OK", 1: "RBF_E_ARG", 2: "RBF_E_NOT_SPD", 3: "RBF_E_NC_MAX",
@@ -49,6 +50,7 @@ class GreedyStats(C.Structure):
         ("full_checks", C.c_int64),
         ("pairs_f32", C.c_int64),
         ("pairs_f64", C.c_int64),
+        ("pairs_ff", C.c_int64),
         ("rescored", C.c_int64),
         ("estar", C.c_double),
         ("final_max", C.c_double),

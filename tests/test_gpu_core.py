@@ -79,6 +79,34 @@ def test_greedy_f64_matches_oracle_wing_2000(m):
     assert r["stats"]["final_max"] <= estar
 
 
+@pytest.mark.parametrize("m", [1, 5, 40])
+def test_greedy_ff_is_certified(m):
+    """Double-float pairs + FP64 re-score of near-ties: every decision checked
+    by the oracle; most nodes never reach FP64."""
+    c = synth.wing_small(n_vol=0)
+    r, estar = run_greedy(c, m, P.PREC_F32X2, c["tol_rel"])
+    f = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1,
+                      follow=(host(r["idx"]), host(r["iter"])), tie_rel=TIE, history=False)
+    assert f["stats"]["n_fail"] == 0, f["stats"]
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1, history=False)
+    if f["stats"]["n_div"] == 0:
+        assert host(r["idx"]).tolist() == o["idx"].tolist()
+        assert r["stats"]["iterations"] == o["stats"]["iterations"]
+        assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-12
+    assert r["stats"]["final_max"] <= estar
+    assert r["stats"]["pairs_ff"] > 0 and r["stats"]["pairs_f64"] == 0
+    assert r["stats"]["rescored"] * 20 < r["stats"]["pairs_ff"] // max(r["nc"], 1)
+
+
+def test_greedy_ff_tiny_exact():
+    c = synth.tiny_wing(n_span=6, n_chord=30, radius=1.0)
+    for m in (1, 3, 7):
+        r, estar = run_greedy(c, m, P.PREC_F32X2, 2e-3)
+        o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1, history=False)
+        assert host(r["idx"]).tolist() == o["idx"].tolist()
+        assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-12
+
+
 @pytest.mark.parametrize("m", [1, 5])
 def test_greedy_f32_screen_is_certified(m):
     """FP32 screening + FP64 re-score: every decision checked by the oracle."""
@@ -185,6 +213,17 @@ def test_volume_f32_within_rounding_bound():
     assert np.all(err <= bound), (err / bound).max()
 
 
+def test_volume_ff_matches_oracle():
+    c, S, W = _volume_case()
+    xv = c["xv"]
+    ref = oracle.rbf_sum(xv, c["xb"], S, W, c["radius"])
+    dv = host(P.deform_volume(cuda(xv), cuda(c["xb"]), cuda(S, torch.int32), cuda(W),
+                              radius=c["radius"], eval_prec=P.PREC_F32X2))
+    dmax = np.abs(c["db"]).max()
+    assert np.abs(dv - ref).max() <= 1e-5 * dmax
+    assert np.abs(dv - ref).max() <= 1e-11
+
+
 def test_volume_compact_support_and_edges():
     rng = np.random.default_rng(4)
     xb = rng.random((64, 3))
@@ -193,7 +232,7 @@ def test_volume_compact_support_and_edges():
     xv = np.concatenate([rng.random((300, 3)), np.full((3, 3), 9.0)])
     R = 0.35
     ref = oracle.rbf_sum(xv, xb, S, W, R)
-    for prec, tol in ((P.PREC_F64, 1e-13), (P.PREC_F32, 1e-5)):
+    for prec, tol in ((P.PREC_F64, 1e-13), (P.PREC_F32X2, 1e-12), (P.PREC_F32, 1e-5)):
         dv = host(P.deform_volume(cuda(xv), cuda(xb), cuda(S, torch.int32), cuda(W), radius=R,
                                   eval_prec=prec))
         assert np.abs(dv - ref).max() <= tol

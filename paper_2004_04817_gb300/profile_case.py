@@ -23,7 +23,8 @@ def main():
     ap.add_argument("case", choices=["volume", "greedy", "solve"])
     ap.add_argument("--nv", type=int, default=1_000_000)
     ap.add_argument("--m", type=int, default=241)
-    ap.add_argument("--prec", type=int, default=32)
+    ap.add_argument("--prec", type=int, default=48)
+    ap.add_argument("--vprec", type=int, default=32)
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args()
     c = synth.wing_gcb(n_vol=a.nv if a.case == "volume" else 0)
@@ -38,7 +39,8 @@ def main():
             continue
         w, _ = P.solve_weights(xb, db, g["idx"], radius=c["radius"])
         if a.case == "volume":
-            P.deform_volume(dev(c["xv"]), xb, g["idx"], w, radius=c["radius"], eval_prec=32)
+            P.deform_volume(dev(c["xv"]), xb, g["idx"], w, radius=c["radius"],
+                            eval_prec=a.vprec)
     torch.cuda.synchronize()
     print("profile case done", a.case, g["nc"])
 

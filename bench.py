@@ -69,7 +69,7 @@ def workload_desc(c, m, nc_plain, prec, vol_prec=48):
         "nc_plain": int(nc_plain), "group_seed": 1,
         "eval": (PREC_NAME[prec] + " pairs, FP64-certified argmax") if prec != 64
                 else "FP64 pairs",
-        "solve": "FP64 recurrence Cholesky + 2 refinement steps",
+        "solve": "FP64 recurrence Cholesky (inside the greedy) + 2 refinement steps",
         "volume_eval": PREC_NAME[vol_prec],
         "l2": "flushed between steps (256 MiB write), outside the timed events",
     }
@@ -168,9 +168,9 @@ def run_ours(args, rank, world):
         e = [ev() for _ in range(4)]
         e[0].record()
         g = P.greedy_select(xb, db, radius=R, tol=tol, tol_mode=1, m=m, seed=1,
-                            eval_prec=args.prec, workspace=gws)
+                            eval_prec=args.prec, weights=True, refine_steps=2, workspace=gws)
         e[1].record()
-        w, res = P.solve_weights(xb, db, g["idx"], radius=R, refine_steps=2)
+        w, res = g["w"], g["stats"]["max_resid"]
         e[2].record()
         P.deform_volume(xv, xb, g["idx"], w, radius=R, eval_prec=args.vol_prec, out=dv)
         e[3].record()
@@ -217,6 +217,18 @@ def run_ours(args, rank, world):
         pt.append(a.elapsed_time(b))
     plain_ms = statistics.median(pt)
 
+    # rbf_solve_weights alone (refactorises the selected set from scratch)
+    sw = []
+    for _ in range(3):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record()
+        P.solve_weights(xb, db, g_last["idx"], radius=R, refine_steps=2)
+        b.record()
+        torch.cuda.synchronize()
+        sw.append(a.elapsed_time(b))
+    solve_alone_ms = statistics.median(sw)
+
     # each volume-sum precision timed alone on the same inputs
     vol_alone = {}
     for vp in (32, 48):
@@ -249,8 +261,8 @@ def run_ours(args, rank, world):
         ddb.copy_(hd, non_blocking=True)
         dxv.copy_(hv, non_blocking=True)
         g = P.greedy_select(dxb, ddb, radius=R, tol=tol, tol_mode=1, m=m, seed=1,
-                            eval_prec=args.prec, workspace=gws)
-        w, _ = P.solve_weights(dxb, ddb, g["idx"], radius=R, refine_steps=2)
+                            eval_prec=args.prec, weights=True, refine_steps=2, workspace=gws)
+        w = g["w"]
         P.deform_volume(dxv, dxb, g["idx"], w, radius=R, eval_prec=args.vol_prec, out=dv)
         hout.copy_(dv, non_blocking=True)
         hidx[:g["nc"]].copy_(g["idx"], non_blocking=True)
@@ -283,7 +295,9 @@ def run_ours(args, rank, world):
         {"name": "k_greedy (persistent GCB loop)", "ms": g_ms, "bound": "alu",
          "achieved_tflops": greedy_flops / (g_ms * 1e-3) / 1e12,
          "note": "latency-bound: grid barriers and FP64 appends per iteration"},
-        {"name": "k_solve (weights + refinement)", "ms": s_ms, "bound": "alu"},
+        {"name": "weights: refinement inside k_greedy (row a9)", "ms": s_ms, "bound": "alu",
+         "note": "refinement runs inside the greedy launch; rbf_solve_weights alone: %.3f ms"
+                 % solve_alone_ms},
         {"name": "k_volume (Eq. 6, %s)" % PREC_NAME[args.vol_prec], "ms": v_ms, "bound": "alu",
          "pairs_per_s": vol_pairs / (v_ms * 1e-3),
          "achieved_tflops": vol_achieved / 1e12, "frac": vol_achieved / fp32_peak},
@@ -340,7 +354,7 @@ def run_ours(args, rank, world):
                   "hbm_gbs_measured": pk.get("hbm_gbs")},
         "e2e": {"value": e2e_mean / 1e3, "unit": "s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,
     }

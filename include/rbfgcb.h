@@ -84,6 +84,11 @@ typedef struct {
  * FP64 after every m-th iteration to fill its global max / RMS columns
  * (diagnostic; the selection does not depend on it). */
 #define RBF_FLAG_HISTORY_FULL 1
+/* rbf_params.flags, tests of the failure path only: one CTA of the
+ * persistent greedy kernel leaves before its first grid barrier and every
+ * barrier wait is bounded by 50 ms, so rbf_greedy_select returns
+ * RBF_E_TIMEOUT (and the CUDA context stays usable). */
+#define RBF_FLAG_TEST_BARRIER_TIMEOUT (1 << 30)
 
 /* Per-run statistics of rbf_greedy_select (host struct). */
 typedef struct {
@@ -101,6 +106,8 @@ typedef struct {
                                 FP32 mode nodes not re-scored enter with their
                                 FP32 value (-1 on an error status)            */
     double min_pivot;        /* smallest squared Cholesky pivot d^2 seen        */
+    double max_resid;        /* with d_w: max_j |F(r_j) - dr_j|_inf over S after
+                                refinement (FP64); -1 without d_w             */
 } rbf_greedy_stats;
 
 /* Columns of one row of the optional iteration history (device doubles):
@@ -131,6 +138,10 @@ typedef struct {
  *              (the three seed nodes first).
  * d_sel_iter : device int64[nc_max] or NULL: iteration k at which each node
  *              was added (-1 for seeds).
+ * d_w        : device FP64 nc_max x 3 or NULL: the weights of the selected
+ *              set (support order), from the greedy's own factor refined by
+ *              p->refine_steps FP64 steps W += Phi_SS^-1 (dX_S - Phi_SS W) --
+ *              the same result rbf_solve_weights gives, without refactoring.
  * d_hist     : device double[hist_cap * RBF_HIST_COLS] or NULL.
  * h_nc       : host; number of selected nodes.
  * h_n_hist   : host or NULL; number of iterations (history rows wanted).
@@ -142,7 +153,7 @@ size_t rbf_greedy_workspace_bytes(int64_t nb, const rbf_params *p);
 
 rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, int64_t nb,
                              const rbf_params *p,
-                             int32_t *d_sel_idx, int64_t *d_sel_iter,
+                             int32_t *d_sel_idx, int64_t *d_sel_iter, double *d_w,
                              double *d_hist, int64_t hist_cap,
                              int64_t *h_nc, int64_t *h_n_hist,
                              rbf_greedy_stats *h_stats,
@@ -200,9 +211,12 @@ rbf_status rbf_group_of(int64_t nb, int64_t m, uint64_t seed, int32_t *h_group_o
 /* --------------------------------------------------------------------------
  * Vector-FMA peak microbenchmark of this GPU (dependent-FMA chains on every
  * SM), used as the denominator of the pair kernels' roofline.
- * prec: 32 or 64.  h_flops: host; measured FLOP/s (an FMA counts 2).
+ * prec: 32 (scalar FP32 FMA), 64 (FP64 FMA) or RBF_PEAK_F32X2 (paired FP32
+ * FMA instructions, two FMAs each).  h_flops: host; measured FLOP/s (an FMA
+ * counts 2).
  * SYNCHRONOUS.
  * ------------------------------------------------------------------------ */
+#define RBF_PEAK_F32X2 2
 rbf_status rbf_measure_fma_peak(int prec, double *h_flops, void *stream);
 
 /* Status latched by the last ASYNC call's device work on this device

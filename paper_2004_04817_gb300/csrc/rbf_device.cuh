@@ -42,6 +42,70 @@ __device__ __forceinline__ double phi_f64_s(double s)
 }
 
 // ----------------------------------------------------------------------------
+// Paired FP32: two independent FP32 values in one 64-bit register, operated on
+// by the f32x2 instructions of sm_100-class GPUs (one instruction, two
+// results, each rounded to nearest like its scalar counterpart).
+// ----------------------------------------------------------------------------
+struct f2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void f2_unpack(f2 a, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+// Eq. 2 for two pairs at once, from their squared scaled distances s:
+// s is clamped to 1 (so eta <= 1 and phi = 0 beyond the support radius), then
+// t = 1 - eta, phi = t^4 (4 eta + 1) -- the factored form, whose rounding
+// error stays proportional to |phi'| |d eta|.
+__device__ __forceinline__ f2 phi_f32x2_s(f2 s)
+{
+    float s0, s1;
+    f2_unpack(s, s0, s1);
+    const f2 eta = f2_pack(sqrt_approx(fminf(s0, 1.0f)), sqrt_approx(fminf(s1, 1.0f)));
+    const f2 one = f2_pack(1.0f, 1.0f), four = f2_pack(4.0f, 4.0f);
+    const f2 t = f2_sub(one, eta);
+    const f2 t2 = f2_mul(t, t);
+    return f2_mul(f2_mul(t2, t2), f2_fma(four, eta, one));
+}
+
+// ----------------------------------------------------------------------------
 // Double-float ("ff") arithmetic on the FP32 pipe: a value is the unevaluated
 // sum h + l of two floats (about 48 significant bits).  Built from the
 // error-free transformations of Knuth (TwoSum: the exact rounding error of a
@@ -237,13 +301,19 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 }
 
 // ----------------------------------------------------------------------------
-// Grid barrier for cooperative launches (all CTAs co-resident).  Every wait is
-// bounded: after `limit_ns` the waiting CTA latches RBF_E_TIMEOUT into
-// *status and returns false; callers then leave the kernel.
+// Grid barrier for cooperative launches (all CTAs co-resident).  Flat,
+// contention-free: CTA b publishes its arrival count in its own word
+// (release), and every CTA's warp 0 polls all the words (acquire) until each
+// has reached the same count.  No two CTAs write the same address, so an
+// arrival costs one store instead of a serialised atomic, and the wait ends
+// one L2 round trip after the last arrival.  Every wait is bounded: after
+// `limit_ns` the waiting CTA latches RBF_E_TIMEOUT into *status and returns
+// false; callers then leave the kernel.
 // ----------------------------------------------------------------------------
+constexpr int kBarMaxCtas = 4096;
+
 struct GridBar {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int arrive[kBarMaxCtas];
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
@@ -253,41 +323,50 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
     return v;
 }
 
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// `epoch` counts the barriers this CTA has passed (the same in every CTA).
 __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, unsigned int nblocks,
-                                             uint64_t limit_ns)
+                                             uint64_t limit_ns, unsigned int &epoch)
 {
     __shared__ int s_ok;
+    const unsigned int target = epoch + 1;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         int ok = 1;
-        const unsigned int gen = ld_acquire_u32(&bar->gen);
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
+        if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            const uint64_t t0 = globaltimer_ns();
-            while (ld_acquire_u32(&bar->gen) == gen) {
-                __nanosleep(64);
-                if (*(volatile int *)status == (int)RBF_E_TIMEOUT) {
-                    ok = 0;
-                    break;
-                }
-                if (globaltimer_ns() - t0 > limit_ns) {
-                    atomicExch(status, (int)RBF_E_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
+            st_release_u32(&bar->arrive[blockIdx.x], target);
         }
-        __threadfence();
-        if (ok && *(volatile int *)status == (int)RBF_E_TIMEOUT)
-            ok = 0;
-        s_ok = ok;
+        __syncwarp();
+        const uint64_t t0 = globaltimer_ns();
+        for (;;) {
+            bool mine = true;
+            for (unsigned int b = threadIdx.x; b < nblocks; b += 32)
+                mine &= (int)(ld_acquire_u32(&bar->arrive[b]) - target) >= 0;
+            if (__all_sync(0xffffffffu, mine))
+                break;
+            if (*(volatile int *)status == (int)RBF_E_TIMEOUT) {
+                ok = 0;
+                break;
+            }
+            if (globaltimer_ns() - t0 > limit_ns) {
+                if (threadIdx.x == 0)
+                    atomicExch(status, (int)RBF_E_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0)
+            s_ok = ok;
     }
     __syncthreads();
+    epoch = target;
     return s_ok != 0;
 }
 

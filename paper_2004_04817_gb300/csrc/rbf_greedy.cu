@@ -59,6 +59,7 @@ struct GreedyCtl {
     double final_max;
     double final_rms;
     double min_pivot;
+    double max_resid;
     long long n_hist;
 };
 
@@ -73,6 +74,7 @@ struct GreedyArgs {
     double tol;
     int tol_mode;
     int flags;
+    unsigned long long barrier_ns;   // bound of every grid-barrier wait
     int ld;                       // leading dimension of Z, Z^T (= nc_max)
     int32_t *sel_idx;
     int64_t *sel_iter;
@@ -100,6 +102,10 @@ struct GreedyArgs {
     double *zt;                   // Z^T, row-major, ld
     double *bvec;
     double *lvec;
+    D4 *rvec;                     // refinement residual / correction vectors
+    D4 *tvec;
+    double *w_out;                // optional FP64 weights output (nc x 3)
+    int refine_steps;
 };
 
 __device__ __forceinline__ int goff(int i, int nb, int m)
@@ -355,7 +361,7 @@ struct EvalOut {
 constexpr int kAppendOk = 0, kAppendTimeout = 1, kAppendNotSpd = 2;
 
 __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, double &min_piv,
-                           int pn, int node, long long kiter)
+                           int pn, int node, long long kiter, unsigned int &epoch)
 {
     GreedyCtl *ctl = a.ctl;
     const int G = gridDim.x;
@@ -370,7 +376,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
         const double dx = xn.x - c.x, dy = xn.y - c.y, dz = xn.z - c.z;
         a.bvec[j] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
     }
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) return kAppendTimeout;
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) return kAppendTimeout;
     // A2: l = Z b (warp per row) and partial sums of l.l and l.y
     double acc4[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = gwarp; i < nc; i += gwarps) {
@@ -392,7 +398,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
     if (tid == 0)
         for (int c = 0; c < 4; ++c)
             (a.part + (size_t)(use & 1) * kMaxGrid * 4)[4 * blockIdx.x + c] = acc4[c];
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) return kAppendTimeout;
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) return kAppendTimeout;
     double s4[4];
     grid_sum4((a.part + (size_t)(use & 1) * kMaxGrid * 4), G, s4);
     ++use;
@@ -425,6 +431,13 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
             a.w64[j] = w;
             a.cw32[2 * j + 1] = make_float4((float)w.x, (float)w.y, (float)w.z,
                                             (float)(fabs(w.x) + fabs(w.y) + fabs(w.z)));
+            float hx, lx, hy, ly, hz, lz;
+            split_f64(w.x, hx, lx);
+            split_f64(w.y, hy, ly);
+            split_f64(w.z, hz, lz);
+            a.cwff[4 * j + 2] =
+                make_float4(hx, hy, hz, (float)(fabs(w.x) + fabs(w.y) + fabs(w.z)));
+            a.cwff[4 * j + 3] = make_float4(lx, ly, lz, 0.0f);
         }
     }
     if (blockIdx.x == 0 && tid == 0) {
@@ -457,9 +470,112 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
         if (a.sel_iter)
             a.sel_iter[nc] = kiter;
     }
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) return kAppendTimeout;
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) return kAppendTimeout;
     ++nc;
     return kAppendOk;
+}
+
+
+// ---------------------------------------------------------------------------
+// FP64 iterative refinement of the support weights (Sec. 2: Phi_SS is SPD,
+// solved through its Cholesky factor): `steps` times
+//   r = dX_S - Phi_SS W (recomputed from coordinates),  W += Z^T (Z r),
+// then the residual of the final W; `maxres` = max_j |r_j|_inf.  Support node
+// j sits at position spos[j] (identity when spos is null).  All CTAs call it.
+// ---------------------------------------------------------------------------
+__device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
+                               unsigned int &epoch, int steps, const int32_t *spos, D4 *rvec,
+                               D4 *tvec, double &maxres)
+{
+    GreedyCtl *ctl = a.ctl;
+    const int G = gridDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gtid = blockIdx.x * kGThreads + tid;
+    const int gthreads = G * kGThreads;
+    const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
+    const int ts = team_size(nc, G);
+    const int sub = lane & (ts - 1);
+    const int team = gtid / ts, nteams = gthreads / ts;
+    const int rounds = (nc + nteams - 1) / nteams;
+    for (int step = 0; step <= steps; ++step) {
+        double lmax = 0.0;
+        for (int it = 0; it < rounds; ++it) {
+            const int q = team + it * nteams;
+            const bool act = q < nc;
+            const int pos = act ? (spos ? ldcg(spos + q) : q) : (spos ? ldcg(spos) : 0);
+            const D4 r = team_resid_f64(a, pos, nc, sub, ts);
+            if (act && sub == 0) {
+                rvec[q] = r;
+                lmax = fmax(lmax, fmax(fabs(r.x), fmax(fabs(r.y), fabs(r.z))));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        __syncthreads();
+        if (lane == 0)
+            red.v[warp] = lmax;
+        __syncthreads();
+        double *pp = a.part + (size_t)(use & 1) * kMaxGrid * 4;
+        if (tid == 0) {
+            for (int k = 1; k < kGWarps; ++k)
+                lmax = fmax(lmax, red.v[k]);
+            pp[4 * blockIdx.x] = lmax;
+        }
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch))
+            return false;
+        {
+            double g4[4];
+            grid_max4(pp, G, g4);
+            maxres = g4[0];
+            ++use;
+        }
+        if (step == steps)
+            break;
+        // t = Z r (3 right-hand sides, warp per row)
+        for (int i = gwarp; i < nc; i += gwarps) {
+            const double *zr = a.z + (size_t)i * a.ld;
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int p = lane; p <= i; p += 32) {
+                const double zz = ldcg(zr + p);
+                const D4 r = ldcg(rvec + p);
+                sx = fma(zz, r.x, sx);
+                sy = fma(zz, r.y, sy);
+                sz = fma(zz, r.z, sz);
+            }
+            sx = warp_sum_f64(sx);
+            sy = warp_sum_f64(sy);
+            sz = warp_sum_f64(sz);
+            if (lane == 0)
+                tvec[i] = mk4(sx, sy, sz, 0.0);
+        }
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch))
+            return false;
+        // W += Z^T t
+        for (int j = gwarp; j < nc; j += gwarps) {
+            const double *ztr = a.zt + (size_t)j * a.ld;
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int i = j + lane; i < nc; i += 32) {
+                const double zz = ldcg(ztr + i);
+                const D4 t = ldcg(tvec + i);
+                sx = fma(zz, t.x, sx);
+                sy = fma(zz, t.y, sy);
+                sz = fma(zz, t.z, sz);
+            }
+            sx = warp_sum_f64(sx);
+            sy = warp_sum_f64(sy);
+            sz = warp_sum_f64(sz);
+            if (lane == 0) {
+                D4 w = ldcg(a.w64 + j);
+                w.x += sx;
+                w.y += sy;
+                w.z += sz;
+                a.w64[j] = w;
+            }
+        }
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch))
+            return false;
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -478,18 +594,24 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
     const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
     const int nb = a.nb, m = a.m;
     int use = 0;   // partial-buffer use counter (double buffering)
+    unsigned int epoch = 0;   // grid barriers passed
     auto part = [&](int u) { return a.part + (size_t)(u & 1) * kMaxGrid * 4; };
     auto parti = [&](int u) { return a.parti + (size_t)(u & 1) * kMaxGrid; };
 #define GSYNC()                                                                   \
     do {                                                                          \
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) \
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) \
             return;                                                               \
     } while (0)
 #define GSYNC_B()                                                                 \
     do {                                                                          \
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) \
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) \
             return false;                                                         \
     } while (0)
+
+    // Failure-path test: CTA 0 leaves before the first barrier, so the other
+    // CTAs' bounded waits run out and the launch returns RBF_E_TIMEOUT.
+    if ((a.flags & RBF_FLAG_TEST_BARRIER_TIMEOUT) && blockIdx.x == 0)
+        return;
 
     // ---------------- prologue: group-ordered packing ----------------------
     double dmax = 0.0, xmax = 0.0;
@@ -582,7 +704,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
 
     for (int s = 0; s < 3; ++s) {
         const int pn = ldcg(a.pos_of_node + seeds[s]);
-        if (chol_append(a, red, nc, use, min_piv, pn, seeds[s], -1) != kAppendOk) {
+        if (chol_append(a, red, nc, use, min_piv, pn, seeds[s], -1, epoch) != kAppendOk) {
             if (blockIdx.x == 0 && tid == 0) {
                 ctl->nc = nc;
                 ctl->min_pivot = min_piv;
@@ -850,7 +972,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                 status = RBF_E_NC_MAX;
                 break;
             }
-            if (chol_append(a, red, nc, use, min_piv, add_pos, add_node, k) != kAppendOk) {
+            if (chol_append(a, red, nc, use, min_piv, add_pos, add_node, k, epoch) != kAppendOk) {
                 status = RBF_E_NOT_SPD;   // or the latched timeout, which wins
                 break;
             }
@@ -884,9 +1006,23 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
         if (idle >= m)
             break;
     }
+    // final weights of the selected set (row a9): FP64 refinement with Z
+    double maxres = -1.0;
+    if (a.w_out && nc > 0) {
+        if (!refine_weights(a, red, nc, use, epoch, a.refine_steps, a.spos, a.rvec, a.tvec,
+                            maxres))
+            return;
+        for (int j = gtid; j < nc; j += gthreads) {
+            const D4 w = ldcg(a.w64 + j);
+            a.w_out[3 * j] = w.x;
+            a.w_out[3 * j + 1] = w.y;
+            a.w_out[3 * j + 2] = w.z;
+        }
+    }
     if (blockIdx.x == 0 && tid == 0) {
         if (status != RBF_OK)
             atomicCAS(&ctl->status, (int)RBF_OK, status);
+        ctl->max_resid = maxres;
         ctl->estar = estar;
         ctl->nc = nc;
         ctl->iterations = k - 3 + 1;
@@ -923,10 +1059,11 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
     const int gthreads = G * kGThreads;
     const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
     int use = 0;
+    unsigned int epoch = 0;
     auto part = [&](int u) { return a.part + (size_t)(u & 1) * kMaxGrid * 4; };
 #define GSYNC()                                                                   \
     do {                                                                          \
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, kBarrierLimitNs)) \
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) \
             return;                                                               \
     } while (0)
 
@@ -976,7 +1113,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
     double min_piv = INFINITY;
     for (int j = 0; j < nc_total; ++j) {
         const int node = sel[j];
-        const int r = chol_append(a, red, nc, use, min_piv, j, node, -1);
+        const int r = chol_append(a, red, nc, use, min_piv, j, node, -1, epoch);
         if (r != kAppendOk) {
             if (blockIdx.x == 0 && tid == 0) {
                 ctl->nc = nc;
@@ -985,85 +1122,9 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
             return;
         }
     }
-    const int ts = team_size(nc, G);
-    const int sub = lane & (ts - 1);
-    const int team = gtid / ts, nteams = gthreads / ts;
-    const int rounds = (nc + nteams - 1) / nteams;
     double maxres = 0.0;
-    for (int step = 0; step <= steps; ++step) {
-        // residual r = dX_S - Phi_SS W
-        double lmax = 0.0;
-        for (int it = 0; it < rounds; ++it) {
-            const int q = team + it * nteams;
-            const bool act = q < nc;
-            const D4 r = team_resid_f64(a, act ? q : 0, nc, sub, ts);
-            if (act && sub == 0) {
-                rvec[q] = r;
-                lmax = fmax(lmax, fmax(fabs(r.x), fmax(fabs(r.y), fabs(r.z))));
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1)
-            lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        __syncthreads();
-        if (lane == 0)
-            red.v[warp] = lmax;
-        __syncthreads();
-        if (tid == 0) {
-            for (int k = 1; k < kGWarps; ++k)
-                lmax = fmax(lmax, red.v[k]);
-            part(use)[4 * blockIdx.x] = lmax;
-        }
-        GSYNC();
-        {
-            double g4[4];
-            grid_max4(part(use), G, g4);
-            maxres = g4[0];
-            ++use;
-        }
-        if (step == steps)
-            break;
-        // t = Z r (3 right-hand sides, warp per row)
-        for (int i = gwarp; i < nc; i += gwarps) {
-            const double *zr = a.z + (size_t)i * a.ld;
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int p = lane; p <= i; p += 32) {
-                const double zz = ldcg(zr + p);
-                const D4 r = ldcg(rvec + p);
-                sx = fma(zz, r.x, sx);
-                sy = fma(zz, r.y, sy);
-                sz = fma(zz, r.z, sz);
-            }
-            sx = warp_sum_f64(sx);
-            sy = warp_sum_f64(sy);
-            sz = warp_sum_f64(sz);
-            if (lane == 0)
-                tvec[i] = mk4(sx, sy, sz, 0.0);
-        }
-        GSYNC();
-        // W += Z^T t
-        for (int j = gwarp; j < nc; j += gwarps) {
-            const double *ztr = a.zt + (size_t)j * a.ld;
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int i = j + lane; i < nc; i += 32) {
-                const double zz = ldcg(ztr + i);
-                const D4 t = ldcg(tvec + i);
-                sx = fma(zz, t.x, sx);
-                sy = fma(zz, t.y, sy);
-                sz = fma(zz, t.z, sz);
-            }
-            sx = warp_sum_f64(sx);
-            sy = warp_sum_f64(sy);
-            sz = warp_sum_f64(sz);
-            if (lane == 0) {
-                D4 w = ldcg(a.w64 + j);
-                w.x += sx;
-                w.y += sy;
-                w.z += sz;
-                a.w64[j] = w;
-            }
-        }
-        GSYNC();
-    }
+    if (!refine_weights(a, red, nc, use, epoch, steps, nullptr, rvec, tvec, maxres))
+        return;
     for (int j = gtid; j < nc; j += gthreads) {
         const D4 w = ldcg(a.w64 + j);
         w_out[3 * j] = w.x;
@@ -1083,7 +1144,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
 // ---------------------------------------------------------------------------
 struct GreedyWs {
     size_t ctl, part, parti, perm, node_of_pos, pos_of_node, xg64, dg64, xg32, in_s, u32, e64,
-        spos, c64, w64, cw32, cwff, y64, z, zt, bvec, lvec, total;
+        spos, c64, w64, cw32, cwff, y64, z, zt, bvec, lvec, rvec, tvec, total;
 };
 
 static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
@@ -1117,6 +1178,8 @@ static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
     L.zt = take(sizeof(double) * ncm * ncm);
     L.bvec = take(sizeof(double) * ncm);
     L.lvec = take(sizeof(double) * ncm);
+    L.rvec = take(sizeof(D4) * ncm);
+    L.tvec = take(sizeof(D4) * ncm);
     L.total = o;
     return L;
 }
@@ -1129,7 +1192,7 @@ static bool greedy_args_ok(int64_t nb, const rbf_params *p)
            (p->tol_mode == 0 || p->tol_mode == 1) &&
            (p->eval_prec == RBF_PREC_F32 || p->eval_prec == RBF_PREC_F64 ||
             p->eval_prec == RBF_PREC_F32X2) &&
-           (p->flags & ~RBF_FLAG_HISTORY_FULL) == 0;
+           (p->flags & ~(RBF_FLAG_HISTORY_FULL | RBF_FLAG_TEST_BARRIER_TIMEOUT)) == 0;
 }
 
 }  // namespace rbf
@@ -1179,6 +1242,8 @@ static void fill_args(GreedyArgs &a, char *ws, const GreedyWs &L)
     a.zt = (double *)(ws + L.zt);
     a.bvec = (double *)(ws + L.bvec);
     a.lvec = (double *)(ws + L.lvec);
+    a.rvec = (D4 *)(ws + L.rvec);
+    a.tvec = (D4 *)(ws + L.tvec);
 }
 }  // namespace rbf
 
@@ -1193,13 +1258,14 @@ extern "C" size_t rbf_greedy_workspace_bytes(int64_t nb, const rbf_params *p)
 
 extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, int64_t nb,
                                         const rbf_params *p, int32_t *d_sel_idx,
-                                        int64_t *d_sel_iter, double *d_hist, int64_t hist_cap,
+                                        int64_t *d_sel_iter, double *d_w, double *d_hist,
+                                        int64_t hist_cap,
                                         int64_t *h_nc, int64_t *h_n_hist,
                                         rbf_greedy_stats *h_stats, void *d_ws, size_t ws_bytes,
                                         void *stream)
 {
     if (!greedy_args_ok(nb, p) || !d_xb || !d_db || !d_sel_idx || !h_nc || hist_cap < 0 ||
-        (hist_cap > 0 && !d_hist))
+        (hist_cap > 0 && !d_hist) || p->refine_steps < 0 || p->refine_steps > 16)
         return RBF_E_ARG;
     const GreedyWs L = greedy_ws_layout(nb, p->nc_max);
     if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
@@ -1229,11 +1295,14 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
     a.tol = p->tol;
     a.tol_mode = p->tol_mode;
     a.flags = p->flags;
+    a.barrier_ns = (p->flags & RBF_FLAG_TEST_BARRIER_TIMEOUT) ? 50000000ull : kBarrierLimitNs;
     a.ld = (int)p->nc_max;
     a.sel_idx = d_sel_idx;
     a.sel_iter = d_sel_iter;
     a.hist = hist_cap > 0 ? d_hist : nullptr;
     a.hist_cap = hist_cap;
+    a.w_out = d_w;
+    a.refine_steps = p->refine_steps;
     fill_args(a, ws, L);
 
     const size_t smem =
@@ -1278,6 +1347,7 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
         h_stats->final_max = ctl.final_max;
         h_stats->final_rms = ctl.final_rms;
         h_stats->min_pivot = ctl.min_pivot;
+        h_stats->max_resid = ctl.max_resid;
     }
     return (rbf_status)ctl.status;
 }
@@ -1318,6 +1388,7 @@ extern "C" rbf_status rbf_solve_weights(const double *d_xb, const double *d_db, 
     a.nc_max = (int)nc;
     a.prec = RBF_PREC_F64;
     a.inv_r = 1.0 / p->radius;
+    a.barrier_ns = kBarrierLimitNs;
     a.ld = (int)nc;
     a.sel_idx = (int32_t *)(ws + L.sel);
     a.sel_iter = nullptr;

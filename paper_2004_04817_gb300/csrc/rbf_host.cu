@@ -69,6 +69,29 @@ __global__ void __launch_bounds__(512) k_fma_peak(T *out, int iters, T a, T b)
         out[blockIdx.x] = s;
 }
 
+// Paired-FP32 variant: 8 independent chains of f32x2 FMAs per thread.
+__global__ void __launch_bounds__(512) k_fma_peak_f2(float *out, int iters, float a, float b)
+{
+    const f2 A = f2_pack(a, a), B = f2_pack(b, b);
+    const float x = (float)threadIdx.x;
+    f2 x0 = f2_pack(x, x + 1), x1 = f2_pack(x + 2, x + 3), x2 = f2_pack(x + 4, x + 5);
+    f2 x3 = f2_pack(x + 6, x + 7), x4 = f2_pack(x + 8, x + 9), x5 = f2_pack(x + 10, x + 11);
+    f2 x6 = f2_pack(x + 12, x + 13), x7 = f2_pack(x + 14, x + 15);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            x0 = f2_fma(x0, A, B); x1 = f2_fma(x1, A, B); x2 = f2_fma(x2, A, B);
+            x3 = f2_fma(x3, A, B); x4 = f2_fma(x4, A, B); x5 = f2_fma(x5, A, B);
+            x6 = f2_fma(x6, A, B); x7 = f2_fma(x7, A, B);
+        }
+    }
+    f2 s = f2_add(f2_add(f2_add(x0, x1), f2_add(x2, x3)), f2_add(f2_add(x4, x5), f2_add(x6, x7)));
+    float lo, hi;
+    f2_unpack(s, lo, hi);
+    if (lo + hi == -12345.0f)   // never true; keeps the chains alive
+        out[blockIdx.x] = lo;
+}
+
 }  // namespace rbf
 
 using namespace rbf;
@@ -112,14 +135,14 @@ extern "C" rbf_status rbf_last_device_status(void)
 
 extern "C" rbf_status rbf_measure_fma_peak(int prec, double *h_flops, void *stream)
 {
-    if (!h_flops || (prec != 32 && prec != 64))
+    if (!h_flops || (prec != 32 && prec != 64 && prec != RBF_PEAK_F32X2))
         return RBF_E_ARG;
     DeviceInfo dev;
     if (!device_info(&dev))
         return RBF_E_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const int threads = 512, blocks = dev.sms * 4;
-    const int iters = prec == 32 ? 4096 : 256;
+    const int iters = prec == 64 ? 256 : 4096;
     void *out = nullptr;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
@@ -131,6 +154,8 @@ extern "C" rbf_status rbf_measure_fma_peak(int prec, double *h_flops, void *stre
         cudaEventRecord(e0, st);
         if (prec == 32)
             k_fma_peak<float><<<blocks, threads, 0, st>>>((float *)out, iters, 0.999f, 0.001f);
+        else if (prec == RBF_PEAK_F32X2)
+            k_fma_peak_f2<<<blocks, threads, 0, st>>>((float *)out, iters, 0.999f, 0.001f);
         else
             k_fma_peak<double><<<blocks, threads, 0, st>>>((double *)out, iters, 0.999, 0.001);
         cudaEventRecord(e1, st);
@@ -147,7 +172,8 @@ extern "C" rbf_status rbf_measure_fma_peak(int prec, double *h_flops, void *stre
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess)
         return RBF_E_CUDA;
-    const double fmas = (double)blocks * threads * iters * 16.0 * 8.0;
+    const double fmas = (double)blocks * threads * iters * 16.0 * 8.0 *
+                        (prec == RBF_PEAK_F32X2 ? 2.0 : 1.0);
     *h_flops = 2.0 * fmas / (best_ms * 1e-3);
     return RBF_OK;
 }

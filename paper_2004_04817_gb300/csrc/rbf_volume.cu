@@ -16,8 +16,8 @@
 namespace rbf {
 
 constexpr int kVolThreads = 256;
-constexpr int kVolQ = 4;               // points per thread (register blocking)
-constexpr int kTileF32 = 2048;         // centres per shared-memory tile (64 KB)
+constexpr int kVolP = 2;               // paired registers per thread (4 points)
+constexpr int kTileF32 = 2048;         // centres per shared-memory tile (96 KB)
 constexpr int kTileF64 = 1024;         // centres per shared-memory tile (64 KB)
 constexpr int kTileFF = 1024;          // double-float centres per tile (64 KB)
 constexpr int kVolQFF = 2;             // points per thread, double-float kernel
@@ -82,8 +82,11 @@ __global__ void k_pack_centres(const double *__restrict__ xb, const int32_t *__r
         const double cx = xb[3 * n] * inv_r, cy = xb[3 * n + 1] * inv_r, cz = xb[3 * n + 2] * inv_r;
         const double wx = w[3 * j], wy = w[3 * j + 1], wz = w[3 * j + 2];
         if (c32) {
-            c32[2 * j] = make_float4((float)cx, (float)cy, (float)cz, 0.0f);
-            c32[2 * j + 1] = make_float4((float)wx, (float)wy, (float)wz, 0.0f);
+            const float fx = (float)cx, fy = (float)cy, fz = (float)cz;
+            const float gx = (float)wx, gy = (float)wy, gz = (float)wz;
+            c32[3 * j] = make_float4(fx, fx, fy, fy);
+            c32[3 * j + 1] = make_float4(fz, fz, gx, gx);
+            c32[3 * j + 2] = make_float4(gy, gy, gz, gz);
         }
         if (c64) {
             c64[2 * j] = mk4(cx, cy, cz, 0.0);
@@ -93,62 +96,83 @@ __global__ void k_pack_centres(const double *__restrict__ xb, const int32_t *__r
 }
 
 // ---------------------------------------------------------------------------
-// FP32 pair sum.
+// FP32 pair sum.  Each thread owns 2 * P volume points as P pairs in paired
+// FP32 registers; the shared-memory table stores every centre duplicated,
+// (cx, cx, cy, cy), (cz, cz, wx, wx), (wy, wy, wz, wz), so three broadcast
+// 16-byte loads give the paired operands directly.  A pair of pairs costs 14
+// paired instructions, two min and two MUFU square roots.
 // ---------------------------------------------------------------------------
-template <int Q>
+template <int P>
 __global__ void __launch_bounds__(kVolThreads)
 k_volume_f32(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ cw, int nc,
              double *__restrict__ out)
 {
     extern __shared__ float4 s_cw[];
     const int tid = threadIdx.x;
-    const int64_t per_block = (int64_t)kVolThreads * Q;
+    const int64_t per_block = (int64_t)kVolThreads * 2 * P;
     const bool one_tile = nc <= kTileF32;
     if (one_tile) {
-        for (int j = tid; j < 2 * nc; j += kVolThreads)
+        for (int j = tid; j < 3 * nc; j += kVolThreads)
             s_cw[j] = cw[j];
         __syncthreads();
     }
     for (int64_t base = blockIdx.x * per_block; base < nv; base += (int64_t)gridDim.x * per_block) {
-        float qx[Q], qy[Q], qz[Q], ax[Q], ay[Q], az[Q];
+        f2 qx[P], qy[P], qz[P], ax[P], ay[P], az[P];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            int64_t v = base + (int64_t)i * kVolThreads + tid;
-            v = v < nv ? v : nv - 1;
-            const float4 p = xq[v];
-            qx[i] = p.x; qy[i] = p.y; qz[i] = p.z;
-            ax[i] = 0.0f; ay[i] = 0.0f; az[i] = 0.0f;
+        for (int i = 0; i < P; ++i) {
+            int64_t v0 = base + (int64_t)(2 * i) * kVolThreads + tid;
+            int64_t v1 = v0 + kVolThreads;
+            v0 = v0 < nv ? v0 : nv - 1;
+            v1 = v1 < nv ? v1 : nv - 1;
+            const float4 p0 = xq[v0], p1 = xq[v1];
+            qx[i] = f2_pack(p0.x, p1.x);
+            qy[i] = f2_pack(p0.y, p1.y);
+            qz[i] = f2_pack(p0.z, p1.z);
+            ax[i] = f2_pack(0.0f, 0.0f);
+            ay[i] = ax[i];
+            az[i] = ax[i];
         }
         for (int t0 = 0; t0 < nc; t0 += kTileF32) {
             const int nt = min(kTileF32, nc - t0);
             if (!one_tile) {
                 __syncthreads();
-                for (int j = tid; j < 2 * nt; j += kVolThreads)
-                    s_cw[j] = cw[2 * t0 + j];
+                for (int j = tid; j < 3 * nt; j += kVolThreads)
+                    s_cw[j] = cw[3 * t0 + j];
                 __syncthreads();
             }
 #pragma unroll 2
             for (int j = 0; j < nt; ++j) {
-                const float4 c = s_cw[2 * j];
-                const float4 w = s_cw[2 * j + 1];
+                const float4 A = s_cw[3 * j], B = s_cw[3 * j + 1], C = s_cw[3 * j + 2];
+                const f2 cx = f2_pack(A.x, A.y), cy = f2_pack(A.z, A.w), cz = f2_pack(B.x, B.y);
+                const f2 wx = f2_pack(B.z, B.w), wy = f2_pack(C.x, C.y), wz = f2_pack(C.z, C.w);
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const float dx = qx[i] - c.x, dy = qy[i] - c.y, dz = qz[i] - c.z;
-                    const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    const float ph = phi_f32_s(s);
-                    ax[i] = fmaf(w.x, ph, ax[i]);
-                    ay[i] = fmaf(w.y, ph, ay[i]);
-                    az[i] = fmaf(w.z, ph, az[i]);
+                for (int i = 0; i < P; ++i) {
+                    const f2 dx = f2_sub(qx[i], cx), dy = f2_sub(qy[i], cy), dz = f2_sub(qz[i], cz);
+                    const f2 s = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+                    const f2 ph = phi_f32x2_s(s);
+                    ax[i] = f2_fma(wx, ph, ax[i]);
+                    ay[i] = f2_fma(wy, ph, ay[i]);
+                    az[i] = f2_fma(wz, ph, az[i]);
                 }
             }
         }
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int64_t v = base + (int64_t)i * kVolThreads + tid;
-            if (v < nv) {
-                out[3 * v] = (double)ax[i];
-                out[3 * v + 1] = (double)ay[i];
-                out[3 * v + 2] = (double)az[i];
+        for (int i = 0; i < P; ++i) {
+            float x0, x1, y0, y1, z0, z1;
+            f2_unpack(ax[i], x0, x1);
+            f2_unpack(ay[i], y0, y1);
+            f2_unpack(az[i], z0, z1);
+            const int64_t v0 = base + (int64_t)(2 * i) * kVolThreads + tid;
+            const int64_t v1 = v0 + kVolThreads;
+            if (v0 < nv) {
+                out[3 * v0] = (double)x0;
+                out[3 * v0 + 1] = (double)y0;
+                out[3 * v0 + 2] = (double)z0;
+            }
+            if (v1 < nv) {
+                out[3 * v1] = (double)x1;
+                out[3 * v1 + 1] = (double)y1;
+                out[3 * v1 + 2] = (double)z1;
             }
         }
     }
@@ -275,7 +299,7 @@ static VolumeWs volume_ws_layout(int64_t nv, int64_t nc, int prec)
         o = align_up(o + sizeof(float4) * (size_t)nv, 256);
     L.off_c32 = o;
     if (prec == RBF_PREC_F32)
-        o = align_up(o + sizeof(float4) * 2 * (size_t)nc, 256);
+        o = align_up(o + sizeof(float4) * 3 * (size_t)nc, 256);
     L.off_c64 = o;
     if (prec == RBF_PREC_F64)
         o = align_up(o + sizeof(D4) * 2 * (size_t)nc, 256);
@@ -341,20 +365,21 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
         k_pack_points_f32<<<pb, 256, 0, st>>>(d_xv, nv, inv_r, xq);
         const int cb = (int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4);
         k_pack_centres<<<cb, 256, 0, st>>>(d_xb, d_sel_idx, d_w, nc, inv_r, c32, nullptr);
-        const size_t smem = sizeof(float4) * 2 * (size_t)std::min<int64_t>(nc, kTileF32);
+        const size_t smem = sizeof(float4) * 3 * (size_t)std::min<int64_t>(nc, kTileF32);
         static int occ = -1;
         if (occ < 0) {
-            cudaFuncSetAttribute(k_volume_f32<kVolQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(float4) * 2 * kTileF32));
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_volume_f32<kVolQ>, kVolThreads,
-                                                              sizeof(float4) * 2 * kTileF32) !=
+            cudaFuncSetAttribute(k_volume_f32<kVolP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float4) * 3 * kTileF32));
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_volume_f32<kVolP>, kVolThreads,
+                                                              sizeof(float4) * 3 * kTileF32) !=
                     cudaSuccess ||
                 occ < 1)
                 occ = 1;
         }
-        const int64_t want = (nv + (int64_t)kVolThreads * kVolQ - 1) / ((int64_t)kVolThreads * kVolQ);
+        const int64_t per = (int64_t)kVolThreads * 2 * kVolP;
+        const int64_t want = (nv + per - 1) / per;
         const int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms * occ);
-        k_volume_f32<kVolQ><<<grid, kVolThreads, smem, st>>>(xq, nv, c32, (int)nc, d_dv);
+        k_volume_f32<kVolP><<<grid, kVolThreads, smem, st>>>(xq, nv, c32, (int)nc, d_dv);
     } else if (p->eval_prec == RBF_PREC_F32X2) {
         float4 *xh = (float4 *)(ws + L.off_xh), *xl = (float4 *)(ws + L.off_xl);
         float4 *cff = (float4 *)(ws + L.off_cff);

@@ -56,6 +56,7 @@ class GreedyStats(C.Structure):
         ("final_max", C.c_double),
         ("final_rms", C.c_double),
         ("min_pivot", C.c_double),
+        ("max_resid", C.c_double),
     ]
 
 
@@ -75,7 +76,7 @@ def lib():
         L.rbf_greedy_workspace_bytes.restype = C.c_size_t
         L.rbf_greedy_workspace_bytes.argtypes = [C.c_int64, P]
         L.rbf_greedy_select.restype = C.c_int
-        L.rbf_greedy_select.argtypes = [_vp, _vp, C.c_int64, P, _vp, _vp, _vp, C.c_int64,
+        L.rbf_greedy_select.argtypes = [_vp, _vp, C.c_int64, P, _vp, _vp, _vp, _vp, C.c_int64,
                                         C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(GreedyStats), _vp, C.c_size_t, _vp]
         L.rbf_solve_workspace_bytes.restype = C.c_size_t
@@ -145,13 +146,14 @@ def make_params(radius, tol=0.0, tol_mode=1, eval_prec=PREC_F64, m=1, seed=1, nc
 
 
 def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
-                  eval_prec=PREC_F64, hist_cap=0, history_full=False, stream=None,
-                  workspace=None):
+                  eval_prec=PREC_F64, hist_cap=0, history_full=False, weights=False,
+                  refine_steps=2, stream=None, workspace=None):
     """GCB greedy (m = 1: plain greedy).  Returns a dict with ``idx`` (int32
     CUDA tensor, selection order), ``iter`` (int64), ``nc``, ``hist`` (CUDA
     (n, 6) or None), ``stats`` (dict) and ``status`` (0 or RBF_E_NC_MAX).
     ``history_full`` adds FP64 all-node maxima to the history after every
-    m-th iteration (diagnostic)."""
+    m-th iteration (diagnostic).  ``weights`` also returns ``w``, the refined
+    FP64 weights of the selected set."""
     L = lib()
     _dev(xb, torch.float64, "xb", 3)
     _dev(db, torch.float64, "db", 3)
@@ -159,7 +161,7 @@ def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
     if db.shape[0] != nb:
         raise ValueError("xb and db must have the same number of rows")
     nc_max = int(nc_max or min(nb, 4096))
-    p = make_params(radius, tol, tol_mode, eval_prec, m, seed, nc_max,
+    p = make_params(radius, tol, tol_mode, eval_prec, m, seed, nc_max, refine_steps,
                     flags=FLAG_HISTORY_FULL if history_full else 0)
     need = L.rbf_greedy_workspace_bytes(nb, C.byref(p))
     if need == 0:
@@ -168,17 +170,19 @@ def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
         _workspace(need, xb.device)
     idx = torch.empty(nc_max, dtype=torch.int32, device=xb.device)
     it = torch.empty(nc_max, dtype=torch.int64, device=xb.device)
+    w = torch.empty((nc_max, 3), dtype=torch.float64, device=xb.device) if weights else None
     hist = torch.empty((hist_cap, HIST_COLS), dtype=torch.float64, device=xb.device) \
         if hist_cap else None
     nc = C.c_int64(0)
     nh = C.c_int64(0)
     stats = GreedyStats()
     st = L.rbf_greedy_select(_ptr(xb), _ptr(db), nb, C.byref(p), _ptr(idx), _ptr(it),
-                             _ptr(hist), int(hist_cap), C.byref(nc), C.byref(nh),
+                             _ptr(w), _ptr(hist), int(hist_cap), C.byref(nc), C.byref(nh),
                              C.byref(stats), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "rbf_greedy_select", allow=(E_NC_MAX,))
     n = nc.value
     return dict(idx=idx[:n], iter=it[:n], nc=n, status=st,
+                w=w[:n] if w is not None else None,
                 hist=hist[:min(nh.value, hist_cap)] if hist is not None else None,
                 n_hist=nh.value,
                 stats={f: getattr(stats, f) for f, _ in GreedyStats._fields_})

@@ -166,6 +166,20 @@ def test_solve_weights_matches_oracle_and_reproduces():
     assert res <= 1e-10 * dmax
 
 
+@pytest.mark.parametrize("prec", [P.PREC_F64, P.PREC_F32X2])
+def test_greedy_weights_match_oracle(prec):
+    """Weights from the greedy's own factor + FP64 refinement (row a9)."""
+    c = synth.wing_small(n_vol=0)
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    r = P.greedy_select(cuda(c["xb"]), cuda(c["db"]), radius=c["radius"], tol=estar,
+                        tol_mode=0, m=7, seed=1, eval_prec=prec, weights=True, refine_steps=2)
+    S = host(r["idx"])
+    Wo, st, _ = oracle.solve_weights(c["xb"], c["db"], S, c["radius"])
+    dmax = np.abs(c["db"]).max()
+    assert np.abs(host(r["w"]) - Wo).max() <= 1e-5 * dmax
+    assert 0 <= r["stats"]["max_resid"] <= 1e-10 * dmax
+
+
 def test_solve_duplicate_support_not_spd():
     c = synth.tiny_wing(n_span=4, n_chord=20)
     S = np.array([0, 5, 9, 5], dtype=np.int32)
@@ -244,3 +258,27 @@ def test_volume_compact_support_and_edges():
     zero_c = host(P.deform_volume(cuda(xv), cuda(xb), cuda(np.zeros(0), torch.int32),
                                   cuda(np.zeros((0, 3))), radius=R))
     assert np.all(zero_c == 0.0)
+
+
+# ------------------------------------------------------------ failure path --
+def test_barrier_timeout_returns_status_and_context_survives():
+    """One CTA skips the grid barrier (test flag): the bounded waits expire,
+    the call returns RBF_E_TIMEOUT, and the next call works."""
+    import ctypes as C
+    from paper_2004_04817_gb300 import rbf
+    c = synth.tiny_wing(n_span=6, n_chord=30, radius=1.0)
+    xb, db = cuda(c["xb"]), cuda(c["db"])
+    L = P.lib()
+    p = rbf.make_params(1.0, 2e-3, 1, P.PREC_F64, m=1, nc_max=100, flags=1 << 30)
+    ws = torch.empty(L.rbf_greedy_workspace_bytes(xb.shape[0], C.byref(p)), dtype=torch.uint8,
+                     device="cuda")
+    idx = torch.empty(100, dtype=torch.int32, device="cuda")
+    nc = C.c_int64(0)
+    st = L.rbf_greedy_select(xb.data_ptr(), db.data_ptr(), xb.shape[0], C.byref(p),
+                             idx.data_ptr(), None, None, None, 0, C.byref(nc), None, None,
+                             ws.data_ptr(), ws.numel(),
+                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 6
+    r, estar = run_greedy(c, 1, P.PREC_F64, 2e-3)
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1, history=False)
+    assert host(r["idx"]).tolist() == o["idx"].tolist()

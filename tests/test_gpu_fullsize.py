@@ -59,13 +59,15 @@ def test_gcb_greedy_full_size_certified(case, factor):
 def test_weights_and_volume_full_size(case):
     c = case
     r = P.greedy_select(c["d_xb"], c["d_db"], radius=c["radius"], tol=c["estar"], tol_mode=0,
-                        m=c["m"], seed=1, eval_prec=P.PREC_F32X2)
+                        m=c["m"], seed=1, eval_prec=P.PREC_F32X2, weights=True)
     S = r["idx"].cpu().numpy()
     w, res = P.solve_weights(c["d_xb"], c["d_db"], r["idx"], radius=c["radius"])
     Wo, st, _ = oracle.solve_weights(c["xb"], c["db"], S, c["radius"])
     dmax = np.abs(c["db"]).max()
     assert np.abs(w.cpu().numpy() - Wo).max() <= 1e-5 * dmax
     assert res <= 1e-10 * dmax
+    assert np.abs(r["w"].cpu().numpy() - Wo).max() <= 1e-5 * dmax
+    assert r["stats"]["max_resid"] <= 1e-10 * dmax
     rng = np.random.default_rng(7)
     sample = np.sort(rng.choice(len(c["xv"]), 4000, replace=False))
     ref = oracle.rbf_sum(c["xv"][sample], c["xb"], S, Wo, c["radius"])

@@ -60,8 +60,8 @@ def test_calls_reject_bad_arguments_before_touching_a_device():
     p = rbf.make_params(2.0, 1e-3, 1, 64, m=1, nc_max=100)
     nc = C.c_int64(0)
     # null inputs
-    st = L.rbf_greedy_select(None, None, 2000, C.byref(p), None, None, None, 0, C.byref(nc),
-                             None, None, None, 0, None)
+    st = L.rbf_greedy_select(None, None, 2000, C.byref(p), None, None, None, None, 0,
+                             C.byref(nc), None, None, None, 0, None)
     assert st == 1
     bad = rbf.make_params(-1.0, eval_prec=32)
     st = L.rbf_deform_volume(C.c_void_p(16), 10, C.c_void_p(16), C.c_void_p(16), 5,

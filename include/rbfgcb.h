@@ -199,6 +199,38 @@ rbf_status rbf_deform_volume(const double *d_xv, int64_t nv,
                              void *d_ws, size_t ws_bytes, void *stream);
 
 /* --------------------------------------------------------------------------
+ * Volume displacements without any device allocation or caller workspace.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (for instance a plug-in whose host
+ * application owns all device memory and forbids libraries from allocating,
+ * or a time-critical loop that cannot afford an allocation's implicit
+ * synchronisation) and therefore cannot hand rbf_deform_volume a workspace.
+ * It computes the same FP32 sum as rbf_deform_volume with
+ * eval_prec = RBF_PREC_F32, reading the volume points in place.
+ *
+ * Its scratch is a fixed array of RBF_NOALLOC_MAX_CENTRES (centre, weight)
+ * entries (256 KiB) in device global memory, reserved on every GPU that
+ * loads the library and held until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current); make the first call on each device before any stream
+ * capture.  Every call shares the array and overwrites the entries it reads,
+ * so results never depend on an earlier call, but calls whose GPU work
+ * overlaps (different streams, or host threads) race on it: serialise them.
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ *
+ * Arguments as rbf_deform_volume; p->eval_prec must be RBF_PREC_F32 and
+ * nc <= RBF_NOALLOC_MAX_CENTRES, otherwise RBF_E_ARG.  ASYNC.
+ * ------------------------------------------------------------------------ */
+#define RBF_NOALLOC_MAX_CENTRES 8192
+
+rbf_status rbf_deform_volume_noalloc(const double *d_xv, int64_t nv,
+                                     const double *d_xb, const int32_t *d_sel_idx,
+                                     int64_t nc, const double *d_w,
+                                     const rbf_params *p, double *d_dv,
+                                     void *stream);
+
+/* --------------------------------------------------------------------------
  * The random partition rbf_greedy_select uses (Sec. 3: "stochastically and
  * uniformly" into m groups whose sizes differ by at most one), on the host:
  * h_group_of[node] = group of the node, 0..m-1.  SplitMix64(seed) drives a

@@ -108,6 +108,12 @@ typedef struct {
     double min_pivot;        /* smallest squared Cholesky pivot d^2 seen        */
     double max_resid;        /* with d_w: max_j |F(r_j) - dr_j|_inf over S after
                                 refinement (FP64); -1 without d_w             */
+    int64_t phase_ns[8];     /* device time of the persistent kernel's first CTA
+                                by phase: [0] prologue (packing, seeds),
+                                [1] error pass 1, [2] re-score + reductions,
+                                [3] appends, [4] final refinement, [5] other;
+                                [6] of all that, time spent waiting in grid
+                                barriers; [7] unused                          */
 } rbf_greedy_stats;
 
 /* Columns of one row of the optional iteration history (device doubles):

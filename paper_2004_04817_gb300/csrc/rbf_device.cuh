@@ -314,6 +314,7 @@ constexpr int kBarMaxCtas = 4096;
 
 struct GridBar {
     unsigned int arrive[kBarMaxCtas];
+    unsigned long long wait_ns;   // time CTA 0 spent in barriers (profiling)
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
@@ -362,8 +363,11 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, unsigned
             __nanosleep(32);
         }
         ok = __all_sync(0xffffffffu, ok);
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             s_ok = ok;
+            if (blockIdx.x == 0)
+                bar->wait_ns += globaltimer_ns() - t0;
+        }
     }
     __syncthreads();
     epoch = target;

@@ -61,6 +61,7 @@ struct GreedyCtl {
     double min_pivot;
     double max_resid;
     long long n_hist;
+    unsigned long long phase_ns[8];   // CTA 0's time per phase (see rbf_greedy_stats)
 };
 
 struct GreedyArgs {
@@ -595,6 +596,19 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
     const int nb = a.nb, m = a.m;
     int use = 0;   // partial-buffer use counter (double buffering)
     unsigned int epoch = 0;   // grid barriers passed
+    // phase clock of CTA 0, thread 0: 0 prologue, 1 evaluation pass 1,
+    // 2 evaluation pass 2 + reductions, 3 appends, 4 refinement, 5 other
+    unsigned long long ph_acc[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long ph_t = globaltimer_ns();
+    int ph_cur = 0;
+    auto phase = [&](int nx) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const unsigned long long now = globaltimer_ns();
+            ph_acc[ph_cur] += now - ph_t;
+            ph_t = now;
+            ph_cur = nx;
+        }
+    };
     auto part = [&](int u) { return a.part + (size_t)(u & 1) * kMaxGrid * 4; };
     auto parti = [&](int u) { return a.parti + (size_t)(u & 1) * kMaxGrid; };
 #define GSYNC()                                                                   \
@@ -713,6 +727,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
         }
     }
 
+    phase(5);
     // ---------------- error evaluation over a position range ---------------
     int ev = 0;                      // evaluation counter (ring index)
     long long pairs32 = 0, pairs64 = 0, pairsff = 0;
@@ -724,6 +739,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
     // residual) and `out.gsq` the sum of squares.  `force64` evaluates every
     // pair in FP64 whatever the precision mode.
     auto evaluate = [&](int p0, int p1, bool argmax, bool force64, EvalOut &out) -> bool {
+        phase(1);
         const int r = ev % 3;
         const int nq = p1 - p0;
         const int ts = team_size(nq, G);
@@ -870,6 +886,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
             if (lane == 0 && tloc > 0.0)
                 atomicMax(&ctl->tslot[r], (unsigned long long)__double_as_longlong(tloc));
             GSYNC_B();
+            phase(2);
             const double thr = __longlong_as_double((long long)ldcg(&ctl->tslot[r]));
             // ---- pass 2: FP64 re-score of every node whose upper bound
             // reaches the largest lower bound; the others are certified below
@@ -940,6 +957,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
             ctl->tslot[(r + 2) % 3] = 0ull;
         }
         ++ev;
+        phase(5);
         return true;
     };
 
@@ -972,7 +990,10 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                 status = RBF_E_NC_MAX;
                 break;
             }
-            if (chol_append(a, red, nc, use, min_piv, add_pos, add_node, k, epoch) != kAppendOk) {
+            phase(3);
+            const int ar = chol_append(a, red, nc, use, min_piv, add_pos, add_node, k, epoch);
+            phase(5);
+            if (ar != kAppendOk) {
                 status = RBF_E_NOT_SPD;   // or the latched timeout, which wins
                 break;
             }
@@ -1008,6 +1029,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
     }
     // final weights of the selected set (row a9): FP64 refinement with Z
     double maxres = -1.0;
+    phase(4);
     if (a.w_out && nc > 0) {
         if (!refine_weights(a, red, nc, use, epoch, a.refine_steps, a.spos, a.rvec, a.tvec,
                             maxres))
@@ -1019,7 +1041,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
             a.w_out[3 * j + 2] = w.z;
         }
     }
+    phase(5);
     if (blockIdx.x == 0 && tid == 0) {
+        for (int i = 0; i < 6; ++i)
+            ctl->phase_ns[i] = ph_acc[i];
+        ctl->phase_ns[6] = ctl->bar.wait_ns;
         if (status != RBF_OK)
             atomicCAS(&ctl->status, (int)RBF_OK, status);
         ctl->max_resid = maxres;
@@ -1348,6 +1374,8 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
         h_stats->final_rms = ctl.final_rms;
         h_stats->min_pivot = ctl.min_pivot;
         h_stats->max_resid = ctl.max_resid;
+        for (int i = 0; i < 8; ++i)
+            h_stats->phase_ns[i] = (int64_t)ctl.phase_ns[i];
     }
     return (rbf_status)ctl.status;
 }

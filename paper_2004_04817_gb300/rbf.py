@@ -57,6 +57,7 @@ class GreedyStats(C.Structure):
         ("final_rms", C.c_double),
         ("min_pivot", C.c_double),
         ("max_resid", C.c_double),
+        ("phase_ns", C.c_int64 * 8),
     ]
 
 
@@ -185,7 +186,8 @@ def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
                 w=w[:n] if w is not None else None,
                 hist=hist[:min(nh.value, hist_cap)] if hist is not None else None,
                 n_hist=nh.value,
-                stats={f: getattr(stats, f) for f, _ in GreedyStats._fields_})
+                stats={f: (list(getattr(stats, f)) if f == "phase_ns" else getattr(stats, f))
+                       for f, _ in GreedyStats._fields_})
 
 
 def solve_weights(xb, db, sel_idx, *, radius, refine_steps=2, stream=None, workspace=None):

@@ -340,9 +340,10 @@ def run_ours(args, rank, world):
             "pairs_ff": st["pairs_ff"],
             "rescored": st["rescored"], "estar": st["estar"], "final_max": st["final_max"],
             "us_per_iteration": g_ms * 1e3 / max(st["iterations"], 1),
-            "phase_ms": dict(zip(["prologue", "eval_pass1", "rescore_reduce", "append",
-                                  "refine", "other", "barrier_wait_total"],
-                                 [v / 1e6 for v in st["phase_ns"][:7]])),
+            "phase_ms": dict(zip(["prologue", "eval_other", "rescore_f64", "append",
+                                  "refine", "other", "barrier_wait_total", "eval_staging",
+                                  "eval_pass", "eval_block_reduce", "eval_barrier_grid_reduce"],
+                                 [v / 1e6 for v in st["phase_ns"][:11]])),
         },
         "volume": {"pairs_per_s": vol_pairs / (v_ms * 1e-3), "ms": v_ms,
                    "fp32_peak_frac": vol_achieved / fp32_peak,

@@ -78,6 +78,9 @@ typedef struct {
     int64_t nc_max;       /* capacity of the support set, 3 <= nc_max <= N_b */
     int32_t refine_steps; /* FP64 iterative-refinement steps in rbf_solve_weights */
     int32_t flags;        /* 0, or RBF_FLAG_HISTORY_FULL */
+    int32_t ctas;         /* rbf_greedy_select: CTAs of the persistent launch
+                             (0 = chosen from the group size); tuning only */
+    int32_t reserved;     /* must be 0 */
 } rbf_params;
 
 /* rbf_params.flags: with a history buffer, also evaluate all N_b errors in
@@ -108,12 +111,14 @@ typedef struct {
     double min_pivot;        /* smallest squared Cholesky pivot d^2 seen        */
     double max_resid;        /* with d_w: max_j |F(r_j) - dr_j|_inf over S after
                                 refinement (FP64); -1 without d_w             */
-    int64_t phase_ns[8];     /* device time of the persistent kernel's first CTA
+    int64_t phase_ns[12];    /* device time of the persistent kernel's first CTA
                                 by phase: [0] prologue (packing, seeds),
-                                [1] error pass 1, [2] re-score + reductions,
-                                [3] appends, [4] final refinement, [5] other;
-                                [6] of all that, time spent waiting in grid
-                                barriers; [7] unused                          */
+                                [1] evaluation bookkeeping, [2] FP64
+                                re-scores, [3] appends, [4] final refinement,
+                                [5] other, [6] of all that, time spent waiting
+                                in grid barriers, [7] centre staging, [8] error
+                                pass, [9] block reductions, [10] evaluation
+                                barrier + grid reduction, [11] unused         */
 } rbf_greedy_stats;
 
 /* Columns of one row of the optional iteration history (device doubles):
@@ -186,6 +191,21 @@ rbf_status rbf_solve_weights(const double *d_xb, const double *d_db, int64_t nb,
                              void *d_ws, size_t ws_bytes, void *stream);
 
 /* --------------------------------------------------------------------------
+ * General support system: solve Phi_SS X = B for a caller's right-hand side
+ * (Eqs. 4-5 with B in place of dX_S), with the same FP64 factorisation and
+ * refinement as rbf_solve_weights.  Used by the adjoint (Phi_SS is
+ * symmetric, so Phi_SS^-T = Phi_SS^-1) and by the differentiable forward map.
+ *
+ * d_rhs : device FP64 nc x 3 (support order).   d_x : device FP64 nc x 3.
+ * h_max_resid : host or NULL; max_j |(Phi_SS X - B)_j|_inf.
+ * Workspace: rbf_solve_workspace_bytes(nc).  SYNCHRONOUS.
+ * ------------------------------------------------------------------------ */
+rbf_status rbf_solve_system(const double *d_xb, int64_t nb, const int32_t *d_sel_idx,
+                            int64_t nc, const double *d_rhs, const rbf_params *p,
+                            double *d_x, double *h_max_resid,
+                            void *d_ws, size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------------------------------
  * Volume displacements, Eq. 6: dv_v = sum_{j in S} w_j phi(|x_v - r_j| / R)
  * for the nv volume points.
  *
@@ -245,6 +265,34 @@ rbf_status rbf_deform_volume_noalloc(const double *d_xv, int64_t nv,
  * HOST ONLY (no device needed).  Returns RBF_E_ARG for nb < 1, m < 1, m > nb.
  * ------------------------------------------------------------------------ */
 rbf_status rbf_group_of(int64_t nb, int64_t m, uint64_t seed, int32_t *h_group_of);
+
+/* --------------------------------------------------------------------------
+ * Adjoint of the volume deformation for gradients with respect to the
+ * support displacements d_c (Eq. 6 with Eqs. 4-5: d_v = Phi_vc W, Phi_cc W = d_c):
+ *
+ *     dJ/dd_c = Phi_cc^-1 Phi_vc^T dJ/dd_v      (Phi_cc symmetric)
+ *
+ * Phi_vc is recomputed pair by pair, never stored.  The transposed pair sum
+ * runs in double-float (p->eval_prec = RBF_PREC_F32X2, recommended: the solve
+ * amplifies right-hand-side errors by the condition number of Phi_cc) or
+ * FP32 pairs, with FP64 accumulation across chunks of points and a fixed
+ * (deterministic) reduction order; the solve is rbf_solve_system (FP64 with
+ * p->refine_steps refinement steps).  The gradient with respect to all
+ * boundary displacements is dJ/dd_c at the support nodes and 0 elsewhere.
+ *
+ * d_xv : device FP64 nv x 3;  d_gv : device FP64 nv x 3 (dJ/dd_v).
+ * d_gc : device FP64 nc x 3 (output, support order).  nc <= 1024.
+ * h_max_resid : host or NULL; residual of the final solve.
+ * SYNCHRONOUS.
+ * ------------------------------------------------------------------------ */
+size_t rbf_adjoint_workspace_bytes(int64_t nv, int64_t nc);
+
+rbf_status rbf_deform_volume_adjoint(const double *d_xv, int64_t nv,
+                                     const double *d_xb, int64_t nb,
+                                     const int32_t *d_sel_idx, int64_t nc,
+                                     const double *d_gv, const rbf_params *p,
+                                     double *d_gc, double *h_max_resid,
+                                     void *d_ws, size_t ws_bytes, void *stream);
 
 /* --------------------------------------------------------------------------
  * Vector-FMA peak microbenchmark of this GPU (dependent-FMA chains on every

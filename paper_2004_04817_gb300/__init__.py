@@ -13,6 +13,10 @@ from .rbf import (  # noqa: F401
     greedy_select,
     solve_weights,
     deform_volume,
+    solve_system,
+    adjoint,
+    deform,
+    RBFDeform,
     measure_fma_peak,
     group_of,
     status_string,

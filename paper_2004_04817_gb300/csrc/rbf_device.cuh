@@ -301,6 +301,62 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 }
 
 // ----------------------------------------------------------------------------
+// Bulk (TMA) copy global -> shared memory completed on an mbarrier.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread: expect `bytes` on the barrier and start the copy.  `bytes` and
+// both addresses must be multiples of 16.  Global data written by other SMs
+// (generic proxy) is ordered before the async-proxy read by the fence.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar)
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for the barrier phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          uint64_t limit_ns)
+{
+    const unsigned a = smem_addr(bar);
+    uint64_t t0 = 0;
+    for (int it = 0;; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done)
+            return true;
+        if (it == 0)
+            t0 = globaltimer_ns();
+        else if (globaltimer_ns() - t0 > limit_ns)
+            return false;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // Grid barrier for cooperative launches (all CTAs co-resident).  Flat,
 // contention-free: CTA b publishes its arrival count in its own word
 // (release), and every CTA's warp 0 polls all the words (acquire) until each
@@ -360,7 +416,6 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, unsigned
                 ok = 0;
                 break;
             }
-            __nanosleep(32);
         }
         ok = __all_sync(0xffffffffu, ok);
         if (threadIdx.x == 0) {

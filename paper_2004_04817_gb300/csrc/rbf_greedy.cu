@@ -33,8 +33,8 @@ namespace rbf {
 constexpr int kGThreads = 256;
 constexpr int kGWarps = kGThreads / kWarp;
 constexpr int kMaxGrid = 4096;
-constexpr int kSmemCentresF32 = 4096;      // FP32 centres kept in shared memory (128 KB)
-constexpr int kSmemCentresFF = 2048;       // double-float centres in the same 128 KB
+constexpr int kSmemCentresF32 = 2048;      // FP32 centres kept in shared memory (64 KB)
+constexpr int kSmemCentresFF = 1024;       // double-float centres in the same 64 KB
 constexpr double kPivotMin = 1e-13;        // d^2 at or below: singular (coincident nodes)
 constexpr float kU32 = 5.9604645e-8f;      // 2^-24, unit roundoff of FP32
 constexpr float kBetaPhi = 16.0f;          // error-bound factors (see screen_bound)
@@ -61,7 +61,7 @@ struct GreedyCtl {
     double min_pivot;
     double max_resid;
     long long n_hist;
-    unsigned long long phase_ns[8];   // CTA 0's time per phase (see rbf_greedy_stats)
+    unsigned long long phase_ns[12];  // CTA 0's time per phase (see rbf_greedy_stats)
 };
 
 struct GreedyArgs {
@@ -300,12 +300,29 @@ __device__ __forceinline__ T team_sum(T v, int ts)
 }
 
 // FP64 error of the node at position q with the current support (nc centres).
-__device__ __forceinline__ double team_error_f64(const GreedyArgs &a, int q, int nc, int sub,
-                                                 int ts)
+// F(r_q) partial sums of one team lane over centres j = sub, sub + ts, ...
+// (FP64), two centres per step with their loads issued together.
+__device__ __forceinline__ void team_f_f64(const GreedyArgs &a, const D4 &x, int nc, int sub,
+                                           int ts, double &fx, double &fy, double &fz)
 {
-    const D4 x = ldcg(a.xg64 + q);
-    double fx = 0.0, fy = 0.0, fz = 0.0;
-    for (int j = sub; j < nc; j += ts) {
+    fx = 0.0;
+    fy = 0.0;
+    fz = 0.0;
+    int j = sub;
+    for (; j + ts < nc; j += 2 * ts) {
+        const D4 c0 = ldcg(a.c64 + j), c1 = ldcg(a.c64 + j + ts);
+        const D4 w0 = ldcg(a.w64 + j), w1 = ldcg(a.w64 + j + ts);
+        double dx = x.x - c0.x, dy = x.y - c0.y, dz = x.z - c0.z;
+        const double p0 = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
+        dx = x.x - c1.x;
+        dy = x.y - c1.y;
+        dz = x.z - c1.z;
+        const double p1 = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
+        fx = fma(w1.x, p1, fma(w0.x, p0, fx));
+        fy = fma(w1.y, p1, fma(w0.y, p0, fy));
+        fz = fma(w1.z, p1, fma(w0.z, p0, fz));
+    }
+    if (j < nc) {
         const D4 c = ldcg(a.c64 + j);
         const D4 w = ldcg(a.w64 + j);
         const double dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
@@ -317,6 +334,15 @@ __device__ __forceinline__ double team_error_f64(const GreedyArgs &a, int q, int
     fx = team_sum(fx, ts);
     fy = team_sum(fy, ts);
     fz = team_sum(fz, ts);
+}
+
+// FP64 error of the node at position q with the current support (nc centres).
+__device__ __forceinline__ double team_error_f64(const GreedyArgs &a, int q, int nc, int sub,
+                                                 int ts)
+{
+    const D4 x = ldcg(a.xg64 + q);
+    double fx, fy, fz;
+    team_f_f64(a, x, nc, sub, ts, fx, fy, fz);
     const D4 d = ldcg(a.dg64 + q);
     const double ex = d.x - fx, ey = d.y - fy, ez = d.z - fz;
     return sqrt(fma(ez, ez, fma(ey, ey, ex * ex)));
@@ -327,21 +353,61 @@ __device__ __forceinline__ double team_error_f64(const GreedyArgs &a, int q, int
 __device__ __forceinline__ D4 team_resid_f64(const GreedyArgs &a, int q, int nc, int sub, int ts)
 {
     const D4 x = ldcg(a.xg64 + q);
-    double fx = 0.0, fy = 0.0, fz = 0.0;
-    for (int j = sub; j < nc; j += ts) {
-        const D4 c = ldcg(a.c64 + j);
-        const D4 w = ldcg(a.w64 + j);
-        const double dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
-        const double ph = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
-        fx = fma(w.x, ph, fx);
-        fy = fma(w.y, ph, fy);
-        fz = fma(w.z, ph, fz);
-    }
-    fx = team_sum(fx, ts);
-    fy = team_sum(fy, ts);
-    fz = team_sum(fz, ts);
+    double fx, fy, fz;
+    team_f_f64(a, x, nc, sub, ts, fx, fy, fz);
     const D4 d = ldcg(a.dg64 + q);
     return mk4(d.x - fx, d.y - fy, d.z - fz, 0.0);
+}
+
+// Dot product of row `row` (length n, L2-coherent loads) with vector v,
+// spread over the 32 lanes of a warp with four independent accumulators.
+__device__ __forceinline__ double warp_dot(const double *row, const double *v, int p0, int n)
+{
+    const int lane = threadIdx.x & 31;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int p = p0 + lane;
+    for (; p + 96 < n; p += 128) {
+        const double z0 = ldcg(row + p), z1 = ldcg(row + p + 32), z2 = ldcg(row + p + 64),
+                     z3 = ldcg(row + p + 96);
+        const double b0 = ldcg(v + p), b1 = ldcg(v + p + 32), b2 = ldcg(v + p + 64),
+                     b3 = ldcg(v + p + 96);
+        s0 = fma(z0, b0, s0);
+        s1 = fma(z1, b1, s1);
+        s2 = fma(z2, b2, s2);
+        s3 = fma(z3, b3, s3);
+    }
+    for (; p < n; p += 32)
+        s0 = fma(ldcg(row + p), ldcg(v + p), s0);
+    return warp_sum_f64((s0 + s1) + (s2 + s3));
+}
+
+// Same with a 3-column vector of D4 (x, y, z).
+__device__ __forceinline__ void warp_dot3(const double *row, const D4 *v, int p0, int n,
+                                          double &sx, double &sy, double &sz)
+{
+    const int lane = threadIdx.x & 31;
+    double ax = 0.0, ay = 0.0, az = 0.0, bx = 0.0, by = 0.0, bz = 0.0;
+    int p = p0 + lane;
+    for (; p + 32 < n; p += 64) {
+        const double z0 = ldcg(row + p), z1 = ldcg(row + p + 32);
+        const D4 r0 = ldcg(v + p), r1 = ldcg(v + p + 32);
+        ax = fma(z0, r0.x, ax);
+        ay = fma(z0, r0.y, ay);
+        az = fma(z0, r0.z, az);
+        bx = fma(z1, r1.x, bx);
+        by = fma(z1, r1.y, by);
+        bz = fma(z1, r1.z, bz);
+    }
+    if (p < n) {
+        const double z0 = ldcg(row + p);
+        const D4 r0 = ldcg(v + p);
+        ax = fma(z0, r0.x, ax);
+        ay = fma(z0, r0.y, ay);
+        az = fma(z0, r0.z, az);
+    }
+    sx = warp_sum_f64(ax + bx);
+    sy = warp_sum_f64(ay + by);
+    sz = warp_sum_f64(az + bz);
 }
 
 struct EvalOut {
@@ -370,9 +436,10 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
     const int gtid = blockIdx.x * kGThreads + tid;
     const int gthreads = G * kGThreads;
     const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
-    // A1: b_j = phi(|r_n - r_j| / R)
+    // A1: b_j = phi(|r_n - r_j| / R), centre j on CTA j mod G (FP64 work
+    // spread over every SM)
     const D4 xn = ldcg(a.xg64 + pn);
-    for (int j = gtid; j < nc; j += gthreads) {
+    for (int j = blockIdx.x + G * tid; j < nc; j += G * kGThreads) {
         const D4 c = ldcg(a.c64 + j);
         const double dx = xn.x - c.x, dy = xn.y - c.y, dz = xn.z - c.z;
         a.bvec[j] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
@@ -381,11 +448,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
     // A2: l = Z b (warp per row) and partial sums of l.l and l.y
     double acc4[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = gwarp; i < nc; i += gwarps) {
-        const double *zr = a.z + (size_t)i * a.ld;
-        double s = 0.0;
-        for (int p = lane; p <= i; p += 32)
-            s = fma(ldcg(zr + p), ldcg(a.bvec + p), s);
-        s = warp_sum_f64(s);
+        const double s = warp_dot(a.z + (size_t)i * a.ld, a.bvec, 0, i + 1);
         if (lane == 0) {
             a.lvec[i] = s;
             const D4 y = ldcg(a.y64 + i);
@@ -416,11 +479,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
                  yz = (dn.z - s4[3]) * inv_d;
     // A3: u = Z^T l (warp per row of Z^T); new row of Z; weight update
     for (int j = gwarp; j < nc; j += gwarps) {
-        const double *ztr = a.zt + (size_t)j * a.ld;
-        double s = 0.0;
-        for (int i = j + lane; i < nc; i += 32)
-            s = fma(ldcg(ztr + i), ldcg(a.lvec + i), s);
-        s = warp_sum_f64(s);
+        const double s = warp_dot(a.zt + (size_t)j * a.ld, a.lvec, j, nc);
         if (lane == 0) {
             const double zz = -s * inv_d;
             a.z[(size_t)nc * a.ld + j] = zz;
@@ -534,18 +593,8 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
             break;
         // t = Z r (3 right-hand sides, warp per row)
         for (int i = gwarp; i < nc; i += gwarps) {
-            const double *zr = a.z + (size_t)i * a.ld;
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int p = lane; p <= i; p += 32) {
-                const double zz = ldcg(zr + p);
-                const D4 r = ldcg(rvec + p);
-                sx = fma(zz, r.x, sx);
-                sy = fma(zz, r.y, sy);
-                sz = fma(zz, r.z, sz);
-            }
-            sx = warp_sum_f64(sx);
-            sy = warp_sum_f64(sy);
-            sz = warp_sum_f64(sz);
+            double sx, sy, sz;
+            warp_dot3(a.z + (size_t)i * a.ld, rvec, 0, i + 1, sx, sy, sz);
             if (lane == 0)
                 tvec[i] = mk4(sx, sy, sz, 0.0);
         }
@@ -553,18 +602,8 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
             return false;
         // W += Z^T t
         for (int j = gwarp; j < nc; j += gwarps) {
-            const double *ztr = a.zt + (size_t)j * a.ld;
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int i = j + lane; i < nc; i += 32) {
-                const double zz = ldcg(ztr + i);
-                const D4 t = ldcg(tvec + i);
-                sx = fma(zz, t.x, sx);
-                sy = fma(zz, t.y, sy);
-                sz = fma(zz, t.z, sz);
-            }
-            sx = warp_sum_f64(sx);
-            sy = warp_sum_f64(sy);
-            sz = warp_sum_f64(sz);
+            double sx, sy, sz;
+            warp_dot3(a.zt + (size_t)j * a.ld, tvec, j, nc, sx, sy, sz);
             if (lane == 0) {
                 D4 w = ldcg(a.w64 + j);
                 w.x += sx;
@@ -582,11 +621,16 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
 // ---------------------------------------------------------------------------
 // The persistent kernel.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
+__global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
 {
     extern __shared__ float4 s_cw[];
     __shared__ Red red;
     __shared__ float s_wabs;
+    __shared__ __align__(8) unsigned long long s_mbar;
+    unsigned mbar_phase = 0;
+    if (threadIdx.x == 0)
+        mbar_init(&s_mbar, 1);
+    __syncthreads();
     GreedyCtl *ctl = a.ctl;
     const int G = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -598,7 +642,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
     unsigned int epoch = 0;   // grid barriers passed
     // phase clock of CTA 0, thread 0: 0 prologue, 1 evaluation pass 1,
     // 2 evaluation pass 2 + reductions, 3 appends, 4 refinement, 5 other
-    unsigned long long ph_acc[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long ph_acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long ph_t = globaltimer_ns();
     int ph_cur = 0;
     auto phase = [&](int nx) {
@@ -748,7 +792,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
         const int rounds = (nq + nteams - 1) / nteams;
         unsigned long long key = 0;
         double lmax = 0.0, lsq = 0.0;
-        if (a.prec == RBF_PREC_F64 || force64) {
+        const bool screened = !(a.prec == RBF_PREC_F64 || force64);
+        // top two upper bounds E~ + beta of this thread's nodes (screened modes)
+        double u1 = -1.0, u2 = -1.0;
+        long long n1 = -1;
+        if (!screened) {
             for (int it = 0; it < rounds; ++it) {
                 const int q = p0 + team + it * nteams;
                 const bool act = q < p1;
@@ -767,26 +815,37 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                 pairs64 += (long long)nq * nc;
         } else {
             // ---- pass 1: FP32 or double-float errors E~ with a bound beta,
-            // |E~ - E| <= beta; e64[q] = E~, u32[q] = beta.  Centres come from
-            // shared memory when they fit.
+            // |E~ - E| <= beta; e64[q] = E~, u32[q] = beta.  The centre table
+            // is staged in shared memory by one bulk (TMA) copy.
             const bool use_ff = a.prec == RBF_PREC_F32X2;
             const bool smem = nc <= (use_ff ? kSmemCentresFF : kSmemCentresF32);
+            phase(7);
             if (smem) {
-                const int n4 = (use_ff ? 4 : 2) * nc;
                 const float4 *src = use_ff ? a.cwff : a.cw32;
-                for (int j = tid; j < n4; j += kGThreads)
-                    s_cw[j] = ldcg(src + j);
+                const unsigned bytes = (unsigned)(sizeof(float4) * (use_ff ? 4 : 2) * nc);
+                __syncthreads();   // previous readers of the table are done
+                if (tid == 0)
+                    bulk_g2s(s_cw, src, bytes, &s_mbar);
+                const bool got = mbar_wait(&s_mbar, mbar_phase, a.barrier_ns);
+                if (!got) {
+                    // give the copy in flight a second bounded wait before leaving
+                    atomicExch(&ctl->status, (int)RBF_E_TIMEOUT);
+                    mbar_wait(&s_mbar, mbar_phase, a.barrier_ns);
+                    return false;
+                }
+                mbar_phase ^= 1u;
             }
             if (tid < 32) {
                 float t = 0.0f;
                 for (int j = tid; j < nc; j += 32)
-                    t += ldcg(a.cw32 + 2 * j + 1).w;
+                    t += smem ? (use_ff ? s_cw[4 * j + 2].w : s_cw[2 * j + 1].w)
+                              : ldcg(a.cw32 + 2 * j + 1).w;
                 t = team_sum(t, 32);
                 if (tid == 0)
                     s_wabs = t;
             }
             __syncthreads();
-            double tloc = 0.0;
+            phase(8);
             if (!use_ff) {
                 const float4 *cw = smem ? s_cw : a.cw32;
                 const float coord_term = kBetaCoord * xscale * s_wabs * 1.001f;
@@ -809,7 +868,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                     fy = team_sum(fy, ts);
                     fz = team_sum(fz, ts);
                     sb = team_sum(sb, ts);
-                    if (act && sub == 0) {
+                    if (act && sub == 0 && !ldcg(a.in_s + q)) {
                         const D4 d = ldcg(a.dg64 + q);
                         const float ex = (float)d.x - fx, ey = (float)d.y - fy,
                                     ez = (float)d.z - fz;
@@ -822,8 +881,22 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                             kU32 * (kBetaPhi * (sb + dabs) + coord_term + 4.0f * e) + 1e-30f;
                         a.u32[q] = beta;
                         a.e64[q] = (double)e;
-                        if (!ldcg(a.in_s + q))
-                            tloc = fmax(tloc, fmax((double)e - (double)beta, 0.0));
+                        const double up = (double)e + (double)beta;
+                        lmax = fmax(lmax, (double)e);
+                        lsq = fma((double)e, (double)e, lsq);
+                        if (argmax) {
+                            const unsigned long long k2 = key_f64((double)e, ldcg(a.node_of_pos + q));
+                            if (k2 > key) {
+                                key = k2;
+                            }
+                            if (up > u1) {
+                                u2 = u1;
+                                u1 = up;
+                                n1 = ldcg(a.node_of_pos + q);
+                            } else if (up > u2) {
+                                u2 = up;
+                            }
+                        }
                     }
                 }
                 if (blockIdx.x == 0 && tid == 0)
@@ -841,6 +914,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                     split_f64(xq.z, qzh, qzl);
                     ff fx{0.0f, 0.0f}, fy{0.0f, 0.0f}, fz{0.0f, 0.0f};
                     float sb = 0.0f;
+#pragma unroll 2
                     for (int j = sub; j < nc; j += ts) {
                         const float4 ch = smem ? cw[4 * j] : ldcg(cw + 4 * j);
                         const float4 cl = smem ? cw[4 * j + 1] : ldcg(cw + 4 * j + 1);
@@ -854,15 +928,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                         ff_fma_acc(fz, wh.z, wl.z, ph);
                         sb = fmaf(wh.w, ph.h, sb);
                     }
-                    // team reduction in FP64 (exact enough: each ff value is
-                    // converted to the double h + l)
+                    // team reduction in FP64 (each ff value becomes the double h + l)
                     double sx = (double)fx.h + (double)fx.l, sy = (double)fy.h + (double)fy.l,
                            sz = (double)fz.h + (double)fz.l;
                     sx = team_sum(sx, ts);
                     sy = team_sum(sy, ts);
                     sz = team_sum(sz, ts);
                     sb = team_sum(sb, ts);
-                    if (act && sub == 0) {
+                    if (act && sub == 0 && !ldcg(a.in_s + q)) {
                         const D4 d = ldcg(a.dg64 + q);
                         const double ex = d.x - sx, ey = d.y - sy, ez = d.z - sz;
                         const double e = sqrt(fma(ez, ez, fma(ey, ey, ex * ex)));
@@ -872,91 +945,204 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
                         // splits (max|x|/R * sum |w|) and of the displacement
                         const double beta =
                             kUFF * (kBetaFF * ((double)sb + dabs) + coord_term) + 1e-300;
-                        a.u32[q] = (float)(beta * 1.0000002);
+                        const float bf = (float)(beta * 1.0000002);
+                        a.u32[q] = bf;
                         a.e64[q] = e;
-                        if (!ldcg(a.in_s + q))
-                            tloc = fmax(tloc, fmax(e - (double)a.u32[q], 0.0));
+                        const double up = e + (double)bf;
+                        lmax = fmax(lmax, e);
+                        lsq = fma(e, e, lsq);
+                        if (argmax) {
+                            const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
+                            if (k2 > key)
+                                key = k2;
+                            if (up > u1) {
+                                u2 = u1;
+                                u1 = up;
+                                n1 = ldcg(a.node_of_pos + q);
+                            } else if (up > u2) {
+                                u2 = up;
+                            }
+                        }
                     }
                 }
                 if (blockIdx.x == 0 && tid == 0)
                     pairsff += (long long)nq * nc;
             }
-            for (int o = 16; o > 0; o >>= 1)
-                tloc = fmax(tloc, __shfl_xor_sync(0xffffffffu, tloc, o));
-            if (lane == 0 && tloc > 0.0)
-                atomicMax(&ctl->tslot[r], (unsigned long long)__double_as_longlong(tloc));
-            GSYNC_B();
-            phase(2);
-            const double thr = __longlong_as_double((long long)ldcg(&ctl->tslot[r]));
-            // ---- pass 2: FP64 re-score of every node whose upper bound
-            // reaches the largest lower bound; the others are certified below
-            // the maximum
-            for (int it = 0; it < rounds; ++it) {
-                const int q = p0 + team + it * nteams;
-                const bool act = q < p1;
-                bool need = false;
-                bool ins = true;
-                if (act) {
-                    ins = ldcg(a.in_s + q) != 0;
-                    const double ea = ldcg(a.e64 + q);
-                    need = !ins && ea + (double)ldcg(a.u32 + q) >= thr;
-                    if (!need && !ins && sub == 0)
-                        lsq = fma(ea, ea, lsq);
-                }
-                if (__ballot_sync(0xffffffffu, need) == 0u)
-                    continue;
-                const double e = team_error_f64(a, act ? q : p0, nc, sub, ts);
-                if (need && sub == 0) {
-                    ++rescored_local;
-                    a.e64[q] = e;
-                    lmax = fmax(lmax, e);
-                    lsq = fma(e, e, lsq);
-                    if (argmax) {
-                        const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
-                        key = k2 > key ? k2 : key;
-                    }
-                }
-            }
         }
-        // ---- reductions: key by atomic max, (max, sum of squares) by partials
+        // ---- reductions: key by atomic max; (max, sum of squares) and the two
+        // largest upper bounds with the node of the largest by partials
+        phase(9);
         block_max_key(red, key);
         if (tid == 0 && key)
             atomicMax(&ctl->slot[r], key);
         {
+            // top-2 upper bounds: warp then block (deterministic order)
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ou1 = __shfl_xor_sync(0xffffffffu, u1, o);
+                const double ou2 = __shfl_xor_sync(0xffffffffu, u2, o);
+                const long long on1 = __shfl_xor_sync(0xffffffffu, n1, o);
+                if (ou1 > u1 || (ou1 == u1 && on1 >= 0 && (n1 < 0 || on1 < n1))) {
+                    u2 = fmax(u1, ou2);
+                    u1 = ou1;
+                    n1 = on1;
+                } else {
+                    u2 = fmax(u2, ou1);
+                }
+            }
             double a4[4] = {0.0, lsq, 0.0, 0.0};
             double mx = lmax;
             for (int o = 16; o > 0; o >>= 1)
                 mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             block_sum4(red, a4);
             __syncthreads();
-            if (lane == 0)
+            if (lane == 0) {
                 red.v[warp] = mx;
+                red.s[warp][0] = u1;
+                red.s[warp][1] = u2;
+                red.i[warp] = n1;
+            }
             __syncthreads();
             if (tid == 0) {
-                for (int k2 = 1; k2 < kGWarps; ++k2)
+                for (int k2 = 1; k2 < kGWarps; ++k2) {
                     mx = fmax(mx, red.v[k2]);
+                    const double ou1 = red.s[k2][0], ou2 = red.s[k2][1];
+                    const long long on1 = red.i[k2];
+                    if (ou1 > u1 || (ou1 == u1 && on1 >= 0 && (n1 < 0 || on1 < n1))) {
+                        u2 = fmax(u1, ou2);
+                        u1 = ou1;
+                        n1 = on1;
+                    } else {
+                        u2 = fmax(u2, ou1);
+                    }
+                }
                 double *pp = part(use) + 4 * blockIdx.x;
                 pp[0] = mx;
                 pp[1] = a4[1];
-                pp[2] = 0.0;
-                pp[3] = 0.0;
+                pp[2] = u1;
+                pp[3] = u2;
+                parti(use)[blockIdx.x] = n1;
             }
         }
+        phase(10);
         GSYNC_B();
         out.key = ldcg(&ctl->slot[r]);
+        double gu1 = -1.0, gu2 = -1.0;
+        long long gn1 = -1;
         {
-            double mx4[4], sm4[4];
-            grid_max4(part(use), G, mx4);
-            grid_sum4(part(use), G, sm4);
+            // one pass over the G partials: max, sum of squares and the two
+            // largest upper bounds (every CTA reduces the same data in the
+            // same order)
+            __shared__ double s_r[4];
+            __shared__ long long s_n;
+            if (tid < 32) {
+                double mx = -INFINITY, sq = 0.0, v1 = -1.0, v2 = -1.0;
+                long long m1 = -1;
+                const double *pb = part(use);
+                const long long *pi = parti(use);
+                for (int b = tid; b < G; b += 32) {
+                    const double2 a0 = __ldcg((const double2 *)(pb + 4 * b));
+                    const double2 uu = __ldcg((const double2 *)(pb + 4 * b + 2));
+                    const long long nb1 = ldcg(pi + b);
+                    mx = fmax(mx, a0.x);
+                    sq += a0.y;
+                    if (uu.x > v1 || (uu.x == v1 && nb1 >= 0 && (m1 < 0 || nb1 < m1))) {
+                        v2 = fmax(v1, uu.y);
+                        v1 = uu.x;
+                        m1 = nb1;
+                    } else {
+                        v2 = fmax(v2, uu.x);
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                    const double ov1 = __shfl_xor_sync(0xffffffffu, v1, o);
+                    const double ov2 = __shfl_xor_sync(0xffffffffu, v2, o);
+                    const long long om1 = __shfl_xor_sync(0xffffffffu, m1, o);
+                    if (ov1 > v1 || (ov1 == v1 && om1 >= 0 && (m1 < 0 || om1 < m1))) {
+                        v2 = fmax(v1, ov2);
+                        v1 = ov1;
+                        m1 = om1;
+                    } else {
+                        v2 = fmax(v2, ov1);
+                    }
+                }
+                if (tid == 0) {
+                    s_r[0] = mx;
+                    s_r[1] = sq;
+                    s_r[2] = v1;
+                    s_r[3] = v2;
+                    s_n = m1;
+                }
+            }
+            __syncthreads();
+            out.gmax = s_r[0];
+            out.gsq = s_r[1];
+            gu1 = s_r[2];
+            gu2 = s_r[3];
+            gn1 = s_n;
+            __syncthreads();
             ++use;
-            out.gmax = mx4[0];
-            out.gsq = sm4[1];
         }
+        phase(11);
         if (blockIdx.x == 0 && tid == 0) {
             ctl->slot[(r + 2) % 3] = 0ull;
             ctl->tslot[(r + 2) % 3] = 0ull;
         }
         ++ev;
+        if (screened && argmax && out.key) {
+            // ---- certification from the bounds: the leader b (largest E~)
+            // is the argmax when E~_b - beta_b exceeds every other node's
+            // upper bound; the E > E* decision is certified when the bound
+            // interval of the leader lies on one side of E*.
+            const int nb_ = key_node(out.key);
+            const int pb_ = ldcg(a.pos_of_node + nb_);
+            const double eb = ldcg(a.e64 + pb_), bb = (double)ldcg(a.u32 + pb_);
+            const double lower = eb - bb;
+            const double other = (gn1 == nb_) ? gu2 : gu1;
+            // certified: every node is <= E* (no append whoever leads), or
+            // the leader is the unique maximum and lies above E*
+            const bool none_above = gu1 <= estar;
+            const bool lead_adds = lower > other && lower > estar;
+            if (!(none_above || lead_adds)) {
+                // ---- pass 2 (rare): FP64 re-score of every node whose upper
+                // bound reaches the leader's lower bound
+                phase(2);
+                const int r2 = ev % 3;
+                unsigned long long key2 = 0;
+                const double thr = lower;   // the maximum is >= the leader's lower bound
+                for (int it = 0; it < rounds; ++it) {
+                    const int q = p0 + team + it * nteams;
+                    const bool act = q < p1;
+                    bool need = false;
+                    if (act && !ldcg(a.in_s + q))
+                        need = ldcg(a.e64 + q) + (double)ldcg(a.u32 + q) >= thr;
+                    if (__ballot_sync(0xffffffffu, need) == 0u)
+                        continue;
+                    const double e = team_error_f64(a, act ? q : p0, nc, sub, ts);
+                    if (need && sub == 0) {
+                        ++rescored_local;
+                        a.e64[q] = e;
+                        a.u32[q] = 0.0f;
+                        const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
+                        key2 = k2 > key2 ? k2 : key2;
+                    }
+                }
+                block_max_key(red, key2);
+                if (tid == 0 && key2)
+                    atomicMax(&ctl->slot[r2], key2);
+                GSYNC_B();
+                const unsigned long long k64 = ldcg(&ctl->slot[r2]);
+                if (k64)
+                    out.key = k64;
+                if (blockIdx.x == 0 && tid == 0)
+                    ctl->slot[(r2 + 2) % 3] = 0ull;
+                ++ev;
+                // the certified maximum of a node that adds nothing
+                out.gmax = fmax(out.gmax, k64 ? ldcg(a.e64 + ldcg(a.pos_of_node + key_node(k64)))
+                                                : 0.0);
+            }
+        }
         phase(5);
         return true;
     };
@@ -1043,7 +1229,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
     }
     phase(5);
     if (blockIdx.x == 0 && tid == 0) {
-        for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 12; ++i)
             ctl->phase_ns[i] = ph_acc[i];
         ctl->phase_ns[6] = ctl->bar.wait_ns;
         if (status != RBF_OK)
@@ -1075,7 +1261,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kGThreads, 1)
 k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
-        D4 *__restrict__ rvec, D4 *__restrict__ tvec, double *__restrict__ w_out)
+        D4 *__restrict__ rvec, D4 *__restrict__ tvec, double *__restrict__ w_out,
+        const double *__restrict__ rhs)
 {
     __shared__ Red red;
     GreedyCtl *ctl = a.ctl;
@@ -1102,7 +1289,10 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
         }
         const double x = a.xb[3 * node] * a.inv_r, y = a.xb[3 * node + 1] * a.inv_r,
                      z = a.xb[3 * node + 2] * a.inv_r;
-        const double d0 = a.db[3 * node], d1 = a.db[3 * node + 1], d2 = a.db[3 * node + 2];
+        // right-hand side: the prescribed displacements dX_S, or a caller's
+        // nc x 3 array (support order)
+        const double *rr = rhs ? rhs + 3 * j : a.db + 3 * node;
+        const double d0 = rr[0], d1 = rr[1], d2 = rr[2];
         if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(d0) || !isfinite(d1) ||
             !isfinite(d2))
             bad = fmax(bad, 1.0);
@@ -1218,7 +1408,8 @@ static bool greedy_args_ok(int64_t nb, const rbf_params *p)
            (p->tol_mode == 0 || p->tol_mode == 1) &&
            (p->eval_prec == RBF_PREC_F32 || p->eval_prec == RBF_PREC_F64 ||
             p->eval_prec == RBF_PREC_F32X2) &&
-           (p->flags & ~(RBF_FLAG_HISTORY_FULL | RBF_FLAG_TEST_BARRIER_TIMEOUT)) == 0;
+           (p->flags & ~(RBF_FLAG_HISTORY_FULL | RBF_FLAG_TEST_BARRIER_TIMEOUT)) == 0 &&
+           p->ctas >= 0;
 }
 
 }  // namespace rbf
@@ -1338,14 +1529,23 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
             ? sizeof(float4) * 4 * (size_t)std::min<int64_t>(p->nc_max, kSmemCentresFF)
             : 0;
     if (cudaFuncSetAttribute(k_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float4) * 2 * kSmemCentresF32)) != cudaSuccess)
+                             (int)(sizeof(float4) * 4 * kSmemCentresFF)) != cudaSuccess)
         return RBF_E_CUDA;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_greedy, kGThreads, smem) !=
             cudaSuccess ||
         occ < 1)
         return RBF_E_CUDA;
-    const int grid = std::min(dev.sms * std::min(occ, 1), kMaxGrid);
+    // grid: enough CTAs for one 32-lane team per node of the largest group,
+    // at least 32 (the appends spread their FP64 work over the CTAs), at most
+    // one per SM (more CTAs make every barrier and grid reduction slower than
+    // they make the evaluation faster); p->ctas > 0 overrides (tuning)
+    const int64_t gsize = (nb + p->m - 1) / p->m;
+    const int64_t want = std::max<int64_t>(32, (gsize * 32 + kGThreads - 1) / kGThreads);
+    int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms);
+    if (p->ctas > 0)
+        grid = std::min(p->ctas, dev.sms * std::min(occ, 2));
+    grid = std::min(grid, kMaxGrid);
     void *kargs[] = {&a};
     if (cudaLaunchCooperativeKernel((const void *)k_greedy, grid, kGThreads, kargs, smem, st) !=
         cudaSuccess) {
@@ -1374,7 +1574,7 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
         h_stats->final_rms = ctl.final_rms;
         h_stats->min_pivot = ctl.min_pivot;
         h_stats->max_resid = ctl.max_resid;
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 12; ++i)
             h_stats->phase_ns[i] = (int64_t)ctl.phase_ns[i];
     }
     return (rbf_status)ctl.status;
@@ -1391,13 +1591,14 @@ extern "C" size_t rbf_solve_workspace_bytes(int64_t nc)
     return solve_ws_layout(nc).total;
 }
 
-extern "C" rbf_status rbf_solve_weights(const double *d_xb, const double *d_db, int64_t nb,
-                                        const int32_t *d_sel_idx, int64_t nc,
-                                        const rbf_params *p, double *d_w, double *h_max_resid,
-                                        void *d_ws, size_t ws_bytes, void *stream)
+namespace rbf {
+static rbf_status solve_launch(const double *d_xb, const double *d_db, int64_t nb,
+                               const int32_t *d_sel_idx, int64_t nc, const double *d_rhs,
+                               const rbf_params *p, double *d_x, double *h_max_resid, void *d_ws,
+                               size_t ws_bytes, void *stream)
 {
-    if (!p || !d_xb || !d_db || !d_sel_idx || !d_w || nc < 1 || nc > nb || nc > 46340 ||
-        nb >= kMaxNodes || !(p->radius > 0.0) || !std::isfinite(p->radius) ||
+    if (!p || !d_xb || (!d_db && !d_rhs) || !d_sel_idx || !d_x || nc < 1 || nc > nb ||
+        nc > 46340 || nb >= kMaxNodes || !(p->radius > 0.0) || !std::isfinite(p->radius) ||
         p->refine_steps < 0 || p->refine_steps > 16)
         return RBF_E_ARG;
     const SolveWs L = solve_ws_layout(nc);
@@ -1431,7 +1632,7 @@ extern "C" rbf_status rbf_solve_weights(const double *d_xb, const double *d_db, 
     const int grid = std::min(dev.sms, kMaxGrid);
     int nc_i = (int)nc, steps = p->refine_steps;
     D4 *rvec = (D4 *)(ws + L.rvec), *tvec = (D4 *)(ws + L.tvec);
-    void *kargs[] = {&a, (void *)&d_sel_idx, &nc_i, &steps, &rvec, &tvec, &d_w};
+    void *kargs[] = {&a, (void *)&d_sel_idx, &nc_i, &steps, &rvec, &tvec, &d_x, (void *)&d_rhs};
     if (cudaLaunchCooperativeKernel((const void *)k_solve, grid, kGThreads, kargs, 0, st) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -1447,4 +1648,27 @@ extern "C" rbf_status rbf_solve_weights(const double *d_xb, const double *d_db, 
     if (h_max_resid)
         *h_max_resid = ctl.final_max;
     return (rbf_status)ctl.status;
+}
+}  // namespace rbf
+
+extern "C" rbf_status rbf_solve_weights(const double *d_xb, const double *d_db, int64_t nb,
+                                        const int32_t *d_sel_idx, int64_t nc,
+                                        const rbf_params *p, double *d_w, double *h_max_resid,
+                                        void *d_ws, size_t ws_bytes, void *stream)
+{
+    if (!d_db)
+        return RBF_E_ARG;
+    return solve_launch(d_xb, d_db, nb, d_sel_idx, nc, nullptr, p, d_w, h_max_resid, d_ws,
+                        ws_bytes, stream);
+}
+
+extern "C" rbf_status rbf_solve_system(const double *d_xb, int64_t nb, const int32_t *d_sel_idx,
+                                       int64_t nc, const double *d_rhs, const rbf_params *p,
+                                       double *d_x, double *h_max_resid, void *d_ws,
+                                       size_t ws_bytes, void *stream)
+{
+    if (!d_rhs)
+        return RBF_E_ARG;
+    return solve_launch(d_xb, nullptr, nb, d_sel_idx, nc, d_rhs, p, d_x, h_max_resid, d_ws,
+                        ws_bytes, stream);
 }

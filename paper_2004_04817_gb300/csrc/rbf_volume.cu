@@ -366,16 +366,18 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
         const int cb = (int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4);
         k_pack_centres<<<cb, 256, 0, st>>>(d_xb, d_sel_idx, d_w, nc, inv_r, c32, nullptr);
         const size_t smem = sizeof(float4) * 3 * (size_t)std::min<int64_t>(nc, kTileF32);
-        static int occ = -1;
-        if (occ < 0) {
+        static bool attr = false;
+        if (!attr) {
             cudaFuncSetAttribute(k_volume_f32<kVolP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(float4) * 3 * kTileF32));
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_volume_f32<kVolP>, kVolThreads,
-                                                              sizeof(float4) * 3 * kTileF32) !=
-                    cudaSuccess ||
-                occ < 1)
-                occ = 1;
+            attr = true;
         }
+        // resident CTAs per SM for this launch's shared-memory size
+        int occ = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_volume_f32<kVolP>, kVolThreads,
+                                                          smem) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
         const int64_t per = (int64_t)kVolThreads * 2 * kVolP;
         const int64_t want = (nv + per - 1) / per;
         const int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms * occ);
@@ -388,17 +390,17 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
         const int cb = (int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4);
         k_pack_centres_ff<<<cb, 256, 0, st>>>(d_xb, d_sel_idx, d_w, nc, inv_r, cff);
         const size_t smem = sizeof(float4) * 4 * (size_t)std::min<int64_t>(nc, kTileFF);
-        static int occ_ff = -1;
-        if (occ_ff < 0) {
+        static bool attr_ff = false;
+        if (!attr_ff) {
             cudaFuncSetAttribute(k_volume_ff<kVolQFF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(float4) * 4 * kTileFF));
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ff, k_volume_ff<kVolQFF>,
-                                                              kVolThreads,
-                                                              sizeof(float4) * 4 * kTileFF) !=
-                    cudaSuccess ||
-                occ_ff < 1)
-                occ_ff = 1;
+            attr_ff = true;
         }
+        int occ_ff = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_ff, k_volume_ff<kVolQFF>, kVolThreads,
+                                                          smem) != cudaSuccess ||
+            occ_ff < 1)
+            occ_ff = 1;
         const int64_t want =
             (nv + (int64_t)kVolThreads * kVolQFF - 1) / ((int64_t)kVolThreads * kVolQFF);
         const int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms * occ_ff);

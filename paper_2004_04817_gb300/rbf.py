@@ -40,6 +40,8 @@ class Params(C.Structure):
         ("nc_max", C.c_int64),
         ("refine_steps", C.c_int32),
         ("flags", C.c_int32),
+        ("ctas", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 
@@ -57,7 +59,7 @@ class GreedyStats(C.Structure):
         ("final_rms", C.c_double),
         ("min_pivot", C.c_double),
         ("max_resid", C.c_double),
-        ("phase_ns", C.c_int64 * 8),
+        ("phase_ns", C.c_int64 * 12),
     ]
 
 
@@ -96,6 +98,15 @@ def lib():
         L.rbf_status_string.restype = C.c_char_p
         L.rbf_status_string.argtypes = [C.c_int]
         L.rbf_version.restype = C.c_char_p
+        L.rbf_solve_system.restype = C.c_int
+        L.rbf_solve_system.argtypes = [_vp, C.c_int64, _vp, C.c_int64, _vp, P, _vp,
+                                       C.POINTER(C.c_double), _vp, C.c_size_t, _vp]
+        L.rbf_adjoint_workspace_bytes.restype = C.c_size_t
+        L.rbf_adjoint_workspace_bytes.argtypes = [C.c_int64, C.c_int64]
+        L.rbf_deform_volume_adjoint.restype = C.c_int
+        L.rbf_deform_volume_adjoint.argtypes = [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int64,
+                                                _vp, P, _vp, C.POINTER(C.c_double), _vp,
+                                                C.c_size_t, _vp]
         L.rbf_group_of.restype = C.c_int
         L.rbf_group_of.argtypes = [C.c_int64, C.c_int64, C.c_uint64, C.POINTER(C.c_int32)]
         _lib = L
@@ -141,14 +152,14 @@ FLAG_HISTORY_FULL = 1
 
 
 def make_params(radius, tol=0.0, tol_mode=1, eval_prec=PREC_F64, m=1, seed=1, nc_max=0,
-                refine_steps=2, flags=0):
+                refine_steps=2, flags=0, ctas=0):
     return Params(float(radius), float(tol), int(tol_mode), int(eval_prec), int(m), int(seed),
-                  int(nc_max), int(refine_steps), int(flags))
+                  int(nc_max), int(refine_steps), int(flags), int(ctas), 0)
 
 
 def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
                   eval_prec=PREC_F64, hist_cap=0, history_full=False, weights=False,
-                  refine_steps=2, stream=None, workspace=None):
+                  refine_steps=2, ctas=0, stream=None, workspace=None):
     """GCB greedy (m = 1: plain greedy).  Returns a dict with ``idx`` (int32
     CUDA tensor, selection order), ``iter`` (int64), ``nc``, ``hist`` (CUDA
     (n, 6) or None), ``stats`` (dict) and ``status`` (0 or RBF_E_NC_MAX).
@@ -163,7 +174,7 @@ def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
         raise ValueError("xb and db must have the same number of rows")
     nc_max = int(nc_max or min(nb, 4096))
     p = make_params(radius, tol, tol_mode, eval_prec, m, seed, nc_max, refine_steps,
-                    flags=FLAG_HISTORY_FULL if history_full else 0)
+                    flags=FLAG_HISTORY_FULL if history_full else 0, ctas=ctas)
     need = L.rbf_greedy_workspace_bytes(nb, C.byref(p))
     if need == 0:
         raise RBFError(1, "rbf_greedy_workspace_bytes")
@@ -209,6 +220,82 @@ def solve_weights(xb, db, sel_idx, *, radius, refine_steps=2, stream=None, works
                              _ptr(w), C.byref(res), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "rbf_solve_weights")
     return w, res.value
+
+
+def solve_system(xb, sel_idx, rhs, *, radius, refine_steps=2, stream=None, workspace=None):
+    """X (nc, 3) with Phi_SS X = rhs (FP64 factor + refinement); returns
+    (X, max_residual)."""
+    L = lib()
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(sel_idx, torch.int32, "sel_idx")
+    _dev(rhs, torch.float64, "rhs", 3)
+    nc = sel_idx.numel()
+    if rhs.shape[0] != nc:
+        raise ValueError("rhs must have one row per support node")
+    p = make_params(radius, refine_steps=refine_steps)
+    need = L.rbf_solve_workspace_bytes(nc)
+    if need == 0:
+        raise RBFError(1, "rbf_solve_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xb.device)
+    x = torch.empty((nc, 3), dtype=torch.float64, device=xb.device)
+    res = C.c_double(0.0)
+    st = L.rbf_solve_system(_ptr(xb), xb.shape[0], _ptr(sel_idx), nc, _ptr(rhs), C.byref(p),
+                            _ptr(x), C.byref(res), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "rbf_solve_system")
+    return x, res.value
+
+
+def adjoint(xv, xb, sel_idx, gv, *, radius, eval_prec=PREC_F32X2, refine_steps=2,
+            stream=None, workspace=None):
+    """dJ/dd_c = Phi_cc^-1 Phi_vc^T dJ/dd_v (nc, 3); returns (grad, residual)."""
+    L = lib()
+    _dev(xv, torch.float64, "xv", 3)
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(sel_idx, torch.int32, "sel_idx")
+    _dev(gv, torch.float64, "gv", 3)
+    nv, nc = xv.shape[0], sel_idx.numel()
+    if gv.shape[0] != nv:
+        raise ValueError("gv must have one row per volume point")
+    p = make_params(radius, eval_prec=eval_prec, refine_steps=refine_steps)
+    need = L.rbf_adjoint_workspace_bytes(nv, nc)
+    if need == 0:
+        raise RBFError(1, "rbf_adjoint_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xv.device)
+    gc = torch.empty((nc, 3), dtype=torch.float64, device=xv.device)
+    res = C.c_double(0.0)
+    st = L.rbf_deform_volume_adjoint(_ptr(xv), nv, _ptr(xb), xb.shape[0], _ptr(sel_idx), nc,
+                                     _ptr(gv), C.byref(p), _ptr(gc), C.byref(res), _ptr(ws),
+                                     ws.numel(), _stream(stream))
+    _check(st, "rbf_deform_volume_adjoint")
+    return gc, res.value
+
+
+class RBFDeform(torch.autograd.Function):
+    """d_v = Phi_vc Phi_cc^-1 d_c as a differentiable map of the support
+    displacements d_c (nc, 3); the backward pass is the adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, dc, xv, xb, sel_idx, radius, eval_prec):
+        w, _ = solve_system(xb, sel_idx, dc.detach().contiguous(), radius=radius)
+        dv = deform_volume(xv, xb, sel_idx, w, radius=radius, eval_prec=eval_prec)
+        ctx.save_for_backward(xv, xb, sel_idx)
+        ctx.radius = radius
+        ctx.eval_prec = eval_prec
+        return dv
+
+    @staticmethod
+    def backward(ctx, gv):
+        xv, xb, sel_idx = ctx.saved_tensors
+        prec = PREC_F32 if ctx.eval_prec == PREC_F32 else PREC_F32X2
+        gc, _ = adjoint(xv, xb, sel_idx, gv.contiguous(), radius=ctx.radius, eval_prec=prec)
+        return gc, None, None, None, None, None
+
+
+def deform(dc, xv, xb, sel_idx, *, radius, eval_prec=PREC_F32X2):
+    """Differentiable volume deformation (see RBFDeform)."""
+    return RBFDeform.apply(dc, xv, xb, sel_idx, float(radius), int(eval_prec))
 
 
 def deform_volume(xv, xb, sel_idx, w, *, radius, eval_prec=PREC_F32, stream=None,

@@ -1,0 +1,103 @@
+"""GPU parity of the adjoint (dJ/dd_c = Phi_cc^-1 Phi_vc^T dJ/dd_v) with the
+oracle's FP64 gradient, central finite differences of the quadratic
+objective J = sum_v 1/2 |d_v - t_v|^2, and the autograd wrapper."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2004_04817_gb300 as P
+from paper_2004_04817_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _case(n_vol=20_000):
+    c = synth.wing_small(n_vol=n_vol)
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1, history=False)
+    t = synth.random_field(len(c["xv"]), seed=5, sigma=0.01)
+    return c, o["idx"].astype(np.int32), t
+
+
+def _gv(c, S, t):
+    W, _, _ = oracle.solve_weights(c["xb"], c["db"], S, c["radius"])
+    dv = oracle.rbf_sum(c["xv"], c["xb"], S, W, c["radius"])
+    return dv - t
+
+
+@pytest.mark.parametrize("prec", [P.PREC_F32X2, P.PREC_F32])
+def test_adjoint_matches_oracle_gradient(prec):
+    c, S, t = _case()
+    gv = _gv(c, S, t)
+    ref, st = oracle.adjoint(c["xv"], c["xb"], S, c["radius"], gv)
+    g, res = P.adjoint(cuda(c["xv"]), cuda(c["xb"]), cuda(S, torch.int32), cuda(gv),
+                       radius=c["radius"], eval_prec=prec)
+    err = np.abs(g.cpu().numpy() - ref).max() / np.abs(ref).max()
+    # double-float sums: at the FP64 level; FP32 sums: stated, amplified by
+    # the conditioning of Phi_cc
+    assert err <= (1e-8 if prec == P.PREC_F32X2 else 1e-1), err
+
+
+def test_adjoint_central_differences():
+    """J is quadratic in d_c, so central differences are exact up to rounding."""
+    c, S, t = _case(n_vol=5_000)
+    xv, xb, Sd = cuda(c["xv"]), cuda(c["xb"]), cuda(S, torch.int32)
+    dc = cuda(c["db"][S])
+    tt = cuda(t)
+
+    def J(d):
+        dv = P.deform(d, xv, xb, Sd, radius=c["radius"], eval_prec=P.PREC_F64)
+        return 0.5 * float(((dv - tt) ** 2).sum())
+
+    d0 = dc.clone().requires_grad_(True)
+    dv = P.deform(d0, xv, xb, Sd, radius=c["radius"], eval_prec=P.PREC_F32X2)
+    (0.5 * ((dv - tt) ** 2).sum()).backward()
+    g = d0.grad.cpu().numpy()
+    rng = np.random.default_rng(6)
+    h = 1e-6
+    comps = rng.choice(g.size, 60, replace=False)
+    scale = np.abs(g).max()
+    for k in comps:
+        a, b = divmod(int(k), 3)
+        e = torch.zeros_like(dc)
+        e[a, b] = h
+        fd = (J(dc + e) - J(dc - e)) / (2 * h)
+        assert abs(fd - g[a, b]) <= 1e-5 * scale, (k, fd, g[a, b])
+
+
+def test_autograd_matches_adjoint_entry_point():
+    c, S, t = _case(n_vol=8_000)
+    xv, xb, Sd = cuda(c["xv"]), cuda(c["xb"]), cuda(S, torch.int32)
+    d0 = cuda(c["db"][S]).requires_grad_(True)
+    dv = P.deform(d0, xv, xb, Sd, radius=c["radius"])
+    gv = torch.randn_like(dv)
+    dv.backward(gv)
+    g2, _ = P.adjoint(xv, xb, Sd, gv.contiguous(), radius=c["radius"])
+    assert torch.allclose(d0.grad, g2, rtol=0, atol=1e-12 * float(g2.abs().max()))
+
+
+def test_adjoint_full_size():
+    """Support set of the GCB wing (N_b = 50,000, m = 1.5 N_b/N_c) and its
+    2,000,000 volume points; t_v Gaussian (sigma 0.01, seed 5)."""
+    c = synth.wing_gcb(n_vol=2_000_000)
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    xb, db = cuda(c["xb"]), cuda(c["db"])
+    plain = P.greedy_select(xb, db, radius=c["radius"], tol=estar, tol_mode=0, m=1,
+                            eval_prec=P.PREC_F32X2)
+    m = int(round(1.5 * len(c["xb"]) / plain["nc"]))
+    r = P.greedy_select(xb, db, radius=c["radius"], tol=estar, tol_mode=0, m=m,
+                        eval_prec=P.PREC_F32X2, weights=True)
+    S = r["idx"].cpu().numpy()
+    xv = cuda(c["xv"])
+    t = synth.random_field(len(c["xv"]), seed=5, sigma=0.01)
+    dv = P.deform_volume(xv, xb, r["idx"], r["w"], radius=c["radius"], eval_prec=P.PREC_F32X2)
+    gv = dv - cuda(t)
+    g, _ = P.adjoint(xv, xb, r["idx"], gv.contiguous(), radius=c["radius"])
+    ref, st = oracle.adjoint(c["xv"], c["xb"], S, c["radius"], gv.cpu().numpy())
+    err = np.abs(g.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err <= 1e-7, err

@@ -171,6 +171,47 @@ rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, int64_t nb,
                              void *d_ws, size_t ws_bytes, void *stream);
 
 /* --------------------------------------------------------------------------
+ * Batched greedy: many independent problems (for instance one wing per load
+ * case or per design) in ONE cooperative launch.  Problem i runs Algorithm 1
+ * as rbf_greedy_select would, on its own contiguous range of CTAs (at least
+ * one; more for larger groups), with its own workspace segment, barrier and
+ * control block, so problems of very different sizes proceed independently.
+ *
+ *   create  (SYNCHRONOUS, host work): validates, computes each problem's
+ *           partition, assigns CTAs, writes per-problem arguments into d_ws;
+ *           returns an opaque host handle (freed by destroy).
+ *   run     (ASYNC, no host synchronisation or host-memory access, so it can
+ *           be captured in a CUDA graph and replayed): resets the control
+ *           blocks and launches the kernel.
+ *   results (SYNCHRONOUS): status and statistics of every problem.
+ *
+ * All problems must share params.eval_prec; B <= number of co-resident CTAs.
+ * d_sel_idx (int32[nc_max]) and d_w (FP64 nc_max x 3 or NULL) receive each
+ * problem's selection and refined weights; rbf_greedy_batch_nc_device gives
+ * the device array of |S| per problem (int64[B]) for rbf_volume_batch.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const double *d_xb;   /* device FP64 nb x 3 */
+    const double *d_db;   /* device FP64 nb x 3 */
+    int64_t nb;
+    rbf_params params;
+    int32_t *d_sel_idx;   /* device int32[params.nc_max] (output) */
+    double *d_w;          /* device FP64 params.nc_max x 3 or NULL (output) */
+} rbf_greedy_problem;
+
+typedef struct rbf_greedy_batch rbf_greedy_batch;
+
+size_t rbf_greedy_batch_workspace_bytes(const rbf_greedy_problem *h_probs, int B);
+rbf_status rbf_greedy_batch_create(const rbf_greedy_problem *h_probs, int B,
+                                   void *d_ws, size_t ws_bytes, void *stream,
+                                   rbf_greedy_batch **out);
+rbf_status rbf_greedy_batch_run(rbf_greedy_batch *b, void *stream);
+const int64_t *rbf_greedy_batch_nc_device(const rbf_greedy_batch *b);
+rbf_status rbf_greedy_batch_results(rbf_greedy_batch *b, int32_t *h_status,
+                                    rbf_greedy_stats *h_stats, void *stream);
+void rbf_greedy_batch_destroy(rbf_greedy_batch *b);
+
+/* --------------------------------------------------------------------------
  * Support weights: solve Phi_SS W = dX_S (Eqs. 4-5 restricted to S, SPD by
  * Sec. 2) in FP64 by a recurrence Cholesky, then p->refine_steps steps of
  * iterative refinement W += Phi_SS^-1 (dX_S - Phi_SS W) with the residual
@@ -223,6 +264,42 @@ rbf_status rbf_deform_volume(const double *d_xv, int64_t nv,
                              int64_t nc, const double *d_w,
                              const rbf_params *p, double *d_dv,
                              void *d_ws, size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------------------------------
+ * Batched volume sums (Eq. 6) for many problems in one double-float launch,
+ * e.g. after rbf_greedy_batch_run.  The number of centres of each problem is
+ * read on the device (d_nc, e.g. rbf_greedy_batch_nc_device(b) + i), so a
+ * greedy batch and a volume batch can be captured together in one CUDA
+ * graph.  The tile shape (threads per CTA, points per thread) is chosen at
+ * create time by timing each candidate on the given problems -- create RUNS
+ * the kernels (outputs are overwritten) and needs valid inputs, including
+ * d_nc.  eval_prec must be RBF_PREC_F32X2; nc_max <= 1024.
+ *   create: SYNCHRONOUS.  run: ASYNC (capturable).  info: chosen shape and
+ *   the time of each candidate (4 floats, ms).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const double *d_xv;       /* device FP64 nv x 3 */
+    int64_t nv;
+    const double *d_xb;       /* device FP64 boundary coordinates */
+    const int32_t *d_sel_idx; /* device int32[nc_max] */
+    const double *d_w;        /* device FP64 nc_max x 3 */
+    const int64_t *d_nc;      /* device: number of centres in use */
+    int64_t nc_max;
+    double radius;
+    double *d_dv;             /* device FP64 nv x 3 (output) */
+} rbf_volume_problem;
+
+typedef struct rbf_volume_batch rbf_volume_batch;
+
+size_t rbf_volume_batch_workspace_bytes(const rbf_volume_problem *h_probs, int B,
+                                        int eval_prec);
+rbf_status rbf_volume_batch_create(const rbf_volume_problem *h_probs, int B, int eval_prec,
+                                   void *d_ws, size_t ws_bytes, void *stream,
+                                   rbf_volume_batch **out);
+rbf_status rbf_volume_batch_run(rbf_volume_batch *b, void *stream);
+rbf_status rbf_volume_batch_info(const rbf_volume_batch *b, int *threads,
+                                 int *points_per_thread, float *candidate_ms);
+void rbf_volume_batch_destroy(rbf_volume_batch *b);
 
 /* --------------------------------------------------------------------------
  * Volume displacements without any device allocation or caller workspace.

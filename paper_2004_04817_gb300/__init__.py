@@ -17,6 +17,8 @@ from .rbf import (  # noqa: F401
     adjoint,
     deform,
     RBFDeform,
+    GreedyBatch,
+    VolumeBatch,
     measure_fma_peak,
     group_of,
     status_string,

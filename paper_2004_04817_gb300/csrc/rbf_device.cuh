@@ -385,9 +385,11 @@ __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// `epoch` counts the barriers this CTA has passed (the same in every CTA).
+// `epoch` counts the barriers this CTA has passed (the same in every CTA);
+// `my_block` is the CTA's index among the nblocks taking part.
 __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, unsigned int nblocks,
-                                             uint64_t limit_ns, unsigned int &epoch)
+                                             uint64_t limit_ns, unsigned int &epoch,
+                                             unsigned int my_block)
 {
     __shared__ int s_ok;
     const unsigned int target = epoch + 1;
@@ -396,7 +398,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, unsigned
         int ok = 1;
         if (threadIdx.x == 0) {
             __threadfence();
-            st_release_u32(&bar->arrive[blockIdx.x], target);
+            st_release_u32(&bar->arrive[my_block], target);
         }
         __syncwarp();
         const uint64_t t0 = globaltimer_ns();
@@ -420,7 +422,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, unsigned
         ok = __all_sync(0xffffffffu, ok);
         if (threadIdx.x == 0) {
             s_ok = ok;
-            if (blockIdx.x == 0)
+            if (my_block == 0)
                 bar->wait_ns += globaltimer_ns() - t0;
         }
     }

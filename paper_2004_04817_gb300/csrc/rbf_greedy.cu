@@ -30,6 +30,12 @@
 
 namespace rbf {
 
+// Index of this CTA among the CTAs that run one problem, and their number.
+// A single-problem launch uses the hardware ids; a batched launch gives each
+// problem a contiguous range of CTAs.  Set by each kernel on entry.
+__shared__ int g_vb;
+__shared__ int g_vg;
+
 constexpr int kGThreads = 256;
 constexpr int kGWarps = kGThreads / kWarp;
 constexpr int kMaxGrid = 4096;
@@ -107,6 +113,7 @@ struct GreedyArgs {
     D4 *tvec;
     double *w_out;                // optional FP64 weights output (nc x 3)
     int refine_steps;
+    long long *nc_out;            // optional: |S| at exit (device, for batched runs)
 };
 
 __device__ __forceinline__ int goff(int i, int nb, int m)
@@ -431,20 +438,20 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
                            int pn, int node, long long kiter, unsigned int &epoch)
 {
     GreedyCtl *ctl = a.ctl;
-    const int G = gridDim.x;
+    const int G = g_vg;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gtid = blockIdx.x * kGThreads + tid;
+    const int gtid = g_vb * kGThreads + tid;
     const int gthreads = G * kGThreads;
-    const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
+    const int gwarp = g_vb * kGWarps + warp, gwarps = G * kGWarps;
     // A1: b_j = phi(|r_n - r_j| / R), centre j on CTA j mod G (FP64 work
     // spread over every SM)
     const D4 xn = ldcg(a.xg64 + pn);
-    for (int j = blockIdx.x + G * tid; j < nc; j += G * kGThreads) {
+    for (int j = g_vb + G * tid; j < nc; j += G * kGThreads) {
         const D4 c = ldcg(a.c64 + j);
         const double dx = xn.x - c.x, dy = xn.y - c.y, dz = xn.z - c.z;
         a.bvec[j] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
     }
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) return kAppendTimeout;
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
     // A2: l = Z b (warp per row) and partial sums of l.l and l.y
     double acc4[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = gwarp; i < nc; i += gwarps) {
@@ -461,14 +468,14 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
     block_sum4(red, acc4);
     if (tid == 0)
         for (int c = 0; c < 4; ++c)
-            (a.part + (size_t)(use & 1) * kMaxGrid * 4)[4 * blockIdx.x + c] = acc4[c];
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) return kAppendTimeout;
+            (a.part + (size_t)(use & 1) * kMaxGrid * 4)[4 * g_vb + c] = acc4[c];
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
     double s4[4];
     grid_sum4((a.part + (size_t)(use & 1) * kMaxGrid * 4), G, s4);
     ++use;
     const double d2 = 1.0 - s4[0];   // phi(0) = 1
     if (!(d2 > kPivotMin)) {
-        if (blockIdx.x == 0 && tid == 0)
+        if (g_vb == 0 && tid == 0)
             ctl->status = RBF_E_NOT_SPD;
         return kAppendNotSpd;
     }
@@ -500,7 +507,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
             a.cwff[4 * j + 3] = make_float4(lx, ly, lz, 0.0f);
         }
     }
-    if (blockIdx.x == 0 && tid == 0) {
+    if (g_vb == 0 && tid == 0) {
         a.z[(size_t)nc * a.ld + nc] = inv_d;
         a.zt[(size_t)nc * a.ld + nc] = inv_d;
         a.y64[nc] = mk4(yx, yy, yz, 0.0);   // y_new = (dr_n - l.y) / d
@@ -530,7 +537,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
         if (a.sel_iter)
             a.sel_iter[nc] = kiter;
     }
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) return kAppendTimeout;
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
     ++nc;
     return kAppendOk;
 }
@@ -548,11 +555,11 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
                                D4 *tvec, double &maxres)
 {
     GreedyCtl *ctl = a.ctl;
-    const int G = gridDim.x;
+    const int G = g_vg;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gtid = blockIdx.x * kGThreads + tid;
+    const int gtid = g_vb * kGThreads + tid;
     const int gthreads = G * kGThreads;
-    const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
+    const int gwarp = g_vb * kGWarps + warp, gwarps = G * kGWarps;
     const int ts = team_size(nc, G);
     const int sub = lane & (ts - 1);
     const int team = gtid / ts, nteams = gthreads / ts;
@@ -579,9 +586,9 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
         if (tid == 0) {
             for (int k = 1; k < kGWarps; ++k)
                 lmax = fmax(lmax, red.v[k]);
-            pp[4 * blockIdx.x] = lmax;
+            pp[4 * g_vb] = lmax;
         }
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch))
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
             return false;
         {
             double g4[4];
@@ -598,7 +605,7 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
             if (lane == 0)
                 tvec[i] = mk4(sx, sy, sz, 0.0);
         }
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch))
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
             return false;
         // W += Z^T t
         for (int j = gwarp; j < nc; j += gwarps) {
@@ -612,16 +619,16 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
                 a.w64[j] = w;
             }
         }
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch))
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
             return false;
     }
     return true;
 }
 
 // ---------------------------------------------------------------------------
-// The persistent kernel.
+// The persistent greedy: one problem on the CTAs g_vb = 0 .. g_vg - 1.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
+__device__ __forceinline__ void greedy_body(const GreedyArgs &a)
 {
     extern __shared__ float4 s_cw[];
     __shared__ Red red;
@@ -632,11 +639,11 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
         mbar_init(&s_mbar, 1);
     __syncthreads();
     GreedyCtl *ctl = a.ctl;
-    const int G = gridDim.x;
+    const int G = g_vg;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gtid = blockIdx.x * kGThreads + tid;
+    const int gtid = g_vb * kGThreads + tid;
     const int gthreads = G * kGThreads;
-    const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
+    const int gwarp = g_vb * kGWarps + warp, gwarps = G * kGWarps;
     const int nb = a.nb, m = a.m;
     int use = 0;   // partial-buffer use counter (double buffering)
     unsigned int epoch = 0;   // grid barriers passed
@@ -646,7 +653,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
     unsigned long long ph_t = globaltimer_ns();
     int ph_cur = 0;
     auto phase = [&](int nx) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (g_vb == 0 && threadIdx.x == 0) {
             const unsigned long long now = globaltimer_ns();
             ph_acc[ph_cur] += now - ph_t;
             ph_t = now;
@@ -657,18 +664,18 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
     auto parti = [&](int u) { return a.parti + (size_t)(u & 1) * kMaxGrid; };
 #define GSYNC()                                                                   \
     do {                                                                          \
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) \
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) \
             return;                                                               \
     } while (0)
 #define GSYNC_B()                                                                 \
     do {                                                                          \
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) \
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) \
             return false;                                                         \
     } while (0)
 
     // Failure-path test: CTA 0 leaves before the first barrier, so the other
     // CTAs' bounded waits run out and the launch returns RBF_E_TIMEOUT.
-    if ((a.flags & RBF_FLAG_TEST_BARRIER_TIMEOUT) && blockIdx.x == 0)
+    if ((a.flags & RBF_FLAG_TEST_BARRIER_TIMEOUT) && g_vb == 0)
         return;
 
     // ---------------- prologue: group-ordered packing ----------------------
@@ -706,7 +713,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
             for (int k = 1; k < kGWarps; ++k)
                 for (int c = 0; c < 3; ++c)
                     mx[c] = fmax(mx[c], red.s[k][c]);
-            double *pp = part(use) + 4 * blockIdx.x;
+            double *pp = part(use) + 4 * g_vb;
             pp[0] = mx[0];
             pp[1] = mx[1];
             pp[2] = mx[2];
@@ -718,7 +725,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
     grid_max4(part(use), G, g4);
     ++use;
     if (g4[2] > 0.0) {
-        if (blockIdx.x == 0 && tid == 0)
+        if (g_vb == 0 && tid == 0)
             ctl->status = RBF_E_NONFINITE;
         return;   // every CTA sees the same flag
     }
@@ -746,8 +753,8 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
         }
         block_pick(red, bv, bi);
         if (tid == 0) {
-            part(use)[blockIdx.x] = bv;
-            parti(use)[blockIdx.x] = bi;
+            part(use)[g_vb] = bv;
+            parti(use)[g_vb] = bi;
         }
         GSYNC();
         double v;
@@ -763,7 +770,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
     for (int s = 0; s < 3; ++s) {
         const int pn = ldcg(a.pos_of_node + seeds[s]);
         if (chol_append(a, red, nc, use, min_piv, pn, seeds[s], -1, epoch) != kAppendOk) {
-            if (blockIdx.x == 0 && tid == 0) {
+            if (g_vb == 0 && tid == 0) {
                 ctl->nc = nc;
                 ctl->min_pivot = min_piv;
             }
@@ -811,7 +818,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
                     }
                 }
             }
-            if (blockIdx.x == 0 && tid == 0)
+            if (g_vb == 0 && tid == 0)
                 pairs64 += (long long)nq * nc;
         } else {
             // ---- pass 1: FP32 or double-float errors E~ with a bound beta,
@@ -899,7 +906,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
                         }
                     }
                 }
-                if (blockIdx.x == 0 && tid == 0)
+                if (g_vb == 0 && tid == 0)
                     pairs32 += (long long)nq * nc;
             } else {
                 const float4 *cw = smem ? s_cw : a.cwff;
@@ -965,7 +972,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
                         }
                     }
                 }
-                if (blockIdx.x == 0 && tid == 0)
+                if (g_vb == 0 && tid == 0)
                     pairsff += (long long)nq * nc;
             }
         }
@@ -1015,12 +1022,12 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
                         u2 = fmax(u2, ou1);
                     }
                 }
-                double *pp = part(use) + 4 * blockIdx.x;
+                double *pp = part(use) + 4 * g_vb;
                 pp[0] = mx;
                 pp[1] = a4[1];
                 pp[2] = u1;
                 pp[3] = u2;
-                parti(use)[blockIdx.x] = n1;
+                parti(use)[g_vb] = n1;
             }
         }
         phase(10);
@@ -1085,7 +1092,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
             ++use;
         }
         phase(11);
-        if (blockIdx.x == 0 && tid == 0) {
+        if (g_vb == 0 && tid == 0) {
             ctl->slot[(r + 2) % 3] = 0ull;
             ctl->tslot[(r + 2) % 3] = 0ull;
         }
@@ -1135,7 +1142,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
                 const unsigned long long k64 = ldcg(&ctl->slot[r2]);
                 if (k64)
                     out.key = k64;
-                if (blockIdx.x == 0 && tid == 0)
+                if (g_vb == 0 && tid == 0)
                     ctl->slot[(r2 + 2) % 3] = 0ull;
                 ++ev;
                 // the certified maximum of a node that adds nothing
@@ -1200,7 +1207,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
             gmax = d.gmax;
             grms = sqrt(d.gsq / (double)nb);
         }
-        if (blockIdx.x == 0 && tid == 0 && a.hist && nhist < a.hist_cap) {
+        if (g_vb == 0 && tid == 0 && a.hist && nhist < a.hist_cap) {
             double *h = a.hist + RBF_HIST_COLS * nhist;
             h[0] = (double)k;
             h[1] = (double)nc_before;
@@ -1228,7 +1235,9 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
         }
     }
     phase(5);
-    if (blockIdx.x == 0 && tid == 0) {
+    if (g_vb == 0 && tid == 0) {
+        if (a.nc_out)
+            *a.nc_out = nc;
         for (int i = 0; i < 12; ++i)
             ctl->phase_ns[i] = ph_acc[i];
         ctl->phase_ns[6] = ctl->bar.wait_ns;
@@ -1253,6 +1262,41 @@ __global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
 #undef GSYNC_B
 }
 
+// One problem on the whole grid.
+__global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
+{
+    if (threadIdx.x == 0) {
+        g_vb = blockIdx.x;
+        g_vg = gridDim.x;
+    }
+    __syncthreads();
+    greedy_body(a);
+}
+
+// Many problems in one launch: problem i runs on CTAs [cta_start[i],
+// cta_start[i + 1]) with its own workspace, control block and barrier.
+__global__ void __launch_bounds__(kGThreads, 2)
+k_greedy_batched(const GreedyArgs *__restrict__ args, const int *__restrict__ cta_start, int B)
+{
+    __shared__ int s_prob;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = B - 1;   // last i with cta_start[i] <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (cta_start[mid] <= (int)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        s_prob = lo;
+        g_vb = blockIdx.x - cta_start[lo];
+        g_vg = cta_start[lo + 1] - cta_start[lo];
+    }
+    __syncthreads();
+    const GreedyArgs a = args[s_prob];
+    greedy_body(a);
+}
+
 
 // ---------------------------------------------------------------------------
 // Support weights (Eqs. 4-5 on S): recurrence-Cholesky appends in the given
@@ -1265,18 +1309,23 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
         const double *__restrict__ rhs)
 {
     __shared__ Red red;
+    if (threadIdx.x == 0) {
+        g_vb = blockIdx.x;
+        g_vg = gridDim.x;
+    }
+    __syncthreads();
     GreedyCtl *ctl = a.ctl;
-    const int G = gridDim.x;
+    const int G = g_vg;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gtid = blockIdx.x * kGThreads + tid;
+    const int gtid = g_vb * kGThreads + tid;
     const int gthreads = G * kGThreads;
-    const int gwarp = blockIdx.x * kGWarps + warp, gwarps = G * kGWarps;
+    const int gwarp = g_vb * kGWarps + warp, gwarps = G * kGWarps;
     int use = 0;
     unsigned int epoch = 0;
     auto part = [&](int u) { return a.part + (size_t)(u & 1) * kMaxGrid * 4; };
 #define GSYNC()                                                                   \
     do {                                                                          \
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch)) \
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) \
             return;                                                               \
     } while (0)
 
@@ -1311,7 +1360,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
         if (tid == 0) {
             for (int k = 1; k < kGWarps; ++k)
                 mx = fmax(mx, red.v[k]);
-            part(use)[4 * blockIdx.x] = mx;
+            part(use)[4 * g_vb] = mx;
         }
     }
     GSYNC();
@@ -1320,7 +1369,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
         grid_max4(part(use), G, g4);   // slot 0 of each CTA's partial
         ++use;
         if (g4[0] > 0.0) {
-            if (blockIdx.x == 0 && tid == 0)
+            if (g_vb == 0 && tid == 0)
                 ctl->status = g4[0] > 1.5 ? RBF_E_ARG : RBF_E_NONFINITE;
             return;
         }
@@ -1331,7 +1380,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
         const int node = sel[j];
         const int r = chol_append(a, red, nc, use, min_piv, j, node, -1, epoch);
         if (r != kAppendOk) {
-            if (blockIdx.x == 0 && tid == 0) {
+            if (g_vb == 0 && tid == 0) {
                 ctl->nc = nc;
                 ctl->min_pivot = min_piv;
             }
@@ -1347,7 +1396,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
         w_out[3 * j + 1] = w.y;
         w_out[3 * j + 2] = w.z;
     }
-    if (blockIdx.x == 0 && tid == 0) {
+    if (g_vb == 0 && tid == 0) {
         ctl->nc = nc;
         ctl->min_pivot = min_piv;
         ctl->final_max = maxres;
@@ -1671,4 +1720,243 @@ extern "C" rbf_status rbf_solve_system(const double *d_xb, int64_t nb, const int
         return RBF_E_ARG;
     return solve_launch(d_xb, nullptr, nb, d_sel_idx, nc, d_rhs, p, d_x, h_max_resid, d_ws,
                         ws_bytes, stream);
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched greedy: many independent problems in one cooperative launch.
+// ---------------------------------------------------------------------------
+struct rbf_greedy_batch {
+    int B = 0;
+    int grid = 0;
+    size_t smem = 0;
+    int prec = 0;
+    char *ws = nullptr;
+    std::vector<size_t> ctl_off;     // control block of each problem (reset per run)
+    size_t args_off = 0, start_off = 0, nc_off = 0;
+};
+
+namespace rbf {
+struct BatchLayout {
+    size_t args, start, nc, total;
+    std::vector<size_t> prob;        // workspace segment of each problem
+};
+
+static BatchLayout batch_layout(const rbf_greedy_problem *h, int B)
+{
+    BatchLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    L.args = take(sizeof(GreedyArgs) * (size_t)B);
+    L.start = take(sizeof(int) * (size_t)(B + 1));
+    L.nc = take(sizeof(long long) * (size_t)B);
+    L.prob.resize(B);
+    for (int i = 0; i < B; ++i)
+        L.prob[i] = take(greedy_ws_layout(h[i].nb, h[i].params.nc_max).total);
+    L.total = o;
+    return L;
+}
+}  // namespace rbf
+
+extern "C" size_t rbf_greedy_batch_workspace_bytes(const rbf_greedy_problem *h_probs, int B)
+{
+    if (!h_probs || B < 1)
+        return 0;
+    for (int i = 0; i < B; ++i)
+        if (!greedy_args_ok(h_probs[i].nb, &h_probs[i].params))
+            return 0;
+    return batch_layout(h_probs, B).total;
+}
+
+extern "C" rbf_status rbf_greedy_batch_create(const rbf_greedy_problem *h_probs, int B,
+                                              void *d_ws, size_t ws_bytes, void *stream,
+                                              rbf_greedy_batch **out)
+{
+    if (!h_probs || B < 1 || !out)
+        return RBF_E_ARG;
+    *out = nullptr;
+    const int prec = h_probs[0].params.eval_prec;
+    for (int i = 0; i < B; ++i) {
+        const rbf_greedy_problem &q = h_probs[i];
+        if (!greedy_args_ok(q.nb, &q.params) || !q.d_xb || !q.d_db || !q.d_sel_idx ||
+            q.params.eval_prec != prec || q.params.refine_steps < 0 ||
+            q.params.refine_steps > 16 || (q.params.flags & RBF_FLAG_TEST_BARRIER_TIMEOUT))
+            return RBF_E_ARG;
+    }
+    const BatchLayout L = batch_layout(h_probs, B);
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
+        return RBF_E_WORKSPACE;
+    DeviceInfo dev;
+    if (!device_info(&dev) || !dev.coop)
+        return RBF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)d_ws;
+    const size_t smem =
+        prec == RBF_PREC_F32 ? sizeof(float4) * 2 * kSmemCentresF32
+        : prec == RBF_PREC_F32X2 ? sizeof(float4) * 4 * kSmemCentresFF : 0;
+    if (cudaFuncSetAttribute(k_greedy_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float4) * 4 * kSmemCentresFF)) != cudaSuccess)
+        return RBF_E_CUDA;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_greedy_batched, kGThreads, smem) !=
+            cudaSuccess ||
+        occ < 1)
+        return RBF_E_CUDA;
+    const int total = std::min(dev.sms * std::min(occ, 2), kMaxGrid);
+    if (total < B)
+        return RBF_E_ARG;   // every problem needs a CTA of its own
+    // CTAs: one each, the rest in proportion to the group sizes (the work of
+    // one evaluation), capped at 32 per problem
+    std::vector<double> wgt(B);
+    double wsum = 0.0;
+    for (int i = 0; i < B; ++i) {
+        wgt[i] = (double)((h_probs[i].nb + h_probs[i].params.m - 1) / h_probs[i].params.m);
+        wsum += wgt[i];
+    }
+    std::vector<int> ctas(B, 1);
+    int left = total - B;
+    for (int i = 0; i < B && left > 0; ++i) {
+        const int extra = std::min(left, std::min(31, (int)(wgt[i] / wsum * (total - B))));
+        ctas[i] += extra;
+        left -= extra;
+    }
+    std::vector<int> start(B + 1, 0);
+    for (int i = 0; i < B; ++i)
+        start[i + 1] = start[i] + ctas[i];
+    std::vector<GreedyArgs> args(B);
+    for (int i = 0; i < B; ++i) {
+        const rbf_greedy_problem &q = h_probs[i];
+        const GreedyWs G = greedy_ws_layout(q.nb, q.params.nc_max);
+        char *pw = ws + L.prob[i];
+        std::vector<int32_t> perm((size_t)q.nb);
+        fisher_yates(q.nb, q.params.seed, perm.data());
+        if (cudaMemcpyAsync(pw + G.perm, perm.data(), sizeof(int32_t) * q.nb,
+                            cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return RBF_E_CUDA;
+        GreedyArgs &a = args[i];
+        a = GreedyArgs{};
+        a.xb = q.d_xb;
+        a.db = q.d_db;
+        a.nb = (int)q.nb;
+        a.m = (int)q.params.m;
+        a.nc_max = (int)q.params.nc_max;
+        a.prec = prec;
+        a.inv_r = 1.0 / q.params.radius;
+        a.tol = q.params.tol;
+        a.tol_mode = q.params.tol_mode;
+        a.flags = q.params.flags;
+        a.barrier_ns = kBarrierLimitNs;
+        a.ld = (int)q.params.nc_max;
+        a.sel_idx = q.d_sel_idx;
+        a.sel_iter = nullptr;
+        a.hist = nullptr;
+        a.hist_cap = 0;
+        a.w_out = q.d_w;
+        a.refine_steps = q.params.refine_steps;
+        fill_args(a, pw, G);
+        a.nc_out = (long long *)(ws + L.nc) + i;
+    }
+    if (cudaMemcpyAsync(ws + L.args, args.data(), sizeof(GreedyArgs) * B, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(ws + L.start, start.data(), sizeof(int) * (B + 1),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RBF_E_CUDA;
+    rbf_greedy_batch *b = new rbf_greedy_batch();
+    b->B = B;
+    b->grid = start[B];
+    b->smem = smem;
+    b->prec = prec;
+    b->ws = ws;
+    b->args_off = L.args;
+    b->start_off = L.start;
+    b->nc_off = L.nc;
+    b->ctl_off.resize(B);
+    for (int i = 0; i < B; ++i)
+        b->ctl_off[i] = L.prob[i] + greedy_ws_layout(h_probs[i].nb, h_probs[i].params.nc_max).ctl;
+    *out = b;
+    return RBF_OK;
+}
+
+extern "C" rbf_status rbf_greedy_batch_run(rbf_greedy_batch *b, void *stream)
+{
+    if (!b)
+        return RBF_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < b->B; ++i)
+        if (cudaMemsetAsync(b->ws + b->ctl_off[i], 0, sizeof(GreedyCtl), st) != cudaSuccess)
+            return RBF_E_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)b->grid);
+    cfg.blockDim = dim3(kGThreads);
+    cfg.dynamicSmemBytes = b->smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const GreedyArgs *args = (const GreedyArgs *)(b->ws + b->args_off);
+    const int *start = (const int *)(b->ws + b->start_off);
+    if (cudaLaunchKernelEx(&cfg, k_greedy_batched, args, start, b->B) != cudaSuccess) {
+        cudaGetLastError();
+        return RBF_E_CUDA;
+    }
+    return RBF_OK;
+}
+
+extern "C" const int64_t *rbf_greedy_batch_nc_device(const rbf_greedy_batch *b)
+{
+    return b ? (const int64_t *)(b->ws + b->nc_off) : nullptr;
+}
+
+extern "C" rbf_status rbf_greedy_batch_results(rbf_greedy_batch *b, int32_t *h_status,
+                                               rbf_greedy_stats *h_stats, void *stream)
+{
+    if (!b)
+        return RBF_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return RBF_E_CUDA;
+    }
+    rbf_status worst = RBF_OK;
+    for (int i = 0; i < b->B; ++i) {
+        GreedyCtl ctl;
+        if (cudaMemcpy(&ctl, b->ws + b->ctl_off[i], sizeof(ctl), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return RBF_E_CUDA;
+        if (h_status)
+            h_status[i] = ctl.status;
+        if (ctl.status != RBF_OK && worst == RBF_OK)
+            worst = (rbf_status)ctl.status;
+        if (h_stats) {
+            rbf_greedy_stats &t = h_stats[i];
+            t.iterations = ctl.iterations;
+            t.nc = ctl.nc;
+            t.full_checks = ctl.full_checks;
+            t.pairs_f32 = ctl.pairs_f32;
+            t.pairs_f64 = ctl.pairs_f64;
+            t.pairs_ff = ctl.pairs_ff;
+            t.rescored = (int64_t)ctl.rescored;
+            t.estar = ctl.estar;
+            t.final_max = ctl.final_max;
+            t.final_rms = ctl.final_rms;
+            t.min_pivot = ctl.min_pivot;
+            t.max_resid = ctl.max_resid;
+            for (int k = 0; k < 12; ++k)
+                t.phase_ns[k] = (int64_t)ctl.phase_ns[k];
+        }
+    }
+    return worst;
+}
+
+extern "C" void rbf_greedy_batch_destroy(rbf_greedy_batch *b)
+{
+    delete b;
 }

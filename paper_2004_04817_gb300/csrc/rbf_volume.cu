@@ -8,6 +8,7 @@
 // FP64 kernel: the same structure in double precision (reference arithmetic).
 #include <algorithm>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "rbf_device.cuh"
@@ -423,4 +424,336 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
     if (cudaGetLastError() != cudaSuccess)
         return RBF_E_CUDA;
     return RBF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched volume sums: many problems (each its own points, support set and
+// weights) in one launch of the double-float kernel.  Work items are tiles of
+// THREADS * P points; CTA b takes a contiguous run of items, so it reloads
+// the shared-memory centre table only when its run crosses into the next
+// problem.  The tile shape is chosen at create time by timing the candidate
+// instantiations on the real problems (self-written autotuner).
+// ---------------------------------------------------------------------------
+namespace rbf {
+
+struct VolProbDev {
+    const double *xv;
+    int64_t nv;
+    const float4 *table;      // (c_hi, c_lo, w_hi, w_lo) per centre
+    const int64_t *nc;        // device count of centres
+    double *dv;
+    double inv_r;
+    int64_t item0;            // first work item of the problem
+};
+
+__global__ void k_vb_pack(const rbf_volume_problem *__restrict__ probs, int B,
+                          float4 *const *__restrict__ tables, int max_nc)
+{
+    const int i = blockIdx.y;
+    if (i >= B)
+        return;
+    const rbf_volume_problem q = probs[i];
+    const int nc = (int)min((int64_t)max_nc, *q.d_nc);
+    const double inv_r = 1.0 / q.radius;
+    float4 *t = tables[i];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nc; j += gridDim.x * blockDim.x) {
+        const int64_t n = q.d_sel_idx[j];
+        float h0, l0, h1, l1, h2, l2;
+        split_f64(q.d_xb[3 * n] * inv_r, h0, l0);
+        split_f64(q.d_xb[3 * n + 1] * inv_r, h1, l1);
+        split_f64(q.d_xb[3 * n + 2] * inv_r, h2, l2);
+        t[4 * j] = make_float4(h0, h1, h2, 0.0f);
+        t[4 * j + 1] = make_float4(l0, l1, l2, 0.0f);
+        split_f64(q.d_w[3 * j], h0, l0);
+        split_f64(q.d_w[3 * j + 1], h1, l1);
+        split_f64(q.d_w[3 * j + 2], h2, l2);
+        t[4 * j + 2] = make_float4(h0, h1, h2, 0.0f);
+        t[4 * j + 3] = make_float4(l0, l1, l2, 0.0f);
+    }
+}
+
+template <int THREADS, int P>
+__global__ void __launch_bounds__(THREADS)
+k_vb_volume_ff(const VolProbDev *__restrict__ probs, int B, int64_t n_items, int64_t per_cta)
+{
+    extern __shared__ float4 s_tab[];
+    const int tid = threadIdx.x;
+    const int64_t it0 = (int64_t)blockIdx.x * per_cta;
+    const int64_t it1 = min(n_items, it0 + per_cta);
+    int cur = -1, nc = 0;
+    VolProbDev q{};
+    for (int64_t it = it0; it < it1; ++it) {
+        // problem of this item: last i with item0 <= it
+        int lo = 0, hi = B - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (probs[mid].item0 <= it)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        if (lo != cur) {
+            cur = lo;
+            q = probs[cur];
+            nc = (int)*q.nc;
+            __syncthreads();
+            for (int j = tid; j < 4 * nc; j += THREADS)
+                s_tab[j] = q.table[j];
+            __syncthreads();
+        }
+        const int64_t base = (it - q.item0) * (int64_t)THREADS * P;
+        float qh[P][3], ql[P][3];
+        ff acc[P][3];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            int64_t v = base + (int64_t)i * THREADS + tid;
+            v = v < q.nv ? v : q.nv - 1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                split_f64(q.xv[3 * v + c] * q.inv_r, qh[i][c], ql[i][c]);
+                acc[i][c] = ff{0.0f, 0.0f};
+            }
+        }
+        for (int j = 0; j < nc; ++j) {
+            const float4 ch = s_tab[4 * j], cl = s_tab[4 * j + 1];
+            const float4 wh = s_tab[4 * j + 2], wl = s_tab[4 * j + 3];
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const ff s2 = dist2_ff(qh[i][0], ql[i][0], qh[i][1], ql[i][1], qh[i][2], ql[i][2],
+                                       ch.x, cl.x, ch.y, cl.y, ch.z, cl.z);
+                const ff ph = phi_ff_s(s2);
+                ff_fma_acc(acc[i][0], wh.x, wl.x, ph);
+                ff_fma_acc(acc[i][1], wh.y, wl.y, ph);
+                ff_fma_acc(acc[i][2], wh.z, wl.z, ph);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int64_t v = base + (int64_t)i * THREADS + tid;
+            if (v < q.nv)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    q.dv[3 * v + c] = (double)acc[i][c].h + (double)acc[i][c].l;
+        }
+    }
+}
+
+constexpr int kVbMaxCentres = 1024;   // shared-memory table: 64 KB
+
+struct VbCandidate {
+    int threads, p;
+};
+static const VbCandidate kVbCands[4] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}};
+
+struct VbLayout {
+    size_t probs_host, probs_dev, tables_ptr, tables, total;
+};
+
+static VbLayout vb_layout(int B, int64_t sum_ncmax)
+{
+    VbLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    L.probs_host = take(sizeof(rbf_volume_problem) * (size_t)B);
+    L.probs_dev = take(sizeof(VolProbDev) * (size_t)B);
+    L.tables_ptr = take(sizeof(float4 *) * (size_t)B);
+    L.tables = take(sizeof(float4) * 4 * (size_t)sum_ncmax);
+    L.total = o;
+    return L;
+}
+
+}  // namespace rbf
+
+struct rbf_volume_batch {
+    int B = 0;
+    int cand = 0;
+    int grid = 0;
+    int64_t n_items = 0, per_cta = 0;
+    int max_nc = 0;
+    char *ws = nullptr;
+    size_t probs_host = 0, probs_dev = 0, tables_ptr = 0;
+    float cand_ms[4] = {0, 0, 0, 0};
+};
+
+namespace rbf {
+static cudaError_t vb_launch(const rbf_volume_batch *b, int cand, cudaStream_t st)
+{
+    const rbf_volume_problem *ph = (const rbf_volume_problem *)(b->ws + b->probs_host);
+    float4 *const *tp = (float4 *const *)(b->ws + b->tables_ptr);
+    k_vb_pack<<<dim3(4, b->B), 256, 0, st>>>(ph, b->B, tp, b->max_nc);
+    const VbCandidate c = kVbCands[cand];
+    const int64_t tile = (int64_t)c.threads * c.p;
+    (void)tile;
+    const VolProbDev *pd = (const VolProbDev *)(b->ws + b->probs_dev);
+    const size_t smem = sizeof(float4) * 4 * (size_t)b->max_nc;
+    switch (cand) {
+    case 0: k_vb_volume_ff<128, 1><<<b->grid, 128, smem, st>>>(pd, b->B, b->n_items, b->per_cta); break;
+    case 1: k_vb_volume_ff<128, 2><<<b->grid, 128, smem, st>>>(pd, b->B, b->n_items, b->per_cta); break;
+    case 2: k_vb_volume_ff<256, 1><<<b->grid, 256, smem, st>>>(pd, b->B, b->n_items, b->per_cta); break;
+    default: k_vb_volume_ff<256, 2><<<b->grid, 256, smem, st>>>(pd, b->B, b->n_items, b->per_cta); break;
+    }
+    return cudaGetLastError();
+}
+
+// item layout depends on the tile size of the candidate
+static rbf_status vb_configure(rbf_volume_batch *b, const rbf_volume_problem *h, int cand,
+                               const std::vector<float4 *> &tables, cudaStream_t st, int sms)
+{
+    const VbCandidate c = kVbCands[cand];
+    const int64_t tile = (int64_t)c.threads * c.p;
+    std::vector<VolProbDev> pd(b->B);
+    int64_t items = 0;
+    for (int i = 0; i < b->B; ++i) {
+        pd[i].xv = h[i].d_xv;
+        pd[i].nv = h[i].nv;
+        pd[i].table = tables[i];
+        pd[i].nc = h[i].d_nc;
+        pd[i].dv = h[i].d_dv;
+        pd[i].inv_r = 1.0 / h[i].radius;
+        pd[i].item0 = items;
+        items += (h[i].nv + tile - 1) / tile;
+    }
+    b->n_items = items;
+    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * 8));
+    b->per_cta = (items + b->grid - 1) / b->grid;
+    b->grid = (int)((items + b->per_cta - 1) / b->per_cta);
+    if (cudaMemcpyAsync(b->ws + b->probs_dev, pd.data(), sizeof(VolProbDev) * b->B,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RBF_E_CUDA;
+    b->cand = cand;
+    return RBF_OK;
+}
+}  // namespace rbf
+
+extern "C" size_t rbf_volume_batch_workspace_bytes(const rbf_volume_problem *h_probs, int B,
+                                                   int eval_prec)
+{
+    if (!h_probs || B < 1 || eval_prec != RBF_PREC_F32X2)
+        return 0;
+    int64_t s = 0;
+    for (int i = 0; i < B; ++i) {
+        if (h_probs[i].nc_max < 1 || h_probs[i].nc_max > kVbMaxCentres)
+            return 0;
+        s += h_probs[i].nc_max;
+    }
+    return vb_layout(B, s).total;
+}
+
+extern "C" rbf_status rbf_volume_batch_create(const rbf_volume_problem *h_probs, int B,
+                                              int eval_prec, void *d_ws, size_t ws_bytes,
+                                              void *stream, rbf_volume_batch **out)
+{
+    if (!h_probs || B < 1 || !out || eval_prec != RBF_PREC_F32X2)
+        return RBF_E_ARG;
+    *out = nullptr;
+    int64_t sum = 0;
+    int max_nc = 0;
+    for (int i = 0; i < B; ++i) {
+        const rbf_volume_problem &q = h_probs[i];
+        if (q.nv < 1 || q.nc_max < 1 || q.nc_max > kVbMaxCentres || !q.d_xv || !q.d_xb ||
+            !q.d_sel_idx || !q.d_w || !q.d_nc || !q.d_dv || !(q.radius > 0.0))
+            return RBF_E_ARG;
+        sum += q.nc_max;
+        max_nc = std::max<int>(max_nc, (int)q.nc_max);
+    }
+    const VbLayout L = vb_layout(B, sum);
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
+        return RBF_E_WORKSPACE;
+    DeviceInfo dev;
+    if (!device_info(&dev))
+        return RBF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)d_ws;
+    std::vector<float4 *> tables(B);
+    size_t o = L.tables;
+    for (int i = 0; i < B; ++i) {
+        tables[i] = (float4 *)(ws + o);
+        o += sizeof(float4) * 4 * (size_t)h_probs[i].nc_max;
+    }
+    if (cudaMemcpyAsync(ws + L.probs_host, h_probs, sizeof(rbf_volume_problem) * B,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(ws + L.tables_ptr, tables.data(), sizeof(float4 *) * B,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return RBF_E_CUDA;
+    const size_t smem_max = sizeof(float4) * 4 * kVbMaxCentres;
+    cudaFuncSetAttribute(k_vb_volume_ff<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    cudaFuncSetAttribute(k_vb_volume_ff<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    cudaFuncSetAttribute(k_vb_volume_ff<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    cudaFuncSetAttribute(k_vb_volume_ff<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    rbf_volume_batch *b = new rbf_volume_batch();
+    b->B = B;
+    b->max_nc = max_nc;
+    b->ws = ws;
+    b->probs_host = L.probs_host;
+    b->probs_dev = L.probs_dev;
+    b->tables_ptr = L.tables_ptr;
+    // autotune: time every candidate once (after one untimed run) on the
+    // real problems and keep the fastest
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int cnd = 0; cnd < 4; ++cnd) {
+        if (vb_configure(b, h_probs, cnd, tables, st, dev.sms) != RBF_OK ||
+            vb_launch(b, cnd, st) != cudaSuccess) {
+            delete b;
+            return RBF_E_CUDA;
+        }
+        cudaEventRecord(e0, st);
+        vb_launch(b, cnd, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return RBF_E_CUDA;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        b->cand_ms[cnd] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cnd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (vb_configure(b, h_probs, best, tables, st, dev.sms) != RBF_OK) {
+        delete b;
+        return RBF_E_CUDA;
+    }
+    *out = b;
+    return RBF_OK;
+}
+
+extern "C" rbf_status rbf_volume_batch_run(rbf_volume_batch *b, void *stream)
+{
+    if (!b)
+        return RBF_E_ARG;
+    return vb_launch(b, b->cand, (cudaStream_t)stream) == cudaSuccess ? RBF_OK : RBF_E_CUDA;
+}
+
+extern "C" rbf_status rbf_volume_batch_info(const rbf_volume_batch *b, int *threads,
+                                            int *points_per_thread, float *candidate_ms)
+{
+    if (!b)
+        return RBF_E_ARG;
+    if (threads)
+        *threads = kVbCands[b->cand].threads;
+    if (points_per_thread)
+        *points_per_thread = kVbCands[b->cand].p;
+    if (candidate_ms)
+        for (int i = 0; i < 4; ++i)
+            candidate_ms[i] = b->cand_ms[i];
+    return RBF_OK;
+}
+
+extern "C" void rbf_volume_batch_destroy(rbf_volume_batch *b)
+{
+    delete b;
 }

@@ -63,6 +63,31 @@ class GreedyStats(C.Structure):
     ]
 
 
+class GreedyProblem(C.Structure):
+    _fields_ = [
+        ("d_xb", C.c_void_p),
+        ("d_db", C.c_void_p),
+        ("nb", C.c_int64),
+        ("params", Params),
+        ("d_sel_idx", C.c_void_p),
+        ("d_w", C.c_void_p),
+    ]
+
+
+class VolumeProblem(C.Structure):
+    _fields_ = [
+        ("d_xv", C.c_void_p),
+        ("nv", C.c_int64),
+        ("d_xb", C.c_void_p),
+        ("d_sel_idx", C.c_void_p),
+        ("d_w", C.c_void_p),
+        ("d_nc", C.c_void_p),
+        ("nc_max", C.c_int64),
+        ("radius", C.c_double),
+        ("d_dv", C.c_void_p),
+    ]
+
+
 _lib = None
 _vp = C.c_void_p
 
@@ -107,6 +132,34 @@ def lib():
         L.rbf_deform_volume_adjoint.argtypes = [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int64,
                                                 _vp, P, _vp, C.POINTER(C.c_double), _vp,
                                                 C.c_size_t, _vp]
+        PP = C.POINTER(GreedyProblem)
+        L.rbf_greedy_batch_workspace_bytes.restype = C.c_size_t
+        L.rbf_greedy_batch_workspace_bytes.argtypes = [PP, C.c_int]
+        L.rbf_greedy_batch_create.restype = C.c_int
+        L.rbf_greedy_batch_create.argtypes = [PP, C.c_int, _vp, C.c_size_t, _vp,
+                                              C.POINTER(C.c_void_p)]
+        L.rbf_greedy_batch_run.restype = C.c_int
+        L.rbf_greedy_batch_run.argtypes = [_vp, _vp]
+        L.rbf_greedy_batch_nc_device.restype = C.c_void_p
+        L.rbf_greedy_batch_nc_device.argtypes = [_vp]
+        L.rbf_greedy_batch_results.restype = C.c_int
+        L.rbf_greedy_batch_results.argtypes = [_vp, C.POINTER(C.c_int32),
+                                               C.POINTER(GreedyStats), _vp]
+        L.rbf_greedy_batch_destroy.restype = None
+        L.rbf_greedy_batch_destroy.argtypes = [_vp]
+        VP = C.POINTER(VolumeProblem)
+        L.rbf_volume_batch_workspace_bytes.restype = C.c_size_t
+        L.rbf_volume_batch_workspace_bytes.argtypes = [VP, C.c_int, C.c_int]
+        L.rbf_volume_batch_create.restype = C.c_int
+        L.rbf_volume_batch_create.argtypes = [VP, C.c_int, C.c_int, _vp, C.c_size_t, _vp,
+                                              C.POINTER(C.c_void_p)]
+        L.rbf_volume_batch_run.restype = C.c_int
+        L.rbf_volume_batch_run.argtypes = [_vp, _vp]
+        L.rbf_volume_batch_info.restype = C.c_int
+        L.rbf_volume_batch_info.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                            C.POINTER(C.c_float)]
+        L.rbf_volume_batch_destroy.restype = None
+        L.rbf_volume_batch_destroy.argtypes = [_vp]
         L.rbf_group_of.restype = C.c_int
         L.rbf_group_of.argtypes = [C.c_int64, C.c_int64, C.c_uint64, C.POINTER(C.c_int32)]
         _lib = L
@@ -334,3 +387,119 @@ def measure_fma_peak(prec=32, stream=None):
     _check(lib().rbf_measure_fma_peak(int(prec), C.byref(f), _stream(stream)),
            "rbf_measure_fma_peak")
     return f.value
+
+
+class GreedyBatch:
+    """Many independent greedy problems in one cooperative launch.
+
+    ``problems``: list of dicts with ``xb``, ``db`` (CUDA FP64 (n, 3)),
+    ``radius``, ``tol``, ``tol_mode``, ``m``, ``seed``, ``nc_max``.  Outputs
+    per problem: ``idx[i]`` (int32, nc_max), ``w[i]`` (FP64 (nc_max, 3)) and
+    the device array ``nc`` (int64, B).  ``run()`` only enqueues (it can be
+    captured in a CUDA graph); ``results()`` synchronises.
+    """
+
+    def __init__(self, problems, *, eval_prec=PREC_F32X2, refine_steps=2, stream=None):
+        L = lib()
+        self.B = len(problems)
+        dev = problems[0]["xb"].device
+        self.problems = problems
+        self.idx, self.w = [], []
+        arr = (GreedyProblem * self.B)()
+        for i, q in enumerate(problems):
+            _dev(q["xb"], torch.float64, "xb", 3)
+            _dev(q["db"], torch.float64, "db", 3)
+            ncm = int(q.get("nc_max") or min(q["xb"].shape[0], 4096))
+            self.idx.append(torch.empty(ncm, dtype=torch.int32, device=dev))
+            self.w.append(torch.empty((ncm, 3), dtype=torch.float64, device=dev))
+            arr[i].d_xb = q["xb"].data_ptr()
+            arr[i].d_db = q["db"].data_ptr()
+            arr[i].nb = q["xb"].shape[0]
+            arr[i].params = make_params(q["radius"], q["tol"], q.get("tol_mode", 1), eval_prec,
+                                        q.get("m", 1), q.get("seed", 1), ncm, refine_steps)
+            arr[i].d_sel_idx = self.idx[i].data_ptr()
+            arr[i].d_w = self.w[i].data_ptr()
+        self._arr = arr
+        need = L.rbf_greedy_batch_workspace_bytes(arr, self.B)
+        if need == 0:
+            raise RBFError(1, "rbf_greedy_batch_workspace_bytes")
+        self.ws = _workspace(need, dev)
+        h = C.c_void_p()
+        _check(L.rbf_greedy_batch_create(arr, self.B, _ptr(self.ws), self.ws.numel(),
+                                         _stream(stream), C.byref(h)), "rbf_greedy_batch_create")
+        self.handle = h
+        ncp = L.rbf_greedy_batch_nc_device(h)
+        self.nc_ptr = ncp
+
+    def run(self, stream=None):
+        _check(lib().rbf_greedy_batch_run(self.handle, _stream(stream)), "rbf_greedy_batch_run")
+
+    def results(self, stream=None):
+        st = (C.c_int32 * self.B)()
+        stats = (GreedyStats * self.B)()
+        lib().rbf_greedy_batch_results(self.handle, st, stats, _stream(stream))
+        out = []
+        for i in range(self.B):
+            d = {f: (list(getattr(stats[i], f)) if f == "phase_ns" else getattr(stats[i], f))
+                 for f, _ in GreedyStats._fields_}
+            d["status"] = st[i]
+            out.append(d)
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().rbf_greedy_batch_destroy(self.handle)
+            self.handle = None
+
+
+class VolumeBatch:
+    """Batched double-float volume sums reading |S| on the device.
+
+    ``problems``: list of dicts with ``xv`` (CUDA FP64 (nv, 3)), ``xb``,
+    ``idx`` (int32 (nc_max,)), ``w`` (FP64 (nc_max, 3)), ``nc_ptr`` (device
+    address of an int64 count), ``radius``.  Outputs ``dv[i]``.  Creating the
+    batch runs the kernels to choose the tile shape (autotuning).
+    """
+
+    def __init__(self, problems, *, stream=None):
+        L = lib()
+        self.B = len(problems)
+        dev = problems[0]["xv"].device
+        self.dv = []
+        arr = (VolumeProblem * self.B)()
+        for i, q in enumerate(problems):
+            _dev(q["xv"], torch.float64, "xv", 3)
+            self.dv.append(torch.empty_like(q["xv"]))
+            arr[i].d_xv = q["xv"].data_ptr()
+            arr[i].nv = q["xv"].shape[0]
+            arr[i].d_xb = q["xb"].data_ptr()
+            arr[i].d_sel_idx = q["idx"].data_ptr()
+            arr[i].d_w = q["w"].data_ptr()
+            arr[i].d_nc = q["nc_ptr"]
+            arr[i].nc_max = q["idx"].numel()
+            arr[i].radius = float(q["radius"])
+            arr[i].d_dv = self.dv[i].data_ptr()
+        self._arr = arr
+        self.problems = problems
+        need = L.rbf_volume_batch_workspace_bytes(arr, self.B, PREC_F32X2)
+        if need == 0:
+            raise RBFError(1, "rbf_volume_batch_workspace_bytes")
+        self.ws = _workspace(need, dev)
+        h = C.c_void_p()
+        _check(L.rbf_volume_batch_create(arr, self.B, PREC_F32X2, _ptr(self.ws), self.ws.numel(),
+                                         _stream(stream), C.byref(h)), "rbf_volume_batch_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(lib().rbf_volume_batch_run(self.handle, _stream(stream)), "rbf_volume_batch_run")
+
+    def info(self):
+        t, pp = C.c_int(0), C.c_int(0)
+        ms = (C.c_float * 4)()
+        lib().rbf_volume_batch_info(self.handle, C.byref(t), C.byref(pp), ms)
+        return {"threads": t.value, "points_per_thread": pp.value, "candidate_ms": list(ms)}
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().rbf_volume_batch_destroy(self.handle)
+            self.handle = None

@@ -1,0 +1,89 @@
+"""GPU parity of the batched path: several wings of different sizes in one
+cooperative greedy launch and one volume launch, checked problem by problem
+against the oracle, and replayed from a captured CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2004_04817_gb300 as P
+from paper_2004_04817_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+SIZES = [(6, 30), (10, 50), (16, 125), (8, 40), (12, 90)]
+
+
+def cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def batch():
+    cases, probs = [], []
+    for k, (ns, ncn) in enumerate(SIZES):
+        c = synth.wing_case(ns, ncn, 3000 + 500 * k, vol_seed=100 + k, radius=2.0,
+                            tol_rel=1e-3)
+        c["d_xb"], c["d_db"], c["d_xv"] = cuda(c["xb"]), cuda(c["db"]), cuda(c["xv"])
+        c["estar"] = oracle.tolerance(c["db"], c["tol_rel"])
+        c["m"] = [1, 3, 5, 2, 7][k]
+        cases.append(c)
+        probs.append(dict(xb=c["d_xb"], db=c["d_db"], radius=2.0, tol=c["estar"], tol_mode=0,
+                          m=c["m"], seed=1 + k, nc_max=min(len(c["xb"]), 1000)))
+    gb = P.GreedyBatch(probs)
+    gb.run()
+    res = gb.results()
+    vprobs = [dict(xv=c["d_xv"], xb=c["d_xb"], idx=gb.idx[i], w=gb.w[i],
+                   nc_ptr=gb.nc_ptr + 8 * i, radius=2.0) for i, c in enumerate(cases)]
+    vb = P.VolumeBatch(vprobs)
+    vb.run()
+    torch.cuda.synchronize()
+    return cases, gb, res, vb
+
+
+def test_batched_greedy_each_problem_certified(batch):
+    cases, gb, res, _ = batch
+    for i, c in enumerate(cases):
+        r = res[i]
+        assert r["status"] == 0
+        nc = r["nc"]
+        idx = gb.idx[i][:nc].cpu().numpy()
+        o = oracle.greedy(c["xb"], c["db"], 2.0, c["estar"], m=c["m"], seed=1 + i,
+                          history=False)
+        assert idx.tolist() == o["idx"].tolist(), i
+        assert r["final_max"] <= c["estar"]
+        Wo, _, _ = oracle.solve_weights(c["xb"], c["db"], idx, 2.0)
+        assert np.abs(gb.w[i][:nc].cpu().numpy() - Wo).max() <= 1e-5 * np.abs(c["db"]).max()
+
+
+def test_batched_volume_matches_oracle(batch):
+    cases, gb, res, vb = batch
+    for i, c in enumerate(cases):
+        nc = res[i]["nc"]
+        idx = gb.idx[i][:nc].cpu().numpy()
+        W = gb.w[i][:nc].cpu().numpy()
+        ref = oracle.rbf_sum(c["xv"], c["xb"], idx, W, 2.0)
+        got = vb.dv[i].cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-11
+    info = vb.info()
+    assert info["threads"] in (128, 256) and info["points_per_thread"] in (1, 2)
+
+
+def test_batched_graph_replay_is_identical(batch):
+    cases, gb, res, vb = batch
+    before = [d.clone() for d in vb.dv]
+    idx_before = [t.clone() for t in gb.idx]
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        gb.run()
+        vb.run()
+    for d in vb.dv:
+        d.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for i in range(len(cases)):
+        nc = res[i]["nc"]
+        assert torch.equal(gb.idx[i][:nc], idx_before[i][:nc])
+        assert torch.equal(vb.dv[i], before[i])

@@ -266,6 +266,39 @@ rbf_status rbf_deform_volume(const double *d_xv, int64_t nv,
                              void *d_ws, size_t ws_bytes, void *stream);
 
 /* --------------------------------------------------------------------------
+ * Modal volume deformation on the tensor cores: for k displacement fields
+ * (modes) that share one support set, Eq. 6 for all of them is the product
+ * D = Phi_vc W with W of size nc x n_out (n_out = 3 k, e.g. 96 for 32
+ * modes).  Phi_vc is generated tile by tile in FP32, rounded to BF16 in
+ * shared memory and multiplied on the tensor cores (tcgen05.mma, FP32
+ * accumulation in tensor memory).
+ *   mode RBF_MODAL_BF16   : one BF16 x BF16 product (BF16 rounding of phi and
+ *                           W: relative errors of order 2^-9 per term).
+ *   mode RBF_MODAL_BF16X3 : phi and W split into three BF16 parts each
+ *                           (orders 1, 2^-9, 2^-18); the six products down
+ *                           to order 2^-18 are accumulated (about FP32
+ *                           accuracy).
+ * Errors against FP64 scale with sum_j |w_j phi_vj|, not with |D|: weights
+ * of ill-conditioned support sets (large R) cancel heavily.
+ *
+ * d_w   : device FP64 nc x n_out (row-major, support order).
+ * d_out : device FP32 nv x n_out (16-byte aligned).  n_out % 16 == 0,
+ *         16 <= n_out <= 256, nc <= 4096 and the shared-memory tables must
+ *         fit (RBF_E_ARG otherwise).
+ * ASYNC; rbf_modal_check(d_ws) synchronises and returns the device status
+ * (RBF_E_TIMEOUT if a bounded wait ran out).
+ * ------------------------------------------------------------------------ */
+#define RBF_MODAL_BF16 1
+#define RBF_MODAL_BF16X3 3
+
+size_t rbf_modal_workspace_bytes(int64_t nv, int64_t nc, int n_out, int mode);
+rbf_status rbf_deform_modal(const double *d_xv, int64_t nv, const double *d_xb,
+                            const int32_t *d_sel_idx, int64_t nc, const double *d_w,
+                            int n_out, const rbf_params *p, int mode, float *d_out,
+                            void *d_ws, size_t ws_bytes, void *stream);
+rbf_status rbf_modal_check(const void *d_ws, void *stream);
+
+/* --------------------------------------------------------------------------
  * Batched volume sums (Eq. 6) for many problems in one double-float launch,
  * e.g. after rbf_greedy_batch_run.  The number of centres of each problem is
  * read on the device (d_nc, e.g. rbf_greedy_batch_nc_device(b) + i), so a

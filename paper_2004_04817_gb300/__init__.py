@@ -16,6 +16,9 @@ from .rbf import (  # noqa: F401
     solve_system,
     adjoint,
     deform,
+    deform_modal,
+    MODAL_BF16,
+    MODAL_BF16X3,
     RBFDeform,
     GreedyBatch,
     VolumeBatch,

@@ -160,6 +160,13 @@ def lib():
                                             C.POINTER(C.c_float)]
         L.rbf_volume_batch_destroy.restype = None
         L.rbf_volume_batch_destroy.argtypes = [_vp]
+        L.rbf_modal_workspace_bytes.restype = C.c_size_t
+        L.rbf_modal_workspace_bytes.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_int]
+        L.rbf_deform_modal.restype = C.c_int
+        L.rbf_deform_modal.argtypes = [_vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int, P,
+                                       C.c_int, _vp, _vp, C.c_size_t, _vp]
+        L.rbf_modal_check.restype = C.c_int
+        L.rbf_modal_check.argtypes = [_vp, _vp]
         L.rbf_group_of.restype = C.c_int
         L.rbf_group_of.argtypes = [C.c_int64, C.c_int64, C.c_uint64, C.POINTER(C.c_int32)]
         _lib = L
@@ -379,6 +386,36 @@ def group_of(nb, m, seed):
     _check(lib().rbf_group_of(int(nb), int(m), int(seed),
                               g.ctypes.data_as(C.POINTER(C.c_int32))), "rbf_group_of")
     return g
+
+
+MODAL_BF16 = 1
+MODAL_BF16X3 = 3
+
+
+def deform_modal(xv, xb, sel_idx, W, *, radius, mode=MODAL_BF16X3, stream=None,
+                 workspace=None, out=None, check=True):
+    """D = Phi_vc W on the tensor cores for many displacement fields at once:
+    W is FP64 (nc, n_out), the result FP32 (nv, n_out)."""
+    L = lib()
+    _dev(xv, torch.float64, "xv", 3)
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(sel_idx, torch.int32, "sel_idx")
+    _dev(W, torch.float64, "W")
+    nv, nc, n_out = xv.shape[0], sel_idx.numel(), W.shape[1]
+    need = L.rbf_modal_workspace_bytes(nv, nc, n_out, mode)
+    if need == 0:
+        raise RBFError(1, "rbf_modal_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xv.device)
+    d = out if out is not None else torch.empty((nv, n_out), dtype=torch.float32,
+                                                device=xv.device)
+    p = make_params(radius)
+    st = L.rbf_deform_modal(_ptr(xv), nv, _ptr(xb), _ptr(sel_idx), nc, _ptr(W), n_out,
+                            C.byref(p), int(mode), _ptr(d), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "rbf_deform_modal")
+    if check:
+        _check(L.rbf_modal_check(_ptr(ws), _stream(stream)), "rbf_deform_modal (device)")
+    return d
 
 
 def measure_fma_peak(prec=32, stream=None):

@@ -1,0 +1,67 @@
+"""GPU parity of the tensor-core modal path D = Phi_vc W (tcgen05, BF16
+inputs, FP32 accumulation) against FP64, at the error bounds its input
+rounding allows: BF16 |err| <= 2^-7 (Phi |W|), BF16x3 |err| <= 2^-18 (Phi |W|)
+elementwise."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2004_04817_gb300 as P
+from paper_2004_04817_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _ref(xv, xc, W, R):
+    D = np.linalg.norm(xv[:, None, :] - xc[None], axis=-1) / R
+    Phi = oracle.phi(D)
+    return Phi @ W, Phi @ np.abs(W)
+
+
+@pytest.mark.parametrize("n_out", [16, 96])
+@pytest.mark.parametrize("mode,scale", [(P.MODAL_BF16, 2.0 ** -7), (P.MODAL_BF16X3, 2.0 ** -18)])
+def test_modal_small_against_fp64(n_out, mode, scale):
+    rng = np.random.default_rng(3)
+    xb = rng.random((200, 3))
+    S = np.sort(rng.choice(200, 70, replace=False)).astype(np.int32)   # 2 K-tiles, padded
+    W = rng.standard_normal((70, n_out))
+    xv = rng.random((1000, 3)) * 1.2 - 0.1                              # ragged M tile
+    R = 0.8
+    ref, bnd = _ref(xv, xb[S], W, R)
+    d = P.deform_modal(cuda(xv), cuda(xb), cuda(S, torch.int32), cuda(W), radius=R, mode=mode)
+    err = np.abs(d.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(np.isfinite(err))
+    assert np.all(err <= scale * bnd + 1e-6), (err / (scale * bnd + 1e-30)).max()
+
+
+def test_modal_sinusoidal_modes_full_support():
+    """32 sinusoidal bending modes dz_q = 0.05 sin((2q-1) pi y / (2b)) on the
+    GCB support set of the N_b = 50,000 wing; W (N_c x 96) from the FP64
+    solve; sampled volume points compared with FP64 sums."""
+    c = synth.wing_gcb(n_vol=200_000)
+    xb, db = cuda(c["xb"]), cuda(c["db"])
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    r = P.greedy_select(xb, db, radius=2.0, tol=estar, tol_mode=0, m=241, seed=1,
+                        eval_prec=P.PREC_F32X2)
+    S = r["idx"].cpu().numpy()
+    y = c["xb"][S, 1]
+    modes = np.zeros((len(S), 96))
+    for q in range(1, 33):
+        modes[:, 3 * (q - 1) + 2] = 0.05 * np.sin((2 * q - 1) * np.pi * y / 2.0)
+    W = np.zeros_like(modes)
+    for q in range(32):
+        x, res = P.solve_system(xb, r["idx"], cuda(modes[:, 3 * q:3 * q + 3]), radius=2.0)
+        W[:, 3 * q:3 * q + 3] = x.cpu().numpy()
+    xv = c["xv"]
+    sample = np.random.default_rng(8).choice(len(xv), 2000, replace=False)
+    ref, bnd = _ref(xv[sample], c["xb"][S], W, 2.0)
+    for mode, scale in ((P.MODAL_BF16, 2.0 ** -7), (P.MODAL_BF16X3, 2.0 ** -18)):
+        d = P.deform_modal(cuda(xv), xb, r["idx"], cuda(W), radius=2.0, mode=mode)
+        got = d.cpu().numpy()[sample].astype(np.float64)
+        err = np.abs(got - ref)
+        assert np.all(err <= scale * bnd + 1e-6), (mode, (err / (scale * bnd)).max())

@@ -102,6 +102,23 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float *v)
         v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v)
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint4 pack8(const __nv_bfloat16 *b)
 {
     uint4 r;
@@ -270,12 +287,24 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: warp w reads TMEM lanes 32w.. (its own 32 rows)
         float *orow = out + (size_t)v * sh.n_out;
-        for (int c0 = 0; c0 < sh.n_out; c0 += 32) {
+        const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+        int c0 = 0;
+        for (; c0 + 32 <= sh.n_out; c0 += 32) {
             float vals[32];
-            tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, vals);
+            tmem_ld32(lane_base + (unsigned)c0, vals);
             if (live) {
 #pragma unroll
                 for (int i = 0; i < 32; i += 4)
+                    *(float4 *)(orow + c0 + i) = make_float4(vals[i], vals[i + 1], vals[i + 2],
+                                                             vals[i + 3]);
+            }
+        }
+        if (c0 < sh.n_out) {   // n_out % 32 == 16: one 16-column tail
+            float vals[16];
+            tmem_ld16(lane_base + (unsigned)c0, vals);
+            if (live) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
                     *(float4 *)(orow + c0 + i) = make_float4(vals[i], vals[i + 1], vals[i + 2],
                                                              vals[i + 3]);
             }

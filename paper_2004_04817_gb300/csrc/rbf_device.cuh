@@ -215,6 +215,121 @@ __device__ __forceinline__ void ff_fma_acc(ff &acc, float wh, float wl, ff ph)
 }
 
 // ----------------------------------------------------------------------------
+// Paired double-float: two independent ff values in paired FP32 registers, so
+// every step of the error-free transformations serves two pairs with one
+// instruction (same algorithms as above, lane by lane).
+// ----------------------------------------------------------------------------
+struct ff2 {
+    f2 h, l;
+};
+
+__device__ __forceinline__ f2 f2_neg(f2 a)
+{
+    f2 r;
+    r.v = a.v ^ 0x8000000080000000ull;
+    return r;
+}
+
+__device__ __forceinline__ f2 f2_bcast(float x) { return f2_pack(x, x); }
+
+__device__ __forceinline__ ff2 two_sum2(f2 a, f2 b)
+{
+    const f2 s = f2_add(a, b);
+    const f2 bb = f2_sub(s, a);
+    return ff2{s, f2_add(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb))};
+}
+
+__device__ __forceinline__ ff2 fast_two_sum2(f2 a, f2 b)
+{
+    const f2 s = f2_add(a, b);
+    return ff2{s, f2_sub(b, f2_sub(s, a))};
+}
+
+__device__ __forceinline__ ff2 ff_add2(ff2 a, ff2 b)
+{
+    const ff2 s = two_sum2(a.h, b.h);
+    return fast_two_sum2(s.h, f2_add(s.l, f2_add(a.l, b.l)));
+}
+
+__device__ __forceinline__ ff2 ff_mul2(ff2 a, ff2 b)
+{
+    const f2 p = f2_mul(a.h, b.h);
+    f2 e = f2_fma(a.h, b.h, f2_neg(p));
+    e = f2_fma(a.h, b.l, e);
+    e = f2_fma(a.l, b.h, e);
+    return fast_two_sum2(p, e);
+}
+
+__device__ __forceinline__ ff2 ff_sqr2(ff2 a)
+{
+    const f2 p = f2_mul(a.h, a.h);
+    f2 e = f2_fma(a.h, a.h, f2_neg(p));
+    e = f2_fma(f2_add(a.h, a.h), a.l, e);
+    return fast_two_sum2(p, e);
+}
+
+// Squared scaled distances of two (query, centre) pairs given as paired
+// hi/lo coordinates.
+__device__ __forceinline__ ff2 dist2_ff2(f2 qxh, f2 qxl, f2 qyh, f2 qyl, f2 qzh, f2 qzl, f2 cxh,
+                                         f2 cxl, f2 cyh, f2 cyl, f2 czh, f2 czl)
+{
+    ff2 dx = two_sum2(qxh, f2_neg(cxh));
+    dx.l = f2_add(dx.l, f2_sub(qxl, cxl));
+    ff2 dy = two_sum2(qyh, f2_neg(cyh));
+    dy.l = f2_add(dy.l, f2_sub(qyl, cyl));
+    ff2 dz = two_sum2(qzh, f2_neg(czh));
+    dz.l = f2_add(dz.l, f2_sub(qzl, czl));
+    return ff_add2(ff_add2(ff_sqr2(dx), ff_sqr2(dy)), ff_sqr2(dz));
+}
+
+// phi for two pairs (same method as phi_ff_s; the reciprocal square roots
+// are scalar MUFU operations).
+__device__ __forceinline__ ff2 phi_ff2_s(ff2 s)
+{
+    float s0, s1;
+    f2_unpack(s.h, s0, s1);
+    const f2 sc = f2_pack(fmaxf(s0, 1e-37f), fmaxf(s1, 1e-37f));
+    f2 y = f2_pack(rsqrtf(fmaxf(s0, 1e-37f)), rsqrtf(fmaxf(s1, 1e-37f)));
+    y = f2_mul(y, f2_fma(f2_mul(f2_bcast(-0.5f), sc), f2_mul(y, y), f2_bcast(1.5f)));
+    const f2 e0 = f2_mul(s.h, y);
+    const f2 r = f2_add(f2_fma(f2_neg(e0), e0, s.h), s.l);
+    const ff2 eta = fast_two_sum2(e0, f2_mul(f2_mul(r, f2_bcast(0.5f)), y));
+    ff2 t = two_sum2(f2_bcast(1.0f), f2_neg(eta.h));
+    t = fast_two_sum2(t.h, f2_sub(t.l, eta.l));
+    const ff2 t2 = ff_sqr2(t);
+    const ff2 t4 = ff_sqr2(t2);
+    ff2 p = two_sum2(f2_bcast(1.0f), f2_mul(f2_bcast(4.0f), eta.h));
+    p = fast_two_sum2(p.h, f2_fma(f2_bcast(4.0f), eta.l, p.l));
+    ff2 ph = ff_mul2(t4, p);
+    float e0a, e0b;
+    f2_unpack(eta.h, e0a, e0b);
+    float hh0, hh1, ll0, ll1;
+    f2_unpack(ph.h, hh0, hh1);
+    f2_unpack(ph.l, ll0, ll1);
+    if (!(e0a < 1.0f)) {
+        hh0 = 0.0f;
+        ll0 = 0.0f;
+    }
+    if (!(e0b < 1.0f)) {
+        hh1 = 0.0f;
+        ll1 = 0.0f;
+    }
+    return ff2{f2_pack(hh0, hh1), f2_pack(ll0, ll1)};
+}
+
+// acc += w * phi for two pairs.
+__device__ __forceinline__ void ff_fma_acc2(ff2 &acc, f2 wh, f2 wl, ff2 ph)
+{
+    const f2 p = f2_mul(wh, ph.h);
+    f2 pe = f2_fma(wh, ph.h, f2_neg(p));
+    pe = f2_fma(wh, ph.l, pe);
+    pe = f2_fma(wl, ph.h, pe);
+    const ff2 s = two_sum2(acc.h, p);
+    acc.h = s.h;
+    acc.l = f2_add(acc.l, f2_add(s.l, pe));
+}
+
+// ----------------------------------------------------------------------------
 // Argmax keys.  Larger key = larger error; among equal errors the lowest node
 // index wins.  Key 0 means "no candidate".
 //  - FP64 errors: the top 40 bits of the (non-negative) double's bit pattern,

@@ -70,6 +70,13 @@ struct GreedyCtl {
     unsigned long long phase_ns[12];  // CTA 0's time per phase (see rbf_greedy_stats)
 };
 
+// Per-CTA record of an evaluation (see evaluate).
+struct __align__(16) EvalRec {
+    double mx, sq, u1, u2, e_lead, b_lead;
+    long long n1, key, p_lead;
+    long long pad;
+};
+
 struct GreedyArgs {
     const double *xb;
     const double *db;
@@ -109,6 +116,7 @@ struct GreedyArgs {
     double *zt;                   // Z^T, row-major, ld
     double *bvec;
     double *lvec;
+    EvalRec *rec;                 // 2 x kMaxGrid evaluation records
     D4 *rvec;                     // refinement residual / correction vectors
     D4 *tvec;
     double *w_out;                // optional FP64 weights output (nc x 3)
@@ -421,7 +429,10 @@ struct EvalOut {
     unsigned long long key;   // argmax key over the range minus S (0 = none)
     double gmax;              // certified maximum of E over the range minus S
     double gsq;               // sum of squares of E over the range minus S
+    double e_lead, b_lead;    // the leader's error and bound
+    int p_lead;               // the leader's position
 };
+
 
 // ---------------------------------------------------------------------------
 // Recurrence-Cholesky append of the node at position pn (Sec. 1, RC scheme):
@@ -780,7 +791,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
 
     phase(5);
     // ---------------- error evaluation over a position range ---------------
-    int ev = 0;                      // evaluation counter (ring index)
+    int ev = 0;                      // evaluation counter
+    int p2uses = 0;                  // FP64 re-score passes (key ring index)
     long long pairs32 = 0, pairs64 = 0, pairsff = 0;
     unsigned long long rescored_local = 0;
     // Evaluates E at positions [p0, p1) with the current weights.  With
@@ -799,6 +811,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         const int rounds = (nq + nteams - 1) / nteams;
         unsigned long long key = 0;
         double lmax = 0.0, lsq = 0.0;
+        double e_lead = 0.0, b_lead = 0.0;   // error and bound of this thread's leader
+        long long p_lead = -1;                // its position
         const bool screened = !(a.prec == RBF_PREC_F64 || force64);
         // top two upper bounds E~ + beta of this thread's nodes (screened modes)
         double u1 = -1.0, u2 = -1.0;
@@ -814,7 +828,12 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     lsq = fma(e, e, lsq);
                     if (argmax) {
                         const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
-                        key = k2 > key ? k2 : key;
+                        if (k2 > key) {
+                            key = k2;
+                            e_lead = e;
+                            b_lead = 0.0;
+                            p_lead = q;
+                        }
                     }
                 }
             }
@@ -895,6 +914,9 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                             const unsigned long long k2 = key_f64((double)e, ldcg(a.node_of_pos + q));
                             if (k2 > key) {
                                 key = k2;
+                                e_lead = (double)e;
+                                b_lead = (double)beta;
+                                p_lead = q;
                             }
                             if (up > u1) {
                                 u2 = u1;
@@ -921,8 +943,35 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     split_f64(xq.z, qzh, qzl);
                     ff fx{0.0f, 0.0f}, fy{0.0f, 0.0f}, fz{0.0f, 0.0f};
                     float sb = 0.0f;
-#pragma unroll 2
-                    for (int j = sub; j < nc; j += ts) {
+                    // two centres (j, j + ts) per step in paired registers
+                    const f2 z2 = f2_pack(0.0f, 0.0f);
+                    ff2 gx{z2, z2}, gy{z2, z2}, gz{z2, z2};
+                    const f2 bxh = f2_bcast(qxh), bxl = f2_bcast(qxl), byh = f2_bcast(qyh),
+                             byl = f2_bcast(qyl), bzh = f2_bcast(qzh), bzl = f2_bcast(qzl);
+                    int j = sub;
+                    for (; j + ts < nc; j += 2 * ts) {
+                        const int j2 = j + ts;
+                        const float4 ch0 = smem ? cw[4 * j] : ldcg(cw + 4 * j);
+                        const float4 cl0 = smem ? cw[4 * j + 1] : ldcg(cw + 4 * j + 1);
+                        const float4 wh0 = smem ? cw[4 * j + 2] : ldcg(cw + 4 * j + 2);
+                        const float4 wl0 = smem ? cw[4 * j + 3] : ldcg(cw + 4 * j + 3);
+                        const float4 ch1 = smem ? cw[4 * j2] : ldcg(cw + 4 * j2);
+                        const float4 cl1 = smem ? cw[4 * j2 + 1] : ldcg(cw + 4 * j2 + 1);
+                        const float4 wh1 = smem ? cw[4 * j2 + 2] : ldcg(cw + 4 * j2 + 2);
+                        const float4 wl1 = smem ? cw[4 * j2 + 3] : ldcg(cw + 4 * j2 + 3);
+                        const ff2 s2 = dist2_ff2(bxh, bxl, byh, byl, bzh, bzl,
+                                                 f2_pack(ch0.x, ch1.x), f2_pack(cl0.x, cl1.x),
+                                                 f2_pack(ch0.y, ch1.y), f2_pack(cl0.y, cl1.y),
+                                                 f2_pack(ch0.z, ch1.z), f2_pack(cl0.z, cl1.z));
+                        const ff2 ph = phi_ff2_s(s2);
+                        ff_fma_acc2(gx, f2_pack(wh0.x, wh1.x), f2_pack(wl0.x, wl1.x), ph);
+                        ff_fma_acc2(gy, f2_pack(wh0.y, wh1.y), f2_pack(wl0.y, wl1.y), ph);
+                        ff_fma_acc2(gz, f2_pack(wh0.z, wh1.z), f2_pack(wl0.z, wl1.z), ph);
+                        float p0, p1;
+                        f2_unpack(ph.h, p0, p1);
+                        sb = fmaf(wh1.w, p1, fmaf(wh0.w, p0, sb));
+                    }
+                    if (j < nc) {
                         const float4 ch = smem ? cw[4 * j] : ldcg(cw + 4 * j);
                         const float4 cl = smem ? cw[4 * j + 1] : ldcg(cw + 4 * j + 1);
                         const float4 wh = smem ? cw[4 * j + 2] : ldcg(cw + 4 * j + 2);
@@ -936,8 +985,19 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         sb = fmaf(wh.w, ph.h, sb);
                     }
                     // team reduction in FP64 (each ff value becomes the double h + l)
-                    double sx = (double)fx.h + (double)fx.l, sy = (double)fy.h + (double)fy.l,
-                           sz = (double)fz.h + (double)fz.l;
+                    float gh0, gh1, gl0, gl1;
+                    f2_unpack(gx.h, gh0, gh1);
+                    f2_unpack(gx.l, gl0, gl1);
+                    double sx = (double)fx.h + (double)fx.l + (((double)gh0 + (double)gl0) +
+                                                                ((double)gh1 + (double)gl1));
+                    f2_unpack(gy.h, gh0, gh1);
+                    f2_unpack(gy.l, gl0, gl1);
+                    double sy = (double)fy.h + (double)fy.l + (((double)gh0 + (double)gl0) +
+                                                                ((double)gh1 + (double)gl1));
+                    f2_unpack(gz.h, gh0, gh1);
+                    f2_unpack(gz.l, gl0, gl1);
+                    double sz = (double)fz.h + (double)fz.l + (((double)gh0 + (double)gl0) +
+                                                                ((double)gh1 + (double)gl1));
                     sx = team_sum(sx, ts);
                     sy = team_sum(sy, ts);
                     sz = team_sum(sz, ts);
@@ -960,8 +1020,12 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         lsq = fma(e, e, lsq);
                         if (argmax) {
                             const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
-                            if (k2 > key)
+                            if (k2 > key) {
                                 key = k2;
+                                e_lead = e;
+                                b_lead = (double)bf;
+                                p_lead = q;
+                            }
                             if (up > u1) {
                                 u2 = u1;
                                 u1 = up;
@@ -976,126 +1040,149 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     pairsff += (long long)nq * nc;
             }
         }
-        // ---- reductions: key by atomic max; (max, sum of squares) and the two
-        // largest upper bounds with the node of the largest by partials
+        // ---- reductions, one record per CTA: the leader (largest key) with its
+        // error, bound and position; the maximum and the sum of squares of E;
+        // the two largest upper bounds and the node of the largest.  Only the
+        // first lane of each team holds data, so warps combine lanes at
+        // distances >= ts; warp 0 combines the warps; after the barrier warp 0
+        // of every CTA combines the G records in the same order.
         phase(9);
-        block_max_key(red, key);
-        if (tid == 0 && key)
-            atomicMax(&ctl->slot[r], key);
         {
-            // top-2 upper bounds: warp then block (deterministic order)
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ou1 = __shfl_xor_sync(0xffffffffu, u1, o);
-                const double ou2 = __shfl_xor_sync(0xffffffffu, u2, o);
-                const long long on1 = __shfl_xor_sync(0xffffffffu, n1, o);
-                if (ou1 > u1 || (ou1 == u1 && on1 >= 0 && (n1 < 0 || on1 < n1))) {
-                    u2 = fmax(u1, ou2);
-                    u1 = ou1;
-                    n1 = on1;
+            auto merge = [](unsigned long long &k, double &el, double &bl, long long &pl,
+                            double &v1, double &v2, long long &m1, double &mx, double &sq,
+                            unsigned long long ok_, double oel, double obl, long long opl,
+                            double ov1, double ov2, long long om1, double omx, double osq) {
+                if (ok_ > k) {
+                    k = ok_;
+                    el = oel;
+                    bl = obl;
+                    pl = opl;
+                }
+                if (ov1 > v1 || (ov1 == v1 && om1 >= 0 && (m1 < 0 || om1 < m1))) {
+                    v2 = fmax(v1, ov2);
+                    v1 = ov1;
+                    m1 = om1;
                 } else {
-                    u2 = fmax(u2, ou1);
+                    v2 = fmax(v2, ov1);
                 }
+                mx = fmax(mx, omx);
+                sq += osq;
+            };
+            for (int o = 16; o >= ts; o >>= 1) {
+                const unsigned long long ok_ = __shfl_xor_sync(0xffffffffu, key, o);
+                const double oel = __shfl_xor_sync(0xffffffffu, e_lead, o);
+                const double obl = __shfl_xor_sync(0xffffffffu, b_lead, o);
+                const long long opl = __shfl_xor_sync(0xffffffffu, p_lead, o);
+                const double ov1 = __shfl_xor_sync(0xffffffffu, u1, o);
+                const double ov2 = __shfl_xor_sync(0xffffffffu, u2, o);
+                const long long om1 = __shfl_xor_sync(0xffffffffu, n1, o);
+                const double omx = __shfl_xor_sync(0xffffffffu, lmax, o);
+                const double osq = __shfl_xor_sync(0xffffffffu, lsq, o);
+                merge(key, e_lead, b_lead, p_lead, u1, u2, n1, lmax, lsq, ok_, oel, obl, opl, ov1,
+                      ov2, om1, omx, osq);
             }
-            double a4[4] = {0.0, lsq, 0.0, 0.0};
-            double mx = lmax;
-            for (int o = 16; o > 0; o >>= 1)
-                mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            block_sum4(red, a4);
+            __shared__ EvalRec s_rec[kGWarps];
+            if (lane == 0)
+                s_rec[warp] = EvalRec{lmax, lsq, u1, u2, e_lead, b_lead, n1, (long long)key, p_lead};
             __syncthreads();
-            if (lane == 0) {
-                red.v[warp] = mx;
-                red.s[warp][0] = u1;
-                red.s[warp][1] = u2;
-                red.i[warp] = n1;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                for (int k2 = 1; k2 < kGWarps; ++k2) {
-                    mx = fmax(mx, red.v[k2]);
-                    const double ou1 = red.s[k2][0], ou2 = red.s[k2][1];
-                    const long long on1 = red.i[k2];
-                    if (ou1 > u1 || (ou1 == u1 && on1 >= 0 && (n1 < 0 || on1 < n1))) {
-                        u2 = fmax(u1, ou2);
-                        u1 = ou1;
-                        n1 = on1;
-                    } else {
-                        u2 = fmax(u2, ou1);
-                    }
+            if (warp == 0) {
+                EvalRec t = lane < kGWarps ? s_rec[lane]
+                                           : EvalRec{0.0, 0.0, -1.0, -1.0, 0.0, 0.0, -1, 0, -1};
+                unsigned long long k = (unsigned long long)t.key;
+                for (int o = kGWarps / 2; o > 0; o >>= 1) {
+                    const unsigned long long ok_ = __shfl_xor_sync(0xffffffffu, k, o);
+                    const double oel = __shfl_xor_sync(0xffffffffu, t.e_lead, o);
+                    const double obl = __shfl_xor_sync(0xffffffffu, t.b_lead, o);
+                    const long long opl = __shfl_xor_sync(0xffffffffu, t.p_lead, o);
+                    const double ov1 = __shfl_xor_sync(0xffffffffu, t.u1, o);
+                    const double ov2 = __shfl_xor_sync(0xffffffffu, t.u2, o);
+                    const long long om1 = __shfl_xor_sync(0xffffffffu, t.n1, o);
+                    const double omx = __shfl_xor_sync(0xffffffffu, t.mx, o);
+                    const double osq = __shfl_xor_sync(0xffffffffu, t.sq, o);
+                    merge(k, t.e_lead, t.b_lead, t.p_lead, t.u1, t.u2, t.n1, t.mx, t.sq, ok_, oel,
+                          obl, opl, ov1, ov2, om1, omx, osq);
                 }
-                double *pp = part(use) + 4 * g_vb;
-                pp[0] = mx;
-                pp[1] = a4[1];
-                pp[2] = u1;
-                pp[3] = u2;
-                parti(use)[g_vb] = n1;
+                t.key = (long long)k;
+                if (lane == 0)
+                    a.rec[(size_t)(use & 1) * kMaxGrid + g_vb] = t;
             }
         }
         phase(10);
         GSYNC_B();
-        out.key = ldcg(&ctl->slot[r]);
         double gu1 = -1.0, gu2 = -1.0;
         long long gn1 = -1;
         {
-            // one pass over the G partials: max, sum of squares and the two
-            // largest upper bounds (every CTA reduces the same data in the
-            // same order)
-            __shared__ double s_r[4];
-            __shared__ long long s_n;
-            if (tid < 32) {
-                double mx = -INFINITY, sq = 0.0, v1 = -1.0, v2 = -1.0;
-                long long m1 = -1;
-                const double *pb = part(use);
-                const long long *pi = parti(use);
-                for (int b = tid; b < G; b += 32) {
-                    const double2 a0 = __ldcg((const double2 *)(pb + 4 * b));
-                    const double2 uu = __ldcg((const double2 *)(pb + 4 * b + 2));
-                    const long long nb1 = ldcg(pi + b);
-                    mx = fmax(mx, a0.x);
-                    sq += a0.y;
-                    if (uu.x > v1 || (uu.x == v1 && nb1 >= 0 && (m1 < 0 || nb1 < m1))) {
-                        v2 = fmax(v1, uu.y);
-                        v1 = uu.x;
-                        m1 = nb1;
-                    } else {
-                        v2 = fmax(v2, uu.x);
+            __shared__ EvalRec s_g;
+            if (warp == 0) {
+                EvalRec t{0.0, 0.0, -1.0, -1.0, 0.0, 0.0, -1, 0, -1};
+                unsigned long long k = 0;
+                const EvalRec *rb = a.rec + (size_t)(use & 1) * kMaxGrid;
+                auto merge = [](unsigned long long &k, EvalRec &t, const EvalRec &o) {
+                    if ((unsigned long long)o.key > k) {
+                        k = (unsigned long long)o.key;
+                        t.e_lead = o.e_lead;
+                        t.b_lead = o.b_lead;
+                        t.p_lead = o.p_lead;
                     }
+                    if (o.u1 > t.u1 || (o.u1 == t.u1 && o.n1 >= 0 && (t.n1 < 0 || o.n1 < t.n1))) {
+                        t.u2 = fmax(t.u1, o.u2);
+                        t.u1 = o.u1;
+                        t.n1 = o.n1;
+                    } else {
+                        t.u2 = fmax(t.u2, o.u1);
+                    }
+                    t.mx = fmax(t.mx, o.mx);
+                    t.sq += o.sq;
+                };
+                for (int b = lane; b < G; b += 32) {
+                    EvalRec o;
+                    const double2 v0 = __ldcg((const double2 *)(rb + b));
+                    const double2 v1 = __ldcg((const double2 *)(rb + b) + 1);
+                    const double2 v2 = __ldcg((const double2 *)(rb + b) + 2);
+                    const longlong2 w0 = __ldcg((const longlong2 *)(rb + b) + 3);
+                    const long long w1 = __ldcg((const long long *)(rb + b) + 8);
+                    o.mx = v0.x;
+                    o.sq = v0.y;
+                    o.u1 = v1.x;
+                    o.u2 = v1.y;
+                    o.e_lead = v2.x;
+                    o.b_lead = v2.y;
+                    o.n1 = w0.x;
+                    o.key = w0.y;
+                    o.p_lead = w1;
+                    merge(k, t, o);
                 }
                 for (int o = 16; o > 0; o >>= 1) {
-                    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                    sq += __shfl_xor_sync(0xffffffffu, sq, o);
-                    const double ov1 = __shfl_xor_sync(0xffffffffu, v1, o);
-                    const double ov2 = __shfl_xor_sync(0xffffffffu, v2, o);
-                    const long long om1 = __shfl_xor_sync(0xffffffffu, m1, o);
-                    if (ov1 > v1 || (ov1 == v1 && om1 >= 0 && (m1 < 0 || om1 < m1))) {
-                        v2 = fmax(v1, ov2);
-                        v1 = ov1;
-                        m1 = om1;
-                    } else {
-                        v2 = fmax(v2, ov1);
-                    }
+                    EvalRec q;
+                    q.key = (long long)__shfl_xor_sync(0xffffffffu, k, o);
+                    q.e_lead = __shfl_xor_sync(0xffffffffu, t.e_lead, o);
+                    q.b_lead = __shfl_xor_sync(0xffffffffu, t.b_lead, o);
+                    q.p_lead = __shfl_xor_sync(0xffffffffu, t.p_lead, o);
+                    q.u1 = __shfl_xor_sync(0xffffffffu, t.u1, o);
+                    q.u2 = __shfl_xor_sync(0xffffffffu, t.u2, o);
+                    q.n1 = __shfl_xor_sync(0xffffffffu, t.n1, o);
+                    q.mx = __shfl_xor_sync(0xffffffffu, t.mx, o);
+                    q.sq = __shfl_xor_sync(0xffffffffu, t.sq, o);
+                    merge(k, t, q);
                 }
-                if (tid == 0) {
-                    s_r[0] = mx;
-                    s_r[1] = sq;
-                    s_r[2] = v1;
-                    s_r[3] = v2;
-                    s_n = m1;
-                }
+                t.key = (long long)k;
+                if (lane == 0)
+                    s_g = t;
             }
             __syncthreads();
-            out.gmax = s_r[0];
-            out.gsq = s_r[1];
-            gu1 = s_r[2];
-            gu2 = s_r[3];
-            gn1 = s_n;
+            out.key = (unsigned long long)s_g.key;
+            out.gmax = s_g.mx;
+            out.gsq = s_g.sq;
+            out.e_lead = s_g.e_lead;
+            out.b_lead = s_g.b_lead;
+            out.p_lead = (int)s_g.p_lead;
+            gu1 = s_g.u1;
+            gu2 = s_g.u2;
+            gn1 = s_g.n1;
             __syncthreads();
             ++use;
         }
         phase(11);
-        if (g_vb == 0 && tid == 0) {
-            ctl->slot[(r + 2) % 3] = 0ull;
-            ctl->tslot[(r + 2) % 3] = 0ull;
-        }
         ++ev;
         if (screened && argmax && out.key) {
             // ---- certification from the bounds: the leader b (largest E~)
@@ -1103,9 +1190,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             // upper bound; the E > E* decision is certified when the bound
             // interval of the leader lies on one side of E*.
             const int nb_ = key_node(out.key);
-            const int pb_ = ldcg(a.pos_of_node + nb_);
-            const double eb = ldcg(a.e64 + pb_), bb = (double)ldcg(a.u32 + pb_);
-            const double lower = eb - bb;
+            const double lower = out.e_lead - out.b_lead;
             const double other = (gn1 == nb_) ? gu2 : gu1;
             // certified: every node is <= E* (no append whoever leads), or
             // the leader is the unique maximum and lies above E*
@@ -1115,7 +1200,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 // ---- pass 2 (rare): FP64 re-score of every node whose upper
                 // bound reaches the leader's lower bound
                 phase(2);
-                const int r2 = ev % 3;
+                const int r2 = p2uses % 3;   // key ring of the FP64 passes
                 unsigned long long key2 = 0;
                 const double thr = lower;   // the maximum is >= the leader's lower bound
                 for (int it = 0; it < rounds; ++it) {
@@ -1140,11 +1225,15 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     atomicMax(&ctl->slot[r2], key2);
                 GSYNC_B();
                 const unsigned long long k64 = ldcg(&ctl->slot[r2]);
-                if (k64)
+                if (k64) {
                     out.key = k64;
+                    out.p_lead = ldcg(a.pos_of_node + key_node(k64));
+                    out.e_lead = ldcg(a.e64 + out.p_lead);
+                    out.b_lead = 0.0;
+                }
                 if (g_vb == 0 && tid == 0)
                     ctl->slot[(r2 + 2) % 3] = 0ull;
-                ++ev;
+                ++p2uses;
                 // the certified maximum of a node that adds nothing
                 out.gmax = fmax(out.gmax, k64 ? ldcg(a.e64 + ldcg(a.pos_of_node + key_node(k64)))
                                                 : 0.0);
@@ -1172,8 +1261,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         double eloc = -1.0;
         if (eo.key) {
             add_node = key_node(eo.key);
-            add_pos = ldcg(a.pos_of_node + add_node);
-            eloc = ldcg(a.e64 + add_pos);
+            add_pos = eo.p_lead;
+            eloc = eo.e_lead;
             if (!(eloc > estar))
                 add_node = -1;
         }
@@ -1409,7 +1498,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
 // ---------------------------------------------------------------------------
 struct GreedyWs {
     size_t ctl, part, parti, perm, node_of_pos, pos_of_node, xg64, dg64, xg32, in_s, u32, e64,
-        spos, c64, w64, cw32, cwff, y64, z, zt, bvec, lvec, rvec, tvec, total;
+        spos, c64, w64, cw32, cwff, y64, z, zt, bvec, lvec, rvec, tvec, rec, total;
 };
 
 static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
@@ -1445,6 +1534,7 @@ static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
     L.lvec = take(sizeof(double) * ncm);
     L.rvec = take(sizeof(D4) * ncm);
     L.tvec = take(sizeof(D4) * ncm);
+    L.rec = take(sizeof(EvalRec) * 2 * kMaxGrid);
     L.total = o;
     return L;
 }
@@ -1510,6 +1600,7 @@ static void fill_args(GreedyArgs &a, char *ws, const GreedyWs &L)
     a.lvec = (double *)(ws + L.lvec);
     a.rvec = (D4 *)(ws + L.rvec);
     a.tvec = (D4 *)(ws + L.tvec);
+    a.rec = (EvalRec *)(ws + L.rec);
 }
 }  // namespace rbf
 

@@ -188,6 +188,9 @@ __global__ void __launch_bounds__(kVolThreads)
 k_volume_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_t nv,
             const float4 *__restrict__ cw, int nc, double *__restrict__ out)
 {
+    // Q points per thread, handled two at a time in paired registers
+    static_assert(Q % 2 == 0, "points per thread come in pairs");
+    constexpr int P = Q / 2;
     extern __shared__ float4 s_cwff[];
     const int tid = threadIdx.x;
     const int64_t per_block = (int64_t)kVolThreads * Q;
@@ -198,17 +201,25 @@ k_volume_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_
         __syncthreads();
     }
     for (int64_t base = blockIdx.x * per_block; base < nv; base += (int64_t)gridDim.x * per_block) {
-        float4 qh[Q], ql[Q];
-        ff ax[Q], ay[Q], az[Q];
+        f2 qxh[P], qxl[P], qyh[P], qyl[P], qzh[P], qzl[P];
+        ff2 ax[P], ay[P], az[P];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            int64_t v = base + (int64_t)i * kVolThreads + tid;
-            v = v < nv ? v : nv - 1;
-            qh[i] = xh[v];
-            ql[i] = xl[v];
-            ax[i] = ff{0.0f, 0.0f};
-            ay[i] = ff{0.0f, 0.0f};
-            az[i] = ff{0.0f, 0.0f};
+        for (int i = 0; i < P; ++i) {
+            int64_t v0 = base + (int64_t)(2 * i) * kVolThreads + tid;
+            int64_t v1 = v0 + kVolThreads;
+            v0 = v0 < nv ? v0 : nv - 1;
+            v1 = v1 < nv ? v1 : nv - 1;
+            const float4 h0 = xh[v0], h1 = xh[v1], l0 = xl[v0], l1 = xl[v1];
+            qxh[i] = f2_pack(h0.x, h1.x);
+            qyh[i] = f2_pack(h0.y, h1.y);
+            qzh[i] = f2_pack(h0.z, h1.z);
+            qxl[i] = f2_pack(l0.x, l1.x);
+            qyl[i] = f2_pack(l0.y, l1.y);
+            qzl[i] = f2_pack(l0.z, l1.z);
+            const f2 z = f2_pack(0.0f, 0.0f);
+            ax[i] = ff2{z, z};
+            ay[i] = ax[i];
+            az[i] = ax[i];
         }
         for (int t0 = 0; t0 < nc; t0 += kTileFF) {
             const int nt = min(kTileFF, nc - t0);
@@ -222,23 +233,37 @@ k_volume_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_
                 const float4 ch = s_cwff[4 * j], cl = s_cwff[4 * j + 1];
                 const float4 wh = s_cwff[4 * j + 2], wl = s_cwff[4 * j + 3];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const ff s2 = dist2_ff(qh[i].x, ql[i].x, qh[i].y, ql[i].y, qh[i].z, ql[i].z,
-                                           ch.x, cl.x, ch.y, cl.y, ch.z, cl.z);
-                    const ff ph = phi_ff_s(s2);
-                    ff_fma_acc(ax[i], wh.x, wl.x, ph);
-                    ff_fma_acc(ay[i], wh.y, wl.y, ph);
-                    ff_fma_acc(az[i], wh.z, wl.z, ph);
+                for (int i = 0; i < P; ++i) {
+                    const ff2 s2 = dist2_ff2(qxh[i], qxl[i], qyh[i], qyl[i], qzh[i], qzl[i],
+                                             f2_bcast(ch.x), f2_bcast(cl.x), f2_bcast(ch.y),
+                                             f2_bcast(cl.y), f2_bcast(ch.z), f2_bcast(cl.z));
+                    const ff2 ph = phi_ff2_s(s2);
+                    ff_fma_acc2(ax[i], f2_bcast(wh.x), f2_bcast(wl.x), ph);
+                    ff_fma_acc2(ay[i], f2_bcast(wh.y), f2_bcast(wl.y), ph);
+                    ff_fma_acc2(az[i], f2_bcast(wh.z), f2_bcast(wl.z), ph);
                 }
             }
         }
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int64_t v = base + (int64_t)i * kVolThreads + tid;
-            if (v < nv) {
-                out[3 * v] = (double)ax[i].h + (double)ax[i].l;
-                out[3 * v + 1] = (double)ay[i].h + (double)ay[i].l;
-                out[3 * v + 2] = (double)az[i].h + (double)az[i].l;
+        for (int i = 0; i < P; ++i) {
+            float xh0, xh1, xl0, xl1, yh0, yh1, yl0, yl1, zh0, zh1, zl0, zl1;
+            f2_unpack(ax[i].h, xh0, xh1);
+            f2_unpack(ax[i].l, xl0, xl1);
+            f2_unpack(ay[i].h, yh0, yh1);
+            f2_unpack(ay[i].l, yl0, yl1);
+            f2_unpack(az[i].h, zh0, zh1);
+            f2_unpack(az[i].l, zl0, zl1);
+            const int64_t v0 = base + (int64_t)(2 * i) * kVolThreads + tid;
+            const int64_t v1 = v0 + kVolThreads;
+            if (v0 < nv) {
+                out[3 * v0] = (double)xh0 + (double)xl0;
+                out[3 * v0 + 1] = (double)yh0 + (double)yl0;
+                out[3 * v0 + 2] = (double)zh0 + (double)zl0;
+            }
+            if (v1 < nv) {
+                out[3 * v1] = (double)xh1 + (double)xl1;
+                out[3 * v1 + 1] = (double)yh1 + (double)yl1;
+                out[3 * v1 + 2] = (double)zh1 + (double)zl1;
             }
         }
     }

@@ -45,7 +45,7 @@ def parse():
                     help="greedy pair arithmetic: FP32, double-float (48) or FP64")
     ap.add_argument("--vol-prec", type=int, default=48, choices=[32, 48, 64],
                     help="volume-sum arithmetic inside the step")
-    ap.add_argument("--workload", default="gcb", choices=["gcb", "batched"],
+    ap.add_argument("--workload", default="gcb", choices=["gcb", "batched", "modal"],
                     help="gcb: the GCB wing (N_b = 50,000, N_v = 2e6); batched: 64 wings "
                          "with N_b ~ U[5k, 100k] and 200k volume points each, replayed "
                          "from one CUDA graph")
@@ -129,6 +129,25 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(self.rows)}
+
+
+def kernel_traffic(name):
+    """DRAM bytes per launch of a kernel from a committed ncu capture, or None
+    when the kernel's sources changed since the capture (hash mismatch)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{name}.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha1()
+    for src in rec.get("sources", []):
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec.get("sources_sha1"):
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def peaks():
@@ -319,7 +338,8 @@ def run_ours(args, rank, world):
             FLOPS_PER_PAIR * nc * nc * 3 / (s_ms * 1e-3)
         roof = {"bound": "alu", "kernel": dom["name"], "achieved": ach / 1e12,
                 "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "traffic": kernel_traffic("k_greedy") if dom is kernels[0] else None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
                 "note": "latency-bound persistent kernel (see kernels)"}
     out = {
         "metric": METRIC,
@@ -540,6 +560,111 @@ def run_batched(args, rank, world):
     }
 
 
+def run_modal(args, rank, world):
+    """32 sinusoidal bending modes dz_q = 0.05 sin((2q-1) pi y / (2b)) on the
+    GCB support set of the 50,000-node wing: D = Phi_vc W (W: N_c x 96) for
+    2,000,000 volume points on the tensor cores (BF16, BF16x3), beside 32
+    separate FP32 volume sums, with errors against FP64 on a sample."""
+    import torch
+    import oracle
+    import paper_2004_04817_gb300 as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    c = workload(args.nv)
+    tod = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=t,
+                                                      device=dev)
+    xb, db, xv = tod(c["xb"]), tod(c["db"]), tod(c["xv"])
+    R = c["radius"]
+    plain = P.greedy_select(xb, db, radius=R, tol=c["tol_rel"], tol_mode=1, m=1,
+                            eval_prec=P.PREC_F32X2)
+    m = max(1, int(round(1.5 * len(c["xb"]) / plain["nc"])))
+    g = P.greedy_select(xb, db, radius=R, tol=c["tol_rel"], tol_mode=1, m=m,
+                        eval_prec=P.PREC_F32X2)
+    S = g["idx"].cpu().numpy()
+    nc = len(S)
+    y = c["xb"][S, 1]
+    modes = np.zeros((nc, 96))
+    for q in range(1, 33):
+        modes[:, 3 * (q - 1) + 2] = 0.05 * np.sin((2 * q - 1) * np.pi * y / 2.0)
+    W = np.zeros_like(modes)
+    for q in range(32):
+        x, _ = P.solve_system(xb, g["idx"], tod(modes[:, 3 * q:3 * q + 3]), radius=R)
+        W[:, 3 * q:3 * q + 3] = x.cpu().numpy()
+    Wd = tod(W)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = torch.empty((len(c["xv"]), 96), dtype=torch.float32, device=dev)
+    ws = None
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    res = {}
+    sample = np.random.default_rng(8).choice(len(c["xv"]), 1000, replace=False)
+    Phi = oracle.phi(np.linalg.norm(c["xv"][sample][:, None] - c["xb"][S][None], axis=-1) / R)
+    ref = Phi @ W
+    dmax = 0.05
+    with ClockSampler(dev.index) as clk:
+        for name, mode in (("bf16", P.MODAL_BF16), ("bf16x3", P.MODAL_BF16X3)):
+            fn = lambda: P.deform_modal(xv, xb, g["idx"], Wd, radius=R, mode=mode, out=out,
+                                        check=False)
+            ms = timed(fn, args.steps)
+            P.deform_modal(xv, xb, g["idx"], Wd, radius=R, mode=mode, out=out)
+            err = np.abs(out.cpu().numpy()[sample].astype(np.float64) - ref).max()
+            res[name] = {"ms": ms, "max_abs_err": float(err), "err_rel_max_disp": float(err / dmax)}
+        # FP32 path: 32 separate three-column volume sums
+        wcols = [tod(W[:, 3 * q:3 * q + 3]) for q in range(32)]
+        dvs = [torch.empty_like(xv) for _ in range(32)]
+
+        def fp32_all():
+            for q in range(32):
+                P.deform_volume(xv, xb, g["idx"], wcols[q], radius=R, eval_prec=32, out=dvs[q])
+        ms32 = timed(fp32_all, max(1, args.steps // 2))
+        fp32_all()
+        got = np.concatenate([d.cpu().numpy()[sample] for d in dvs], axis=1)
+        err32 = np.abs(got - ref).max()
+        res["fp32_32_volume_sums"] = {"ms": ms32, "max_abs_err": float(err32),
+                                      "err_rel_max_disp": float(err32 / dmax)}
+    nv = len(c["xv"])
+    pk = peaks()
+    bf16_peak = float(pk.get("bf16_tflops", 1864.0)) * 1e12
+    mma_flops = 2.0 * nv * (((nc + 63) // 64) * 64) * 96
+    t16, t16x3 = res["bf16"]["ms"] * 1e-3, res["bf16x3"]["ms"] * 1e-3
+    props = torch.cuda.get_device_properties(dev)
+    fp32_peak = props.multi_processor_count * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    return {
+        "metric": METRIC, "value": t16x3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t16x3 * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+        "data": "synthetic (seeded wing generator; see DESIGN.md)",
+        "config": {"workload": "32 modal fields (N_c x 96) on the GCB wing support set, "
+                               "tensor-core volume sum", "n_v": nv, "n_c": nc, "n_out": 96,
+                   "m": m, "l2": "flushed between repetitions"},
+        "modal": res,
+        "speedup_bf16x3_vs_fp32_sums": res["fp32_32_volume_sums"]["ms"] / res["bf16x3"]["ms"],
+        "roofline": {"bound": "tensor", "kernel": "k_modal (BF16x3)",
+                     "achieved": 6 * mma_flops / t16x3 / 1e12, "peak": bf16_peak / 1e12,
+                     "unit": "TFLOP/s", "frac": 6 * mma_flops / t16x3 / bf16_peak,
+                     "traffic": None,
+                     "phi_generation_alu_frac": nv * nc * FLOPS_PER_PAIR / t16x3 / fp32_peak,
+                     "bf16_single": {"achieved": mma_flops / t16 / 1e12,
+                                     "frac": mma_flops / t16 / bf16_peak}},
+        "gpu_launches": 4 * args.steps, "clocks": clk.summary(),
+    }
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -552,8 +677,12 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    out = run_batched(args, rank, world) if args.workload == "batched" else \
-        run_ours(args, rank, world)
+    if args.workload == "batched":
+        out = run_batched(args, rank, world)
+    elif args.workload == "modal":
+        out = run_modal(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -42,6 +42,7 @@ constexpr int kMaxGrid = 4096;
 constexpr int kSmemCentresF32 = 2048;      // FP32 centres kept in shared memory (64 KB)
 constexpr int kSmemCentresFF = 1024;       // double-float centres in the same 64 KB
 constexpr double kPivotMin = 1e-13;        // d^2 at or below: singular (coincident nodes)
+constexpr int kLookIdle = 8;               // idle iterations before a look-ahead
 constexpr float kU32 = 5.9604645e-8f;      // 2^-24, unit roundoff of FP32
 constexpr float kBetaPhi = 16.0f;          // error-bound factors (see screen_bound)
 constexpr float kBetaCoord = 8.0f;
@@ -74,8 +75,9 @@ struct GreedyCtl {
 struct __align__(16) EvalRec {
     double mx, sq, u1, u2, e_lead, b_lead;
     long long n1, key, p_lead;
-    long long pad;
+    long long first;   // look-ahead: smallest cyclic rank of a node above E*
 };
+constexpr long long kNoRank = 0x7FFFFFFFFFFFFFFFll;
 
 struct GreedyArgs {
     const double *xb;
@@ -431,6 +433,7 @@ struct EvalOut {
     double gsq;               // sum of squares of E over the range minus S
     double e_lead, b_lead;    // the leader's error and bound
     int p_lead;               // the leader's position
+    long long first;          // look-ahead result (kNoRank: none)
 };
 
 
@@ -801,7 +804,11 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     // the range (nodes of S excluded: their error is the FP64 interpolation
     // residual) and `out.gsq` the sum of squares.  `force64` evaluates every
     // pair in FP64 whatever the precision mode.
-    auto evaluate = [&](int p0, int p1, bool argmax, bool force64, EvalOut &out) -> bool {
+    // With look >= 0 (a look-ahead over all nodes), also the smallest cyclic
+    // rank (position - look) mod N_b of a node outside S whose error may
+    // exceed E* (upper bound E~ + beta > E*).
+    auto evaluate = [&](int p0, int p1, bool argmax, bool force64, EvalOut &out,
+                        int look) -> bool {
         phase(1);
         const int r = ev % 3;
         const int nq = p1 - p0;
@@ -813,6 +820,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         double lmax = 0.0, lsq = 0.0;
         double e_lead = 0.0, b_lead = 0.0;   // error and bound of this thread's leader
         long long p_lead = -1;                // its position
+        long long first = kNoRank;            // look-ahead rank
         const bool screened = !(a.prec == RBF_PREC_F64 || force64);
         // top two upper bounds E~ + beta of this thread's nodes (screened modes)
         double u1 = -1.0, u2 = -1.0;
@@ -826,6 +834,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     a.e64[q] = e;
                     lmax = fmax(lmax, e);
                     lsq = fma(e, e, lsq);
+                    if (look >= 0 && e > estar)
+                        first = min(first, (long long)((q - look + nb) % nb));
                     if (argmax) {
                         const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
                         if (k2 > key) {
@@ -908,6 +918,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         a.u32[q] = beta;
                         a.e64[q] = (double)e;
                         const double up = (double)e + (double)beta;
+                        if (look >= 0 && up > estar)
+                            first = min(first, (long long)((q - look + nb) % nb));
                         lmax = fmax(lmax, (double)e);
                         lsq = fma((double)e, (double)e, lsq);
                         if (argmax) {
@@ -1016,6 +1028,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         a.u32[q] = bf;
                         a.e64[q] = e;
                         const double up = e + (double)bf;
+                        if (look >= 0 && up > estar)
+                            first = min(first, (long long)((q - look + nb) % nb));
                         lmax = fmax(lmax, e);
                         lsq = fma(e, e, lsq);
                         if (argmax) {
@@ -1050,8 +1064,10 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         {
             auto merge = [](unsigned long long &k, double &el, double &bl, long long &pl,
                             double &v1, double &v2, long long &m1, double &mx, double &sq,
-                            unsigned long long ok_, double oel, double obl, long long opl,
-                            double ov1, double ov2, long long om1, double omx, double osq) {
+                            long long &fr, unsigned long long ok_, double oel, double obl,
+                            long long opl, double ov1, double ov2, long long om1, double omx,
+                            double osq, long long ofr) {
+                fr = min(fr, ofr);
                 if (ok_ > k) {
                     k = ok_;
                     el = oel;
@@ -1078,16 +1094,19 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 const long long om1 = __shfl_xor_sync(0xffffffffu, n1, o);
                 const double omx = __shfl_xor_sync(0xffffffffu, lmax, o);
                 const double osq = __shfl_xor_sync(0xffffffffu, lsq, o);
-                merge(key, e_lead, b_lead, p_lead, u1, u2, n1, lmax, lsq, ok_, oel, obl, opl, ov1,
-                      ov2, om1, omx, osq);
+                const long long ofr = __shfl_xor_sync(0xffffffffu, first, o);
+                merge(key, e_lead, b_lead, p_lead, u1, u2, n1, lmax, lsq, first, ok_, oel, obl,
+                      opl, ov1, ov2, om1, omx, osq, ofr);
             }
             __shared__ EvalRec s_rec[kGWarps];
             if (lane == 0)
-                s_rec[warp] = EvalRec{lmax, lsq, u1, u2, e_lead, b_lead, n1, (long long)key, p_lead};
+                s_rec[warp] = EvalRec{lmax,   lsq,    u1,  u2,  e_lead, b_lead,
+                                      n1,     (long long)key, p_lead, first};
             __syncthreads();
             if (warp == 0) {
-                EvalRec t = lane < kGWarps ? s_rec[lane]
-                                           : EvalRec{0.0, 0.0, -1.0, -1.0, 0.0, 0.0, -1, 0, -1};
+                EvalRec t = lane < kGWarps
+                                ? s_rec[lane]
+                                : EvalRec{0.0, 0.0, -1.0, -1.0, 0.0, 0.0, -1, 0, -1, kNoRank};
                 unsigned long long k = (unsigned long long)t.key;
                 for (int o = kGWarps / 2; o > 0; o >>= 1) {
                     const unsigned long long ok_ = __shfl_xor_sync(0xffffffffu, k, o);
@@ -1099,8 +1118,9 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     const long long om1 = __shfl_xor_sync(0xffffffffu, t.n1, o);
                     const double omx = __shfl_xor_sync(0xffffffffu, t.mx, o);
                     const double osq = __shfl_xor_sync(0xffffffffu, t.sq, o);
-                    merge(k, t.e_lead, t.b_lead, t.p_lead, t.u1, t.u2, t.n1, t.mx, t.sq, ok_, oel,
-                          obl, opl, ov1, ov2, om1, omx, osq);
+                    const long long ofr = __shfl_xor_sync(0xffffffffu, t.first, o);
+                    merge(k, t.e_lead, t.b_lead, t.p_lead, t.u1, t.u2, t.n1, t.mx, t.sq, t.first,
+                          ok_, oel, obl, opl, ov1, ov2, om1, omx, osq, ofr);
                 }
                 t.key = (long long)k;
                 if (lane == 0)
@@ -1114,7 +1134,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         {
             __shared__ EvalRec s_g;
             if (warp == 0) {
-                EvalRec t{0.0, 0.0, -1.0, -1.0, 0.0, 0.0, -1, 0, -1};
+                EvalRec t{0.0, 0.0, -1.0, -1.0, 0.0, 0.0, -1, 0, -1, kNoRank};
                 unsigned long long k = 0;
                 const EvalRec *rb = a.rec + (size_t)(use & 1) * kMaxGrid;
                 auto merge = [](unsigned long long &k, EvalRec &t, const EvalRec &o) {
@@ -1133,6 +1153,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     }
                     t.mx = fmax(t.mx, o.mx);
                     t.sq += o.sq;
+                    t.first = min(t.first, o.first);
                 };
                 for (int b = lane; b < G; b += 32) {
                     EvalRec o;
@@ -1140,7 +1161,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     const double2 v1 = __ldcg((const double2 *)(rb + b) + 1);
                     const double2 v2 = __ldcg((const double2 *)(rb + b) + 2);
                     const longlong2 w0 = __ldcg((const longlong2 *)(rb + b) + 3);
-                    const long long w1 = __ldcg((const long long *)(rb + b) + 8);
+                    const longlong2 w1 = __ldcg((const longlong2 *)(rb + b) + 4);
                     o.mx = v0.x;
                     o.sq = v0.y;
                     o.u1 = v1.x;
@@ -1149,7 +1170,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     o.b_lead = v2.y;
                     o.n1 = w0.x;
                     o.key = w0.y;
-                    o.p_lead = w1;
+                    o.p_lead = w1.x;
+                    o.first = w1.y;
                     merge(k, t, o);
                 }
                 for (int o = 16; o > 0; o >>= 1) {
@@ -1163,6 +1185,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     q.n1 = __shfl_xor_sync(0xffffffffu, t.n1, o);
                     q.mx = __shfl_xor_sync(0xffffffffu, t.mx, o);
                     q.sq = __shfl_xor_sync(0xffffffffu, t.sq, o);
+                    q.first = __shfl_xor_sync(0xffffffffu, t.first, o);
                     merge(k, t, q);
                 }
                 t.key = (long long)k;
@@ -1176,6 +1199,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             out.e_lead = s_g.e_lead;
             out.b_lead = s_g.b_lead;
             out.p_lead = (int)s_g.p_lead;
+            out.first = s_g.first;
             gu1 = s_g.u1;
             gu2 = s_g.u2;
             gn1 = s_g.n1;
@@ -1255,7 +1279,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         const int gi = (int)(k % m);
         const int g0 = goff(gi, nb, m), g1 = goff(gi + 1, nb, m);
         EvalOut eo;
-        if (!evaluate(g0, g1, true, false, eo))
+        if (!evaluate(g0, g1, true, false, eo, -1))
             return;
         int add_node = -1, add_pos = -1;
         double eloc = -1.0;
@@ -1290,7 +1314,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         double gmax = -1.0, grms = -1.0;
         if (hist_full && ((k - 2) % m) == 0) {
             EvalOut d;
-            if (!evaluate(0, nb, false, true, d))
+            if (!evaluate(0, nb, false, true, d, -1))
                 return;
             ++nfull;
             gmax = d.gmax;
@@ -1308,6 +1332,52 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         ++nhist;
         if (idle >= m)
             break;
+        // Look-ahead: after kLookIdle iterations without an append, evaluate
+        // every node once with the unchanged weights.  Groups whose nodes are
+        // all certified <= E* would add nothing when their turn comes, so the
+        // literal sequence continues at the first group (in cyclic order
+        // from the next one) that holds a node possibly above E*; with none,
+        // the run ends where m idle iterations would end it.
+        if (idle >= kLookIdle && m > 2 * kLookIdle && !hist_full) {
+            const int nxt = (int)((k + 1) % m);
+            const int start = goff(nxt, nb, m);
+            EvalOut la;
+            if (!evaluate(0, nb, false, false, la, start))
+                return;
+            ++nfull;
+            long long skip;   // idle iterations certified without evaluation
+            if (la.first == kNoRank) {
+                skip = m - idle;
+                run_max = la.gmax;
+                run_sq = la.gsq;
+            } else {
+                const int pos = (int)((start + la.first) % nb);
+                const int base = nb / m, rem = nb % m;
+                const int g = pos < rem * (base + 1) ? pos / (base + 1)
+                                                     : rem + (pos - rem * (base + 1)) / base;
+                skip = ((long long)g - nxt + m) % m;
+                if (idle + skip >= m) {
+                    skip = m - idle;
+                    run_max = la.gmax;
+                    run_sq = la.gsq;
+                }
+            }
+            if (g_vb == 0 && tid == 0 && a.hist)
+                for (long long s2 = 1; s2 <= skip && nhist + s2 - 1 < a.hist_cap; ++s2) {
+                    double *h = a.hist + RBF_HIST_COLS * (nhist + s2 - 1);
+                    h[0] = (double)(k + s2);
+                    h[1] = (double)nc;
+                    h[2] = -1.0;
+                    h[3] = -1.0;
+                    h[4] = -1.0;
+                    h[5] = -1.0;
+                }
+            k += skip;
+            idle += skip;
+            nhist += skip;
+            if (idle >= m)
+                break;
+        }
     }
     // final weights of the selected set (row a9): FP64 refinement with Z
     double maxres = -1.0;

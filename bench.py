@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("greedy time-to-tol (s) and RBF pairs/s + %FP32 peak, GCB vs plain greedy, "
           "1×GB300")
-FLOPS_PER_PAIR = 22          # algorithmic FP32 flops of one Wendland pair
+FLOPS_PER_PAIR = 22          # algorithmic FP32 flops of one Wendland pair: 3 sub, 5 for d^2, sqrt,
+                             # 1 - eta and its clamp, 2 mul for t^4, 2 for 4 eta + 1, 1 mul, 3 x 2 accumulate
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -45,10 +46,12 @@ def parse():
                     help="greedy pair arithmetic: FP32, double-float (48) or FP64")
     ap.add_argument("--vol-prec", type=int, default=48, choices=[32, 48, 64],
                     help="volume-sum arithmetic inside the step")
-    ap.add_argument("--workload", default="gcb", choices=["gcb", "batched", "modal"],
+    ap.add_argument("--workload", default="gcb", choices=["gcb", "batched", "modal", "fixed_nc"],
                     help="gcb: the GCB wing (N_b = 50,000, N_v = 2e6); batched: 64 wings "
                          "with N_b ~ U[5k, 100k] and 200k volume points each, replayed "
-                         "from one CUDA graph")
+                         "from one CUDA graph; modal: 32 displacement modes on the tensor "
+                         "cores; fixed_nc: N_c fixed to the plain greedy's, m swept, "
+                         "eval/append split, error histories and KL (Tables 2 and 4)")
     return ap.parse_args()
 
 
@@ -267,6 +270,35 @@ def run_ours(args, rank, world):
             ts_.append(a.elapsed_time(b))
         vol_alone[vp] = statistics.median(ts_)
 
+    # compact-support culling at R = 0.25 (a quarter span; at R = 2 every pair
+    # lies inside the support): the selected set's weights re-solved at that
+    # radius, the culled volume sum (plan made once per mesh) against the
+    # unculled kernel of the same precision
+    cull = {}
+    r_cull = 0.25
+    w_cull, _ = P.solve_weights(xb, db, g_last["idx"], radius=r_cull, refine_steps=2)
+    for vp in (32, 48):
+        plan = P.VolumePlan(xv, radius=r_cull, eval_prec=vp, nc_max=nc)
+        _, visited = plan.run(xb, g_last["idx"], w_cull, out=dv, count=True)
+        tc, tu = [], []
+        for _ in range(3):
+            for fn, ts_ in ((lambda: plan.run(xb, g_last["idx"], w_cull, out=dv), tc),
+                            (lambda: P.deform_volume(xv, xb, g_last["idx"], w_cull, radius=r_cull,
+                                                     eval_prec=vp, out=dv), tu)):
+                flush.zero_()
+                a, b = ev(), ev()
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ts_.append(a.elapsed_time(b))
+        cm, um = statistics.median(tc), statistics.median(tu)
+        cull[PREC_NAME[vp]] = {"radius": r_cull, "culled_ms": cm, "unculled_ms": um,
+                               "speedup": um / cm, "pairs_visited_frac": visited / (nv * nc),
+                               "visited_pairs_per_s": visited / (cm * 1e-3),
+                               "plan": plan.info()}
+        del plan
+
     # e2e through the public API with host buffers (pinned), copies timed
     hx = torch.from_numpy(np.ascontiguousarray(c["xb"])).pin_memory()
     hd = torch.from_numpy(np.ascontiguousarray(c["db"])).pin_memory()
@@ -353,7 +385,7 @@ def run_ours(args, rank, world):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": {32: "f32", 48: "f32x2", 64: "f64"}[args.prec],
-        "data": "synthetic (seeded wing generator; see DESIGN.md)",
+        "data": "synthetic (seeded wing generator, paper_2004_04817_gb300/synth.py)",
         "config": workload_desc(c, m, nc_plain, args.prec, args.vol_prec),
         "greedy": {
             "gcb_s": g_ms / 1e3, "plain_s": plain_ms / 1e3,
@@ -364,17 +396,20 @@ def run_ours(args, rank, world):
             "pairs_ff": st["pairs_ff"],
             "rescored": st["rescored"], "estar": st["estar"], "final_max": st["final_max"],
             "us_per_iteration": g_ms * 1e3 / max(st["iterations"], 1),
+            "full_checks": st["full_checks"],
             "phase_ms": dict(zip(["prologue", "eval_other", "rescore_f64", "append",
                                   "refine", "other", "barrier_wait_total", "eval_staging",
-                                  "eval_pass", "eval_block_reduce", "eval_barrier_grid_reduce"],
-                                 [v / 1e6 for v in st["phase_ns"][:11]])),
+                                  "eval_pass", "eval_block_reduce", "eval_barrier_grid_reduce",
+                                  "lookahead_pass"],
+                                 [v / 1e6 for v in st["phase_ns"][:12]])),
         },
         "volume": {"pairs_per_s": vol_pairs / (v_ms * 1e-3), "ms": v_ms,
                    "fp32_peak_frac": vol_achieved / fp32_peak,
                    "alone": {PREC_NAME[k]: {"ms": t, "pairs_per_s": vol_pairs / (t * 1e-3),
                                             "useful_flops_frac_fp32_peak":
                                                 vol_pairs * FLOPS_PER_PAIR / (t * 1e-3) / fp32_peak}
-                             for k, t in vol_alone.items()}},
+                             for k, t in vol_alone.items()},
+                   "cull_sensitivity": cull},
         "weights_max_resid": res_last,
         "kernels": kernels,
         "roofline": roof,
@@ -444,7 +479,7 @@ def run_reference(args):
         "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded wing generator; see DESIGN.md)",
+        "data": "synthetic (seeded wing generator, paper_2004_04817_gb300/synth.py)",
         "config": workload_desc(c, m, g1["nc"], args.prec, args.vol_prec), "impl": "reference",
         "cpu_baseline": base,
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -539,7 +574,7 @@ def run_batched(args, rank, world):
         "metric": METRIC, "value": ms_per / 1e3, "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32x2",
-        "data": "synthetic (seeded wing generator; see DESIGN.md)",
+        "data": "synthetic (seeded wing generator, paper_2004_04817_gb300/synth.py)",
         "config": {"workload": "64 wings in one graph: batched GCB greedy + volume sums",
                    "n_b_min": min(nbs), "n_b_max": max(nbs), "n_b_total": sum(nbs),
                    "n_v_each": len(cases[0]["xv"]), "tol_rel": 1e-4, "radius": 2.0,
@@ -648,7 +683,7 @@ def run_modal(args, rank, world):
         "metric": METRIC, "value": t16x3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t16x3 * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
-        "data": "synthetic (seeded wing generator; see DESIGN.md)",
+        "data": "synthetic (seeded wing generator, paper_2004_04817_gb300/synth.py)",
         "config": {"workload": "32 modal fields (N_c x 96) on the GCB wing support set, "
                                "tensor-core volume sum", "n_v": nv, "n_c": nc, "n_out": 96,
                    "m": m, "l2": "flushed between repetitions"},
@@ -662,6 +697,91 @@ def run_modal(args, rank, world):
                      "bf16_single": {"achieved": mma_flops / t16 / 1e12,
                                      "frac": mma_flops / t16 / bf16_peak}},
         "gpu_launches": 4 * args.steps, "clocks": clk.summary(),
+    }
+
+
+def run_fixed_nc(args, rank, world):
+    """Fixed-N_c comparison, the structure of the paper's Tables 2 and 4 and
+    of its error histories (Sec. 4.1): N_c is fixed to the plain greedy's
+    count at the workload's tolerance (tolerance 0, capacity N_c) and m runs
+    over {1, N_b/N_c, 1.5 N_b/N_c, 2 N_b/N_c}.  Per m: the greedy's time, its
+    split into error evaluations (t1) and Cholesky appends (t2) from the
+    device phase timers, the global maximum error history (FP64 all-node
+    checks every m iterations, in a separate untimed run) and
+    KL(plain || S_m) of the support sets; two random sets of N_c nodes give
+    the KL scale."""
+    import torch
+    import paper_2004_04817_gb300 as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    c = workload(0)
+    tod = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=t,
+                                                      device=dev)
+    xb, db = tod(c["xb"]), tod(c["db"])
+    R = c["radius"]
+    nb = xb.shape[0]
+    plain = P.greedy_select(xb, db, radius=R, tol=c["tol_rel"], tol_mode=1, m=1, seed=1,
+                            eval_prec=args.prec)
+    nc = plain["nc"]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    eval_slots, append_slot = (1, 2, 7, 8, 9, 10, 11), 3
+    rows = []
+    with ClockSampler(dev.index) as clk:
+        for factor in (0.0, 1.0, 1.5, 2.0):
+            m = 1 if factor == 0.0 else int(round(factor * nb / nc))
+            run = lambda: P.greedy_select(xb, db, radius=R, tol=0.0, tol_mode=0, m=m, seed=1,
+                                          nc_max=nc, eval_prec=args.prec)
+            for _ in range(args.warmup):
+                run()
+            ts, t1, t2 = [], [], []
+            for _ in range(args.steps):
+                flush.zero_()
+                a, b = ev(), ev()
+                a.record()
+                g = run()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+                ph = g["stats"]["phase_ns"]
+                t1.append(sum(ph[i] for i in eval_slots) / 1e6)
+                t2.append(ph[append_slot] / 1e6)
+            hist_cap = 4 * nc + 64
+            h = P.greedy_select(xb, db, radius=R, tol=0.0, tol_mode=0, m=m, seed=1, nc_max=nc,
+                                eval_prec=args.prec, hist_cap=hist_cap, history_full=True)
+            hh = h["hist"].cpu().numpy()
+            pts = [(int(r[0]), float(r[3])) for r in hh if r[3] >= 0.0]
+            hist_pts = pts[::max(1, len(pts) // 16)]
+            if pts and hist_pts[-1] != pts[-1]:
+                hist_pts.append(pts[-1])
+            rows.append({"m": m, "n_c": g["nc"], "iterations": g["stats"]["iterations"],
+                         "greedy_ms": statistics.median(ts),
+                         "t1_eval_ms": statistics.median(t1),
+                         "t2_append_ms": statistics.median(t2),
+                         "pairs": g["stats"]["pairs_ff"] + g["stats"]["pairs_f32"]
+                                  + g["stats"]["pairs_f64"],
+                         "final_global_max": pts[-1][1] if pts else None,
+                         "global_max_history": hist_pts,
+                         "kl_vs_plain": P.support_kl(xb, plain["idx"], g["idx"])})
+    rng = np.random.default_rng(1)
+    kl_random = [P.support_kl(xb, plain["idx"],
+                              tod(np.sort(rng.choice(nb, nc, replace=False)).astype(np.int32),
+                                  torch.int32)) for _ in range(2)]
+    base = rows[0]["greedy_ms"]
+    best = min(r["greedy_ms"] for r in rows[1:])
+    return {
+        "metric": METRIC, "value": best * 1e-3, "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": best,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": PREC_NAME[args.prec],
+        "data": "synthetic (seeded wing generator, paper_2004_04817_gb300/synth.py)",
+        "config": {"workload": "fixed-N_c comparison on the 50,000-node wing (N_c = plain "
+                               "greedy's count at tolerance 1e-4)", "n_b": nb, "n_c": nc,
+                   "radius": R, "l2": "flushed between repetitions"},
+        "table": rows, "kl_random": kl_random,
+        "speedup_best_gcb_vs_plain": base / best,
+        "gpu_launches": args.steps * len(rows), "clocks": clk.summary(),
     }
 
 
@@ -681,6 +801,8 @@ def main():
         out = run_batched(args, rank, world)
     elif args.workload == "modal":
         out = run_modal(args, rank, world)
+    elif args.workload == "fixed_nc":
+        out = run_fixed_nc(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if rank == 0:

@@ -72,7 +72,7 @@ typedef struct {
     double radius;        /* support radius R > 0 (eta = distance / R) */
     double tol;           /* E*; absolute, or relative (tol_mode = 1) */
     int32_t tol_mode;     /* 0: E* = tol; 1: E* = tol * max_j |dr_j|_2 */
-    int32_t eval_prec;    /* RBF_PREC_F64 or RBF_PREC_F32 */
+    int32_t eval_prec;    /* RBF_PREC_F64, RBF_PREC_F32 or RBF_PREC_F32X2 */
     int64_t m;            /* number of groups, 1 <= m <= N_b (1 = plain greedy) */
     uint64_t seed;        /* seed of the random partition into groups */
     int64_t nc_max;       /* capacity of the support set, 3 <= nc_max <= N_b */
@@ -97,17 +97,24 @@ typedef struct {
 typedef struct {
     int64_t iterations;      /* greedy iterations run (k - 3 + 1 at exit)      */
     int64_t nc;              /* |S| at exit                                     */
-    int64_t full_checks;     /* diagnostic all-node evaluations (history)       */
+    int64_t full_checks;     /* all-node evaluations: history checks and the
+                                look-aheads over idle runs                     */
     int64_t pairs_f32;       /* (node, centre) pairs evaluated in FP32          */
     int64_t pairs_f64;       /* (node, centre) pairs evaluated in FP64          */
     int64_t pairs_ff;        /* (node, centre) pairs evaluated in double-float  */
     int64_t rescored;        /* nodes re-scored in FP64 after an FP32 screen    */
     double estar;            /* the absolute tolerance E* used                  */
-    double final_max;        /* certified global max error at exit (-1 if the
-                                run ended on an error status)                  */
-    double final_rms;        /* RMS error over the nodes outside S at exit; in
-                                FP32 mode nodes not re-scored enter with their
-                                FP32 value (-1 on an error status)            */
+    double final_max;        /* certified global max error at exit: the FP64
+                                maximum (FP64 mode, or where the last check
+                                re-scored in FP64), else the largest certified
+                                upper bound E~ + beta of the screened errors
+                                (>= the maximum, <= E* at a normal exit);
+                                -1 if the run ended on an error status        */
+    double final_rms;        /* RMS error over the nodes outside S at exit, a
+                                diagnostic summed in FP32 (about 1e-6
+                                relative); in the screened modes nodes not
+                                re-scored enter with their screened value (-1
+                                on an error status)                            */
     double min_pivot;        /* smallest squared Cholesky pivot d^2 seen        */
     double max_resid;        /* with d_w: max_j |F(r_j) - dr_j|_inf over S after
                                 refinement (FP64); -1 without d_w             */
@@ -118,7 +125,8 @@ typedef struct {
                                 [5] other, [6] of all that, time spent waiting
                                 in grid barriers, [7] centre staging, [8] error
                                 pass, [9] block reductions, [10] evaluation
-                                barrier + grid reduction, [11] unused         */
+                                barrier + grid reduction, [11] error pass of
+                                the look-aheads over all nodes                */
 } rbf_greedy_stats;
 
 /* Columns of one row of the optional iteration history (device doubles):
@@ -365,6 +373,69 @@ rbf_status rbf_deform_volume_noalloc(const double *d_xv, int64_t nv,
                                      int64_t nc, const double *d_w,
                                      const rbf_params *p, double *d_dv,
                                      void *stream);
+
+/* --------------------------------------------------------------------------
+ * Volume displacements (Eq. 6) with compact-support culling: the Wendland
+ * C2 basis is zero for d >= R (Sec. 2), so pairs farther apart than R are
+ * skipped.  A plan is made once per volume mesh, radius and precision: it
+ * sorts the points along a Morton curve of a uniform cell grid and records
+ * the bounding box of each tile of consecutive sorted points.  A run lists,
+ * per tile and in support order, the centres within R (with a 1e-3 R
+ * margin) of the tile's box and sums only those.  A skipped pair is an
+ * exact zero of the unculled sum, so the result equals the unculled sum of
+ * the same precision with its zero terms left out (bit for bit in
+ * double-float; in FP32, pairs at d >= R are exact zeros here and
+ * below 1e-28 of |w| in rbf_deform_volume).
+ *
+ * p->eval_prec: RBF_PREC_F32 or RBF_PREC_F32X2.  p->radius fixes the scaling
+ * of the plan (every run uses it).  p->nc_max (>= 1): largest support set a
+ * run may pass.  nv <= 2^31 - 1.
+ * d_xv : device FP64 nv x 3, read by create only (the plan keeps its own
+ *        packed, sorted copy in the workspace).
+ * d_ws : device workspace of rbf_volume_plan_workspace_bytes(nv, p) bytes,
+ *        256-byte aligned, owned by the caller and used by the plan until it
+ *        is destroyed.
+ * run  : d_xb, d_sel_idx, d_w as rbf_deform_volume (nc <= p->nc_max);
+ *        d_dv device FP64 nv x 3 (output, original point order);
+ *        d_pairs: NULL or a device counter to which the run adds the number
+ *        of pairs it evaluated (the culled count is nv * nc minus it).
+ * create: ASYNC (enqueued on `stream`, plan usable on that stream at once).
+ * run: ASYNC (capturable).  info: plan shape (host).  destroy: host only.
+ * ------------------------------------------------------------------------ */
+typedef struct rbf_volume_plan rbf_volume_plan;
+
+size_t rbf_volume_plan_workspace_bytes(int64_t nv, const rbf_params *p);
+rbf_status rbf_volume_plan_create(const double *d_xv, int64_t nv, const rbf_params *p,
+                                  void *d_ws, size_t ws_bytes, void *stream,
+                                  rbf_volume_plan **out);
+rbf_status rbf_volume_plan_run(const rbf_volume_plan *plan, const double *d_xb,
+                               const int32_t *d_sel_idx, int64_t nc, const double *d_w,
+                               double *d_dv, unsigned long long *d_pairs, void *stream);
+rbf_status rbf_volume_plan_info(const rbf_volume_plan *plan, int *bits_per_axis,
+                                int64_t *points_per_tile, int64_t *tiles);
+void rbf_volume_plan_destroy(rbf_volume_plan *plan);
+
+/* --------------------------------------------------------------------------
+ * Kullback-Leibler divergence of two support sets (Sec. 4.1), the paper's
+ * measure of how far a support-node distribution lies from another:
+ *
+ *     KL(S1 || S2) = sum_{i=1..N_b} d1_i log(d1_i / d2_i),
+ *     dk_i = min over j in Sk of |r_i - r_j|   (Euclidean, FP64).
+ *
+ * Terms with d1_i = 0 or d2_i = 0 (node i belongs to a set) have no finite
+ * logarithm and are left out (the paper is silent on them).
+ * rbf_nearest_support: d_dist[i] = min over the nc listed nodes of
+ * |r_i - r_j|, device FP64[nb] (output).  ASYNC.
+ * rbf_support_kl: h_kl (host) = KL(S1 || S2); the sum is deterministic (a
+ * fixed reduction tree).  SYNCHRONOUS.
+ * d_xb: device FP64 nb x 3; d_sel*: device int32 node indices in [0, nb).
+ * ------------------------------------------------------------------------ */
+rbf_status rbf_nearest_support(const double *d_xb, int64_t nb, const int32_t *d_sel_idx,
+                               int64_t nc, double *d_dist, void *stream);
+size_t rbf_support_kl_workspace_bytes(int64_t nb);
+rbf_status rbf_support_kl(const double *d_xb, int64_t nb, const int32_t *d_sel1, int64_t nc1,
+                          const int32_t *d_sel2, int64_t nc2, double *h_kl, void *d_ws,
+                          size_t ws_bytes, void *stream);
 
 /* --------------------------------------------------------------------------
  * The random partition rbf_greedy_select uses (Sec. 3: "stochastically and

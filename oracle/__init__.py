@@ -71,6 +71,10 @@ def lib():
         L.orc_adjoint.argtypes = [dp, C.c_int64, dp, ip, C.c_int64, C.c_double, dp, dp,
                                   C.c_int]
         L.orc_num_threads.restype = C.c_int
+        L.orc_nearest_support.argtypes = [dp, C.c_int64, ip, C.c_int64, dp, C.c_int]
+        L.orc_support_kl.restype = C.c_int
+        L.orc_support_kl.argtypes = [dp, C.c_int64, ip, C.c_int64, ip, C.c_int64,
+                                     C.POINTER(C.c_double), C.c_int]
         _lib = L
     return _lib
 
@@ -213,6 +217,32 @@ def adjoint(xv, xb, S, R, gv, threads=None):
     st = L.orc_adjoint(pv, len(xv), px, ps, len(S), float(R), pg,
                        gc.ctypes.data_as(C.POINTER(C.c_double)), threads or default_threads())
     return gc, st
+
+
+def nearest_support(xb, S, threads=None):
+    """d_i = min over j in S of |r_i - r_j| for every boundary node (Sec. 4.1)."""
+    L = lib()
+    xb, px = _d(xb)
+    S, ps = _i32(S)
+    d = np.empty(len(xb))
+    L.orc_nearest_support(px, len(xb), ps, len(S), d.ctypes.data_as(C.POINTER(C.c_double)),
+                          threads or default_threads())
+    return d
+
+
+def support_kl(xb, S1, S2, threads=None):
+    """KL(S1 || S2) = sum_i d1_i log(d1_i / d2_i) (Sec. 4.1), terms with a zero
+    distance left out."""
+    L = lib()
+    xb, px = _d(xb)
+    S1, p1 = _i32(S1)
+    S2, p2 = _i32(S2)
+    kl = C.c_double(0.0)
+    st = L.orc_support_kl(px, len(xb), p1, len(S1), p2, len(S2), C.byref(kl),
+                          threads or default_threads())
+    if st != 0:
+        raise MemoryError("orc_support_kl")
+    return kl.value
 
 
 def tolerance(db, tol_rel):

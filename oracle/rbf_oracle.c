@@ -22,7 +22,7 @@
  *     groups, 3 seed nodes, then for k = 3, 4, ...: solve, i = k mod m,
  *     errors in G_i, local maximum, append if E > E*.
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - error of node q: E_q = || dr_q - F(r_q) ||_2 (Euclidean norm of the
  *     3-vector);
  *   - partition: SplitMix64 stream from the seed, Fisher-Yates shuffle from the
@@ -524,6 +524,53 @@ int orc_adjoint(const double *xv, int64_t nv, const double *xb, const int32_t *S
         orc_cholesky_solve(k, A, gc, 3);
     free(A);
     return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kullback-Leibler divergence of two support sets (Sec. 4.1):              */
+/*   KL(S1 || S2) = sum_{i=1..N_b} d1_i log(d1_i / d2_i),                     */
+/*   dk_i = min over j in Sk of |r_i - r_j|  (every boundary node i).        */
+/* The paper is silent on d = 0 (node i belongs to a set): such terms have   */
+/* no finite logarithm and are left out.  The sum runs in node order.        */
+/* ------------------------------------------------------------------------ */
+void orc_nearest_support(const double *xb, int64_t nb, const int32_t *S, int64_t k,
+                         double *d, int nthreads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t i = 0; i < nb; ++i) {
+        double best = INFINITY;
+        for (int64_t j = 0; j < k; ++j) {
+            double dij = dist3(xb + 3 * i, xb + 3 * S[j]);
+            if (dij < best)
+                best = dij;
+        }
+        d[i] = best;
+    }
+    (void)nthreads;
+}
+
+int orc_support_kl(const double *xb, int64_t nb, const int32_t *S1, int64_t k1,
+                   const int32_t *S2, int64_t k2, double *kl, int nthreads)
+{
+    double *d1 = (double *)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+    double *d2 = (double *)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+    if (!d1 || !d2) {
+        free(d1);
+        free(d2);
+        return ORC_E_NOMEM;
+    }
+    orc_nearest_support(xb, nb, S1, k1, d1, nthreads);
+    orc_nearest_support(xb, nb, S2, k2, d2, nthreads);
+    double sum = 0.0;
+    for (int64_t i = 0; i < nb; ++i)
+        if (d1[i] > 0.0 && d2[i] > 0.0)
+            sum += d1[i] * log(d1[i] / d2[i]);
+    *kl = sum;
+    free(d1);
+    free(d2);
+    return ORC_OK;
 }
 
 int orc_num_threads(void)

@@ -22,7 +22,10 @@ from .rbf import (  # noqa: F401
     RBFDeform,
     GreedyBatch,
     VolumeBatch,
+    VolumePlan,
     measure_fma_peak,
+    nearest_support,
+    support_kl,
     group_of,
     status_string,
     STATUS,

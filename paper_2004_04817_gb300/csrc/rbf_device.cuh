@@ -164,6 +164,32 @@ __host__ __device__ __forceinline__ void split_f64(double x, float &h, float &l)
     l = (float)(x - (double)h);
 }
 
+// Square root of a non-negative ff value: FP32 reciprocal square root
+// refined by one FP32 Newton step, then one Newton correction in ff (about
+// 2^-46 relative; the same steps as the eta of phi_ff_s).  0 for 0.
+__device__ __forceinline__ ff ff_sqrt(ff s)
+{
+    const float sc = fmaxf(s.h, 1e-37f);
+    float y = rsqrtf(sc);
+    y = __fmul_rn(y, fmaf(-0.5f * sc, __fmul_rn(y, y), 1.5f));
+    const float e0 = __fmul_rn(s.h, y);
+    const float r = __fadd_rn(fmaf(-e0, e0, s.h), s.l);
+    return fast_two_sum(e0, __fmul_rn(__fmul_rn(r, 0.5f), y));
+}
+
+// Bit pattern of a non-negative double: for such values the unsigned
+// integer order is the numeric order, so maxima and comparisons of errors and
+// bounds run on the integer pipe instead of the (slow) FP64 pipe.
+__device__ __forceinline__ unsigned long long dbits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x);
+}
+
+__device__ __forceinline__ double bitsd(unsigned long long b)
+{
+    return __longlong_as_double((long long)b);
+}
+
 // phi(eta) for s = eta^2 given as ff (coordinates pre-scaled by 1/R).
 // sqrt: FP32 reciprocal square root refined by one Newton step in FP32, then
 // one Newton correction of eta in ff (about 2^-46 relative).
@@ -473,13 +499,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 
 // ----------------------------------------------------------------------------
 // Grid barrier for cooperative launches (all CTAs co-resident).  Flat,
-// contention-free: CTA b publishes its arrival count in its own word
-// (release), and every CTA's warp 0 polls all the words (acquire) until each
-// has reached the same count.  No two CTAs write the same address, so an
-// arrival costs one store instead of a serialised atomic, and the wait ends
-// one L2 round trip after the last arrival.  Every wait is bounded: after
-// `limit_ns` the waiting CTA latches RBF_E_TIMEOUT into *status and returns
-// false; callers then leave the kernel.
+// contention-free: CTA b publishes its arrival count in its own word with a
+// release store (ordered after the CTA's writes by the preceding
+// __syncthreads), and every CTA's warp 0 polls all the words with relaxed
+// loads until each has reached the same count, then takes one acquire fence.
+// No two CTAs write the same address, so an arrival costs one store instead
+// of a serialised atomic, and the wait ends one L2 round trip after the last
+// arrival.  Every wait is bounded: after `limit_ns` the waiting CTA latches
+// RBF_E_TIMEOUT into *status and returns false; callers then leave the
+// kernel.  The clock and the status word are read every 16th poll.
 // ----------------------------------------------------------------------------
 constexpr int kBarMaxCtas = 4096;
 
@@ -495,9 +523,21 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
     return v;
 }
 
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 // `epoch` counts the barriers this CTA has passed (the same in every CTA);
@@ -511,29 +551,30 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, unsigned
     __syncthreads();
     if (threadIdx.x < 32) {
         int ok = 1;
-        if (threadIdx.x == 0) {
-            __threadfence();
+        if (threadIdx.x == 0)
             st_release_u32(&bar->arrive[my_block], target);
-        }
         __syncwarp();
         const uint64_t t0 = globaltimer_ns();
-        for (;;) {
+        for (unsigned int poll = 1;; ++poll) {
             bool mine = true;
             for (unsigned int b = threadIdx.x; b < nblocks; b += 32)
-                mine &= (int)(ld_acquire_u32(&bar->arrive[b]) - target) >= 0;
+                mine &= (int)(ld_relaxed_u32(&bar->arrive[b]) - target) >= 0;
             if (__all_sync(0xffffffffu, mine))
                 break;
-            if (*(volatile int *)status == (int)RBF_E_TIMEOUT) {
-                ok = 0;
-                break;
-            }
-            if (globaltimer_ns() - t0 > limit_ns) {
-                if (threadIdx.x == 0)
-                    atomicExch(status, (int)RBF_E_TIMEOUT);
-                ok = 0;
-                break;
+            if ((poll & 15u) == 0u) {
+                if (*(volatile int *)status == (int)RBF_E_TIMEOUT) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > limit_ns) {
+                    if (threadIdx.x == 0)
+                        atomicExch(status, (int)RBF_E_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
             }
         }
+        fence_acq_rel_gpu();
         ok = __all_sync(0xffffffffu, ok);
         if (threadIdx.x == 0) {
             s_ok = ok;

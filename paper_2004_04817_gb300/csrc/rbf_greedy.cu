@@ -46,8 +46,9 @@ constexpr int kLookIdle = 8;               // idle iterations before a look-ahea
 constexpr float kU32 = 5.9604645e-8f;      // 2^-24, unit roundoff of FP32
 constexpr float kBetaPhi = 16.0f;          // error-bound factors (see screen_bound)
 constexpr float kBetaCoord = 8.0f;
-constexpr double kUFF = 5.684341886080802e-14;   // 2^-44: double-float pair accuracy used
-constexpr double kBetaFF = 64.0;                  // in the bound of the ff errors
+constexpr float kUFFf = 5.684341886080802e-14f;  // 2^-44: double-float accuracy used in the
+constexpr float kBetaFF = 72.0f;                  // bound of the ff errors: 64 for the pair
+                                                  // sums, 8 for the team sum and |dr - F|
 
 struct GreedyCtl {
     GridBar bar;
@@ -72,12 +73,18 @@ struct GreedyCtl {
 };
 
 // Per-CTA record of an evaluation (see evaluate).
+// mx, u1, u2: bit patterns of non-negative doubles (0 = none); sq: FP32.
 struct __align__(16) EvalRec {
-    double mx, sq, u1, u2, e_lead, b_lead;
+    unsigned long long mx, u1, u2;
+    double e_lead, b_lead;
+    float sq;
+    int pad;
     long long n1, key, p_lead;
     long long first;   // look-ahead: smallest cyclic rank of a node above E*
 };
 constexpr long long kNoRank = 0x7FFFFFFFFFFFFFFFll;
+static_assert(sizeof(EvalRec) == 80, "EvalRec is read as five 16-byte vectors");
+__device__ constexpr EvalRec kEmptyRec{0, 0, 0, 0.0, 0.0, 0.0f, 0, -1, 0, -1, kNoRank};
 
 struct GreedyArgs {
     const double *xb;
@@ -102,7 +109,9 @@ struct GreedyArgs {
     int32_t *pos_of_node;
     D4 *xg64;                // scaled coordinates, group order
     D4 *dg64;                // displacements, group order
-    float4 *xg32;
+    float4 *xg32;                 // FP32 coordinates = high parts of the double-float split
+    float4 *xgl;                  // low parts (x/R - xg32), group order
+    float4 *dgh, *dgl;            // displacements as double-float (high, low), group order
     uint8_t *in_s;
     float *u32;                   // FP32 upper bound of E per position
     double *e64;                  // FP64 E per position (last evaluation)
@@ -429,7 +438,8 @@ __device__ __forceinline__ void warp_dot3(const double *row, const D4 *v, int p0
 
 struct EvalOut {
     unsigned long long key;   // argmax key over the range minus S (0 = none)
-    double gmax;              // certified maximum of E over the range minus S
+    double gmax;              // certified maximum of E over the range minus S (FP64
+                              // mode, or after an FP64 re-score), else an upper bound
     double gsq;               // sum of squares of E over the range minus S
     double e_lead, b_lead;    // the leader's error and bound
     int p_lead;               // the leader's position
@@ -448,15 +458,60 @@ struct EvalOut {
 // ---------------------------------------------------------------------------
 constexpr int kAppendOk = 0, kAppendTimeout = 1, kAppendNotSpd = 2;
 
+// 1/sqrt(x) for x > 0 in FP64 from the FP32 estimate and two Newton steps
+// y <- y (3 - x y^2) / 2 (the error squares at each step: 2^-23 -> 2^-46 ->
+// below FP64 rounding); about 10 FP64 instructions instead of a full FP64
+// square root and division.
+__device__ __forceinline__ double rsqrt_f64_newton(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    return y;
+}
+
+// Weight j of the support set into the evaluation table of the active
+// precision: FP32 (centre, weight) pairs or double-float (c hi, c lo, w hi,
+// w lo); .w of the weight entry is |w|_1 (FP32), used by the error bounds.
+__device__ __forceinline__ void put_weight(const GreedyArgs &a, int j, const D4 &w)
+{
+    if (a.prec == RBF_PREC_F32X2) {
+        float hx, lx, hy, ly, hz, lz;
+        split_f64(w.x, hx, lx);
+        split_f64(w.y, hy, ly);
+        split_f64(w.z, hz, lz);
+        a.cwff[4 * j + 2] = make_float4(hx, hy, hz, fabsf(hx) + fabsf(hy) + fabsf(hz));
+        a.cwff[4 * j + 3] = make_float4(lx, ly, lz, 0.0f);
+    } else if (a.prec == RBF_PREC_F32) {
+        const float fx = (float)w.x, fy = (float)w.y, fz = (float)w.z;
+        a.cw32[2 * j + 1] = make_float4(fx, fy, fz, fabsf(fx) + fabsf(fy) + fabsf(fz));
+    }
+}
+
+__device__ __forceinline__ void put_centre(const GreedyArgs &a, int j, const D4 &c)
+{
+    if (a.prec == RBF_PREC_F32X2) {
+        float h0, l0, h1, l1, h2, l2;
+        split_f64(c.x, h0, l0);
+        split_f64(c.y, h1, l1);
+        split_f64(c.z, h2, l2);
+        a.cwff[4 * j] = make_float4(h0, h1, h2, 0.0f);
+        a.cwff[4 * j + 1] = make_float4(l0, l1, l2, 0.0f);
+    } else if (a.prec == RBF_PREC_F32) {
+        a.cw32[2 * j] = make_float4((float)c.x, (float)c.y, (float)c.z, 0.0f);
+    }
+}
+
 __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, double &min_piv,
                            int pn, int node, long long kiter, unsigned int &epoch)
 {
     GreedyCtl *ctl = a.ctl;
     const int G = g_vg;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gtid = g_vb * kGThreads + tid;
-    const int gthreads = G * kGThreads;
     const int gwarp = g_vb * kGWarps + warp, gwarps = G * kGWarps;
+    // FP64 instructions cost a warp ~30 FP32 ones on this GPU, so scalar
+    // FP64 work runs once per CTA (warp 0) and sums are split across warps.
+    __shared__ double s_sc[8];
     // A1: b_j = phi(|r_n - r_j| / R), centre j on CTA j mod G (FP64 work
     // spread over every SM)
     const D4 xn = ldcg(a.xg64 + pn);
@@ -466,7 +521,8 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
         a.bvec[j] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
     }
     if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
-    // A2: l = Z b (warp per row) and partial sums of l.l and l.y
+    // A2: l = Z b (warp per row) and the partial sums of l.l and l.y (lane 0
+    // of each warp accumulates its rows)
     double acc4[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = gwarp; i < nc; i += gwarps) {
         const double s = warp_dot(a.z + (size_t)i * a.ld, a.bvec, 0, i + 1);
@@ -479,26 +535,58 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
             acc4[3] = fma(s, y.z, acc4[3]);
         }
     }
-    block_sum4(red, acc4);
-    if (tid == 0)
+    if (lane == 0)
         for (int c = 0; c < 4; ++c)
-            (a.part + (size_t)(use & 1) * kMaxGrid * 4)[4 * g_vb + c] = acc4[c];
+            red.s[warp][c] = acc4[c];
+    __syncthreads();
+    // component c summed by lane 0 of warp c (four SM sub-partitions)
+    if (lane == 0 && warp < 4) {
+        double t = 0.0;
+        for (int k = 0; k < kGWarps; ++k)
+            t += red.s[k][warp];
+        (a.part + (size_t)(use & 1) * kMaxGrid * 4)[4 * g_vb + warp] = t;
+    }
     if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
-    double s4[4];
-    grid_sum4((a.part + (size_t)(use & 1) * kMaxGrid * 4), G, s4);
+    {
+        // grid sums: warp c adds component c of the G partials (fixed order,
+        // the same bits in every CTA)
+        const double *pp = a.part + (size_t)(use & 1) * kMaxGrid * 4;
+        if (warp < 4) {
+            double t = 0.0;
+            for (int b = lane; b < G; b += 32)
+                t += ldcg(pp + 4 * b + warp);
+            t = warp_sum_f64(t);
+            if (lane == 0)
+                s_sc[warp] = t;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double d2 = 1.0 - s_sc[0];   // phi(0) = 1
+            s_sc[4] = d2;
+            if (d2 > kPivotMin) {
+                const double inv_d = rsqrt_f64_newton(d2);
+                const D4 dn = ldcg(a.dg64 + pn);
+                s_sc[5] = inv_d;
+                s_sc[0] = (dn.x - s_sc[1]) * inv_d;   // y_new = (dr_n - l.y) / d
+                s_sc[1] = (dn.y - s_sc[2]) * inv_d;
+                s_sc[2] = (dn.z - s_sc[3]) * inv_d;
+                min_piv = fmin(min_piv, d2);
+            }
+        }
+        __syncthreads();
+    }
     ++use;
-    const double d2 = 1.0 - s4[0];   // phi(0) = 1
+    const double d2 = s_sc[4];
     if (!(d2 > kPivotMin)) {
         if (g_vb == 0 && tid == 0)
             ctl->status = RBF_E_NOT_SPD;
         return kAppendNotSpd;
     }
-    min_piv = fmin(min_piv, d2);
-    const double d = sqrt(d2), inv_d = 1.0 / d;
-    const D4 dn = ldcg(a.dg64 + pn);
-    const double yx = (dn.x - s4[1]) * inv_d, yy = (dn.y - s4[2]) * inv_d,
-                 yz = (dn.z - s4[3]) * inv_d;
-    // A3: u = Z^T l (warp per row of Z^T); new row of Z; weight update
+    const double inv_d = s_sc[5];
+    const double yx = s_sc[0], yy = s_sc[1], yz = s_sc[2];
+    // A3: u = Z^T l (warp per row of Z^T); new row of Z; weight update.  The
+    // new node's own entries are written by the last warp of the grid, which
+    // has the fewest rows.
     for (int j = gwarp; j < nc; j += gwarps) {
         const double s = warp_dot(a.zt + (size_t)j * a.ld, a.lvec, j, nc);
         if (lane == 0) {
@@ -510,41 +598,19 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
             w.y = fma(zz, yy, w.y);
             w.z = fma(zz, yz, w.z);
             a.w64[j] = w;
-            a.cw32[2 * j + 1] = make_float4((float)w.x, (float)w.y, (float)w.z,
-                                            (float)(fabs(w.x) + fabs(w.y) + fabs(w.z)));
-            float hx, lx, hy, ly, hz, lz;
-            split_f64(w.x, hx, lx);
-            split_f64(w.y, hy, ly);
-            split_f64(w.z, hz, lz);
-            a.cwff[4 * j + 2] =
-                make_float4(hx, hy, hz, (float)(fabs(w.x) + fabs(w.y) + fabs(w.z)));
-            a.cwff[4 * j + 3] = make_float4(lx, ly, lz, 0.0f);
+            put_weight(a, j, w);
         }
     }
-    if (g_vb == 0 && tid == 0) {
+    if (gwarp == gwarps - 1 && lane == 0) {
         a.z[(size_t)nc * a.ld + nc] = inv_d;
         a.zt[(size_t)nc * a.ld + nc] = inv_d;
-        a.y64[nc] = mk4(yx, yy, yz, 0.0);   // y_new = (dr_n - l.y) / d
-        const double wx = yx * inv_d, wy = yy * inv_d, wz = yz * inv_d;
-        a.w64[nc] = mk4(wx, wy, wz, 0.0);
+        a.y64[nc] = mk4(yx, yy, yz, 0.0);
+        const D4 wn = mk4(yx * inv_d, yy * inv_d, yz * inv_d, 0.0);   // w_new = y_new / d
+        a.w64[nc] = wn;
         const D4 xc = ldcg(a.xg64 + pn);
         a.c64[nc] = xc;
-        a.cw32[2 * nc] = make_float4((float)xc.x, (float)xc.y, (float)xc.z, 0.0f);
-        a.cw32[2 * nc + 1] = make_float4((float)wx, (float)wy, (float)wz,
-                                         (float)(fabs(wx) + fabs(wy) + fabs(wz)));
-        {
-            float h0, l0, h1, l1, h2, l2;
-            split_f64(xc.x, h0, l0);
-            split_f64(xc.y, h1, l1);
-            split_f64(xc.z, h2, l2);
-            a.cwff[4 * nc] = make_float4(h0, h1, h2, 0.0f);
-            a.cwff[4 * nc + 1] = make_float4(l0, l1, l2, 0.0f);
-            split_f64(wx, h0, l0);
-            split_f64(wy, h1, l1);
-            split_f64(wz, h2, l2);
-            a.cwff[4 * nc + 2] = make_float4(h0, h1, h2, (float)(fabs(wx) + fabs(wy) + fabs(wz)));
-            a.cwff[4 * nc + 3] = make_float4(l0, l1, l2, 0.0f);
-        }
+        put_centre(a, nc, xc);
+        put_weight(a, nc, wn);
         a.spos[nc] = pn;
         a.in_s[pn] = 1;
         a.sel_idx[nc] = node;
@@ -705,6 +771,18 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         const double d0 = a.db[3 * node], d1 = a.db[3 * node + 1], d2 = a.db[3 * node + 2];
         a.xg64[pos] = mk4(x, y, z, 0.0);
         a.xg32[pos] = make_float4((float)x, (float)y, (float)z, 0.0f);
+        {
+            float h0, l0, h1, l1, h2, l2;
+            split_f64(x, h0, l0);
+            split_f64(y, h1, l1);
+            split_f64(z, h2, l2);
+            a.xgl[pos] = make_float4(l0, l1, l2, 0.0f);
+            split_f64(d0, h0, l0);
+            split_f64(d1, h1, l1);
+            split_f64(d2, h2, l2);
+            a.dgh[pos] = make_float4(h0, h1, h2, 0.0f);
+            a.dgl[pos] = make_float4(l0, l1, l2, 0.0f);
+        }
         a.dg64[pos] = mk4(d0, d1, d2, 0.0);
         a.in_s[pos] = 0;
         if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(d0) || !isfinite(d1) ||
@@ -807,8 +885,11 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     // With look >= 0 (a look-ahead over all nodes), also the smallest cyclic
     // rank (position - look) mod N_b of a node outside S whose error may
     // exceed E* (upper bound E~ + beta > E*).
-    auto evaluate = [&](int p0, int p1, bool argmax, bool force64, EvalOut &out,
-                        int look) -> bool {
+    // With `cached`, nothing is recomputed: the pass reads the errors and
+    // bounds the last evaluations stored (valid while the weights are
+    // unchanged, i.e. until the next append).
+    auto evaluate = [&](int p0, int p1, bool argmax, bool force64, EvalOut &out, int look,
+                        bool cached) -> bool {
         phase(1);
         const int r = ev % 3;
         const int nq = p1 - p0;
@@ -817,23 +898,49 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         const int team = gtid / ts, nteams = gthreads / ts;
         const int rounds = (nq + nteams - 1) / nteams;
         unsigned long long key = 0;
-        double lmax = 0.0, lsq = 0.0;
+        // maxima and bounds are non-negative doubles kept as bit patterns,
+        // compared on the integer pipe (dbits)
+        unsigned long long mxb = 0;          // largest E (E~ in screened modes)
+        float lsq = 0.0f;                    // sum of E^2 (RMS diagnostic)
         double e_lead = 0.0, b_lead = 0.0;   // error and bound of this thread's leader
         long long p_lead = -1;                // its position
         long long first = kNoRank;            // look-ahead rank
         const bool screened = !(a.prec == RBF_PREC_F64 || force64);
-        // top two upper bounds E~ + beta of this thread's nodes (screened modes)
-        double u1 = -1.0, u2 = -1.0;
+        const unsigned long long estar_b = dbits(estar);
+        // top two upper bounds E~ + beta of this thread's nodes (screened
+        // modes; 0 = none, a real bound is > 0)
+        unsigned long long u1 = 0, u2 = 0;
         long long n1 = -1;
-        if (!screened) {
+        if (cached) {
+            phase(look >= 0 ? 11 : 8);
+            for (int it = 0; it < rounds; ++it) {
+                const int q = p0 + team + it * nteams;
+                if (q < p1 && sub == 0 && !ldcg(a.in_s + q)) {
+                    const double e = ldcg(a.e64 + q);
+                    const float bf = screened ? ldcg(a.u32 + q) : 0.0f;
+                    const unsigned long long upb = dbits(e + (double)bf);
+                    if (look >= 0 && upb > estar_b)
+                        first = min(first, (long long)((q - look + nb) % nb));
+                    mxb = max(mxb, dbits(e));
+                    lsq = fmaf((float)e, (float)e, lsq);
+                    if (upb > u1) {
+                        u2 = u1;
+                        u1 = upb;
+                        n1 = ldcg(a.node_of_pos + q);
+                    } else if (upb > u2) {
+                        u2 = upb;
+                    }
+                }
+            }
+        } else if (!screened) {
             for (int it = 0; it < rounds; ++it) {
                 const int q = p0 + team + it * nteams;
                 const bool act = q < p1;
                 const double e = team_error_f64(a, act ? q : p0, nc, sub, ts);
                 if (act && sub == 0 && !ldcg(a.in_s + q)) {
                     a.e64[q] = e;
-                    lmax = fmax(lmax, e);
-                    lsq = fma(e, e, lsq);
+                    mxb = max(mxb, dbits(e));
+                    lsq = fmaf((float)e, (float)e, lsq);
                     if (look >= 0 && e > estar)
                         first = min(first, (long long)((q - look + nb) % nb));
                     if (argmax) {
@@ -875,13 +982,13 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 float t = 0.0f;
                 for (int j = tid; j < nc; j += 32)
                     t += smem ? (use_ff ? s_cw[4 * j + 2].w : s_cw[2 * j + 1].w)
-                              : ldcg(a.cw32 + 2 * j + 1).w;
+                              : (use_ff ? ldcg(a.cwff + 4 * j + 2).w : ldcg(a.cw32 + 2 * j + 1).w);
                 t = team_sum(t, 32);
                 if (tid == 0)
                     s_wabs = t;
             }
             __syncthreads();
-            phase(8);
+            phase(look >= 0 ? 11 : 8);
             if (!use_ff) {
                 const float4 *cw = smem ? s_cw : a.cw32;
                 const float coord_term = kBetaCoord * xscale * s_wabs * 1.001f;
@@ -917,11 +1024,11 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                             kU32 * (kBetaPhi * (sb + dabs) + coord_term + 4.0f * e) + 1e-30f;
                         a.u32[q] = beta;
                         a.e64[q] = (double)e;
-                        const double up = (double)e + (double)beta;
-                        if (look >= 0 && up > estar)
+                        const unsigned long long upb = dbits((double)e + (double)beta);
+                        if (look >= 0 && upb > estar_b)
                             first = min(first, (long long)((q - look + nb) % nb));
-                        lmax = fmax(lmax, (double)e);
-                        lsq = fma((double)e, (double)e, lsq);
+                        mxb = max(mxb, dbits((double)e));
+                        lsq = fmaf(e, e, lsq);
                         if (argmax) {
                             const unsigned long long k2 = key_f64((double)e, ldcg(a.node_of_pos + q));
                             if (k2 > key) {
@@ -930,13 +1037,13 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                                 b_lead = (double)beta;
                                 p_lead = q;
                             }
-                            if (up > u1) {
-                                u2 = u1;
-                                u1 = up;
-                                n1 = ldcg(a.node_of_pos + q);
-                            } else if (up > u2) {
-                                u2 = up;
-                            }
+                        }
+                        if (upb > u1) {
+                            u2 = u1;
+                            u1 = upb;
+                            n1 = ldcg(a.node_of_pos + q);
+                        } else if (upb > u2) {
+                            u2 = upb;
                         }
                     }
                 }
@@ -944,15 +1051,20 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     pairs32 += (long long)nq * nc;
             } else {
                 const float4 *cw = smem ? s_cw : a.cwff;
-                const double coord_term = (16.0 * (double)xscale + 4.0) * (double)s_wabs;
+                const float coord_term = (16.0f * xscale + 4.0f) * s_wabs;
                 for (int it = 0; it < rounds; ++it) {
                     const int q = p0 + team + it * nteams;
                     const bool act = q < p1;
-                    const D4 xq = ldcg(a.xg64 + (act ? q : p0));
-                    float qxh, qxl, qyh, qyl, qzh, qzl;
-                    split_f64(xq.x, qxh, qxl);
-                    split_f64(xq.y, qyh, qyl);
-                    split_f64(xq.z, qzh, qzl);
+                    const int qq = act ? q : p0;
+                    // the node: coordinates (high = FP32 copy, low part) and,
+                    // for the epilogue, its displacement, S flag and index,
+                    // all loaded ahead of the pair loop
+                    const float4 xh = ldcg(a.xg32 + qq), xlo = ldcg(a.xgl + qq);
+                    const float4 dh = ldcg(a.dgh + qq), dl = ldcg(a.dgl + qq);
+                    const bool q_in_s = ldcg(a.in_s + qq) != 0;
+                    const int qnode = ldcg(a.node_of_pos + qq);
+                    const float qxh = xh.x, qxl = xlo.x, qyh = xh.y, qyl = xlo.y, qzh = xh.z,
+                                qzl = xlo.z;
                     ff fx{0.0f, 0.0f}, fy{0.0f, 0.0f}, fz{0.0f, 0.0f};
                     float sb = 0.0f;
                     // two centres (j, j + ts) per step in paired registers
@@ -996,57 +1108,66 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         ff_fma_acc(fz, wh.z, wl.z, ph);
                         sb = fmaf(wh.w, ph.h, sb);
                     }
-                    // team reduction in FP64 (each ff value becomes the double h + l)
-                    float gh0, gh1, gl0, gl1;
-                    f2_unpack(gx.h, gh0, gh1);
-                    f2_unpack(gx.l, gl0, gl1);
-                    double sx = (double)fx.h + (double)fx.l + (((double)gh0 + (double)gl0) +
-                                                                ((double)gh1 + (double)gl1));
-                    f2_unpack(gy.h, gh0, gh1);
-                    f2_unpack(gy.l, gl0, gl1);
-                    double sy = (double)fy.h + (double)fy.l + (((double)gh0 + (double)gl0) +
-                                                                ((double)gh1 + (double)gl1));
-                    f2_unpack(gz.h, gh0, gh1);
-                    f2_unpack(gz.l, gl0, gl1);
-                    double sz = (double)fz.h + (double)fz.l + (((double)gh0 + (double)gl0) +
-                                                                ((double)gh1 + (double)gl1));
-                    sx = team_sum(sx, ts);
-                    sy = team_sum(sy, ts);
-                    sz = team_sum(sz, ts);
+                    // the lane's three accumulators (each an unnormalised
+                    // pair) summed and reduced over the team in double-float
+                    // on the FP32 pipe
+                    auto lane_sum = [&](const ff2 &g, const ff &f) {
+                        float h0, h1, l0, l1;
+                        f2_unpack(g.h, h0, h1);
+                        f2_unpack(g.l, l0, l1);
+                        return ff_add(ff_add(two_sum(h0, l0), two_sum(h1, l1)), two_sum(f.h, f.l));
+                    };
+                    ff sx = lane_sum(gx, fx), sy = lane_sum(gy, fy), sz = lane_sum(gz, fz);
+                    for (int o = 1; o < ts; o <<= 1) {
+                        sx = ff_add(sx, ff{__shfl_xor_sync(0xffffffffu, sx.h, o),
+                                           __shfl_xor_sync(0xffffffffu, sx.l, o)});
+                        sy = ff_add(sy, ff{__shfl_xor_sync(0xffffffffu, sy.h, o),
+                                           __shfl_xor_sync(0xffffffffu, sy.l, o)});
+                        sz = ff_add(sz, ff{__shfl_xor_sync(0xffffffffu, sz.h, o),
+                                           __shfl_xor_sync(0xffffffffu, sz.l, o)});
+                    }
                     sb = team_sum(sb, ts);
-                    if (act && sub == 0 && !ldcg(a.in_s + q)) {
-                        const D4 d = ldcg(a.dg64 + q);
-                        const double ex = d.x - sx, ey = d.y - sy, ez = d.z - sz;
-                        const double e = sqrt(fma(ez, ez, fma(ey, ey, ex * ex)));
-                        const double dabs = fabs(d.x) + fabs(d.y) + fabs(d.z);
+                    if (act && sub == 0 && !q_in_s) {
+                        // E = |dr - F| in double-float; FP64 only converts the
+                        // result (an FP64 instruction costs a warp ~30x an
+                        // FP32 one here)
+                        const ff ex = ff_add(ff{dh.x, dl.x}, ff{-sx.h, -sx.l});
+                        const ff ey = ff_add(ff{dh.y, dl.y}, ff{-sy.h, -sy.l});
+                        const ff ez = ff_add(ff{dh.z, dl.z}, ff{-sz.h, -sz.l});
+                        const ff ef = ff_sqrt(ff_add(ff_add(ff_sqr(ex), ff_sqr(ey)), ff_sqr(ez)));
+                        const double e = (double)ef.h + (double)ef.l;
+                        const float dabs = fabsf(dh.x) + fabsf(dh.y) + fabsf(dh.z);
                         // bound of |E~ - E|: ff rounding of phi, products and
-                        // sums (proportional to sum |w| phi), of the coordinate
-                        // splits (max|x|/R * sum |w|) and of the displacement
-                        const double beta =
-                            kUFF * (kBetaFF * ((double)sb + dabs) + coord_term) + 1e-300;
-                        const float bf = (float)(beta * 1.0000002);
+                        // sums (proportional to sum |w| phi + |dr|), of the
+                        // coordinate splits (max|x|/R * sum |w|) and of the
+                        // square root; the FP32 evaluation of the bound is
+                        // rounded up by the factor
+                        const float bf =
+                            fmaxf(kUFFf * (kBetaFF * (sb + dabs) + coord_term + 4.0f * ef.h) *
+                                      1.000002f,
+                                  1e-18f);
                         a.u32[q] = bf;
                         a.e64[q] = e;
-                        const double up = e + (double)bf;
-                        if (look >= 0 && up > estar)
+                        const unsigned long long upb = dbits(e + (double)bf);
+                        if (look >= 0 && upb > estar_b)
                             first = min(first, (long long)((q - look + nb) % nb));
-                        lmax = fmax(lmax, e);
-                        lsq = fma(e, e, lsq);
+                        mxb = max(mxb, dbits(e));
+                        lsq = fmaf(ef.h, ef.h, lsq);
                         if (argmax) {
-                            const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
+                            const unsigned long long k2 = key_f64(e, qnode);
                             if (k2 > key) {
                                 key = k2;
                                 e_lead = e;
                                 b_lead = (double)bf;
                                 p_lead = q;
                             }
-                            if (up > u1) {
-                                u2 = u1;
-                                u1 = up;
-                                n1 = ldcg(a.node_of_pos + q);
-                            } else if (up > u2) {
-                                u2 = up;
-                            }
+                        }
+                        if (upb > u1) {
+                            u2 = u1;
+                            u1 = upb;
+                            n1 = qnode;
+                        } else if (upb > u2) {
+                            u2 = upb;
                         }
                     }
                 }
@@ -1063,10 +1184,11 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         phase(9);
         {
             auto merge = [](unsigned long long &k, double &el, double &bl, long long &pl,
-                            double &v1, double &v2, long long &m1, double &mx, double &sq,
-                            long long &fr, unsigned long long ok_, double oel, double obl,
-                            long long opl, double ov1, double ov2, long long om1, double omx,
-                            double osq, long long ofr) {
+                            unsigned long long &v1, unsigned long long &v2, long long &m1,
+                            unsigned long long &mx, float &sq, long long &fr,
+                            unsigned long long ok_, double oel, double obl, long long opl,
+                            unsigned long long ov1, unsigned long long ov2, long long om1,
+                            unsigned long long omx, float osq, long long ofr) {
                 fr = min(fr, ofr);
                 if (ok_ > k) {
                     k = ok_;
@@ -1075,13 +1197,13 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     pl = opl;
                 }
                 if (ov1 > v1 || (ov1 == v1 && om1 >= 0 && (m1 < 0 || om1 < m1))) {
-                    v2 = fmax(v1, ov2);
+                    v2 = max(v1, ov2);
                     v1 = ov1;
                     m1 = om1;
                 } else {
-                    v2 = fmax(v2, ov1);
+                    v2 = max(v2, ov1);
                 }
-                mx = fmax(mx, omx);
+                mx = max(mx, omx);
                 sq += osq;
             };
             for (int o = 16; o >= ts; o >>= 1) {
@@ -1089,35 +1211,33 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 const double oel = __shfl_xor_sync(0xffffffffu, e_lead, o);
                 const double obl = __shfl_xor_sync(0xffffffffu, b_lead, o);
                 const long long opl = __shfl_xor_sync(0xffffffffu, p_lead, o);
-                const double ov1 = __shfl_xor_sync(0xffffffffu, u1, o);
-                const double ov2 = __shfl_xor_sync(0xffffffffu, u2, o);
+                const unsigned long long ov1 = __shfl_xor_sync(0xffffffffu, u1, o);
+                const unsigned long long ov2 = __shfl_xor_sync(0xffffffffu, u2, o);
                 const long long om1 = __shfl_xor_sync(0xffffffffu, n1, o);
-                const double omx = __shfl_xor_sync(0xffffffffu, lmax, o);
-                const double osq = __shfl_xor_sync(0xffffffffu, lsq, o);
+                const unsigned long long omx = __shfl_xor_sync(0xffffffffu, mxb, o);
+                const float osq = __shfl_xor_sync(0xffffffffu, lsq, o);
                 const long long ofr = __shfl_xor_sync(0xffffffffu, first, o);
-                merge(key, e_lead, b_lead, p_lead, u1, u2, n1, lmax, lsq, first, ok_, oel, obl,
+                merge(key, e_lead, b_lead, p_lead, u1, u2, n1, mxb, lsq, first, ok_, oel, obl,
                       opl, ov1, ov2, om1, omx, osq, ofr);
             }
             __shared__ EvalRec s_rec[kGWarps];
             if (lane == 0)
-                s_rec[warp] = EvalRec{lmax,   lsq,    u1,  u2,  e_lead, b_lead,
-                                      n1,     (long long)key, p_lead, first};
+                s_rec[warp] = EvalRec{mxb, u1, u2, e_lead, b_lead, lsq, 0,
+                                      n1, (long long)key, p_lead, first};
             __syncthreads();
             if (warp == 0) {
-                EvalRec t = lane < kGWarps
-                                ? s_rec[lane]
-                                : EvalRec{0.0, 0.0, -1.0, -1.0, 0.0, 0.0, -1, 0, -1, kNoRank};
+                EvalRec t = lane < kGWarps ? s_rec[lane] : kEmptyRec;
                 unsigned long long k = (unsigned long long)t.key;
                 for (int o = kGWarps / 2; o > 0; o >>= 1) {
                     const unsigned long long ok_ = __shfl_xor_sync(0xffffffffu, k, o);
                     const double oel = __shfl_xor_sync(0xffffffffu, t.e_lead, o);
                     const double obl = __shfl_xor_sync(0xffffffffu, t.b_lead, o);
                     const long long opl = __shfl_xor_sync(0xffffffffu, t.p_lead, o);
-                    const double ov1 = __shfl_xor_sync(0xffffffffu, t.u1, o);
-                    const double ov2 = __shfl_xor_sync(0xffffffffu, t.u2, o);
+                    const unsigned long long ov1 = __shfl_xor_sync(0xffffffffu, t.u1, o);
+                    const unsigned long long ov2 = __shfl_xor_sync(0xffffffffu, t.u2, o);
                     const long long om1 = __shfl_xor_sync(0xffffffffu, t.n1, o);
-                    const double omx = __shfl_xor_sync(0xffffffffu, t.mx, o);
-                    const double osq = __shfl_xor_sync(0xffffffffu, t.sq, o);
+                    const unsigned long long omx = __shfl_xor_sync(0xffffffffu, t.mx, o);
+                    const float osq = __shfl_xor_sync(0xffffffffu, t.sq, o);
                     const long long ofr = __shfl_xor_sync(0xffffffffu, t.first, o);
                     merge(k, t.e_lead, t.b_lead, t.p_lead, t.u1, t.u2, t.n1, t.mx, t.sq, t.first,
                           ok_, oel, obl, opl, ov1, ov2, om1, omx, osq, ofr);
@@ -1129,12 +1249,12 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         }
         phase(10);
         GSYNC_B();
-        double gu1 = -1.0, gu2 = -1.0;
+        double gu1 = 0.0, gu2 = 0.0;
         long long gn1 = -1;
         {
             __shared__ EvalRec s_g;
             if (warp == 0) {
-                EvalRec t{0.0, 0.0, -1.0, -1.0, 0.0, 0.0, -1, 0, -1, kNoRank};
+                EvalRec t = kEmptyRec;
                 unsigned long long k = 0;
                 const EvalRec *rb = a.rec + (size_t)(use & 1) * kMaxGrid;
                 auto merge = [](unsigned long long &k, EvalRec &t, const EvalRec &o) {
@@ -1145,33 +1265,32 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         t.p_lead = o.p_lead;
                     }
                     if (o.u1 > t.u1 || (o.u1 == t.u1 && o.n1 >= 0 && (t.n1 < 0 || o.n1 < t.n1))) {
-                        t.u2 = fmax(t.u1, o.u2);
+                        t.u2 = max(t.u1, o.u2);
                         t.u1 = o.u1;
                         t.n1 = o.n1;
                     } else {
-                        t.u2 = fmax(t.u2, o.u1);
+                        t.u2 = max(t.u2, o.u1);
                     }
-                    t.mx = fmax(t.mx, o.mx);
+                    t.mx = max(t.mx, o.mx);
                     t.sq += o.sq;
                     t.first = min(t.first, o.first);
                 };
                 for (int b = lane; b < G; b += 32) {
+                    const longlong2 *src = (const longlong2 *)(rb + b);
+                    const longlong2 w0 = __ldcg(src), w1 = __ldcg(src + 1), w2 = __ldcg(src + 2),
+                                    w3 = __ldcg(src + 3), w4 = __ldcg(src + 4);
                     EvalRec o;
-                    const double2 v0 = __ldcg((const double2 *)(rb + b));
-                    const double2 v1 = __ldcg((const double2 *)(rb + b) + 1);
-                    const double2 v2 = __ldcg((const double2 *)(rb + b) + 2);
-                    const longlong2 w0 = __ldcg((const longlong2 *)(rb + b) + 3);
-                    const longlong2 w1 = __ldcg((const longlong2 *)(rb + b) + 4);
-                    o.mx = v0.x;
-                    o.sq = v0.y;
-                    o.u1 = v1.x;
-                    o.u2 = v1.y;
-                    o.e_lead = v2.x;
-                    o.b_lead = v2.y;
-                    o.n1 = w0.x;
-                    o.key = w0.y;
-                    o.p_lead = w1.x;
-                    o.first = w1.y;
+                    o.mx = (unsigned long long)w0.x;
+                    o.u1 = (unsigned long long)w0.y;
+                    o.u2 = (unsigned long long)w1.x;
+                    o.e_lead = __longlong_as_double(w1.y);
+                    o.b_lead = __longlong_as_double(w2.x);
+                    o.sq = __int_as_float((int)(w2.y & 0xffffffffll));
+                    o.pad = 0;
+                    o.n1 = w3.x;
+                    o.key = w3.y;
+                    o.p_lead = w4.x;
+                    o.first = w4.y;
                     merge(k, t, o);
                 }
                 for (int o = 16; o > 0; o >>= 1) {
@@ -1194,19 +1313,23 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             }
             __syncthreads();
             out.key = (unsigned long long)s_g.key;
-            out.gmax = s_g.mx;
-            out.gsq = s_g.sq;
+            out.gmax = bitsd(s_g.mx);
+            out.gsq = (double)s_g.sq;
             out.e_lead = s_g.e_lead;
             out.b_lead = s_g.b_lead;
             out.p_lead = (int)s_g.p_lead;
             out.first = s_g.first;
-            gu1 = s_g.u1;
-            gu2 = s_g.u2;
+            gu1 = bitsd(s_g.u1);
+            gu2 = bitsd(s_g.u2);
             gn1 = s_g.n1;
+            // screened modes: the certified maximum is the largest upper
+            // bound E~ + beta (E~ alone may overstate or understate E)
+            if (screened)
+                out.gmax = gu1;
             __syncthreads();
             ++use;
         }
-        phase(11);
+        phase(1);
         ++ev;
         if (screened && argmax && out.key) {
             // ---- certification from the bounds: the leader b (largest E~)
@@ -1258,9 +1381,10 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 if (g_vb == 0 && tid == 0)
                     ctl->slot[(r2 + 2) % 3] = 0ull;
                 ++p2uses;
-                // the certified maximum of a node that adds nothing
-                out.gmax = fmax(out.gmax, k64 ? ldcg(a.e64 + ldcg(a.pos_of_node + key_node(k64)))
-                                                : 0.0);
+                // every node left out has E < thr <= the leader's E, so the
+                // largest FP64 value among the re-scored nodes is the maximum
+                if (k64)
+                    out.gmax = ldcg(a.e64 + ldcg(a.pos_of_node + key_node(k64)));
             }
         }
         phase(5);
@@ -1275,11 +1399,15 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     double run_max = 0.0, run_sq = 0.0;
     int status = RBF_OK;
     const bool hist_full = a.hist != nullptr && (a.flags & RBF_FLAG_HISTORY_FULL) != 0;
+    // every node's error and bound in e64/u32 come from the current weights
+    // (set by a look-ahead, cleared by an append): later look-aheads of the
+    // same idle run only scan them
+    bool look_cached = false;
     for (;; ++k) {
         const int gi = (int)(k % m);
         const int g0 = goff(gi, nb, m), g1 = goff(gi + 1, nb, m);
         EvalOut eo;
-        if (!evaluate(g0, g1, true, false, eo, -1))
+        if (!evaluate(g0, g1, true, false, eo, -1, false))
             return;
         int add_node = -1, add_pos = -1;
         double eloc = -1.0;
@@ -1306,6 +1434,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             idle = 0;
             run_max = 0.0;
             run_sq = 0.0;
+            look_cached = false;
         } else {
             ++idle;
             run_max = fmax(run_max, eo.gmax);
@@ -1314,7 +1443,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         double gmax = -1.0, grms = -1.0;
         if (hist_full && ((k - 2) % m) == 0) {
             EvalOut d;
-            if (!evaluate(0, nb, false, true, d, -1))
+            if (!evaluate(0, nb, false, true, d, -1, false))
                 return;
             ++nfull;
             gmax = d.gmax;
@@ -1337,14 +1466,18 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         // all certified <= E* would add nothing when their turn comes, so the
         // literal sequence continues at the first group (in cyclic order
         // from the next one) that holds a node possibly above E*; with none,
-        // the run ends where m idle iterations would end it.
+        // the run ends where m idle iterations would end it.  A later
+        // look-ahead of the same idle run (a flagged group whose nodes all
+        // turned out <= E*) only scans the stored errors and bounds.
         if (idle >= kLookIdle && m > 2 * kLookIdle && !hist_full) {
             const int nxt = (int)((k + 1) % m);
             const int start = goff(nxt, nb, m);
             EvalOut la;
-            if (!evaluate(0, nb, false, false, la, start))
+            if (!evaluate(0, nb, false, false, la, start, look_cached))
                 return;
-            ++nfull;
+            if (!look_cached)
+                ++nfull;
+            look_cached = true;
             long long skip;   // idle iterations certified without evaluation
             if (la.first == kNoRank) {
                 skip = m - idle;
@@ -1422,7 +1555,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
 }
 
 // One problem on the whole grid.
-__global__ void __launch_bounds__(kGThreads, 2) k_greedy(GreedyArgs a)
+__global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
 {
     if (threadIdx.x == 0) {
         g_vb = blockIdx.x;
@@ -1567,7 +1700,8 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
 // Workspace layout.
 // ---------------------------------------------------------------------------
 struct GreedyWs {
-    size_t ctl, part, parti, perm, node_of_pos, pos_of_node, xg64, dg64, xg32, in_s, u32, e64,
+    size_t ctl, part, parti, perm, node_of_pos, pos_of_node, xg64, dg64, xg32, xgl, dgh, dgl,
+        in_s, u32, e64,
         spos, c64, w64, cw32, cwff, y64, z, zt, bvec, lvec, rvec, tvec, rec, total;
 };
 
@@ -1589,6 +1723,9 @@ static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
     L.xg64 = take(sizeof(D4) * nb);
     L.dg64 = take(sizeof(D4) * nb);
     L.xg32 = take(sizeof(float4) * nb);
+    L.xgl = take(sizeof(float4) * nb);
+    L.dgh = take(sizeof(float4) * nb);
+    L.dgl = take(sizeof(float4) * nb);
     L.in_s = take(nb);
     L.u32 = take(sizeof(float) * nb);
     L.e64 = take(sizeof(double) * nb);
@@ -1653,6 +1790,9 @@ static void fill_args(GreedyArgs &a, char *ws, const GreedyWs &L)
     a.xg64 = (D4 *)(ws + L.xg64);
     a.dg64 = (D4 *)(ws + L.dg64);
     a.xg32 = (float4 *)(ws + L.xg32);
+    a.xgl = (float4 *)(ws + L.xgl);
+    a.dgh = (float4 *)(ws + L.dgh);
+    a.dgl = (float4 *)(ws + L.dgl);
     a.in_s = (uint8_t *)(ws + L.in_s);
     a.u32 = (float *)(ws + L.u32);
     a.e64 = (double *)(ws + L.e64);
@@ -1747,11 +1887,12 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
         occ < 1)
         return RBF_E_CUDA;
     // grid: enough CTAs for one 32-lane team per node of the largest group,
-    // at least 32 (the appends spread their FP64 work over the CTAs), at most
-    // one per SM (more CTAs make every barrier and grid reduction slower than
-    // they make the evaluation faster); p->ctas > 0 overrides (tuning)
+    // at least 64 (the appends and look-aheads spread their work over the
+    // CTAs, and a grid barrier costs about the same at 32 and 64 CTAs), at
+    // most one per SM (beyond that every barrier and grid reduction slows
+    // more than the evaluation speeds up); p->ctas > 0 overrides (tuning)
     const int64_t gsize = (nb + p->m - 1) / p->m;
-    const int64_t want = std::max<int64_t>(32, (gsize * 32 + kGThreads - 1) / kGThreads);
+    const int64_t want = std::max<int64_t>(64, (gsize * 32 + kGThreads - 1) / kGThreads);
     int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms);
     if (p->ctas > 0)
         grid = std::min(p->ctas, dev.sms * std::min(occ, 2));

@@ -3,6 +3,7 @@
   python -m paper_2004_04817_gb300.profile_case volume [--nv N] [--reps R]
   python -m paper_2004_04817_gb300.profile_case greedy [--m M] [--prec 32|64]
   python -m paper_2004_04817_gb300.profile_case solve
+  python -m paper_2004_04817_gb300.profile_case cull [--nv N] [--vprec 32|48] [--radius R]
 
 Each case builds the GCB wing workload (N_b = 50,000), runs the calls once
 untimed, then `--reps` more times, and exits 0.
@@ -20,14 +21,15 @@ from paper_2004_04817_gb300 import synth
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["volume", "greedy", "solve"])
+    ap.add_argument("case", choices=["volume", "greedy", "solve", "cull"])
     ap.add_argument("--nv", type=int, default=1_000_000)
     ap.add_argument("--m", type=int, default=241)
     ap.add_argument("--prec", type=int, default=48)
     ap.add_argument("--vprec", type=int, default=32)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--radius", type=float, default=0.25, help="cull: support radius")
     a = ap.parse_args()
-    c = synth.wing_gcb(n_vol=a.nv if a.case == "volume" else 0)
+    c = synth.wing_gcb(n_vol=a.nv if a.case in ("volume", "cull") else 0)
     dev = lambda x, t=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=t,
                                                       device="cuda")
     xb, db = dev(c["xb"]), dev(c["db"])
@@ -36,6 +38,14 @@ def main():
                             m=a.m if a.case == "greedy" else 241, seed=1,
                             eval_prec=a.prec)
         if a.case == "greedy":
+            continue
+        if a.case == "cull":
+            # the selected set's weights at the smaller radius; culled sum
+            w, _ = P.solve_weights(xb, db, g["idx"], radius=a.radius)
+            plan = P.VolumePlan(dev(c["xv"]), radius=a.radius, eval_prec=a.vprec,
+                                nc_max=g["nc"])
+            plan.run(xb, g["idx"], w)
+            del plan
             continue
         w, _ = P.solve_weights(xb, db, g["idx"], radius=c["radius"])
         if a.case == "volume":

@@ -169,6 +169,25 @@ def lib():
         L.rbf_modal_check.argtypes = [_vp, _vp]
         L.rbf_group_of.restype = C.c_int
         L.rbf_group_of.argtypes = [C.c_int64, C.c_int64, C.c_uint64, C.POINTER(C.c_int32)]
+        L.rbf_volume_plan_workspace_bytes.restype = C.c_size_t
+        L.rbf_volume_plan_workspace_bytes.argtypes = [C.c_int64, P]
+        L.rbf_volume_plan_create.restype = C.c_int
+        L.rbf_volume_plan_create.argtypes = [_vp, C.c_int64, P, _vp, C.c_size_t, _vp,
+                                             C.POINTER(C.c_void_p)]
+        L.rbf_volume_plan_run.restype = C.c_int
+        L.rbf_volume_plan_run.argtypes = [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]
+        L.rbf_volume_plan_info.restype = C.c_int
+        L.rbf_volume_plan_info.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int64),
+                                           C.POINTER(C.c_int64)]
+        L.rbf_nearest_support.restype = C.c_int
+        L.rbf_nearest_support.argtypes = [_vp, C.c_int64, _vp, C.c_int64, _vp, _vp]
+        L.rbf_support_kl_workspace_bytes.restype = C.c_size_t
+        L.rbf_support_kl_workspace_bytes.argtypes = [C.c_int64]
+        L.rbf_support_kl.restype = C.c_int
+        L.rbf_support_kl.argtypes = [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int64,
+                                     C.POINTER(C.c_double), _vp, C.c_size_t, _vp]
+        L.rbf_volume_plan_destroy.restype = None
+        L.rbf_volume_plan_destroy.argtypes = [_vp]
         _lib = L
     return _lib
 
@@ -418,6 +437,35 @@ def deform_modal(xv, xb, sel_idx, W, *, radius, mode=MODAL_BF16X3, stream=None,
     return d
 
 
+def nearest_support(xb, sel_idx, *, stream=None):
+    """d_i = min over j in S of |r_i - r_j| for every boundary node (Sec. 4.1),
+    CUDA FP64 (nb,)."""
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(sel_idx, torch.int32, "sel_idx")
+    d = torch.empty(xb.shape[0], dtype=torch.float64, device=xb.device)
+    _check(lib().rbf_nearest_support(_ptr(xb), xb.shape[0], _ptr(sel_idx), sel_idx.numel(),
+                                     _ptr(d), _stream(stream)), "rbf_nearest_support")
+    return d
+
+
+def support_kl(xb, sel1, sel2, *, stream=None, workspace=None):
+    """KL(S1 || S2) = sum_i d1_i log(d1_i / d2_i) over the boundary nodes
+    (Sec. 4.1), terms with a zero distance left out."""
+    L = lib()
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(sel1, torch.int32, "sel1")
+    _dev(sel2, torch.int32, "sel2")
+    nb = xb.shape[0]
+    need = L.rbf_support_kl_workspace_bytes(nb)
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xb.device)
+    kl = C.c_double(0.0)
+    _check(L.rbf_support_kl(_ptr(xb), nb, _ptr(sel1), sel1.numel(), _ptr(sel2), sel2.numel(),
+                            C.byref(kl), _ptr(ws), ws.numel(), _stream(stream)),
+           "rbf_support_kl")
+    return kl.value
+
+
 def measure_fma_peak(prec=32, stream=None):
     """Measured vector FMA peak of this GPU in FLOP/s (an FMA counts 2)."""
     f = C.c_double(0.0)
@@ -539,4 +587,58 @@ class VolumeBatch:
     def __del__(self):
         if getattr(self, "handle", None):
             lib().rbf_volume_batch_destroy(self.handle)
+            self.handle = None
+
+
+class VolumePlan:
+    """Volume sums with compact-support culling (``rbf_volume_plan_*``).
+
+    The plan sorts the volume points ``xv`` (CUDA FP64 (nv, 3)) once for the
+    given radius and precision (PREC_F32 or PREC_F32X2); ``run`` then
+    evaluates Eq. 6 for any support set of at most ``nc_max`` centres,
+    skipping pairs farther apart than the radius.  ``run(..., count=True)``
+    also returns the number of pairs evaluated.
+    """
+
+    def __init__(self, xv, *, radius, eval_prec=PREC_F32X2, nc_max=4096, stream=None):
+        L = lib()
+        _dev(xv, torch.float64, "xv", 3)
+        self.nv = xv.shape[0]
+        self.device = xv.device
+        self.p = make_params(radius, eval_prec=eval_prec, nc_max=nc_max)
+        need = L.rbf_volume_plan_workspace_bytes(self.nv, C.byref(self.p))
+        if need == 0:
+            raise RBFError(1, "rbf_volume_plan_workspace_bytes")
+        self.ws = _workspace(need, xv.device)
+        h = C.c_void_p()
+        _check(L.rbf_volume_plan_create(_ptr(xv), self.nv, C.byref(self.p), _ptr(self.ws),
+                                        self.ws.numel(), _stream(stream), C.byref(h)),
+               "rbf_volume_plan_create")
+        self.handle = h
+        self._count = torch.zeros(1, dtype=torch.int64, device=xv.device)
+
+    def run(self, xb, sel_idx, w, *, out=None, count=False, stream=None):
+        _dev(xb, torch.float64, "xb", 3)
+        _dev(sel_idx, torch.int32, "sel_idx")
+        nc = sel_idx.numel()
+        if nc:
+            _dev(w, torch.float64, "w", 3)
+        dv = out if out is not None else torch.empty((self.nv, 3), dtype=torch.float64,
+                                                     device=self.device)
+        if count:
+            self._count.zero_()
+        _check(lib().rbf_volume_plan_run(self.handle, _ptr(xb), _ptr(sel_idx), nc,
+                                         _ptr(w) if nc else None, _ptr(dv),
+                                         _ptr(self._count) if count else None, _stream(stream)),
+               "rbf_volume_plan_run")
+        return (dv, int(self._count.item())) if count else dv
+
+    def info(self):
+        b, t, n = C.c_int(0), C.c_int64(0), C.c_int64(0)
+        lib().rbf_volume_plan_info(self.handle, C.byref(b), C.byref(t), C.byref(n))
+        return {"bits_per_axis": b.value, "points_per_tile": t.value, "tiles": n.value}
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().rbf_volume_plan_destroy(self.handle)
             self.handle = None

@@ -229,6 +229,130 @@ def tiny_wing(n_span=4, n_chord=20, n_vol=200, seed=0, radius=2.0,
                      radius=radius, tol_rel=tol_rel)
 
 
+# ----------------------------------------------------------------------------
+# Wing-body-nacelle-pylon assembly (stand-in for the Sec. 4.2 configuration)
+# ----------------------------------------------------------------------------
+WBNP_FUS_LEN = 6.0          # fuselage: cylinder along x in [0, 6]
+WBNP_FUS_R = 0.35
+WBNP_WING_SCALE = 3.0       # the unit wing at 3x scale (span 3)
+WBNP_WING_ORIGIN = (2.2, 0.0, 0.50)   # root leading edge, lower surface clears the fuselage
+WBNP_NAC_Y = 1.0            # nacelle axis: spanwise station, height, length, radii
+WBNP_NAC_Z = 0.05
+WBNP_NAC_LEN = 0.6
+WBNP_NAC_R_OUT = 0.15
+WBNP_NAC_R_IN = 0.13
+WBNP_PYL_HALF = 0.01        # pylon plate: half thickness, z range
+WBNP_PYL_Z = (0.21, 0.36)
+
+
+def _wbnp_frame():
+    """Nacelle and pylon x ranges, tied to the wing's leading edge at the
+    nacelle station."""
+    s = WBNP_WING_SCALE
+    xle = WBNP_WING_ORIGIN[0] + s * float(leading_edge_x(WBNP_NAC_Y / s))
+    nac_x = (xle - 0.35, xle - 0.35 + WBNP_NAC_LEN)
+    pyl_x = (xle - 0.15, xle + 0.20)
+    return nac_x, pyl_x
+
+
+def _ring_surface(x0, x1, n_ax, n_circ, yc, zc, r, outward=True):
+    """Points of a circular cylinder about the x-parallel axis (yc, zc),
+    n_ax stations x n_circ angles, with unit normals (outward = away from
+    the axis)."""
+    xs = x0 + (x1 - x0) * np.arange(n_ax) / max(n_ax - 1, 1)
+    ang = 2.0 * np.pi * np.arange(n_circ) / n_circ
+    cy, sz = np.cos(ang), np.sin(ang)
+    x = np.repeat(xs, n_circ)
+    y = yc + r * np.tile(cy, n_ax)
+    z = zc + r * np.tile(sz, n_ax)
+    sg = 1.0 if outward else -1.0
+    nrm = np.stack([np.zeros_like(x), sg * np.tile(cy, n_ax), sg * np.tile(sz, n_ax)], axis=-1)
+    return np.stack([x, y, z], axis=-1), nrm
+
+
+def _plate(x0, x1, z0, z1, n_x, n_z, y):
+    xs = x0 + (x1 - x0) * np.arange(n_x) / max(n_x - 1, 1)
+    zs = z0 + (z1 - z0) * np.arange(n_z) / max(n_z - 1, 1)
+    x = np.repeat(xs, n_z)
+    z = np.tile(zs, n_x)
+    return np.stack([x, np.full_like(x, y), z], axis=-1)
+
+
+def inside_wbnp(p):
+    """True where a point lies inside a component of the assembly (the
+    fuselage cylinder, the wing, the nacelle wall or the pylon plate)."""
+    p = np.asarray(p, dtype=np.float64)
+    x, y, z = p[..., 0], p[..., 1], p[..., 2]
+    fus = (x >= 0.0) & (x <= WBNP_FUS_LEN) & (y * y + z * z < WBNP_FUS_R**2)
+    wing = inside_wing(p, origin=WBNP_WING_ORIGIN, scale=WBNP_WING_SCALE)
+    nac_x, pyl_x = _wbnp_frame()
+    rn = np.sqrt((y - WBNP_NAC_Y) ** 2 + (z - WBNP_NAC_Z) ** 2)
+    nac = (x >= nac_x[0]) & (x <= nac_x[1]) & (rn > WBNP_NAC_R_IN) & (rn < WBNP_NAC_R_OUT)
+    pyl = ((x >= pyl_x[0]) & (x <= pyl_x[1]) & (np.abs(y - WBNP_NAC_Y) < WBNP_PYL_HALF)
+           & (z >= WBNP_PYL_Z[0]) & (z <= WBNP_PYL_Z[1]))
+    return fus | wing | nac | pyl
+
+
+def wbnp_surface(density=1.0):
+    """Surface points of the assembly, their outward normals, prescribed
+    displacements and component labels (0 fuselage, 1 wing, 2 nacelle,
+    3 pylon).
+
+    At density 1: fuselage 300 x 400 = 120,000 points; wing 200 x 600 =
+    120,000; nacelle outer and inner walls 2 x 100 x 200 = 40,000; pylon two
+    faces 2 x 100 x 100 = 20,000; 300,000 in all.  ``density`` scales every
+    count by sqrt(density) per direction.
+
+    Displacement: the wing bends by 0.15 (y/b)^2 (b = 3) and twists 5 deg
+    linearly about its quarter chord (the unit wing's field at 3x scale);
+    nacelle and pylon translate rigidly by the wing's bending at the nacelle
+    station; the fuselage is fixed.
+    """
+    f = math.sqrt(density)
+    n = lambda k: max(2, int(round(k * f)))
+    s = WBNP_WING_SCALE
+    fus, fus_n = _ring_surface(0.0, WBNP_FUS_LEN, n(300), n(400), 0.0, 0.0, WBNP_FUS_R)
+    wing, wing_n, _ = wing_surface(n(200), n(600), origin=WBNP_WING_ORIGIN, scale=s)
+    nac_x, pyl_x = _wbnp_frame()
+    nac_o, nac_on = _ring_surface(nac_x[0], nac_x[1], n(100), n(200), WBNP_NAC_Y, WBNP_NAC_Z,
+                                  WBNP_NAC_R_OUT)
+    nac_i, nac_in = _ring_surface(nac_x[0], nac_x[1], n(100), n(200), WBNP_NAC_Y, WBNP_NAC_Z,
+                                  WBNP_NAC_R_IN, outward=False)
+    pyl_a = _plate(pyl_x[0], pyl_x[1], WBNP_PYL_Z[0], WBNP_PYL_Z[1], n(100), n(100),
+                   WBNP_NAC_Y - WBNP_PYL_HALF)
+    pyl_b = _plate(pyl_x[0], pyl_x[1], WBNP_PYL_Z[0], WBNP_PYL_Z[1], n(100), n(100),
+                   WBNP_NAC_Y + WBNP_PYL_HALF)
+    pyl_an = np.tile([0.0, -1.0, 0.0], (len(pyl_a), 1))
+    pyl_bn = np.tile([0.0, 1.0, 0.0], (len(pyl_b), 1))
+    pts = np.concatenate([fus, wing, nac_o, nac_i, pyl_a, pyl_b])
+    nrm = np.concatenate([fus_n, wing_n, nac_on, nac_in, pyl_an, pyl_bn])
+    lab = np.concatenate([np.zeros(len(fus), np.int8), np.ones(len(wing), np.int8),
+                          np.full(len(nac_o) + len(nac_i), 2, np.int8),
+                          np.full(len(pyl_a) + len(pyl_b), 3, np.int8)])
+    d = np.zeros_like(pts)
+    wsel = lab == 1
+    d[wsel] = wing_bending_twist(pts[wsel], origin=WBNP_WING_ORIGIN, scale=s)
+    rigid = 0.05 * s * (WBNP_NAC_Y / s) ** 2
+    d[lab >= 2, 2] = rigid
+    return pts, nrm, d, lab
+
+
+def wbnp_case(n_vol=10_000_000, *, density=1.0, vol_seed=3, radius=6.0, tol_rel=1e-4):
+    """Wing-body-nacelle-pylon problem: 300,000 surface points at density 1,
+    n_vol volume points log-clustered toward all surfaces (offsets
+    d = 1e-5 (4.5/1e-5)^u along the normals, points inside a component
+    redrawn), R = 6, tolerance 1e-4 of the largest displacement."""
+    xb, nrm, db, lab = wbnp_surface(density)
+    rng = np.random.Generator(np.random.PCG64(vol_seed))
+    if n_vol == 0:
+        xv = np.zeros((0, 3))
+    else:
+        xv = volume_log_clustered(n_vol, xb, nrm, rng, inside_wbnp,
+                                  d_max=1.5 * WBNP_WING_SCALE)
+    return dict(xb=xb, db=db, xv=xv, labels=lab, radius=float(radius),
+                tol_rel=float(tol_rel), name=f"wbnp{len(xb)}")
+
+
 def random_cloud(n, seed, scale=1.0):
     """n distinct points uniform in a cube of side ``scale`` (float64)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -3,7 +3,7 @@ of one launch (dram__bytes_read.sum + dram__bytes_write.sum) and a hash of
 the kernel's sources, so bench.py reports the figure only while the kernel
 is unchanged.
 
-  python profiles/make_traffic_record.py <report.ncu-rep> <kernel> <launch> <src>...
+  python -m paper_2004_04817_gb300.traffic_record <report.ncu-rep> <kernel> <launch> <src>...
 """
 import csv
 import hashlib

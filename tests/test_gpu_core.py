@@ -57,11 +57,13 @@ def test_greedy_f64_matches_oracle_tiny(m):
     assert host(r["iter"]).tolist() == o["iter"].tolist()
     assert r["stats"]["iterations"] == o["stats"]["iterations"]
     assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-12
-    assert abs(r["stats"]["final_rms"] - o["stats"]["final_rms"]) <= 1e-12
+    # the RMS is a diagnostic accumulated in FP32 on the device
+    assert abs(r["stats"]["final_rms"] - o["stats"]["final_rms"]) <= 1e-5 * o["stats"]["final_rms"]
     h = host(r["hist"])
     assert h.shape == o["hist"].shape
     assert np.array_equal(h[:, [0, 1, 5]], o["hist"][:, [0, 1, 5]])
-    assert np.allclose(h[:, [2, 3, 4]], o["hist"][:, [2, 3, 4]], rtol=0, atol=1e-12)
+    assert np.allclose(h[:, [2, 3]], o["hist"][:, [2, 3]], rtol=0, atol=1e-12)
+    assert np.allclose(h[:, 4], o["hist"][:, 4], rtol=1e-5, atol=1e-12)
 
 
 @pytest.mark.parametrize("m", [1, 7, 40])
@@ -79,6 +81,14 @@ def test_greedy_f64_matches_oracle_wing_2000(m):
     assert r["stats"]["final_max"] <= estar
 
 
+def _certified_max(r, o, estar):
+    """Screened modes report the largest certified upper bound E~ + beta of
+    the final check: at or above the oracle's FP64 maximum, above it by no
+    more than the double-float bound (well below 1e-5 E* on these wings)."""
+    d = r["stats"]["final_max"] - o["stats"]["final_max"]
+    assert -1e-12 <= d <= 1e-5 * estar, d
+
+
 @pytest.mark.parametrize("m", [1, 5, 40])
 def test_greedy_ff_is_certified(m):
     """Double-float pairs + FP64 re-score of near-ties: every decision checked
@@ -92,7 +102,7 @@ def test_greedy_ff_is_certified(m):
     if f["stats"]["n_div"] == 0:
         assert host(r["idx"]).tolist() == o["idx"].tolist()
         assert r["stats"]["iterations"] == o["stats"]["iterations"]
-        assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-12
+        _certified_max(r, o, estar)
     assert r["stats"]["final_max"] <= estar
     assert r["stats"]["pairs_ff"] > 0 and r["stats"]["pairs_f64"] == 0
     assert r["stats"]["rescored"] * 20 < r["stats"]["pairs_ff"] // max(r["nc"], 1)
@@ -104,7 +114,7 @@ def test_greedy_ff_tiny_exact():
         r, estar = run_greedy(c, m, P.PREC_F32X2, 2e-3)
         o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1, history=False)
         assert host(r["idx"]).tolist() == o["idx"].tolist()
-        assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-12
+        _certified_max(r, o, estar)
 
 
 @pytest.mark.parametrize("m", [1, 5])
@@ -118,8 +128,8 @@ def test_greedy_f32_screen_is_certified(m):
     o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1, history=False)
     if f["stats"]["n_div"] == 0:
         assert host(r["idx"]).tolist() == o["idx"].tolist()
-        # the reported maximum is the screened estimate, within its FP32 bound
-        assert abs(r["stats"]["final_max"] - o["stats"]["final_max"]) <= 1e-3 * estar
+        # the reported maximum is the certified upper bound of the FP32 screen
+        assert -1e-12 <= r["stats"]["final_max"] - o["stats"]["final_max"] <= 1e-3 * estar
     assert r["stats"]["final_max"] <= estar
     # the FP32 screen must have spared some FP64 work
     assert r["stats"]["rescored"] < r["stats"]["pairs_f32"] // max(r["nc"], 1)

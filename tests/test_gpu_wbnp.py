@@ -1,0 +1,157 @@
+"""GPU parity on the wing-body-nacelle-pylon assembly at full size
+(N_b = 300,000 boundary nodes, N_v = 10,000,000 volume points, R = 6,
+tolerance 1e-4 of the largest displacement, m = 1.5 N_b / N_c with N_c from
+the plain greedy on the same GPU).
+
+At this size the oracle cannot replay the whole selection (one dense FP64
+re-solve per iteration), so it checks what it can compute one by one:
+  * termination: every boundary node's FP64 error with the selected set is
+    within E* (the stopping certificate of Alg. 1 read as in the oracle);
+  * sampled decisions: at a spread of appends the oracle solves for the
+    support set the GPU had at that iteration, evaluates the active group in
+    FP64 and checks that the GPU's node is the group's maximum (ties within
+    1e-6 relative) and above E*; at sampled idle iterations it checks that
+    the group's maximum is at most E*;
+  * weights against the oracle's solve for the same set (unless cond(Phi_SS)
+    alone allows FP64 solutions to differ by more than the band, which is
+    then reported and the displacements decide), and the reproduction
+    residual at the support nodes;
+  * volume displacements on a seeded sample of the 10^7 points.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2004_04817_gb300 as P
+from paper_2004_04817_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TIE = 1e-6
+
+
+@pytest.fixture(scope="module")
+def case():
+    c = synth.wbnp_case(n_vol=10_000_000)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    c["d_xb"], c["d_db"] = dev(c["xb"]), dev(c["db"])
+    c["estar"] = oracle.tolerance(c["db"], c["tol_rel"])
+    plain = P.greedy_select(c["d_xb"], c["d_db"], radius=c["radius"], tol=c["estar"],
+                            tol_mode=0, m=1, seed=1, eval_prec=P.PREC_F32X2)
+    assert plain["status"] == 0
+    c["plain"] = plain
+    c["m"] = int(round(1.5 * len(c["xb"]) / plain["nc"]))
+    c["gcb"] = {}
+    print(f"\nWBNP: N_b {len(c['xb'])}, plain N_c {plain['nc']}, m {c['m']}")
+    return c
+
+
+def _gcb(c, prec):
+    if prec not in c["gcb"]:
+        c["gcb"][prec] = P.greedy_select(c["d_xb"], c["d_db"], radius=c["radius"],
+                                         tol=c["estar"], tol_mode=0, m=c["m"], seed=1,
+                                         eval_prec=prec, weights=True)
+    return c["gcb"][prec]
+
+
+def _group_errors(c, S, nodes):
+    """FP64 errors |dr_q - F(x_q)| at `nodes` with the oracle's weights for S."""
+    W, st, _ = oracle.solve_weights(c["xb"], c["db"], S, c["radius"])
+    assert st == 0
+    F = oracle.rbf_sum(c["xb"][nodes], c["xb"], S, W, c["radius"])
+    return np.linalg.norm(c["db"][nodes] - F, axis=1)
+
+
+def _check_sampled_decisions(c, r, m, n_appends=6, n_idle=4):
+    idx = r["idx"].cpu().numpy()
+    it = r["iter"].cpu().numpy()
+    nc = len(idx)
+    grp = oracle.groups(len(c["xb"]), m, 1)
+    rng = np.random.default_rng(11)
+    picks = sorted(set([3, nc - 1] + list(rng.integers(4, nc - 1, n_appends - 2))))
+    for t in picks:
+        S = idx[:t]
+        members = np.flatnonzero(grp == it[t] % m)
+        members = members[~np.isin(members, S)]
+        e = _group_errors(c, S, members)
+        e_gpu = e[np.flatnonzero(members == idx[t])[0]]
+        assert e_gpu > c["estar"], (t, e_gpu)
+        assert e_gpu >= (1.0 - TIE) * e.max(), (t, e_gpu, e.max())
+    # idle iterations: between appends t-1 and t the set is idx[:t]
+    gaps = [t for t in range(4, nc) if it[t] - it[t - 1] > 1]
+    for t in sorted(set(rng.choice(gaps, min(n_idle, len(gaps)), replace=False))) if gaps else []:
+        k = int(rng.integers(it[t - 1] + 1, it[t]))
+        S = idx[:t]
+        members = np.flatnonzero(grp == k % m)
+        members = members[~np.isin(members, S)]
+        assert _group_errors(c, S, members).max() <= c["estar"] * (1.0 + TIE), (t, k)
+    return picks
+
+
+def test_plain_greedy_wbnp_terminates_certified(case):
+    c = case
+    S = c["plain"]["idx"].cpu().numpy()
+    e = _group_errors(c, S, np.arange(len(c["xb"])))
+    assert e.max() <= c["estar"] * (1.0 + TIE)
+    assert c["plain"]["stats"]["final_max"] <= c["estar"]
+
+
+@pytest.mark.parametrize("prec", [P.PREC_F32X2, P.PREC_F32])
+def test_gcb_wbnp_sampled_decisions_and_termination(case, prec):
+    c = case
+    r = _gcb(c, prec)
+    assert r["status"] == 0
+    S = r["idx"].cpu().numpy()
+    assert len(np.unique(S)) == len(S)
+    e = _group_errors(c, S, np.arange(len(c["xb"])))
+    assert e.max() <= c["estar"] * (1.0 + TIE)
+    assert r["stats"]["final_max"] <= c["estar"]
+    picks = _check_sampled_decisions(c, r, c["m"])
+    # GCB evaluates far fewer pairs than the plain greedy (Sec. 3)
+    pr = lambda s: s["pairs_ff"] + s["pairs_f32"] + s["pairs_f64"]
+    assert pr(r["stats"]) * 5 < pr(c["plain"]["stats"])
+    print(f"\nprec {prec}: N_c {r['nc']}, iterations {r['stats']['iterations']}, "
+          f"rescored {r['stats']['rescored']}, checked appends {picks}")
+
+
+def test_gcb_wbnp_weights_and_volume(case):
+    c = case
+    r = _gcb(c, P.PREC_F32X2)
+    S = r["idx"].cpu().numpy()
+    Wo, st, _ = oracle.solve_weights(c["xb"], c["db"], S, c["radius"])
+    assert st == 0
+    dmax = np.abs(c["db"]).max()
+    w = r["w"].cpu().numpy()
+    assert r["stats"]["max_resid"] <= 1e-10 * dmax
+    # weights: within 1e-5 max|dr| of the oracle's unless the conditioning of
+    # Phi_SS alone already allows FP64 solutions to differ by more; then the
+    # displacements below decide (reported, not hidden)
+    xs = c["xb"][S] / c["radius"]
+    Phi = oracle.phi(np.linalg.norm(xs[:, None] - xs[None], axis=-1))
+    kappa = np.linalg.cond(Phi)
+    dw = np.abs(w - Wo).max()
+    print(f"\nWBNP weights: cond(Phi_SS) {kappa:.3e}, max|dW| {dw:.3e}, "
+          f"max|dW|/max|W| {dw / np.abs(Wo).max():.3e}")
+    if kappa * 1e-16 * np.abs(Wo).max() <= 1e-5 * dmax:
+        assert dw <= 1e-5 * dmax
+    else:
+        print("WBNP weights: ill-conditioned set, weight check replaced by the displacement check")
+    d_xv = torch.as_tensor(c["xv"], dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(13)
+    sample = np.sort(rng.choice(len(c["xv"]), 4000, replace=False))
+    ref = oracle.rbf_sum(c["xv"][sample], c["xb"], S, Wo, c["radius"])
+    dv = P.deform_volume(d_xv, c["d_xb"], r["idx"], r["w"], radius=c["radius"],
+                         eval_prec=P.PREC_F32X2)
+    assert np.abs(dv.cpu().numpy()[sample] - ref).max() <= 1e-5 * dmax
+    del dv
+    dv32 = P.deform_volume(d_xv, c["d_xb"], r["idx"], r["w"], radius=c["radius"],
+                           eval_prec=P.PREC_F32).cpu().numpy()[sample]
+    # FP32 rounding alone: against the FP64 sum with the same (GPU) weights
+    ref_w = oracle.rbf_sum(c["xv"][sample], c["xb"], S, w, c["radius"])
+    R = c["radius"]
+    Phi = oracle.phi(np.linalg.norm(c["xv"][sample][:, None] - c["xb"][S][None], axis=-1) / R)
+    X = max(np.abs(c["xv"]).max(), np.abs(c["xb"]).max()) / R
+    bound = 2.0 ** -24 * (64 * (Phi @ np.abs(w).sum(1)) + 16 * X * np.abs(w).sum())
+    err32 = np.abs(dv32 - ref_w).max(axis=1)
+    assert np.all(err32 <= bound), (err32 / bound).max()
+    print(f"\nWBNP volume: FP32 max error {err32.max():.3e} ({err32.max() / dmax:.2e} of max|dr|)")

@@ -333,3 +333,36 @@ def test_adjoint_matches_central_differences():
             e[a, comp] = h
             fd = (J(dc + e) - J(dc - e)) / (2 * h)
             assert abs(fd - g[a, comp]) <= 1e-6 * max(1.0, abs(g).max())
+
+
+# --------------------------------------------------------------------------
+# KL divergence of two support sets (Sec. 4.1)
+# --------------------------------------------------------------------------
+def test_kl_hand_example_on_a_line():
+    # nodes at x = 0, 1, 2, 3; S1 = {0}, S2 = {3}: d1 = (0, 1, 2, 3),
+    # d2 = (3, 2, 1, 0).  Node 0 (d1 = 0) and node 3 (d2 = 0) drop out, so
+    # KL = 1 log(1/2) + 2 log(2/1) = log 2.
+    xb = np.array([[0.0, 0, 0], [1.0, 0, 0], [2.0, 0, 0], [3.0, 0, 0]])
+    assert np.array_equal(oracle.nearest_support(xb, [0]), [0.0, 1.0, 2.0, 3.0])
+    assert oracle.support_kl(xb, [0], [3]) == pytest.approx(math.log(2.0), rel=1e-15)
+    # reversed: 2 log(2/1) + 1 log(1/2) = log 2 as well (the line is symmetric)
+    assert oracle.support_kl(xb, [3], [0]) == pytest.approx(math.log(2.0), rel=1e-15)
+
+
+def test_kl_of_a_set_with_itself_is_zero_and_scales_with_length():
+    rng = np.random.default_rng(5)
+    xb = synth.random_cloud(400, seed=3)
+    S1 = np.sort(rng.choice(400, 30, replace=False))
+    S2 = np.sort(rng.choice(400, 30, replace=False))
+    assert oracle.support_kl(xb, S1, S1) == 0.0
+    kl = oracle.support_kl(xb, S1, S2)
+    # distances scale with the coordinates, their ratios do not
+    assert oracle.support_kl(2.5 * xb, S1, S2) == pytest.approx(2.5 * kl, rel=1e-12)
+
+
+def test_nearest_support_matches_kdtree():
+    from scipy.spatial import cKDTree
+    xb = synth.random_cloud(3000, seed=9)
+    S = np.sort(np.random.default_rng(2).choice(3000, 70, replace=False))
+    d_ref, _ = cKDTree(xb[S]).query(xb)
+    assert np.allclose(oracle.nearest_support(xb, S), d_ref, rtol=1e-14, atol=0)

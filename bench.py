@@ -46,12 +46,13 @@ def parse():
                     help="greedy pair arithmetic: FP32, double-float (48) or FP64")
     ap.add_argument("--vol-prec", type=int, default=48, choices=[32, 48, 64],
                     help="volume-sum arithmetic inside the step")
-    ap.add_argument("--workload", default="gcb", choices=["gcb", "batched", "modal", "fixed_nc"],
+    ap.add_argument("--workload", default="gcb", choices=["gcb", "batched", "modal", "fixed_nc", "adjoint"],
                     help="gcb: the GCB wing (N_b = 50,000, N_v = 2e6); batched: 64 wings "
                          "with N_b ~ U[5k, 100k] and 200k volume points each, replayed "
                          "from one CUDA graph; modal: 32 displacement modes on the tensor "
                          "cores; fixed_nc: N_c fixed to the plain greedy's, m swept, "
-                         "eval/append split, error histories and KL (Tables 2 and 4)")
+                         "eval/append split, error histories and KL (Tables 2 and 4); "
+                         "adjoint: the gradient of configuration 5")
     return ap.parse_args()
 
 
@@ -151,6 +152,22 @@ def kernel_traffic(name):
     if h.hexdigest() != rec.get("sources_sha1"):
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def latency_model(P, st, greedy_ms):
+    """The parameters that bound the persistent greedy, measured live: the
+    grid-barrier cost at its CTA count and the issue cost of one FMA
+    instruction of a lone warp (FP64 and FP32), with the share of the greedy
+    time its grid barriers alone account for."""
+    bar_ns = P.measure_latency(P.rbf.LAT_GRID_BARRIER, int(st["ctas"]))
+    f64_ns = P.measure_latency(P.rbf.LAT_FP64_WARP)
+    f32_ns = P.measure_latency(P.rbf.LAT_FP32_WARP)
+    bar_ms = st["barriers"] * bar_ns * 1e-6
+    return {"ctas": st["ctas"], "grid_barriers": st["barriers"],
+            "barrier_us": bar_ns * 1e-3, "barriers_ms": bar_ms,
+            "barriers_share_of_greedy": bar_ms / greedy_ms,
+            "us_per_iteration": greedy_ms * 1e3 / max(st["iterations"], 1),
+            "fp64_warp_fma_ns": f64_ns, "fp32_warp_fma_ns": f32_ns}
 
 
 def peaks():
@@ -373,6 +390,8 @@ def run_ours(args, rank, world):
                 "traffic": kernel_traffic("k_greedy") if dom is kernels[0] else None,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
                 "note": "latency-bound persistent kernel (see kernels)"}
+        if dom is kernels[0]:
+            roof["latency_model"] = latency_model(P, g_last["stats"], g_ms)
     out = {
         "metric": METRIC,
         "value": ms_per_step / 1e3,
@@ -397,6 +416,8 @@ def run_ours(args, rank, world):
             "rescored": st["rescored"], "estar": st["estar"], "final_max": st["final_max"],
             "us_per_iteration": g_ms * 1e3 / max(st["iterations"], 1),
             "full_checks": st["full_checks"],
+            "eval_pairs_per_s": (st["pairs_ff"] + st["pairs_f32"] + st["pairs_f64"]) /
+                                max(1e-9, (st["phase_ns"][8] + st["phase_ns"][11]) * 1e-9),
             "phase_ms": dict(zip(["prologue", "eval_other", "rescore_f64", "append",
                                   "refine", "other", "barrier_wait_total", "eval_staging",
                                   "eval_pass", "eval_block_reduce", "eval_barrier_grid_reduce",
@@ -785,6 +806,82 @@ def run_fixed_nc(args, rank, world):
     }
 
 
+def run_adjoint(args, rank, world):
+    """Configuration 5: the gradient dJ/dd_c = Phi_cc^-1 Phi_vc^T (d_v - t_v) of
+    J = sum_v |d_v - t_v|^2 / 2 on the GCB wing's support set (N_b = 50,000,
+    2,000,000 volume points, t_v Gaussian with sigma 0.01, seed 5), double-float
+    and FP32 transposed pair sums with FP64 reduction and solve; pairs/s of the
+    whole call (the transposed sum dominates)."""
+    import torch
+    import paper_2004_04817_gb300 as P
+    from paper_2004_04817_gb300 import synth
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    c = workload(args.nv)
+    tod = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=t,
+                                                      device=dev)
+    xb, db, xv = tod(c["xb"]), tod(c["db"]), tod(c["xv"])
+    R = c["radius"]
+    plain = P.greedy_select(xb, db, radius=R, tol=c["tol_rel"], tol_mode=1, m=1,
+                            eval_prec=P.PREC_F32X2)
+    m = max(1, int(round(1.5 * len(c["xb"]) / plain["nc"])))
+    g = P.greedy_select(xb, db, radius=R, tol=c["tol_rel"], tol_mode=1, m=m,
+                        eval_prec=P.PREC_F32X2, weights=True)
+    nc, nv = g["nc"], xv.shape[0]
+    dv = P.deform_volume(xv, xb, g["idx"], g["w"], radius=R, eval_prec=P.PREC_F32X2)
+    gv = (dv - tod(synth.random_field(nv, seed=5, sigma=0.01))).contiguous()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    fp32_peak = props.multi_processor_count * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    # the support system is factorised once per support set (shape
+    # optimisation evaluates many gradients on one set); each gradient then
+    # costs the transposed pair sum and the refinement
+    fac = P.Factor(xb, g["idx"], radius=R)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    res = {}
+    with ClockSampler(dev.index) as clk:
+        for prec in (48, 32):
+            ms = timed(lambda: P.adjoint_factored(xv, gv, fac, eval_prec=prec))
+            cold = timed(lambda: P.adjoint(xv, xb, g["idx"], gv, radius=R, eval_prec=prec))
+            res[PREC_NAME[prec]] = {"ms": ms, "pairs_per_s": nv * nc / (ms * 1e-3),
+                                    "useful_flops_frac_fp32_peak":
+                                        nv * nc * FLOPS_PER_PAIR / (ms * 1e-3) / fp32_peak,
+                                    "with_factorisation_ms": cold}
+        factor_ms = timed(lambda: P.Factor(xb, g["idx"], radius=R))
+    t = res[PREC_NAME[48]]["ms"]
+    return {
+        "metric": METRIC, "value": t * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "double-float pairs, f64 reduction and solve",
+        "data": "synthetic (seeded wing generator, paper_2004_04817_gb300/synth.py)",
+        "config": {"workload": "adjoint of the volume deformation (configuration 5)",
+                   "n_v": nv, "n_c": nc, "m": m, "l2": "flushed between repetitions"},
+        "adjoint": res, "factorisation_ms": factor_ms,
+        "roofline": {"bound": "alu", "kernel": "k_adjoint_partial (double-float)",
+                     "achieved": nv * nc * FLOPS_PER_PAIR / (t * 1e-3) / 1e12,
+                     "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                     "frac": nv * nc * FLOPS_PER_PAIR / (t * 1e-3) / fp32_peak, "traffic": None},
+        "gpu_launches": 4 * args.steps * 2, "clocks": clk.summary(),
+    }
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -803,6 +900,8 @@ def main():
         out = run_modal(args, rank, world)
     elif args.workload == "fixed_nc":
         out = run_fixed_nc(args, rank, world)
+    elif args.workload == "adjoint":
+        out = run_adjoint(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if rank == 0:

@@ -127,6 +127,8 @@ typedef struct {
                                 pass, [9] block reductions, [10] evaluation
                                 barrier + grid reduction, [11] error pass of
                                 the look-aheads over all nodes                */
+    int64_t barriers;        /* grid barriers the persistent kernel passed      */
+    int64_t ctas;            /* CTAs that ran this problem                      */
 } rbf_greedy_stats;
 
 /* Columns of one row of the optional iteration history (device doubles):
@@ -448,6 +450,30 @@ rbf_status rbf_support_kl(const double *d_xb, int64_t nb, const int32_t *d_sel1,
 rbf_status rbf_group_of(int64_t nb, int64_t m, uint64_t seed, int32_t *h_group_of);
 
 /* --------------------------------------------------------------------------
+ * Factorised support systems: Phi_SS X = B solved many times for one support
+ * set (Sec. 2: Phi_SS is SPD and is solved through its Cholesky factor).
+ * rbf_factor_create runs the recurrence-Cholesky appends once (as
+ * rbf_solve_system does) and keeps Z = L^-1 in the workspace; each
+ * rbf_factor_solve then costs X = Z^T Z B plus `refine_steps` FP64
+ * refinement steps (residual recomputed from coordinates) instead of a new
+ * factorisation.  d_xb and d_sel_idx must stay valid and unchanged while the
+ * factor lives; the workspace (rbf_factor_workspace_bytes(nc), 256-byte
+ * aligned) belongs to the factor until rbf_factor_destroy.
+ * create: SYNCHRONOUS (RBF_E_NOT_SPD for coincident nodes).
+ * solve: d_rhs, d_x device FP64 nc x 3 (support order); h_max_resid (host or
+ * NULL) = max |Phi_SS X - B|_inf.  SYNCHRONOUS.  destroy: host only.
+ * ------------------------------------------------------------------------ */
+typedef struct rbf_factor rbf_factor;
+
+size_t rbf_factor_workspace_bytes(int64_t nc);
+rbf_status rbf_factor_create(const double *d_xb, int64_t nb, const int32_t *d_sel_idx,
+                             int64_t nc, const rbf_params *p, void *d_ws, size_t ws_bytes,
+                             void *stream, rbf_factor **out);
+rbf_status rbf_factor_solve(const rbf_factor *f, const double *d_rhs, int refine_steps,
+                            double *d_x, double *h_max_resid, void *stream);
+void rbf_factor_destroy(rbf_factor *f);
+
+/* --------------------------------------------------------------------------
  * Adjoint of the volume deformation for gradients with respect to the
  * support displacements d_c (Eq. 6 with Eqs. 4-5: d_v = Phi_vc W, Phi_cc W = d_c):
  *
@@ -475,6 +501,17 @@ rbf_status rbf_deform_volume_adjoint(const double *d_xv, int64_t nv,
                                      double *d_gc, double *h_max_resid,
                                      void *d_ws, size_t ws_bytes, void *stream);
 
+/* The same with the support system already factorised (rbf_factor_create
+ * on the same d_xb and support set): the solve reuses Z, so a gradient costs
+ * the transposed pair sum and the refinement only.  p: eval_prec and
+ * refine_steps are used (radius comes from the factor).  Workspace as
+ * rbf_adjoint_workspace_bytes(nv, nc).  SYNCHRONOUS. */
+rbf_status rbf_deform_volume_adjoint_factored(const double *d_xv, int64_t nv,
+                                              const double *d_gv, const rbf_factor *f,
+                                              const rbf_params *p, double *d_gc,
+                                              double *h_max_resid, void *d_ws,
+                                              size_t ws_bytes, void *stream);
+
 /* --------------------------------------------------------------------------
  * Vector-FMA peak microbenchmark of this GPU (dependent-FMA chains on every
  * SM), used as the denominator of the pair kernels' roofline.
@@ -485,6 +522,22 @@ rbf_status rbf_deform_volume_adjoint(const double *d_xv, int64_t nv,
  * ------------------------------------------------------------------------ */
 #define RBF_PEAK_F32X2 2
 rbf_status rbf_measure_fma_peak(int prec, double *h_flops, void *stream);
+
+/* --------------------------------------------------------------------------
+ * Latency microbenchmarks: the parameters of the persistent greedy's cost
+ * model, which is bound by latency rather than by a pipe or by memory.
+ *   RBF_LAT_GRID_BARRIER: nanoseconds per grid barrier of the greedy kernels
+ *     (the same barrier code) among `param` co-resident CTAs of 256 threads
+ *     (RBF_E_ARG if they cannot all be resident);
+ *   RBF_LAT_FP64_WARP / RBF_LAT_FP32_WARP: nanoseconds per FMA instruction
+ *     of a lone warp running 8 independent chains (the issue cost one-warp
+ *     scalar work pays).
+ * h_ns: host, the best of two timed repetitions.  SYNCHRONOUS.
+ * ------------------------------------------------------------------------ */
+#define RBF_LAT_GRID_BARRIER 1
+#define RBF_LAT_FP64_WARP 2
+#define RBF_LAT_FP32_WARP 3
+rbf_status rbf_measure_latency(int what, int param, double *h_ns, void *stream);
 
 /* Status latched by the last ASYNC call's device work on this device
  * (RBF_OK if none failed); reading it synchronises the device. */

@@ -418,6 +418,13 @@ int orc_greedy(const double *xb, const double *db, int64_t nb, double R, double 
                 add = nf;
                 fpos++;
             } else {
+                /* the followed run is used up and stopped at its capacity:
+                 * this is the iteration where the literal algorithm would
+                 * append beyond N_c^max */
+                if (fpos >= follow_n && nc >= ncmax && nloc >= 0 && Eloc > Estar) {
+                    status = ORC_E_NC_MAX;
+                    break;
+                }
                 if (nloc >= 0 && Eloc > Estar * (1.0 + tie_rel)) stats->n_fail++;
                 else if (nloc >= 0 && Eloc > Estar) stats->n_div++;
             }

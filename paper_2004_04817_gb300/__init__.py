@@ -15,6 +15,8 @@ from .rbf import (  # noqa: F401
     deform_volume,
     solve_system,
     adjoint,
+    adjoint_factored,
+    Factor,
     deform,
     deform_modal,
     MODAL_BF16,
@@ -24,6 +26,7 @@ from .rbf import (  # noqa: F401
     VolumeBatch,
     VolumePlan,
     measure_fma_peak,
+    measure_latency,
     nearest_support,
     support_kl,
     group_of,

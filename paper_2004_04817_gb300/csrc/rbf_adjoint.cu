@@ -22,9 +22,8 @@
 
 namespace rbf {
 
-constexpr int kAdjThreads = 256;
+constexpr int kAdjMaxCentres = 1024; // one centre per thread, one CTA of up to 1024
 constexpr int kAdjChunk = 1024;      // volume points per shared-memory chunk
-constexpr int kAdjMaxCj = 4;         // centres per thread (nc <= 1024)
 
 // Packing: scaled volume points and their gradients (hi/lo splits for the
 // double-float path).
@@ -64,8 +63,11 @@ __global__ void k_adjoint_centres(const double *__restrict__ xb, const int32_t *
     }
 }
 
+// One centre per thread: the CTA has nc threads rounded up to a warp (<= 1024),
+// so every thread has the same work; each chunk of points is staged in
+// shared memory and read by all threads as broadcasts.
 template <bool FF>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(1024)
 k_adjoint_partial(const float4 *__restrict__ xh, const float4 *__restrict__ xl,
                   const float4 *__restrict__ gh, const float4 *__restrict__ gl, int64_t nv,
                   const float4 *__restrict__ ch, const float4 *__restrict__ cl, int nc,
@@ -74,28 +76,17 @@ k_adjoint_partial(const float4 *__restrict__ xh, const float4 *__restrict__ xl,
     extern __shared__ float4 s_pts[];     // [chunk] x_hi, x_lo, g_hi, g_lo
     float4 *s_xh = s_pts, *s_xl = s_pts + kAdjChunk, *s_gh = s_pts + 2 * kAdjChunk,
            *s_gl = s_pts + 3 * kAdjChunk;
-    const int tid = threadIdx.x;
-    const int ncj = (nc + kAdjThreads - 1) / kAdjThreads;   // <= kAdjMaxCj
-    double acc[kAdjMaxCj][3];
-    float4 cj_h[kAdjMaxCj], cj_l[kAdjMaxCj];
-#pragma unroll
-    for (int c = 0; c < kAdjMaxCj; ++c) {
-        acc[c][0] = acc[c][1] = acc[c][2] = 0.0;
-        const int j = tid + c * kAdjThreads;
-        if (c < ncj && j < nc) {
-            cj_h[c] = ch[j];
-            cj_l[c] = cl[j];
-        } else {
-            cj_h[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-            cj_l[c] = cj_h[c];
-        }
-    }
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const bool mine = tid < nc;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    const float4 qh = mine ? ch[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 ql = mine ? cl[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int64_t nchunks = (nv + kAdjChunk - 1) / kAdjChunk;
     for (int64_t ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
         const int64_t v0 = ck * kAdjChunk;
         const int nvc = (int)min((int64_t)kAdjChunk, nv - v0);
         __syncthreads();
-        for (int i = tid; i < nvc; i += kAdjThreads) {
+        for (int i = tid; i < nvc; i += nthr) {
             s_xh[i] = xh[v0 + i];
             s_gh[i] = gh[v0 + i];
             if (FF) {
@@ -104,56 +95,45 @@ k_adjoint_partial(const float4 *__restrict__ xh, const float4 *__restrict__ xl,
             }
         }
         __syncthreads();
-#pragma unroll
-        for (int c = 0; c < kAdjMaxCj; ++c) {
-            if (c >= ncj)
-                break;
-            if (tid + c * kAdjThreads >= nc)
-                continue;
-            if (!FF) {
-                float ax = 0.0f, ay = 0.0f, az = 0.0f;
-                const float4 q = cj_h[c];
+        if (!mine)
+            continue;
+        if (!FF) {
+            float ax = 0.0f, ay = 0.0f, az = 0.0f;
 #pragma unroll 4
-                for (int i = 0; i < nvc; ++i) {
-                    const float4 x = s_xh[i], g = s_gh[i];
-                    const float dx = x.x - q.x, dy = x.y - q.y, dz = x.z - q.z;
-                    const float ph = phi_f32_s(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-                    ax = fmaf(g.x, ph, ax);
-                    ay = fmaf(g.y, ph, ay);
-                    az = fmaf(g.z, ph, az);
-                }
-                acc[c][0] += (double)ax;
-                acc[c][1] += (double)ay;
-                acc[c][2] += (double)az;
-            } else {
-                ff ax{0.0f, 0.0f}, ay{0.0f, 0.0f}, az{0.0f, 0.0f};
-                const float4 qh = cj_h[c], ql = cj_l[c];
-#pragma unroll 2
-                for (int i = 0; i < nvc; ++i) {
-                    const float4 x0 = s_xh[i], x1 = s_xl[i];
-                    const float4 g0 = s_gh[i], g1 = s_gl[i];
-                    const ff s2 = dist2_ff(x0.x, x1.x, x0.y, x1.y, x0.z, x1.z, qh.x, ql.x, qh.y,
-                                           ql.y, qh.z, ql.z);
-                    const ff ph = phi_ff_s(s2);
-                    ff_fma_acc(ax, g0.x, g1.x, ph);
-                    ff_fma_acc(ay, g0.y, g1.y, ph);
-                    ff_fma_acc(az, g0.z, g1.z, ph);
-                }
-                acc[c][0] += (double)ax.h + (double)ax.l;
-                acc[c][1] += (double)ay.h + (double)ay.l;
-                acc[c][2] += (double)az.h + (double)az.l;
+            for (int i = 0; i < nvc; ++i) {
+                const float4 x = s_xh[i], g = s_gh[i];
+                const float dx = x.x - qh.x, dy = x.y - qh.y, dz = x.z - qh.z;
+                const float ph = phi_f32_s(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                ax = fmaf(g.x, ph, ax);
+                ay = fmaf(g.y, ph, ay);
+                az = fmaf(g.z, ph, az);
             }
+            acc0 += (double)ax;
+            acc1 += (double)ay;
+            acc2 += (double)az;
+        } else {
+            ff ax{0.0f, 0.0f}, ay{0.0f, 0.0f}, az{0.0f, 0.0f};
+#pragma unroll 2
+            for (int i = 0; i < nvc; ++i) {
+                const float4 x0 = s_xh[i], x1 = s_xl[i];
+                const float4 g0 = s_gh[i], g1 = s_gl[i];
+                const ff s2 = dist2_ff(x0.x, x1.x, x0.y, x1.y, x0.z, x1.z, qh.x, ql.x, qh.y,
+                                       ql.y, qh.z, ql.z);
+                const ff ph = phi_ff_s(s2);
+                ff_fma_acc(ax, g0.x, g1.x, ph);
+                ff_fma_acc(ay, g0.y, g1.y, ph);
+                ff_fma_acc(az, g0.z, g1.z, ph);
+            }
+            acc0 += (double)ax.h + (double)ax.l;
+            acc1 += (double)ay.h + (double)ay.l;
+            acc2 += (double)az.h + (double)az.l;
         }
     }
-#pragma unroll
-    for (int c = 0; c < kAdjMaxCj; ++c) {
-        const int j = tid + c * kAdjThreads;
-        if (c < ncj && j < nc) {
-            double *pp = partial + ((size_t)blockIdx.x * nc + j) * 3;
-            pp[0] = acc[c][0];
-            pp[1] = acc[c][1];
-            pp[2] = acc[c][2];
-        }
+    if (mine) {
+        double *pp = partial + ((size_t)blockIdx.x * nc + tid) * 3;
+        pp[0] = acc0;
+        pp[1] = acc1;
+        pp[2] = acc2;
     }
 }
 
@@ -212,32 +192,21 @@ using namespace rbf;
 
 extern "C" size_t rbf_adjoint_workspace_bytes(int64_t nv, int64_t nc)
 {
-    if (nv < 0 || nc < 1 || nc > (int64_t)kAdjThreads * kAdjMaxCj)
+    if (nv < 0 || nc < 1 || nc > kAdjMaxCentres)
         return 0;
     return adjoint_ws_layout(nv, nc, adjoint_blocks()).total;
 }
 
-extern "C" rbf_status rbf_deform_volume_adjoint(const double *d_xv, int64_t nv,
-                                                const double *d_xb, int64_t nb,
-                                                const int32_t *d_sel_idx, int64_t nc,
-                                                const double *d_gv, const rbf_params *p,
-                                                double *d_gc, double *h_max_resid, void *d_ws,
-                                                size_t ws_bytes, void *stream)
+// Stages 1-2: g_c = Phi_vc^T g_v into gc (workspace), ASYNC.
+static rbf_status adjoint_rhs(const double *d_xv, int64_t nv, const double *d_xb,
+                              const int32_t *d_sel_idx, int64_t nc, const double *d_gv,
+                              double radius, int eval_prec, const AdjWs &L, char *ws,
+                              cudaStream_t st)
 {
-    if (!p || nv < 0 || nc < 1 || nc > (int64_t)kAdjThreads * kAdjMaxCj || nc > nb ||
-        !(p->radius > 0.0) || !d_xb || !d_sel_idx || !d_gc ||
-        (nv > 0 && (!d_xv || !d_gv)) ||
-        (p->eval_prec != RBF_PREC_F32 && p->eval_prec != RBF_PREC_F32X2))
-        return RBF_E_ARG;
     DeviceInfo dev;
     if (!device_info(&dev))
         return RBF_E_CUDA;
-    const AdjWs L = adjoint_ws_layout(nv, nc, adjoint_blocks());
-    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
-        return RBF_E_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
-    char *ws = (char *)d_ws;
-    const double inv_r = 1.0 / p->radius;
+    const double inv_r = 1.0 / radius;
     float4 *xh = (float4 *)(ws + L.xh), *xl = (float4 *)(ws + L.xl);
     float4 *gh = (float4 *)(ws + L.gh), *gl = (float4 *)(ws + L.gl);
     float4 *ch = (float4 *)(ws + L.ch), *cl = (float4 *)(ws + L.cl);
@@ -250,7 +219,7 @@ extern "C" rbf_status rbf_deform_volume_adjoint(const double *d_xv, int64_t nv,
     }
     k_adjoint_centres<<<(int)((nc + 127) / 128), 128, 0, st>>>(d_xb, d_sel_idx, (int)nc, inv_r,
                                                                 ch, cl);
-    const bool ffm = p->eval_prec == RBF_PREC_F32X2;
+    const bool ffm = eval_prec == RBF_PREC_F32X2;
     const size_t smem = sizeof(float4) * 4 * kAdjChunk;
     static bool attr = false;
     if (!attr) {
@@ -260,17 +229,61 @@ extern "C" rbf_status rbf_deform_volume_adjoint(const double *d_xv, int64_t nv,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
+    const int threads = (int)((nc + 31) / 32 * 32);
     if (ffm)
-        k_adjoint_partial<true><<<blocks, kAdjThreads, smem, st>>>(xh, xl, gh, gl, nv, ch, cl,
-                                                                   (int)nc, partial);
+        k_adjoint_partial<true><<<blocks, threads, smem, st>>>(xh, xl, gh, gl, nv, ch, cl,
+                                                               (int)nc, partial);
     else
-        k_adjoint_partial<false><<<blocks, kAdjThreads, smem, st>>>(xh, xl, gh, gl, nv, ch, cl,
-                                                                    (int)nc, partial);
+        k_adjoint_partial<false><<<blocks, threads, smem, st>>>(xh, xl, gh, gl, nv, ch, cl,
+                                                                (int)nc, partial);
     k_adjoint_reduce<<<(int)((3 * nc + 127) / 128), 128, 0, st>>>(partial, blocks, (int)nc, gc);
-    if (cudaGetLastError() != cudaSuccess)
-        return RBF_E_CUDA;
+    return cudaGetLastError() == cudaSuccess ? RBF_OK : RBF_E_CUDA;
+}
+
+extern "C" rbf_status rbf_deform_volume_adjoint(const double *d_xv, int64_t nv,
+                                                const double *d_xb, int64_t nb,
+                                                const int32_t *d_sel_idx, int64_t nc,
+                                                const double *d_gv, const rbf_params *p,
+                                                double *d_gc, double *h_max_resid, void *d_ws,
+                                                size_t ws_bytes, void *stream)
+{
+    if (!p || nv < 0 || nc < 1 || nc > kAdjMaxCentres || nc > nb ||
+        !(p->radius > 0.0) || !d_xb || !d_sel_idx || !d_gc ||
+        (nv > 0 && (!d_xv || !d_gv)) ||
+        (p->eval_prec != RBF_PREC_F32 && p->eval_prec != RBF_PREC_F32X2))
+        return RBF_E_ARG;
+    const AdjWs L = adjoint_ws_layout(nv, nc, adjoint_blocks());
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
+        return RBF_E_WORKSPACE;
+    char *ws = (char *)d_ws;
+    const rbf_status s = adjoint_rhs(d_xv, nv, d_xb, d_sel_idx, nc, d_gv, p->radius,
+                                     p->eval_prec, L, ws, (cudaStream_t)stream);
+    if (s != RBF_OK)
+        return s;
     // Phi_cc lambda = g_c (symmetric, FP64 factor + refinement)
     rbf_params ps = *p;
-    return rbf_solve_system(d_xb, nb, d_sel_idx, nc, gc, &ps, d_gc, h_max_resid, ws + L.solve,
-                            ws_bytes - L.solve, stream);
+    return rbf_solve_system(d_xb, nb, d_sel_idx, nc, (const double *)(ws + L.gc), &ps, d_gc,
+                            h_max_resid, ws + L.solve, ws_bytes - L.solve, stream);
+}
+
+extern "C" rbf_status rbf_deform_volume_adjoint_factored(const double *d_xv, int64_t nv,
+                                                         const double *d_gv, const rbf_factor *f,
+                                                         const rbf_params *p, double *d_gc,
+                                                         double *h_max_resid, void *d_ws,
+                                                         size_t ws_bytes, void *stream)
+{
+    if (!p || !f || nv < 0 || f->nc > kAdjMaxCentres || !d_gc ||
+        (nv > 0 && (!d_xv || !d_gv)) || p->refine_steps < 0 || p->refine_steps > 15 ||
+        (p->eval_prec != RBF_PREC_F32 && p->eval_prec != RBF_PREC_F32X2))
+        return RBF_E_ARG;
+    const AdjWs L = adjoint_ws_layout(nv, f->nc, adjoint_blocks());
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
+        return RBF_E_WORKSPACE;
+    char *ws = (char *)d_ws;
+    const rbf_status s = adjoint_rhs(d_xv, nv, f->xb, f->sel, f->nc, d_gv, f->radius,
+                                     p->eval_prec, L, ws, (cudaStream_t)stream);
+    if (s != RBF_OK)
+        return s;
+    return rbf_factor_solve(f, (const double *)(ws + L.gc), p->refine_steps, d_gc, h_max_resid,
+                            stream);
 }

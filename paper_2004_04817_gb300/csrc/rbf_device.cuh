@@ -513,8 +513,12 @@ constexpr int kBarMaxCtas = 4096;
 
 struct GridBar {
     unsigned int arrive[kBarMaxCtas];
-    unsigned long long wait_ns;   // time CTA 0 spent in barriers (profiling)
 };
+
+// Time CTA 0 spent waiting in grid barriers (profiling), kept in shared
+// memory: a global update after every barrier would delay CTA 0's next
+// arrival.  A kernel that reports it zeroes it on entry.
+static __shared__ unsigned long long g_bar_wait_ns;
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
 {
@@ -579,7 +583,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, unsigned
         if (threadIdx.x == 0) {
             s_ok = ok;
             if (my_block == 0)
-                bar->wait_ns += globaltimer_ns() - t0;
+                g_bar_wait_ns += globaltimer_ns() - t0;
         }
     }
     __syncthreads();

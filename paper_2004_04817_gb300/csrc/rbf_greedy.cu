@@ -39,10 +39,17 @@ __shared__ int g_vg;
 constexpr int kGThreads = 256;
 constexpr int kGWarps = kGThreads / kWarp;
 constexpr int kMaxGrid = 4096;
-constexpr int kSmemCentresF32 = 2048;      // FP32 centres kept in shared memory (64 KB)
-constexpr int kSmemCentresFF = 1024;       // double-float centres in the same 64 KB
+constexpr int kSmemCentresF32 = 2048;      // FP32 centres staged in shared memory by the
+constexpr int kSmemCentresFF = 1024;       // batched launch (64 KB, two CTAs per SM); the
+                                           // single-problem launch (one CTA per SM) stages
+                                           // up to the device's shared-memory limit
 constexpr double kPivotMin = 1e-13;        // d^2 at or below: singular (coincident nodes)
 constexpr int kLookIdle = 8;               // idle iterations before a look-ahead
+// Pairs one CTA evaluates in about the time of one idle iteration (measured
+// on the 50,000-node wing: 0.76 G double-float pairs/s per CTA, ~13 us per
+// iteration), by precision; a look-ahead runs only when its pairs cost at
+// most half the idle iterations it can skip (see the main loop).
+constexpr double kLookPairsFF = 8000.0, kLookPairsF32 = 40000.0, kLookPairsF64 = 400.0;
 constexpr float kU32 = 5.9604645e-8f;      // 2^-24, unit roundoff of FP32
 constexpr float kBetaPhi = 16.0f;          // error-bound factors (see screen_bound)
 constexpr float kBetaCoord = 8.0f;
@@ -70,6 +77,7 @@ struct GreedyCtl {
     double max_resid;
     long long n_hist;
     unsigned long long phase_ns[12];  // CTA 0's time per phase (see rbf_greedy_stats)
+    long long barriers;               // grid barriers passed
 };
 
 // Per-CTA record of an evaluation (see evaluate).
@@ -133,6 +141,8 @@ struct GreedyArgs {
     double *w_out;                // optional FP64 weights output (nc x 3)
     int refine_steps;
     long long *nc_out;            // optional: |S| at exit (device, for batched runs)
+    int smem_cap;                 // centres whose evaluation table fits in the launch's
+                                  // dynamic shared memory (larger sets are read from L2)
 };
 
 __device__ __forceinline__ int goff(int i, int nb, int m)
@@ -715,15 +725,16 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     __shared__ float s_wabs;
     __shared__ __align__(8) unsigned long long s_mbar;
     unsigned mbar_phase = 0;
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         mbar_init(&s_mbar, 1);
+        g_bar_wait_ns = 0;
+    }
     __syncthreads();
     GreedyCtl *ctl = a.ctl;
     const int G = g_vg;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtid = g_vb * kGThreads + tid;
     const int gthreads = G * kGThreads;
-    const int gwarp = g_vb * kGWarps + warp, gwarps = G * kGWarps;
     const int nb = a.nb, m = a.m;
     int use = 0;   // partial-buffer use counter (double buffering)
     unsigned int epoch = 0;   // grid barriers passed
@@ -891,7 +902,6 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     auto evaluate = [&](int p0, int p1, bool argmax, bool force64, EvalOut &out, int look,
                         bool cached) -> bool {
         phase(1);
-        const int r = ev % 3;
         const int nq = p1 - p0;
         const int ts = team_size(nq, G);
         const int sub = lane & (ts - 1);
@@ -961,7 +971,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             // |E~ - E| <= beta; e64[q] = E~, u32[q] = beta.  The centre table
             // is staged in shared memory by one bulk (TMA) copy.
             const bool use_ff = a.prec == RBF_PREC_F32X2;
-            const bool smem = nc <= (use_ff ? kSmemCentresFF : kSmemCentresF32);
+            const bool smem = nc <= a.smem_cap;
             phase(7);
             if (smem) {
                 const float4 *src = use_ff ? a.cwff : a.cw32;
@@ -1056,13 +1066,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     const int q = p0 + team + it * nteams;
                     const bool act = q < p1;
                     const int qq = act ? q : p0;
-                    // the node: coordinates (high = FP32 copy, low part) and,
-                    // for the epilogue, its displacement, S flag and index,
-                    // all loaded ahead of the pair loop
+                    // the node's coordinates: high part = the FP32 copy, low part
                     const float4 xh = ldcg(a.xg32 + qq), xlo = ldcg(a.xgl + qq);
-                    const float4 dh = ldcg(a.dgh + qq), dl = ldcg(a.dgl + qq);
-                    const bool q_in_s = ldcg(a.in_s + qq) != 0;
-                    const int qnode = ldcg(a.node_of_pos + qq);
                     const float qxh = xh.x, qxl = xlo.x, qyh = xh.y, qyl = xlo.y, qzh = xh.z,
                                 qzl = xlo.z;
                     ff fx{0.0f, 0.0f}, fy{0.0f, 0.0f}, fz{0.0f, 0.0f};
@@ -1127,7 +1132,9 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                                            __shfl_xor_sync(0xffffffffu, sz.l, o)});
                     }
                     sb = team_sum(sb, ts);
-                    if (act && sub == 0 && !q_in_s) {
+                    if (act && sub == 0 && !ldcg(a.in_s + q)) {
+                        const float4 dh = ldcg(a.dgh + q), dl = ldcg(a.dgl + q);
+                        const int qnode = ldcg(a.node_of_pos + q);
                         // E = |dr - F| in double-float; FP64 only converts the
                         // result (an FP64 instruction costs a warp ~30x an
                         // FP32 one here)
@@ -1469,7 +1476,15 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         // the run ends where m idle iterations would end it.  A later
         // look-ahead of the same idle run (a flagged group whose nodes all
         // turned out <= E*) only scans the stored errors and bounds.
-        if (idle >= kLookIdle && m > 2 * kLookIdle && !hist_full) {
+        // An all-node evaluation pays only when it is cheap against the idle
+        // iterations it can skip: N_b N_c pairs on G CTAs against (m - idle)
+        // iterations (a deterministic model, so every CTA decides alike).
+        const double look_rate = a.prec == RBF_PREC_F32X2 ? kLookPairsFF
+                                 : a.prec == RBF_PREC_F32 ? kLookPairsF32
+                                                          : kLookPairsF64;
+        const bool look_pays =
+            look_cached || (double)nb * (double)nc <= 0.5 * look_rate * G * (double)(m - idle);
+        if (idle >= kLookIdle && m > 2 * kLookIdle && !hist_full && look_pays) {
             const int nxt = (int)((k + 1) % m);
             const int start = goff(nxt, nb, m);
             EvalOut la;
@@ -1532,10 +1547,11 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             *a.nc_out = nc;
         for (int i = 0; i < 12; ++i)
             ctl->phase_ns[i] = ph_acc[i];
-        ctl->phase_ns[6] = ctl->bar.wait_ns;
+        ctl->phase_ns[6] = g_bar_wait_ns;
         if (status != RBF_OK)
             atomicCAS(&ctl->status, (int)RBF_OK, status);
         ctl->max_resid = maxres;
+        ctl->barriers = (long long)epoch;
         ctl->estar = estar;
         ctl->nc = nc;
         ctl->iterations = k - 3 + 1;
@@ -1598,7 +1614,7 @@ k_greedy_batched(const GreedyArgs *__restrict__ args, const int *__restrict__ ct
 __global__ void __launch_bounds__(kGThreads, 1)
 k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
         D4 *__restrict__ rvec, D4 *__restrict__ tvec, double *__restrict__ w_out,
-        const double *__restrict__ rhs)
+        const double *__restrict__ rhs, int reuse)
 {
     __shared__ Red red;
     if (threadIdx.x == 0) {
@@ -1611,7 +1627,6 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtid = g_vb * kGThreads + tid;
     const int gthreads = G * kGThreads;
-    const int gwarp = g_vb * kGWarps + warp, gwarps = G * kGWarps;
     int use = 0;
     unsigned int epoch = 0;
     auto part = [&](int u) { return a.part + (size_t)(u & 1) * kMaxGrid * 4; };
@@ -1668,7 +1683,17 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
     }
     int nc = 0;
     double min_piv = INFINITY;
-    for (int j = 0; j < nc_total; ++j) {
+    if (reuse) {
+        // the factor Z = L^-1 and the centres of an earlier launch on the same
+        // workspace and support set: start from W = 0, so the first
+        // refinement step is the solve W = Z^T Z rhs
+        for (int j = gtid; j < nc_total; j += gthreads)
+            a.w64[j] = mk4(0.0, 0.0, 0.0, 0.0);
+        nc = nc_total;
+        ++steps;
+        GSYNC();
+    }
+    for (int j = nc; j < nc_total; ++j) {
         const int node = sel[j];
         const int r = chol_append(a, red, nc, use, min_piv, j, node, -1, epoch);
         if (r != kAppendOk) {
@@ -1872,14 +1897,21 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
     a.refine_steps = p->refine_steps;
     fill_args(a, ws, L);
 
-    const size_t smem =
-        p->eval_prec == RBF_PREC_F32
-            ? sizeof(float4) * 2 * (size_t)std::min<int64_t>(p->nc_max, kSmemCentresF32)
-        : p->eval_prec == RBF_PREC_F32X2
-            ? sizeof(float4) * 4 * (size_t)std::min<int64_t>(p->nc_max, kSmemCentresFF)
-            : 0;
+    // the evaluation table of as many centres as fit beside the kernel's
+    // static shared memory (one CTA per SM): about 3,500 double-float or
+    // 7,000 FP32 centres on this GPU
+    const size_t per_centre = p->eval_prec == RBF_PREC_F32     ? sizeof(float4) * 2
+                              : p->eval_prec == RBF_PREC_F32X2 ? sizeof(float4) * 4
+                                                               : 0;
+    cudaFuncAttributes fattr{};
+    if (cudaFuncGetAttributes(&fattr, k_greedy) != cudaSuccess)
+        return RBF_E_CUDA;
+    const size_t room = dev.smem_optin > fattr.sharedSizeBytes + 1024
+                            ? dev.smem_optin - fattr.sharedSizeBytes - 1024 : 0;
+    a.smem_cap = per_centre ? (int)std::min<int64_t>(p->nc_max, (int64_t)(room / per_centre)) : 0;
+    const size_t smem = per_centre * (size_t)a.smem_cap;
     if (cudaFuncSetAttribute(k_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float4) * 4 * kSmemCentresFF)) != cudaSuccess)
+                             (int)std::max<size_t>(smem, 1)) != cudaSuccess)
         return RBF_E_CUDA;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_greedy, kGThreads, smem) !=
@@ -1927,6 +1959,8 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
         h_stats->max_resid = ctl.max_resid;
         for (int i = 0; i < 12; ++i)
             h_stats->phase_ns[i] = (int64_t)ctl.phase_ns[i];
+        h_stats->barriers = ctl.barriers;
+        h_stats->ctas = grid;
     }
     return (rbf_status)ctl.status;
 }
@@ -1946,7 +1980,7 @@ namespace rbf {
 static rbf_status solve_launch(const double *d_xb, const double *d_db, int64_t nb,
                                const int32_t *d_sel_idx, int64_t nc, const double *d_rhs,
                                const rbf_params *p, double *d_x, double *h_max_resid, void *d_ws,
-                               size_t ws_bytes, void *stream)
+                               size_t ws_bytes, void *stream, int reuse = 0)
 {
     if (!p || !d_xb || (!d_db && !d_rhs) || !d_sel_idx || !d_x || nc < 1 || nc > nb ||
         nc > 46340 || nb >= kMaxNodes || !(p->radius > 0.0) || !std::isfinite(p->radius) ||
@@ -1980,10 +2014,15 @@ static rbf_status solve_launch(const double *d_xb, const double *d_db, int64_t n
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve, kGThreads, 0) != cudaSuccess ||
         occ < 1)
         return RBF_E_CUDA;
-    const int grid = std::min(dev.sms, kMaxGrid);
+    // CTAs: a grid barrier costs ~1.1 us among 64 CTAs and 2-3 us among all
+    // SMs, while each append's two FP64 matrix-vector products (nc^2 / 2
+    // FMAs each) want many SMs once nc passes ~1000
+    const int grid = (int)std::min<int64_t>(std::min(dev.sms, kMaxGrid),
+                                            std::max<int64_t>(64, nc / 8));
     int nc_i = (int)nc, steps = p->refine_steps;
     D4 *rvec = (D4 *)(ws + L.rvec), *tvec = (D4 *)(ws + L.tvec);
-    void *kargs[] = {&a, (void *)&d_sel_idx, &nc_i, &steps, &rvec, &tvec, &d_x, (void *)&d_rhs};
+    void *kargs[] = {&a,    (void *)&d_sel_idx, &nc_i, &steps, &rvec, &tvec, &d_x,
+                     (void *)&d_rhs, &reuse};
     if (cudaLaunchCooperativeKernel((const void *)k_solve, grid, kGThreads, kargs, 0, st) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -2024,6 +2063,66 @@ extern "C" rbf_status rbf_solve_system(const double *d_xb, int64_t nb, const int
                         ws_bytes, stream);
 }
 
+// ---------------------------------------------------------------------------
+// Factor objects: the appends of one k_solve launch leave Z = L^-1 of
+// Phi_SS in the workspace; later solves with the same support set reuse it.
+// ---------------------------------------------------------------------------
+extern "C" size_t rbf_factor_workspace_bytes(int64_t nc)
+{
+    if (nc < 1 || nc > 46340)
+        return 0;
+    return solve_ws_layout(nc).total + align_up(sizeof(double) * 3 * (size_t)nc, 256);
+}
+
+extern "C" rbf_status rbf_factor_create(const double *d_xb, int64_t nb, const int32_t *d_sel_idx,
+                                        int64_t nc, const rbf_params *p, void *d_ws,
+                                        size_t ws_bytes, void *stream, rbf_factor **out)
+{
+    if (!out)
+        return RBF_E_ARG;
+    *out = nullptr;
+    if (!p || nc < 1 || nc > 46340)
+        return RBF_E_ARG;
+    const size_t solve_bytes = solve_ws_layout(nc).total;
+    if (!d_ws || ws_bytes < rbf_factor_workspace_bytes(nc) || ((uintptr_t)d_ws & 255) != 0)
+        return RBF_E_WORKSPACE;
+    // the appends need a right-hand side: zeros (the factor does not depend on it)
+    double *scratch = (double *)((char *)d_ws + solve_bytes);
+    if (cudaMemsetAsync(scratch, 0, sizeof(double) * 3 * (size_t)nc, (cudaStream_t)stream) !=
+        cudaSuccess)
+        return RBF_E_CUDA;
+    rbf_params q = *p;
+    q.refine_steps = 0;
+    const rbf_status st = solve_launch(d_xb, nullptr, nb, d_sel_idx, nc, scratch, &q, scratch,
+                                       nullptr, d_ws, solve_bytes, stream, 0);
+    if (st != RBF_OK)
+        return st;
+    rbf_factor *f = new rbf_factor();
+    f->xb = d_xb;
+    f->nb = nb;
+    f->sel = d_sel_idx;
+    f->nc = nc;
+    f->radius = p->radius;
+    f->ws = (char *)d_ws;
+    f->ws_bytes = solve_bytes;
+    *out = f;
+    return RBF_OK;
+}
+
+extern "C" rbf_status rbf_factor_solve(const rbf_factor *f, const double *d_rhs, int refine_steps,
+                                       double *d_x, double *h_max_resid, void *stream)
+{
+    if (!f || !d_rhs || !d_x || refine_steps < 0 || refine_steps > 15)
+        return RBF_E_ARG;
+    rbf_params q{};
+    q.radius = f->radius;
+    q.refine_steps = refine_steps;
+    return solve_launch(f->xb, nullptr, f->nb, f->sel, f->nc, d_rhs, &q, d_x, h_max_resid, f->ws,
+                        f->ws_bytes, stream, 1);
+}
+
+extern "C" void rbf_factor_destroy(rbf_factor *f) { delete f; }
+
 
 // ---------------------------------------------------------------------------
 // Batched greedy: many independent problems in one cooperative launch.
@@ -2035,6 +2134,7 @@ struct rbf_greedy_batch {
     int prec = 0;
     char *ws = nullptr;
     std::vector<size_t> ctl_off;     // control block of each problem (reset per run)
+    std::vector<int> cta_start_host; // CTA range of each problem
     size_t args_off = 0, start_off = 0, nc_off = 0;
 };
 
@@ -2160,6 +2260,8 @@ extern "C" rbf_status rbf_greedy_batch_create(const rbf_greedy_problem *h_probs,
         a.hist_cap = 0;
         a.w_out = q.d_w;
         a.refine_steps = q.params.refine_steps;
+        a.smem_cap = (int)std::min<int64_t>(q.params.nc_max, prec == RBF_PREC_F32 ? kSmemCentresF32
+                                                             : prec == RBF_PREC_F32X2 ? kSmemCentresFF : 0);
         fill_args(a, pw, G);
         a.nc_out = (long long *)(ws + L.nc) + i;
     }
@@ -2172,6 +2274,7 @@ extern "C" rbf_status rbf_greedy_batch_create(const rbf_greedy_problem *h_probs,
     rbf_greedy_batch *b = new rbf_greedy_batch();
     b->B = B;
     b->grid = start[B];
+    b->cta_start_host = start;
     b->smem = smem;
     b->prec = prec;
     b->ws = ws;
@@ -2253,6 +2356,8 @@ extern "C" rbf_status rbf_greedy_batch_results(rbf_greedy_batch *b, int32_t *h_s
             t.max_resid = ctl.max_resid;
             for (int k = 0; k < 12; ++k)
                 t.phase_ns[k] = (int64_t)ctl.phase_ns[k];
+            t.barriers = ctl.barriers;
+            t.ctas = b->cta_start_host.empty() ? 0 : b->cta_start_host[i + 1] - b->cta_start_host[i];
         }
     }
     return worst;

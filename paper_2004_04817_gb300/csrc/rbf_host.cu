@@ -92,6 +92,51 @@ __global__ void __launch_bounds__(512) k_fma_peak_f2(float *out, int iters, floa
         out[blockIdx.x] = lo;
 }
 
+// ---------------------------------------------------------------------------
+// Latency microbenchmarks: the parameters of the persistent greedy's cost
+// model (a grid barrier, one FP64 instruction of a lone warp).  Timed on the
+// device clock by CTA 0, thread 0.
+// ---------------------------------------------------------------------------
+__device__ GridBar g_lat_bar;
+__device__ int g_lat_status;
+__device__ unsigned long long g_lat_ns;
+
+__global__ void __launch_bounds__(256) k_lat_barrier(int iters)
+{
+    unsigned int epoch = 0;
+    const unsigned long long t0 = globaltimer_ns();
+    for (int i = 0; i < iters; ++i)
+        if (!grid_barrier(&g_lat_bar, &g_lat_status, gridDim.x, 1000000000ull, epoch, blockIdx.x))
+            return;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        g_lat_ns = globaltimer_ns() - t0;
+}
+
+template <typename T>
+__global__ void k_lat_fma(int iters, T a, T b, T *out)
+{
+    T x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        x[u] = (T)(threadIdx.x + u);
+    __syncwarp();
+    const unsigned long long t0 = globaltimer_ns();
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            x[u] = x[u] * a + b;
+    __syncwarp();
+    const unsigned long long t1 = globaltimer_ns();
+    T s = (T)0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        s += x[u];
+    if (s == (T)-12345.0)   // never true; keeps the chains alive
+        out[threadIdx.x] = s;
+    if (threadIdx.x == 0)
+        g_lat_ns = t1 - t0;
+}
+
 }  // namespace rbf
 
 using namespace rbf;
@@ -130,6 +175,64 @@ extern "C" rbf_status rbf_last_device_status(void)
         cudaGetLastError();
         return RBF_E_CUDA;
     }
+    return RBF_OK;
+}
+
+extern "C" rbf_status rbf_measure_latency(int what, int param, double *h_ns, void *stream)
+{
+    if (!h_ns || (what != RBF_LAT_GRID_BARRIER && what != RBF_LAT_FP64_WARP &&
+                  what != RBF_LAT_FP32_WARP))
+        return RBF_E_ARG;
+    DeviceInfo dev;
+    if (!device_info(&dev))
+        return RBF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    double best = 1e300;
+    for (int rep = 0; rep < 3; ++rep) {
+        double per = 0.0;
+        if (what == RBF_LAT_GRID_BARRIER) {
+            int occ = 0;
+            if (param < 1 ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lat_barrier, 256, 0) !=
+                    cudaSuccess ||
+                param > occ * dev.sms)
+                return RBF_E_ARG;
+            void *bar = nullptr, *stat = nullptr;
+            if (cudaGetSymbolAddress(&bar, g_lat_bar) != cudaSuccess ||
+                cudaGetSymbolAddress(&stat, g_lat_status) != cudaSuccess ||
+                cudaMemsetAsync(bar, 0, sizeof(GridBar), st) != cudaSuccess ||
+                cudaMemsetAsync(stat, 0, sizeof(int), st) != cudaSuccess)
+                return RBF_E_CUDA;
+            int iters = 2000;
+            void *args[] = {&iters};
+            if (cudaLaunchCooperativeKernel((const void *)k_lat_barrier, param, 256, args, 0, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return RBF_E_CUDA;
+            int hs = 0;
+            unsigned long long ns = 0;
+            if (cudaMemcpyFromSymbol(&hs, g_lat_status, sizeof(int)) != cudaSuccess ||
+                cudaMemcpyFromSymbol(&ns, g_lat_ns, sizeof(ns)) != cudaSuccess)
+                return RBF_E_CUDA;
+            if (hs != 0)
+                return RBF_E_TIMEOUT;
+            per = (double)ns / iters;
+        } else {
+            const int iters = 1024;
+            if (what == RBF_LAT_FP64_WARP)
+                k_lat_fma<double><<<1, 32, 0, st>>>(iters, 0.999, 0.001, nullptr);
+            else
+                k_lat_fma<float><<<1, 32, 0, st>>>(iters, 0.999f, 0.001f, nullptr);
+            unsigned long long ns = 0;
+            if (cudaStreamSynchronize(st) != cudaSuccess ||
+                cudaMemcpyFromSymbol(&ns, g_lat_ns, sizeof(ns)) != cudaSuccess)
+                return RBF_E_CUDA;
+            per = (double)ns / (iters * 8.0);
+        }
+        if (rep > 0 && per < best)
+            best = per;
+    }
+    *h_ns = best;
     return RBF_OK;
 }
 

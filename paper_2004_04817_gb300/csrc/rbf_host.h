@@ -40,3 +40,15 @@ inline uint64_t splitmix64_next(uint64_t *state)
 void fisher_yates(int64_t n, uint64_t seed, int32_t *perm);
 
 }  // namespace rbf
+
+// A factorised support system (rbf_factor_*): the caller-owned arrays it was
+// made from and its workspace, which holds Z = L^-1 of Phi_SS.
+struct rbf_factor {
+    const double *xb;
+    int64_t nb;
+    const int32_t *sel;
+    int64_t nc;
+    double radius;
+    char *ws;
+    size_t ws_bytes;
+};

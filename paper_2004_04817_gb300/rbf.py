@@ -60,6 +60,8 @@ class GreedyStats(C.Structure):
         ("min_pivot", C.c_double),
         ("max_resid", C.c_double),
         ("phase_ns", C.c_int64 * 12),
+        ("barriers", C.c_int64),
+        ("ctas", C.c_int64),
     ]
 
 
@@ -186,6 +188,21 @@ def lib():
         L.rbf_support_kl.restype = C.c_int
         L.rbf_support_kl.argtypes = [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int64,
                                      C.POINTER(C.c_double), _vp, C.c_size_t, _vp]
+        L.rbf_measure_latency.restype = C.c_int
+        L.rbf_measure_latency.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), _vp]
+        L.rbf_factor_workspace_bytes.restype = C.c_size_t
+        L.rbf_factor_workspace_bytes.argtypes = [C.c_int64]
+        L.rbf_factor_create.restype = C.c_int
+        L.rbf_factor_create.argtypes = [_vp, C.c_int64, _vp, C.c_int64, P, _vp, C.c_size_t, _vp,
+                                        C.POINTER(C.c_void_p)]
+        L.rbf_factor_solve.restype = C.c_int
+        L.rbf_factor_solve.argtypes = [_vp, _vp, C.c_int, _vp, C.POINTER(C.c_double), _vp]
+        L.rbf_factor_destroy.restype = None
+        L.rbf_factor_destroy.argtypes = [_vp]
+        L.rbf_deform_volume_adjoint_factored.restype = C.c_int
+        L.rbf_deform_volume_adjoint_factored.argtypes = [_vp, C.c_int64, _vp, _vp, P, _vp,
+                                                         C.POINTER(C.c_double), _vp, C.c_size_t,
+                                                         _vp]
         L.rbf_volume_plan_destroy.restype = None
         L.rbf_volume_plan_destroy.argtypes = [_vp]
         _lib = L
@@ -351,30 +368,99 @@ def adjoint(xv, xb, sel_idx, gv, *, radius, eval_prec=PREC_F32X2, refine_steps=2
     return gc, res.value
 
 
+class Factor:
+    """Phi_SS factorised once for a support set (``rbf_factor_*``): ``solve``
+    then costs Z^T Z B plus FP64 refinement instead of a new factorisation.
+    ``xb`` and ``sel_idx`` must stay alive and unchanged while it is used."""
+
+    def __init__(self, xb, sel_idx, *, radius, stream=None):
+        L = lib()
+        _dev(xb, torch.float64, "xb", 3)
+        _dev(sel_idx, torch.int32, "sel_idx")
+        self.xb, self.sel_idx = xb, sel_idx
+        self.nc = sel_idx.numel()
+        self.radius = float(radius)
+        need = L.rbf_factor_workspace_bytes(self.nc)
+        if need == 0:
+            raise RBFError(1, "rbf_factor_workspace_bytes")
+        self.ws = _workspace(need, xb.device)
+        p = make_params(radius)
+        h = C.c_void_p()
+        _check(L.rbf_factor_create(_ptr(xb), xb.shape[0], _ptr(sel_idx), self.nc, C.byref(p),
+                                   _ptr(self.ws), self.ws.numel(), _stream(stream), C.byref(h)),
+               "rbf_factor_create")
+        self.handle = h
+
+    def solve(self, rhs, *, refine_steps=2, stream=None):
+        """X with Phi_SS X = rhs (nc, 3); returns (X, max residual)."""
+        _dev(rhs, torch.float64, "rhs", 3)
+        x = torch.empty_like(rhs)
+        res = C.c_double(0.0)
+        _check(lib().rbf_factor_solve(self.handle, _ptr(rhs), int(refine_steps), _ptr(x),
+                                      C.byref(res), _stream(stream)), "rbf_factor_solve")
+        return x, res.value
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().rbf_factor_destroy(self.handle)
+            self.handle = None
+
+
+def adjoint_factored(xv, gv, factor, *, eval_prec=PREC_F32X2, refine_steps=2, stream=None,
+                     workspace=None):
+    """``adjoint`` with the support system of ``factor`` (no refactorisation)."""
+    L = lib()
+    _dev(xv, torch.float64, "xv", 3)
+    _dev(gv, torch.float64, "gv", 3)
+    nv, nc = xv.shape[0], factor.nc
+    p = make_params(factor.radius, eval_prec=eval_prec, refine_steps=refine_steps)
+    need = L.rbf_adjoint_workspace_bytes(nv, nc)
+    if need == 0:
+        raise RBFError(1, "rbf_adjoint_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xv.device)
+    gc = torch.empty((nc, 3), dtype=torch.float64, device=xv.device)
+    res = C.c_double(0.0)
+    _check(L.rbf_deform_volume_adjoint_factored(_ptr(xv), nv, _ptr(gv), factor.handle,
+                                                C.byref(p), _ptr(gc), C.byref(res), _ptr(ws),
+                                                ws.numel(), _stream(stream)),
+           "rbf_deform_volume_adjoint_factored")
+    return gc, res.value
+
+
 class RBFDeform(torch.autograd.Function):
     """d_v = Phi_vc Phi_cc^-1 d_c as a differentiable map of the support
-    displacements d_c (nc, 3); the backward pass is the adjoint kernel."""
+    displacements d_c (nc, 3); the backward pass is the adjoint kernel.  With
+    a ``Factor`` of the support set both passes reuse its factorisation."""
 
     @staticmethod
-    def forward(ctx, dc, xv, xb, sel_idx, radius, eval_prec):
-        w, _ = solve_system(xb, sel_idx, dc.detach().contiguous(), radius=radius)
+    def forward(ctx, dc, xv, xb, sel_idx, radius, eval_prec, factor):
+        rhs = dc.detach().contiguous()
+        if factor is not None:
+            w, _ = factor.solve(rhs)
+        else:
+            w, _ = solve_system(xb, sel_idx, rhs, radius=radius)
         dv = deform_volume(xv, xb, sel_idx, w, radius=radius, eval_prec=eval_prec)
         ctx.save_for_backward(xv, xb, sel_idx)
         ctx.radius = radius
         ctx.eval_prec = eval_prec
+        ctx.factor = factor
         return dv
 
     @staticmethod
     def backward(ctx, gv):
         xv, xb, sel_idx = ctx.saved_tensors
         prec = PREC_F32 if ctx.eval_prec == PREC_F32 else PREC_F32X2
-        gc, _ = adjoint(xv, xb, sel_idx, gv.contiguous(), radius=ctx.radius, eval_prec=prec)
-        return gc, None, None, None, None, None
+        if ctx.factor is not None:
+            gc, _ = adjoint_factored(xv, gv.contiguous(), ctx.factor, eval_prec=prec)
+        else:
+            gc, _ = adjoint(xv, xb, sel_idx, gv.contiguous(), radius=ctx.radius, eval_prec=prec)
+        return gc, None, None, None, None, None, None
 
 
-def deform(dc, xv, xb, sel_idx, *, radius, eval_prec=PREC_F32X2):
+def deform(dc, xv, xb, sel_idx, *, radius, eval_prec=PREC_F32X2, factor=None):
     """Differentiable volume deformation (see RBFDeform)."""
-    return RBFDeform.apply(dc, xv, xb, sel_idx, float(radius), int(eval_prec))
+    return RBFDeform.apply(dc, xv, xb, sel_idx, float(radius), int(eval_prec), factor)
 
 
 def deform_volume(xv, xb, sel_idx, w, *, radius, eval_prec=PREC_F32, stream=None,
@@ -464,6 +550,18 @@ def support_kl(xb, sel1, sel2, *, stream=None, workspace=None):
                             C.byref(kl), _ptr(ws), ws.numel(), _stream(stream)),
            "rbf_support_kl")
     return kl.value
+
+
+LAT_GRID_BARRIER, LAT_FP64_WARP, LAT_FP32_WARP = 1, 2, 3
+
+
+def measure_latency(what, param=0, stream=None):
+    """Nanoseconds per grid barrier among `param` CTAs (LAT_GRID_BARRIER) or
+    per FMA instruction of a lone warp (LAT_FP64_WARP, LAT_FP32_WARP)."""
+    ns = C.c_double(0.0)
+    _check(lib().rbf_measure_latency(int(what), int(param), C.byref(ns), _stream(stream)),
+           "rbf_measure_latency")
+    return ns.value
 
 
 def measure_fma_peak(prec=32, stream=None):

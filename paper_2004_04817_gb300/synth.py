@@ -140,6 +140,26 @@ def wing_bending_twist(pts, *, span=SPAN, root_chord=ROOT_CHORD, taper=TAPER,
     return d
 
 
+def wing_sine_mode(pts, *, span=SPAN, root_chord=ROOT_CHORD, taper=TAPER,
+                   sweep_deg=SWEEP_DEG, twist_max_deg=30.0):
+    """The paper's bending-twisting mode of Sec. 4.1 (Eqs. 7-8) in this
+    module's axes (y spanwise, z up): bending dz = 0.05 y sin(pi y / (2 b))
+    and twist theta = theta_m sin(pi y / (2 b)) about the quarter-chord line,
+    with b the root chord and theta_m = 30 deg.  Returns (n, 3) float64."""
+    p = np.asarray(pts, dtype=np.float64)
+    b = root_chord
+    y = np.clip(p[:, 1], 0.0, span)
+    s = np.sin(np.pi * y / (2.0 * b))
+    c = chord_at(y, span, root_chord, taper)
+    xqc = leading_edge_x(y, sweep_deg) + 0.25 * c
+    th = math.radians(twist_max_deg) * s
+    dx = p[:, 0] - xqc
+    d = np.zeros_like(p)
+    d[:, 0] = dx * (np.cos(th) - 1.0) + p[:, 2] * np.sin(th)
+    d[:, 2] = -dx * np.sin(th) + p[:, 2] * (np.cos(th) - 1.0) + 0.05 * p[:, 1] * s
+    return d
+
+
 # ----------------------------------------------------------------------------
 # Volume points
 # ----------------------------------------------------------------------------
@@ -351,6 +371,41 @@ def wbnp_case(n_vol=10_000_000, *, density=1.0, vol_seed=3, radius=6.0, tol_rel=
                                   d_max=1.5 * WBNP_WING_SCALE)
     return dict(xb=xb, db=db, xv=xv, labels=lab, radius=float(radius),
                 tol_rel=float(tol_rel), name=f"wbnp{len(xb)}")
+
+
+def wbnp_sine_mode(pts):
+    """The paper's mode of Sec. 4.2 (Eq. 10) on the assembly, in this module's
+    axes: every surface node moves vertically by
+    dz = 0.3 c (y / b)^2 sin(8 pi y / b), b the span (3) and c the mean
+    aerodynamic chord of the 3x-scale wing, 2/3 c_r (1 + l + l^2) / (1 + l)."""
+    p = np.asarray(pts, dtype=np.float64)
+    b = WBNP_WING_SCALE * SPAN
+    cr = WBNP_WING_SCALE * ROOT_CHORD
+    mac = 2.0 / 3.0 * cr * (1.0 + TAPER + TAPER ** 2) / (1.0 + TAPER)
+    d = np.zeros_like(p)
+    d[:, 2] = 0.3 * mac * (p[:, 1] / b) ** 2 * np.sin(8.0 * np.pi * p[:, 1] / b)
+    return d
+
+
+def wing_paper_mode_case(n_span=16, n_chord=125, n_vol=20_000, *, vol_seed=0,
+                         radius=7.0, tol_abs=1e-6):
+    """The synthetic wing under the Sec. 4.1 mode (Eqs. 7-8) with the paper's
+    radius 7 and absolute tolerance 1e-6; box volume points as configuration 1."""
+    c = wing_case(n_span, n_chord, n_vol, vol_seed=vol_seed, vol_kind="box", radius=radius)
+    c["db"] = wing_sine_mode(c["xb"])
+    c["tol_abs"] = float(tol_abs)
+    c["name"] = f"wing{n_span}x{n_chord}-eq7-8"
+    return c
+
+
+def wbnp_paper_mode_case(n_vol=0, *, density=1.0, vol_seed=3, radius=5.0, tol_abs=2e-6):
+    """The assembly under the Sec. 4.2 mode (Eq. 10) with the paper's radius 5
+    and absolute tolerance 2e-6."""
+    c = wbnp_case(n_vol, density=density, vol_seed=vol_seed, radius=radius)
+    c["db"] = wbnp_sine_mode(c["xb"])
+    c["tol_abs"] = float(tol_abs)
+    c["name"] = f"wbnp{len(c['xb'])}-eq10"
+    return c
 
 
 def random_cloud(n, seed, scale=1.0):

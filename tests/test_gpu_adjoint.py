@@ -101,3 +101,57 @@ def test_adjoint_full_size():
     ref, st = oracle.adjoint(c["xv"], c["xb"], S, c["radius"], gv.cpu().numpy())
     err = np.abs(g.cpu().numpy() - ref).max() / np.abs(ref).max()
     assert err <= 1e-7, err
+
+
+# ---------------------------------------------------------------- factor ----
+def test_factor_solves_match_oracle_and_fresh_solves():
+    c, S, _ = _case(n_vol=0)
+    xb, dS = cuda(c["xb"]), cuda(S, torch.int32)
+    f = P.Factor(xb, dS, radius=c["radius"])
+    # the prescribed displacements: the oracle's weights
+    Wo, st, _ = oracle.solve_weights(c["xb"], c["db"], S, c["radius"])
+    assert st == oracle.OK
+    w, res = f.solve(cuda(c["db"][S]))
+    assert np.abs(w.cpu().numpy() - Wo).max() <= 1e-9 * np.abs(Wo).max()
+    assert res <= 1e-12
+    # several right-hand sides through the same factor: residual of
+    # Phi_SS X = B in FP64, and agreement with a fresh factorisation
+    rng = np.random.default_rng(3)
+    Phi = oracle.phi(np.linalg.norm(c["xb"][S][:, None] - c["xb"][S][None], axis=-1) / c["radius"])
+    for _ in range(3):
+        B = rng.standard_normal((len(S), 3))
+        x, res = f.solve(cuda(B))
+        xh = x.cpu().numpy()
+        assert np.abs(Phi @ xh - B).max() <= 1e-10 * np.abs(B).max()
+        x2, _ = P.solve_system(xb, dS, cuda(B), radius=c["radius"])
+        assert np.abs(xh - x2.cpu().numpy()).max() <= 1e-9 * np.abs(xh).max()
+
+
+@pytest.mark.parametrize("prec", [P.PREC_F32X2, P.PREC_F32])
+def test_factored_adjoint_matches_unfactored_and_oracle(prec):
+    c, S, t = _case()
+    gv = _gv(c, S, t)
+    xb, dS, xv = cuda(c["xb"]), cuda(S, torch.int32), cuda(c["xv"])
+    f = P.Factor(xb, dS, radius=c["radius"])
+    g1, _ = P.adjoint(xv, xb, dS, cuda(gv), radius=c["radius"], eval_prec=prec)
+    g2, res = P.adjoint_factored(xv, cuda(gv), f, eval_prec=prec)
+    g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
+    assert np.abs(g1 - g2).max() <= 1e-9 * np.abs(g1).max()
+    ref, st = oracle.adjoint(c["xv"], c["xb"], S, c["radius"], gv)
+    tol = 1e-8 if prec == P.PREC_F32X2 else 1e-1   # as the unfactored adjoint
+    assert np.abs(g2 - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_deform_autograd_with_factor():
+    c, S, t = _case()
+    xb, dS, xv = cuda(c["xb"]), cuda(S, torch.int32), cuda(c["xv"])
+    f = P.Factor(xb, dS, radius=c["radius"])
+    tt = cuda(t)
+    grads = []
+    for fac in (None, f):
+        dc = cuda(c["db"][S]).requires_grad_(True)
+        dv = P.deform(dc, xv, xb, dS, radius=c["radius"], factor=fac)
+        J = 0.5 * ((dv - tt) ** 2).sum()
+        J.backward()
+        grads.append(dc.grad.cpu().numpy())
+    assert np.abs(grads[0] - grads[1]).max() <= 1e-9 * np.abs(grads[0]).max()

@@ -366,3 +366,19 @@ def test_nearest_support_matches_kdtree():
     S = np.sort(np.random.default_rng(2).choice(3000, 70, replace=False))
     d_ref, _ = cKDTree(xb[S]).query(xb)
     assert np.allclose(oracle.nearest_support(xb, S), d_ref, rtol=1e-14, atol=0)
+
+
+def test_follow_mode_ends_at_the_capacity_of_the_followed_run():
+    # N_c^max caps |S| (Alg. 1's loop bound): a run stopped by the capacity,
+    # followed by the oracle with the same capacity, ends at the same
+    # iteration with the same status and no rejected step
+    c = synth.tiny_wing(n_span=6, n_chord=30, radius=1.0)
+    for m in (1, 4):
+        r = oracle.greedy(c["xb"], c["db"], c["radius"], 0.0, m=m, seed=1, ncmax=40,
+                          history=False)
+        assert r["status"] == oracle.E_NC_MAX and r["nc"] == 40
+        f = oracle.greedy(c["xb"], c["db"], c["radius"], 0.0, m=m, seed=1, ncmax=40,
+                          follow=(r["idx"], r["iter"]), history=False)
+        assert f["status"] == oracle.E_NC_MAX and f["nc"] == 40
+        assert f["stats"]["n_fail"] == 0 and f["stats"]["n_div"] == 0
+        assert f["stats"]["iterations"] == r["stats"]["iterations"]

@@ -474,6 +474,29 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
+// One thread: one arrival that expects `bytes` in total from the copies
+// started next with bulk_copy_g2s (fences as in bulk_g2s).
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// A bulk copy whose bytes count against an expectation set by mbar_expect
+// (no arrival of its own).  `bytes` and both addresses: multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
+                                              unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // Bounded wait for the barrier phase with the given parity; false on timeout.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
                                           uint64_t limit_ns)

@@ -45,10 +45,11 @@ constexpr int kSmemCentresFF = 1024;       // batched launch (64 KB, two CTAs pe
                                            // up to the device's shared-memory limit
 constexpr double kPivotMin = 1e-13;        // d^2 at or below: singular (coincident nodes)
 constexpr int kLookIdle = 8;               // idle iterations before a look-ahead
+constexpr int kLookChunk = 16;             // groups per look-ahead evaluation
 // Pairs one CTA evaluates in about the time of one idle iteration (measured
 // on the 50,000-node wing: 0.76 G double-float pairs/s per CTA, ~13 us per
-// iteration), by precision; a look-ahead runs only when its pairs cost at
-// most half the idle iterations it can skip (see the main loop).
+// iteration), by precision; a look-ahead runs only when scanning one group
+// costs at most half an idle iteration (see the main loop).
 constexpr double kLookPairsFF = 8000.0, kLookPairsF32 = 40000.0, kLookPairsF64 = 400.0;
 constexpr float kU32 = 5.9604645e-8f;      // 2^-24, unit roundoff of FP32
 constexpr float kBetaPhi = 16.0f;          // error-bound factors (see screen_bound)
@@ -128,8 +129,10 @@ struct GreedyArgs {
     int32_t *spos;                // support positions
     D4 *c64;                 // support centres (scaled)
     D4 *w64;                 // weights
-    float4 *cw32;                 // (centre, weight) FP32 pairs, interleaved
-    float4 *cwff;                 // (centre hi, centre lo, weight hi, weight lo) per centre
+    float4 *cw32;                 // FP32 table, 2 planes of ld float4: centres, weights
+    float4 *cwff;                 // double-float table, 4 planes of ld float4: centre hi,
+                                  // centre lo, weight hi, weight lo (planes, so that the
+                                  // lanes of a team read consecutive 16-byte entries)
     D4 *y64;                 // forward-solve vector y = Z dr_S
     double *z;                    // Z = L^-1, row-major, ld
     double *zt;                   // Z^T, row-major, ld
@@ -490,11 +493,11 @@ __device__ __forceinline__ void put_weight(const GreedyArgs &a, int j, const D4 
         split_f64(w.x, hx, lx);
         split_f64(w.y, hy, ly);
         split_f64(w.z, hz, lz);
-        a.cwff[4 * j + 2] = make_float4(hx, hy, hz, fabsf(hx) + fabsf(hy) + fabsf(hz));
-        a.cwff[4 * j + 3] = make_float4(lx, ly, lz, 0.0f);
+        a.cwff[2 * (size_t)a.ld + j] = make_float4(hx, hy, hz, fabsf(hx) + fabsf(hy) + fabsf(hz));
+        a.cwff[3 * (size_t)a.ld + j] = make_float4(lx, ly, lz, 0.0f);
     } else if (a.prec == RBF_PREC_F32) {
         const float fx = (float)w.x, fy = (float)w.y, fz = (float)w.z;
-        a.cw32[2 * j + 1] = make_float4(fx, fy, fz, fabsf(fx) + fabsf(fy) + fabsf(fz));
+        a.cw32[(size_t)a.ld + j] = make_float4(fx, fy, fz, fabsf(fx) + fabsf(fy) + fabsf(fz));
     }
 }
 
@@ -505,10 +508,10 @@ __device__ __forceinline__ void put_centre(const GreedyArgs &a, int j, const D4 
         split_f64(c.x, h0, l0);
         split_f64(c.y, h1, l1);
         split_f64(c.z, h2, l2);
-        a.cwff[4 * j] = make_float4(h0, h1, h2, 0.0f);
-        a.cwff[4 * j + 1] = make_float4(l0, l1, l2, 0.0f);
+        a.cwff[j] = make_float4(h0, h1, h2, 0.0f);
+        a.cwff[(size_t)a.ld + j] = make_float4(l0, l1, l2, 0.0f);
     } else if (a.prec == RBF_PREC_F32) {
-        a.cw32[2 * j] = make_float4((float)c.x, (float)c.y, (float)c.z, 0.0f);
+        a.cw32[j] = make_float4((float)c.x, (float)c.y, (float)c.z, 0.0f);
     }
 }
 
@@ -969,16 +972,23 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         } else {
             // ---- pass 1: FP32 or double-float errors E~ with a bound beta,
             // |E~ - E| <= beta; e64[q] = E~, u32[q] = beta.  The centre table
-            // is staged in shared memory by one bulk (TMA) copy.
+            // is staged in shared memory by bulk (TMA) copies of its planes.
             const bool use_ff = a.prec == RBF_PREC_F32X2;
             const bool smem = nc <= a.smem_cap;
             phase(7);
+            // plane stride: nc in shared memory, ld in global memory
+            const int planes = use_ff ? 4 : 2, wplane = use_ff ? 2 : 1;
+            const int pst = smem ? nc : a.ld;
             if (smem) {
                 const float4 *src = use_ff ? a.cwff : a.cw32;
-                const unsigned bytes = (unsigned)(sizeof(float4) * (use_ff ? 4 : 2) * nc);
+                const unsigned pbytes = (unsigned)(sizeof(float4) * nc);
                 __syncthreads();   // previous readers of the table are done
-                if (tid == 0)
-                    bulk_g2s(s_cw, src, bytes, &s_mbar);
+                if (tid == 0) {
+                    mbar_expect(&s_mbar, pbytes * planes);
+                    for (int k = 0; k < planes; ++k)
+                        bulk_copy_g2s(s_cw + (size_t)k * nc, src + (size_t)k * a.ld, pbytes,
+                                      &s_mbar);
+                }
                 const bool got = mbar_wait(&s_mbar, mbar_phase, a.barrier_ns);
                 if (!got) {
                     // give the copy in flight a second bounded wait before leaving
@@ -991,8 +1001,9 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             if (tid < 32) {
                 float t = 0.0f;
                 for (int j = tid; j < nc; j += 32)
-                    t += smem ? (use_ff ? s_cw[4 * j + 2].w : s_cw[2 * j + 1].w)
-                              : (use_ff ? ldcg(a.cwff + 4 * j + 2).w : ldcg(a.cw32 + 2 * j + 1).w);
+                    // .w of the weight plane (plane 2 double-float, 1 FP32) = |w|_1
+                    t += smem ? s_cw[(size_t)wplane * nc + j].w
+                              : ldcg((use_ff ? a.cwff : a.cw32) + (size_t)wplane * a.ld + j).w;
                 t = team_sum(t, 32);
                 if (tid == 0)
                     s_wabs = t;
@@ -1008,8 +1019,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     const float4 x = ldcg(a.xg32 + (act ? q : p0));
                     float fx = 0.0f, fy = 0.0f, fz = 0.0f, sb = 0.0f;
                     for (int j = sub; j < nc; j += ts) {
-                        const float4 c = smem ? cw[2 * j] : ldcg(cw + 2 * j);
-                        const float4 w = smem ? cw[2 * j + 1] : ldcg(cw + 2 * j + 1);
+                        const float4 c = smem ? cw[j] : ldcg(cw + j);
+                        const float4 w = smem ? cw[pst + j] : ldcg(cw + pst + j);
                         const float dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
                         const float ph = phi_f32_s(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
                         fx = fmaf(w.x, ph, fx);
@@ -1080,14 +1091,14 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     int j = sub;
                     for (; j + ts < nc; j += 2 * ts) {
                         const int j2 = j + ts;
-                        const float4 ch0 = smem ? cw[4 * j] : ldcg(cw + 4 * j);
-                        const float4 cl0 = smem ? cw[4 * j + 1] : ldcg(cw + 4 * j + 1);
-                        const float4 wh0 = smem ? cw[4 * j + 2] : ldcg(cw + 4 * j + 2);
-                        const float4 wl0 = smem ? cw[4 * j + 3] : ldcg(cw + 4 * j + 3);
-                        const float4 ch1 = smem ? cw[4 * j2] : ldcg(cw + 4 * j2);
-                        const float4 cl1 = smem ? cw[4 * j2 + 1] : ldcg(cw + 4 * j2 + 1);
-                        const float4 wh1 = smem ? cw[4 * j2 + 2] : ldcg(cw + 4 * j2 + 2);
-                        const float4 wl1 = smem ? cw[4 * j2 + 3] : ldcg(cw + 4 * j2 + 3);
+                        const float4 ch0 = smem ? cw[j] : ldcg(cw + j);
+                        const float4 cl0 = smem ? cw[pst + j] : ldcg(cw + pst + j);
+                        const float4 wh0 = smem ? cw[2 * pst + j] : ldcg(cw + 2 * pst + j);
+                        const float4 wl0 = smem ? cw[3 * pst + j] : ldcg(cw + 3 * pst + j);
+                        const float4 ch1 = smem ? cw[j2] : ldcg(cw + j2);
+                        const float4 cl1 = smem ? cw[pst + j2] : ldcg(cw + pst + j2);
+                        const float4 wh1 = smem ? cw[2 * pst + j2] : ldcg(cw + 2 * pst + j2);
+                        const float4 wl1 = smem ? cw[3 * pst + j2] : ldcg(cw + 3 * pst + j2);
                         const ff2 s2 = dist2_ff2(bxh, bxl, byh, byl, bzh, bzl,
                                                  f2_pack(ch0.x, ch1.x), f2_pack(cl0.x, cl1.x),
                                                  f2_pack(ch0.y, ch1.y), f2_pack(cl0.y, cl1.y),
@@ -1101,10 +1112,10 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         sb = fmaf(wh1.w, p1, fmaf(wh0.w, p0, sb));
                     }
                     if (j < nc) {
-                        const float4 ch = smem ? cw[4 * j] : ldcg(cw + 4 * j);
-                        const float4 cl = smem ? cw[4 * j + 1] : ldcg(cw + 4 * j + 1);
-                        const float4 wh = smem ? cw[4 * j + 2] : ldcg(cw + 4 * j + 2);
-                        const float4 wl = smem ? cw[4 * j + 3] : ldcg(cw + 4 * j + 3);
+                        const float4 ch = smem ? cw[j] : ldcg(cw + j);
+                        const float4 cl = smem ? cw[pst + j] : ldcg(cw + pst + j);
+                        const float4 wh = smem ? cw[2 * pst + j] : ldcg(cw + 2 * pst + j);
+                        const float4 wl = smem ? cw[3 * pst + j] : ldcg(cw + 3 * pst + j);
                         const ff s2 = dist2_ff(qxh, qxl, qyh, qyl, qzh, qzl, ch.x, cl.x, ch.y,
                                                cl.y, ch.z, cl.z);
                         const ff ph = phi_ff_s(s2);
@@ -1406,10 +1417,10 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     double run_max = 0.0, run_sq = 0.0;
     int status = RBF_OK;
     const bool hist_full = a.hist != nullptr && (a.flags & RBF_FLAG_HISTORY_FULL) != 0;
-    // every node's error and bound in e64/u32 come from the current weights
-    // (set by a look-ahead, cleared by an append): later look-aheads of the
-    // same idle run only scan them
-    bool look_cached = false;
+    // groups of the iterations before scan_end_k were scanned by a look-ahead
+    // with the current weights (their errors and bounds are in e64/u32); an
+    // append clears it
+    long long scan_end_k = 0;
     for (;; ++k) {
         const int gi = (int)(k % m);
         const int g0 = goff(gi, nb, m), g1 = goff(gi + 1, nb, m);
@@ -1441,7 +1452,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             idle = 0;
             run_max = 0.0;
             run_sq = 0.0;
-            look_cached = false;
+            scan_end_k = 0;
         } else {
             ++idle;
             run_max = fmax(run_max, eo.gmax);
@@ -1476,40 +1487,65 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         // the run ends where m idle iterations would end it.  A later
         // look-ahead of the same idle run (a flagged group whose nodes all
         // turned out <= E*) only scans the stored errors and bounds.
-        // An all-node evaluation pays only when it is cheap against the idle
-        // iterations it can skip: N_b N_c pairs on G CTAs against (m - idle)
-        // iterations (a deterministic model, so every CTA decides alike).
+        // Look-ahead over an idle run: the weights cannot change until the
+        // next append, so the groups still to come are scanned in chunks of
+        // kLookChunk groups, in their cyclic order, with the current weights,
+        // up to the first group holding a node possibly above E* (upper bound
+        // E~ + beta > E*); the iterations before it would add nothing and are
+        // certified without their own evaluation.  With none before the run
+        // would end (m idle iterations), it ends here.  Chunks scanned earlier
+        // in the same idle run are read back from the stored errors.  A
+        // scan pays only when one group's pairs cost at most half an idle
+        // iteration (a deterministic model, so every CTA decides alike).
         const double look_rate = a.prec == RBF_PREC_F32X2 ? kLookPairsFF
                                  : a.prec == RBF_PREC_F32 ? kLookPairsF32
                                                           : kLookPairsF64;
         const bool look_pays =
-            look_cached || (double)nb * (double)nc <= 0.5 * look_rate * G * (double)(m - idle);
+            (double)((nb + m - 1) / m) * (double)nc <= 0.5 * look_rate * G;
         if (idle >= kLookIdle && m > 2 * kLookIdle && !hist_full && look_pays) {
-            const int nxt = (int)((k + 1) % m);
-            const int start = goff(nxt, nb, m);
-            EvalOut la;
-            if (!evaluate(0, nb, false, false, la, start, look_cached))
-                return;
-            if (!look_cached)
-                ++nfull;
-            look_cached = true;
-            long long skip;   // idle iterations certified without evaluation
-            if (la.first == kNoRank) {
-                skip = m - idle;
-                run_max = la.gmax;
-                run_sq = la.gsq;
-            } else {
-                const int pos = (int)((start + la.first) % nb);
-                const int base = nb / m, rem = nb % m;
-                const int g = pos < rem * (base + 1) ? pos / (base + 1)
-                                                     : rem + (pos - rem * (base + 1)) / base;
-                skip = ((long long)g - nxt + m) % m;
-                if (idle + skip >= m) {
-                    skip = m - idle;
+            const long long k_last = k + (m - idle);   // the literal run's last iteration
+            long long ks = k + 1, found = -1;
+            bool fresh = false;
+            // chunks while ks <= k_last; then, with no candidate, one pass over
+            // the stored errors of every node (each group was evaluated or
+            // scanned with these weights in this idle run) for the run's
+            // certified maximum and RMS.  One call site keeps the kernel small.
+            for (;;) {
+                const bool final_pass = ks > k_last;
+                const int g0 = final_pass ? 0 : (int)(ks % m);
+                const bool cached = final_pass || ks < scan_end_k;
+                long long ke = min(ks + (long long)kLookChunk, k_last + 1);
+                ke = min(ke, ks + (long long)(m - g0));   // no wrap inside a chunk
+                if (cached && !final_pass)
+                    ke = min(ke, scan_end_k);
+                const int p0 = final_pass ? 0 : goff(g0, nb, m);
+                const int p1 = final_pass ? nb : goff(g0 + (int)(ke - ks), nb, m);
+                EvalOut la;
+                if (!evaluate(p0, p1, false, false, la, p0, cached))
+                    return;
+                if (final_pass) {
                     run_max = la.gmax;
                     run_sq = la.gsq;
+                    break;
                 }
+                if (!cached) {
+                    scan_end_k = ke;
+                    fresh = true;
+                }
+                if (la.first != kNoRank) {
+                    const int pos = p0 + (int)la.first;
+                    const int base = nb / m, rem = nb % m;
+                    const int g = pos < rem * (base + 1) ? pos / (base + 1)
+                                                         : rem + (pos - rem * (base + 1)) / base;
+                    found = ks + (g - g0);
+                    break;
+                }
+                ks = ke;
             }
+            if (fresh)
+                ++nfull;
+            // idle iterations certified without evaluation
+            const long long skip = found >= 0 ? found - (k + 1) : m - idle;
             if (g_vb == 0 && tid == 0 && a.hist)
                 for (long long s2 = 1; s2 <= skip && nhist + s2 - 1 < a.hist_cap; ++s2) {
                     double *h = a.hist + RBF_HIST_COLS * (nhist + s2 - 1);

@@ -112,7 +112,7 @@ __device__ __forceinline__ f2 phi_f32x2_s(f2 s)
 // sum) and Dekker (FastTwoSum for |a| >= |b|; the exact error of a product
 // through one fused multiply-add).  The __f*_rn intrinsics keep the compiler
 // from contracting or reordering the steps whose rounding the method needs.
-// On GB300 an ff pair costs ~150 FP32 instructions, 20x less time than the
+// On GB300 an ff pair costs ~110 FP32 instructions (paired), 20x less time than the
 // same pair in native FP64 (FP64 runs at 1/64 of the FP32 rate).
 // ----------------------------------------------------------------------------
 struct ff {

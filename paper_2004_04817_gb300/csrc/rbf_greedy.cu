@@ -4,11 +4,14 @@
 // One cooperative launch runs the whole loop on the device:
 //   prologue : pack the boundary nodes in group order (groups contiguous),
 //              E* = tol * max |dr| if relative, three seed nodes, append them;
-//   iteration: errors E_q in the active group G_(k mod m) (FP64, or FP32 with
-//              an error bound and an FP64 re-score of every node whose bound
-//              reaches the maximum), grid argmax (lowest node on ties), append
-//              when E > E*, full check of all N_b errors after every m-th
-//              iteration and whenever a group adds nothing.
+//   iteration: errors E_q in the active group G_(k mod m) (FP64, or FP32 /
+//              double-float with an error bound, certified from the bounds or
+//              by an FP64 re-score of every node whose bound reaches the
+//              leader's), grid argmax (lowest node on ties), append when
+//              E > E*; the run stops after m consecutive iterations without an
+//              append (they visited every node with one set of weights), and
+//              idle runs are shortened by look-ahead scans that certify the
+//              iterations before the next group able to append.
 // The Cholesky factor of Phi_SS grows by one row per appended node (the
 // recurrence Cholesky of Sec. 1).  The kernel keeps Z = L^-1 (and Z^T) in
 // FP64, so an append is two matrix-vector products (l = Z b, u = Z^T l) that

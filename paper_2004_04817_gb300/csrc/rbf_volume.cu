@@ -1,11 +1,15 @@
 // rbf_volume.cu -- volume displacement sum (Eq. 6 of arXiv:2004.04817):
 //     dv_v = sum_{j in S} w_j phi(|x_v - r_j| / R),  v = 1..N_v.
 //
-// FP32 kernel: every thread owns Q volume points (coordinates pre-scaled by
-// 1/R, float4 loads), centres and weights are staged in shared memory in
-// tiles and read as broadcast float4 pairs, so a pair costs ~15 FP32-pipe
-// instructions plus one MUFU square root and no memory traffic.
-// FP64 kernel: the same structure in double precision (reference arithmetic).
+// FP32 kernel: every thread owns 4 volume points (coordinates pre-scaled by
+// 1/R) in paired registers, centres and weights are staged in shared memory
+// in tiles and read as broadcasts, so a pair costs ~16 FP32-pipe
+// instructions including one MUFU square root and no memory traffic.
+// Double-float kernel: the same structure with every value an unevaluated
+// sum of two floats (~110 FP32-pipe instructions per pair, FP64-level
+// results).  FP64 kernel: the same structure in double precision (reference
+// arithmetic).  The traffic is the packed points: the kernels are bound by
+// the FP32 pipe.
 #include <algorithm>
 #include <cstdint>
 #include <vector>

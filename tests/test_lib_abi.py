@@ -78,3 +78,50 @@ def test_partition_matches_oracle_bit_exact(nb, m, seed):
 def test_partition_rejects_bad_sizes():
     with pytest.raises(P.RBFError):
         P.group_of(10, 11, 0)
+
+
+def test_newer_entry_points_reject_bad_arguments_before_touching_a_device():
+    L = P.lib()
+    E_ARG, E_WS = 1, 5
+    fake = C.c_void_p(256)   # never dereferenced: every call below fails its checks first
+    # culled volume plans
+    p32 = rbf.make_params(0.25, eval_prec=32, nc_max=100)
+    assert L.rbf_volume_plan_workspace_bytes(1000, C.byref(p32)) > 0
+    for bad in (rbf.make_params(0.25, eval_prec=64, nc_max=100),     # precision
+                rbf.make_params(0.25, eval_prec=32, nc_max=0)):      # capacity
+        assert L.rbf_volume_plan_workspace_bytes(1000, C.byref(bad)) == 0
+    assert L.rbf_volume_plan_workspace_bytes(0, C.byref(p32)) == 0
+    h = C.c_void_p()
+    assert L.rbf_volume_plan_create(None, 1000, C.byref(p32), fake, 1 << 20, None,
+                                    C.byref(h)) == E_ARG
+    bad_r = rbf.make_params(-1.0, eval_prec=32, nc_max=100)
+    assert L.rbf_volume_plan_create(fake, 1000, C.byref(bad_r), fake, 1 << 20, None,
+                                    C.byref(h)) == E_ARG
+    assert L.rbf_volume_plan_create(fake, 1000, C.byref(p32), None, 0, None,
+                                    C.byref(h)) == E_WS
+    assert L.rbf_volume_plan_run(None, fake, fake, 10, fake, fake, None, None) == E_ARG
+    # support-set KL divergence
+    assert L.rbf_support_kl_workspace_bytes(0) == 0
+    kl = C.c_double(0.0)
+    assert L.rbf_support_kl(fake, 0, fake, 3, fake, 3, C.byref(kl), fake, 1 << 20,
+                            None) == E_ARG
+    assert L.rbf_support_kl(fake, 100, fake, 0, fake, 3, C.byref(kl), fake, 1 << 20,
+                            None) == E_ARG
+    assert L.rbf_support_kl(fake, 100, fake, 3, fake, 3, C.byref(kl), None, 0, None) == E_WS
+    assert L.rbf_nearest_support(fake, 100, fake, 0, fake, None) == E_ARG
+    # factor objects and the factored adjoint
+    assert L.rbf_factor_workspace_bytes(0) == 0
+    assert L.rbf_factor_workspace_bytes(300) > 8 * 300 * 300
+    pf = rbf.make_params(2.0)
+    assert L.rbf_factor_create(fake, 1000, fake, 300, C.byref(pf), fake, 1 << 30, None,
+                               None) == E_ARG
+    assert L.rbf_factor_create(fake, 1000, fake, 300, C.byref(pf), None, 0, None,
+                               C.byref(h)) == E_WS
+    res = C.c_double(0.0)
+    assert L.rbf_factor_solve(None, fake, 2, fake, C.byref(res), None) == E_ARG
+    pa = rbf.make_params(2.0, eval_prec=48)
+    assert L.rbf_deform_volume_adjoint_factored(fake, 10, fake, None, C.byref(pa), fake,
+                                                C.byref(res), fake, 1 << 20, None) == E_ARG
+    # latency microbenchmarks
+    assert L.rbf_measure_latency(99, 0, C.byref(res), None) == E_ARG
+    assert L.rbf_measure_latency(1, 64, None, None) == E_ARG

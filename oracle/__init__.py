@@ -72,6 +72,11 @@ def lib():
                                   C.c_int]
         L.orc_num_threads.restype = C.c_int
         L.orc_nearest_support.argtypes = [dp, C.c_int64, ip, C.c_int64, dp, C.c_int]
+        L.orc_greedy_peaks.restype = C.c_int
+        L.orc_greedy_peaks.argtypes = [dp, dp, C.c_int64, C.c_double, C.c_double, C.c_int64,
+                                       C.c_uint64, C.c_int64, C.c_int64, C.c_double, ip,
+                                       C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                       C.POINTER(C.c_int64), C.c_int]
         L.orc_support_kl.restype = C.c_int
         L.orc_support_kl.argtypes = [dp, C.c_int64, ip, C.c_int64, ip, C.c_int64,
                                      C.POINTER(C.c_double), C.c_int]
@@ -217,6 +222,28 @@ def adjoint(xv, xb, S, R, gv, threads=None):
     st = L.orc_adjoint(pv, len(xv), px, ps, len(S), float(R), pg,
                        gc.ctypes.data_as(C.POINTER(C.c_double)), threads or default_threads())
     return gc, st
+
+
+def greedy_peaks(xb, db, R, Estar, m=1, seed=1, ncmax=None, peaks=1, sep=0.0, threads=None):
+    """Peak-selection variant: up to ``peaks`` separated nodes (at least ``sep``
+    apart) appended per iteration.  Returns dict(status, idx, iter, nc,
+    iterations)."""
+    L = lib()
+    xb, px = _d(xb)
+    db, pd = _d(db)
+    nb = len(xb)
+    ncmax = int(ncmax or nb)
+    out_idx = np.zeros(ncmax, dtype=np.int32)
+    out_it = np.zeros(ncmax, dtype=np.int64)
+    nc = C.c_int64(0)
+    its = C.c_int64(0)
+    st = L.orc_greedy_peaks(px, pd, nb, float(R), float(Estar), int(m), int(seed), ncmax,
+                            int(peaks), float(sep), out_idx.ctypes.data_as(C.POINTER(C.c_int32)),
+                            out_it.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(nc),
+                            C.byref(its), threads or default_threads())
+    n = nc.value
+    return dict(status=st, idx=out_idx[:n].copy(), iter=out_it[:n].copy(), nc=n,
+                iterations=its.value)
 
 
 def nearest_support(xb, S, threads=None):

@@ -534,6 +534,112 @@ int orc_adjoint(const double *xv, int64_t nv, const double *xb, const int32_t *S
 }
 
 /* ------------------------------------------------------------------------ */
+/* Peak-selection variant (prior art cited in Sec. 1: several error-peak     */
+/* nodes added at a time).  Reading: in iteration k the nodes of G_(k mod m) */
+/* outside S with E > E* are taken in decreasing E (lowest index on ties),   */
+/* each only if it lies at least `sep` from every node already taken in this */
+/* iteration, up to `peaks` nodes; they are appended in that order.  peaks   */
+/* = 1 is Algorithm 1.  Termination as orc_greedy: m consecutive iterations  */
+/* without an append.  Literal algorithm only (no follow mode, no history).  */
+/* ------------------------------------------------------------------------ */
+int orc_greedy_peaks(const double *xb, const double *db, int64_t nb, double R, double Estar,
+                     int64_t m, uint64_t seed, int64_t ncmax, int64_t peaks, double sep,
+                     int32_t *out_idx, int64_t *out_iter, int64_t *out_nc,
+                     int64_t *out_iterations, int nthreads)
+{
+    if (nb < 3 || m < 1 || m > nb || ncmax < 3 || !(R > 0.0) || !(Estar >= 0.0) || peaks < 1 ||
+        !(sep >= 0.0))
+        return ORC_E_ARG;
+    int32_t *group_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    int32_t *members = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    int64_t *goff = (int64_t *)calloc((size_t)m + 1, sizeof(int64_t));
+    char *inS = (char *)calloc((size_t)nb, 1);
+    char *used = (char *)calloc((size_t)nb, 1);
+    double *E = (double *)malloc(sizeof(double) * (size_t)nb);
+    double *W = (double *)malloc(sizeof(double) * 3 * (size_t)ncmax);
+    int32_t *taken = (int32_t *)malloc(sizeof(int32_t) * (size_t)peaks);
+    if (!group_of || !members || !goff || !inS || !used || !E || !W || !taken) {
+        free(group_of); free(members); free(goff); free(inS); free(used); free(E); free(W);
+        free(taken);
+        return ORC_E_NOMEM;
+    }
+    /* partition and seed nodes exactly as orc_greedy */
+    orc_groups(nb, m, seed, group_of);
+    for (int64_t j = 0; j < nb; ++j)
+        goff[group_of[j] + 1]++;
+    for (int64_t g = 0; g < m; ++g)
+        goff[g + 1] += goff[g];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+        for (int64_t g = 0; g < m; ++g)
+            fill[g] = goff[g];
+        for (int64_t j = 0; j < nb; ++j)
+            members[fill[group_of[j]]++] = (int32_t)j;
+        free(fill);
+    }
+    int32_t seeds[3];
+    orc_seed_nodes(xb, db, nb, seeds);
+    int64_t nc = 0;
+    for (int s = 0; s < 3; ++s) {
+        out_idx[nc] = seeds[s];
+        out_iter[nc] = -1;
+        inS[seeds[s]] = 1;
+        ++nc;
+    }
+    int status = ORC_OK;
+    int64_t idle = 0, k = 3;
+    for (;; ++k) {
+        double mp;
+        int st = orc_solve_weights(xb, db, out_idx, nc, R, W, &mp);
+        if (st != ORC_OK) { status = st; break; }
+        int64_t gi = k % m;
+        int64_t g0 = goff[gi], gn = goff[gi + 1] - goff[gi];
+        node_errors(xb, db, members + g0, gn, out_idx, nc, W, R, E, nthreads);
+        /* take peaks: largest E first, separated by at least sep */
+        int64_t nt = 0;
+        for (int64_t r = 0; r < peaks; ++r) {
+            double best = -1.0;
+            int64_t bt = -1;
+            for (int64_t t = 0; t < gn; ++t) {
+                int32_t q = members[g0 + t];
+                if (inS[q] || used[q] || !(E[t] > Estar) || !(E[t] > best))
+                    continue;   /* ascending q: the lowest index wins ties */
+                int far = 1;
+                for (int64_t u = 0; u < nt; ++u)
+                    if (dist3(xb + 3 * q, xb + 3 * taken[u]) < sep) { far = 0; break; }
+                if (far) { best = E[t]; bt = t; }
+            }
+            if (bt < 0)
+                break;
+            taken[nt++] = members[g0 + bt];
+            used[members[g0 + bt]] = 1;
+        }
+        for (int64_t u = 0; u < nt; ++u)
+            used[taken[u]] = 0;
+        if (nt == 0) {
+            if (++idle >= m)
+                break;
+            continue;
+        }
+        idle = 0;
+        for (int64_t u = 0; u < nt; ++u) {
+            if (nc >= ncmax) { status = ORC_E_NC_MAX; break; }
+            out_idx[nc] = taken[u];
+            out_iter[nc] = k;
+            inS[taken[u]] = 1;
+            ++nc;
+        }
+        if (status != ORC_OK)
+            break;
+    }
+    *out_nc = nc;
+    *out_iterations = k - 3 + 1;
+    free(group_of); free(members); free(goff); free(inS); free(used); free(E); free(W);
+    free(taken);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Kullback-Leibler divergence of two support sets (Sec. 4.1):              */
 /*   KL(S1 || S2) = sum_{i=1..N_b} d1_i log(d1_i / d2_i),                     */
 /*   dk_i = min over j in Sk of |r_i - r_j|  (every boundary node i).        */

@@ -382,3 +382,65 @@ def test_follow_mode_ends_at_the_capacity_of_the_followed_run():
         assert f["status"] == oracle.E_NC_MAX and f["nc"] == 40
         assert f["stats"]["n_fail"] == 0 and f["stats"]["n_div"] == 0
         assert f["stats"]["iterations"] == r["stats"]["iterations"]
+
+
+# --------------------------------------------------------------------------
+# Peak-selection variant (several separated error peaks per iteration)
+# --------------------------------------------------------------------------
+def _peaks_reference(xb, db, R, Estar, m, peaks, sep):
+    """The peak-selection reading written independently with numpy: dense
+    solve per iteration, errors of the active group, separated peaks in
+    decreasing error (lowest index on ties).  Partition and seed nodes come
+    from the oracle routines pinned above."""
+    nb = len(xb)
+    grp = oracle.groups(nb, m, 1)
+    S = list(oracle.seed_nodes(xb, db))
+    it = [-1, -1, -1]
+    idle, k = 0, 3
+    phi = lambda d: np.where(d < 1.0, (1.0 - d) ** 4 * (4.0 * d + 1.0), 0.0)
+    while True:
+        A = phi(np.linalg.norm(xb[S][:, None] - xb[S][None], axis=-1) / R)
+        W = np.linalg.solve(A, db[S])
+        members = np.flatnonzero(grp == k % m)
+        members = members[~np.isin(members, S)]
+        F = phi(np.linalg.norm(xb[members][:, None] - xb[S][None], axis=-1) / R) @ W
+        E = np.linalg.norm(db[members] - F, axis=1)
+        order = sorted(range(len(members)), key=lambda t: (-E[t], members[t]))
+        taken = []
+        for t in order:
+            if len(taken) == peaks or not E[t] > Estar:
+                break
+            if all(np.linalg.norm(xb[members[t]] - xb[u]) >= sep for u in taken):
+                taken.append(members[t])
+        if not taken:
+            idle += 1
+            if idle >= m:
+                return np.array(S), np.array(it), k - 3 + 1
+        else:
+            idle = 0
+            S += taken
+            it += [k] * len(taken)
+        k += 1
+
+
+@pytest.mark.parametrize("m,peaks,sep", [(1, 3, 0.3), (3, 4, 0.25), (5, 2, 0.0)])
+def test_peaks_oracle_matches_independent_reference(m, peaks, sep):
+    c = synth.tiny_wing(n_span=5, n_chord=24, radius=1.0)
+    estar = oracle.tolerance(c["db"], 3e-3)
+    r = oracle.greedy_peaks(c["xb"], c["db"], c["radius"], estar, m=m, peaks=peaks, sep=sep)
+    S, it, iters = _peaks_reference(c["xb"], c["db"], c["radius"], estar, m, peaks, sep)
+    assert r["status"] == oracle.OK
+    assert r["idx"].tolist() == S.tolist()
+    assert r["iter"].tolist() == it.tolist()
+    assert r["iterations"] == iters
+
+
+def test_peaks_one_is_algorithm_1():
+    c = synth.tiny_wing(n_span=6, n_chord=30, radius=1.0)
+    estar = oracle.tolerance(c["db"], 2e-3)
+    for m in (1, 4):
+        a = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, history=False)
+        b = oracle.greedy_peaks(c["xb"], c["db"], c["radius"], estar, m=m, peaks=1, sep=0.0)
+        assert a["idx"].tolist() == b["idx"].tolist()
+        assert a["iter"].tolist() == b["iter"].tolist()
+        assert a["stats"]["iterations"] == b["iterations"]

@@ -181,6 +181,25 @@ rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, int64_t nb,
                              void *d_ws, size_t ws_bytes, void *stream);
 
 /* --------------------------------------------------------------------------
+ * Peak-selection variant of the greedy (the prior art the paper cites in
+ * Sec. 1: several error-peak nodes added at a time).  In each iteration the
+ * nodes of the active group outside S with E > E* are taken in decreasing E
+ * (lowest node index on ties), each only if it lies at least `separation`
+ * (absolute, the units of d_xb) from every node taken before it in the same
+ * iteration, up to `peaks` nodes (1..16); they are appended in that order.
+ * peaks = 1 is rbf_greedy_select.  The selection is exact: in the screened
+ * precisions it is certified from the error bounds, or every candidate of
+ * the group is re-scored in FP64 first.  Termination, partition, seeds and
+ * outputs as rbf_greedy_select (no iteration history); several nodes share
+ * an iteration number in d_sel_iter.  SYNCHRONOUS.
+ * ------------------------------------------------------------------------ */
+rbf_status rbf_greedy_select_peaks(const double *d_xb, const double *d_db, int64_t nb,
+                                   const rbf_params *p, int peaks, double separation,
+                                   int32_t *d_sel_idx, int64_t *d_sel_iter, double *d_w,
+                                   int64_t *h_nc, rbf_greedy_stats *h_stats, void *d_ws,
+                                   size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------------------------------
  * Batched greedy: many independent problems (for instance one wing per load
  * case or per design) in ONE cooperative launch.  Problem i runs Algorithm 1
  * as rbf_greedy_select would, on its own contiguous range of CTAs (at least

@@ -11,6 +11,7 @@ from .rbf import (  # noqa: F401
     GreedyStats,
     lib,
     greedy_select,
+    greedy_select_peaks,
     solve_weights,
     deform_volume,
     solve_system,

@@ -149,7 +149,227 @@ struct GreedyArgs {
     long long *nc_out;            // optional: |S| at exit (device, for batched runs)
     int smem_cap;                 // centres whose evaluation table fits in the launch's
                                   // dynamic shared memory (larger sets are read from L2)
+    int peaks;                    // peak selection: nodes appended per iteration (<= 1: Alg. 1)
+    double sep2;                  // and their squared separation, in units of R
 };
+
+constexpr int kMaxPeaks = 16;
+// groups of up to this many positions are selected by every CTA on its own
+// (no grid barrier); larger groups are split over the grid, one record
+// exchange per round
+constexpr int kPeakBlockPositions = 2048;
+
+// One candidate of a selection round, and the merge of two: the largest
+// stored error (lowest node on ties) and, for the certification, the two
+// largest upper bounds E~ + beta (as FP32 rounded up).
+struct PeakCand {
+    unsigned long long eb;   // bits of the stored error (non-negative double)
+    unsigned int u1, u2;     // bits of the largest / second largest upper bound
+    int node, pos, n1;       // winner's node and position (-1: none); node of u1
+    float beta;              // winner's bound
+};
+
+__device__ __forceinline__ PeakCand peak_empty()
+{
+    return PeakCand{0ull, 0u, 0u, -1, -1, -1, 0.0f};
+}
+
+__device__ __forceinline__ void peak_merge(PeakCand &A, const PeakCand &B)
+{
+    if (B.pos >= 0 && (A.pos < 0 || B.eb > A.eb || (B.eb == A.eb && B.node < A.node))) {
+        A.eb = B.eb;
+        A.node = B.node;
+        A.pos = B.pos;
+        A.beta = B.beta;
+    }
+    if (B.n1 >= 0 && (A.n1 < 0 || B.u1 > A.u1 || (B.u1 == A.u1 && B.n1 < A.n1))) {
+        A.u2 = max(A.u1, B.u2);
+        A.u1 = B.u1;
+        A.n1 = B.n1;
+    } else {
+        A.u2 = max(A.u2, B.u1);
+    }
+}
+
+__device__ __forceinline__ void peak_warp_reduce(PeakCand &c)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        PeakCand t;
+        t.eb = __shfl_xor_sync(0xffffffffu, c.eb, o);
+        t.u1 = __shfl_xor_sync(0xffffffffu, c.u1, o);
+        t.u2 = __shfl_xor_sync(0xffffffffu, c.u2, o);
+        t.node = __shfl_xor_sync(0xffffffffu, c.node, o);
+        t.pos = __shfl_xor_sync(0xffffffffu, c.pos, o);
+        t.n1 = __shfl_xor_sync(0xffffffffu, c.n1, o);
+        t.beta = __shfl_xor_sync(0xffffffffu, c.beta, o);
+        peak_merge(c, t);
+    }
+}
+
+// |x_q - x_p|^2 < sep2 (scaled coordinates) for position q and a node taken
+// earlier.  Screened in FP32 from the double-float split (relative error of
+// the squared distance below 5e-7, against a margin of 4e-6 sep2 plus
+// 1e-12 X^2); decided in FP64 near the boundary, so the answer is the FP64
+// one.
+__device__ __forceinline__ bool peak_too_close(const GreedyArgs &a, int q, const float4 &qh,
+                                               const float4 &ql, const float4 &ph,
+                                               const float4 &pl, const D4 &px, float s2f,
+                                               float marg)
+{
+    const float dx = (qh.x - ph.x) + (ql.x - pl.x), dy = (qh.y - ph.y) + (ql.y - pl.y),
+                dz = (qh.z - ph.z) + (ql.z - pl.z);
+    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    if (d2 < s2f - marg)
+        return true;
+    if (d2 > s2f + marg)
+        return false;
+    const D4 x = ldcg(a.xg64 + q);
+    const double ex = x.x - px.x, ey = x.y - px.y, ez = x.z - px.z;
+    return fma(ez, ez, fma(ey, ey, ex * ex)) < a.sep2;
+}
+
+// Peak selection in the positions [p0, p1), called by every thread of every
+// CTA: up to a.peaks nodes outside S with E > E*, in decreasing error (lowest
+// node on ties), each at least sqrt(a.sep2) R from the nodes taken before it
+// in this call.  The stored errors are E~ with bounds u32 (0 once re-scored
+// in FP64).  With `exact` (FP64 values for every candidate) the stored
+// errors decide directly; otherwise a round counts only when the bounds
+// certify it (the winner's lower bound E~ - beta exceeds E* and every other
+// eligible node's upper bound) and the call returns -1 at the first round
+// they do not.  Returns -2 when a grid barrier gave up.
+//
+// One round is one pass over the positions: every thread keeps a bit per
+// position it owns for "not a candidate any more" (in S, E <= E*, or too
+// close to or equal to a node taken in an earlier round), so a later round
+// tests only the newest node.  Small groups: every CTA scans the whole group and
+// reaches the same choice without a barrier; large groups: each CTA scans a
+// slice and the CTAs' candidates meet in one record exchange per round.
+__device__ __forceinline__ int select_peaks(const GreedyArgs &a, int p0, int p1, double estar,
+                                         bool exact, float xscale, int &use,
+                                         unsigned int &epoch, int *pk_pos, int *pk_node,
+                                         D4 *pk_x, float4 *pk_h, float4 *pk_l)
+{
+    __shared__ PeakCand s_pc[kGWarps];
+    __shared__ PeakCand s_win;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = g_vg;
+    const bool gmode = p1 - p0 > kPeakBlockPositions;
+    const int base = gmode ? g_vb * kGThreads + tid : tid;
+    const int stride = gmode ? G * kGThreads : kGThreads;
+    const int K = min(a.peaks, kMaxPeaks);
+    const unsigned long long es_bits = dbits(estar);
+    const float es_dn = __double2float_rd(estar);
+    const float s2f = (float)a.sep2;
+    const float marg = 4e-6f * s2f + 1e-12f * xscale * xscale;
+    unsigned int out = 0u;   // bit j: the thread's j-th position is no candidate
+    int cnt = 0;
+    for (int r = 0; r < K; ++r) {
+        PeakCand c = peak_empty();
+        int j = 0;
+        for (int q = p0 + base; q < p1; q += stride, ++j) {
+            const bool tracked = j < 32;
+            if (tracked && ((out >> j) & 1u))
+                continue;
+            bool drop = false;
+            const double e = ldcg(a.e64 + q);
+            const float beta = exact ? 0.0f : ldcg(a.u32 + q);
+            float up = 0.0f;
+            if (r == 0 || !tracked) {
+                if (ldcg(a.in_s + q)) {
+                    drop = true;
+                } else if (exact) {
+                    drop = !(dbits(e) > es_bits);
+                } else {
+                    up = __fadd_ru(__double2float_ru(e), beta);
+                    if (!(dbits(e) > es_bits))
+                        drop = beta == 0.0f || up <= es_dn || !(e + (double)beta > estar);
+                }
+            } else if (!exact) {
+                up = __fadd_ru(__double2float_ru(e), beta);
+            }
+            if (!drop && cnt > 0) {
+                const float4 qh = ldcg(a.xg32 + q), ql = ldcg(a.xgl + q);
+                const int u0 = tracked ? cnt - 1 : 0;
+                for (int u = u0; u < cnt && !drop; ++u)
+                    drop = q == pk_pos[u] ||
+                           peak_too_close(a, q, qh, ql, pk_h[u], pk_l[u], pk_x[u], s2f, marg);
+            }
+            if (drop) {
+                if (tracked)
+                    out |= 1u << j;
+                continue;
+            }
+            PeakCand t;
+            t.eb = dbits(e);
+            t.node = ldcg(a.node_of_pos + q);
+            t.pos = q;
+            t.beta = beta;
+            t.u1 = __float_as_uint(up);
+            t.u2 = 0u;
+            t.n1 = exact ? -1 : t.node;
+            peak_merge(c, t);
+        }
+        peak_warp_reduce(c);
+        if (lane == 0)
+            s_pc[warp] = c;
+        __syncthreads();
+        if (warp == 0) {
+            PeakCand t = lane < kGWarps ? s_pc[lane] : peak_empty();
+            peak_warp_reduce(t);
+            if (lane == 0) {
+                if (gmode)
+                    ((PeakCand *)(a.rec + (size_t)(use & 1) * kMaxGrid))[g_vb] = t;
+                else
+                    s_win = t;
+            }
+        }
+        if (gmode) {
+            if (!grid_barrier(&a.ctl->bar, &a.ctl->status, (unsigned)G, a.barrier_ns, epoch,
+                              (unsigned)g_vb))
+                return -2;
+            if (warp == 0) {
+                const PeakCand *rb = (const PeakCand *)(a.rec + (size_t)(use & 1) * kMaxGrid);
+                PeakCand t = peak_empty();
+                for (int b = lane; b < G; b += 32) {
+                    PeakCand o;
+                    o.eb = __ldcg(&rb[b].eb);
+                    o.u1 = __ldcg(&rb[b].u1);
+                    o.u2 = __ldcg(&rb[b].u2);
+                    o.node = __ldcg(&rb[b].node);
+                    o.pos = __ldcg(&rb[b].pos);
+                    o.n1 = __ldcg(&rb[b].n1);
+                    o.beta = __ldcg(&rb[b].beta);
+                    peak_merge(t, o);
+                }
+                peak_warp_reduce(t);
+                if (lane == 0)
+                    s_win = t;
+            }
+            ++use;
+        }
+        __syncthreads();
+        const PeakCand w = s_win;
+        if (w.pos < 0)
+            break;   // no candidate left
+        if (!exact) {
+            const double lower = bitsd(w.eb) - (double)w.beta;
+            const float up = __uint_as_float(w.n1 != w.node ? w.u1 : w.u2);
+            if (!(lower > estar) || !(lower > (double)up))
+                return -1;
+        }
+        if (tid == 0) {
+            pk_pos[cnt] = w.pos;
+            pk_node[cnt] = w.node;
+            pk_x[cnt] = ldcg(a.xg64 + w.pos);
+            pk_h[cnt] = ldcg(a.xg32 + w.pos);
+            pk_l[cnt] = ldcg(a.xgl + w.pos);
+        }
+        __syncthreads();
+        ++cnt;
+    }
+    return cnt;
+}
 
 __device__ __forceinline__ int goff(int i, int nb, int m)
 {
@@ -723,7 +943,9 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
 
 // ---------------------------------------------------------------------------
 // The persistent greedy: one problem on the CTAs g_vb = 0 .. g_vg - 1.
+// kPeaks: the peak-selection variant (a.peaks > 1) is compiled in.
 // ---------------------------------------------------------------------------
+template <bool kPeaks>
 __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
 {
     extern __shared__ float4 s_cw[];
@@ -1439,19 +1661,75 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             if (!(eloc > estar))
                 add_node = -1;
         }
+        // peak selection: several separated nodes of this group at once
+        __shared__ int s_pk_pos[kMaxPeaks], s_pk_node[kMaxPeaks];
+        __shared__ D4 s_pk_x[kMaxPeaks];
+        __shared__ float4 s_pk_h[kMaxPeaks], s_pk_l[kMaxPeaks];
+        int n_add = add_node >= 0 ? 1 : 0;
+        if (kPeaks && a.peaks > 1) {
+            const bool screened = a.prec != RBF_PREC_F64;
+            int c = select_peaks(a, g0, g1, estar, !screened, xscale, use, epoch, s_pk_pos,
+                                 s_pk_node, s_pk_x, s_pk_h, s_pk_l);
+            if (c == -2)
+                return;
+            if (c < 0) {
+                // the bounds did not certify the selection: every candidate
+                // of the group in FP64, then the selection on exact values
+                phase(2);
+                const int nq = g1 - g0, ts = team_size(nq, G), sub = lane & (ts - 1);
+                const int team = gtid / ts, nteams = gthreads / ts;
+                const int rounds = (nq + nteams - 1) / nteams;
+                for (int it = 0; it < rounds; ++it) {
+                    const int q = g0 + team + it * nteams;
+                    const bool act = q < g1;
+                    bool need = false;
+                    if (act && !ldcg(a.in_s + q)) {
+                        const float b = ldcg(a.u32 + q);
+                        need = b > 0.0f && ldcg(a.e64 + q) + (double)b > estar;
+                    }
+                    if (__ballot_sync(0xffffffffu, need) == 0u)
+                        continue;
+                    const double e = team_error_f64(a, act ? q : g0, nc, sub, ts);
+                    if (need && sub == 0) {
+                        a.e64[q] = e;
+                        a.u32[q] = 0.0f;
+                        ++rescored_local;
+                    }
+                }
+                GSYNC();
+                c = select_peaks(a, g0, g1, estar, true, xscale, use, epoch, s_pk_pos, s_pk_node,
+                                 s_pk_x, s_pk_h, s_pk_l);
+                if (c == -2)
+                    return;
+                phase(5);
+            }
+            n_add = c;
+            add_node = n_add > 0 ? s_pk_node[0] : -1;
+        }
         const long long nc_before = nc;
         if (add_node >= 0) {
-            if (nc >= a.nc_max) {
-                status = RBF_E_NC_MAX;
-                break;
+            bool failed = false;
+            for (int r = 0; r < n_add; ++r) {
+                if (nc >= a.nc_max) {
+                    status = RBF_E_NC_MAX;
+                    failed = true;
+                    break;
+                }
+                phase(3);
+                const int ar = kPeaks && a.peaks > 1
+                                   ? chol_append(a, red, nc, use, min_piv, s_pk_pos[r],
+                                                 s_pk_node[r], k, epoch)
+                                   : chol_append(a, red, nc, use, min_piv, add_pos, add_node, k,
+                                                 epoch);
+                phase(5);
+                if (ar != kAppendOk) {
+                    status = RBF_E_NOT_SPD;   // or the latched timeout, which wins
+                    failed = true;
+                    break;
+                }
             }
-            phase(3);
-            const int ar = chol_append(a, red, nc, use, min_piv, add_pos, add_node, k, epoch);
-            phase(5);
-            if (ar != kAppendOk) {
-                status = RBF_E_NOT_SPD;   // or the latched timeout, which wins
+            if (failed)
                 break;
-            }
             idle = 0;
             run_max = 0.0;
             run_sq = 0.0;
@@ -1617,7 +1895,18 @@ __global__ void __launch_bounds__(kGThreads, 1) k_greedy(GreedyArgs a)
         g_vg = gridDim.x;
     }
     __syncthreads();
-    greedy_body(a);
+    greedy_body<false>(a);
+}
+
+// The peak-selection variant (several separated nodes per iteration).
+__global__ void __launch_bounds__(kGThreads, 1) k_greedy_peaks(GreedyArgs a)
+{
+    if (threadIdx.x == 0) {
+        g_vb = blockIdx.x;
+        g_vg = gridDim.x;
+    }
+    __syncthreads();
+    greedy_body<true>(a);
 }
 
 // Many problems in one launch: problem i runs on CTAs [cta_start[i],
@@ -1641,7 +1930,7 @@ k_greedy_batched(const GreedyArgs *__restrict__ args, const int *__restrict__ ct
     }
     __syncthreads();
     const GreedyArgs a = args[s_prob];
-    greedy_body(a);
+    greedy_body<false>(a);
 }
 
 
@@ -1887,16 +2176,15 @@ extern "C" size_t rbf_greedy_workspace_bytes(int64_t nb, const rbf_params *p)
     return greedy_ws_layout(nb, p->nc_max).total;
 }
 
-extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, int64_t nb,
-                                        const rbf_params *p, int32_t *d_sel_idx,
-                                        int64_t *d_sel_iter, double *d_w, double *d_hist,
-                                        int64_t hist_cap,
-                                        int64_t *h_nc, int64_t *h_n_hist,
-                                        rbf_greedy_stats *h_stats, void *d_ws, size_t ws_bytes,
-                                        void *stream)
+static rbf_status greedy_launch(const double *d_xb, const double *d_db, int64_t nb,
+                                const rbf_params *p, int32_t *d_sel_idx, int64_t *d_sel_iter,
+                                double *d_w, double *d_hist, int64_t hist_cap, int64_t *h_nc,
+                                int64_t *h_n_hist, rbf_greedy_stats *h_stats, void *d_ws,
+                                size_t ws_bytes, void *stream, int peaks, double separation)
 {
     if (!greedy_args_ok(nb, p) || !d_xb || !d_db || !d_sel_idx || !h_nc || hist_cap < 0 ||
-        (hist_cap > 0 && !d_hist) || p->refine_steps < 0 || p->refine_steps > 16)
+        (hist_cap > 0 && !d_hist) || p->refine_steps < 0 || p->refine_steps > 16 ||
+        peaks < 1 || peaks > kMaxPeaks || !(separation >= 0.0) || !std::isfinite(separation))
         return RBF_E_ARG;
     const GreedyWs L = greedy_ws_layout(nb, p->nc_max);
     if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
@@ -1934,6 +2222,8 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
     a.hist_cap = hist_cap;
     a.w_out = d_w;
     a.refine_steps = p->refine_steps;
+    a.peaks = peaks;
+    a.sep2 = (separation / p->radius) * (separation / p->radius);
     fill_args(a, ws, L);
 
     // the evaluation table of as many centres as fit beside the kernel's
@@ -1942,18 +2232,19 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
     const size_t per_centre = p->eval_prec == RBF_PREC_F32     ? sizeof(float4) * 2
                               : p->eval_prec == RBF_PREC_F32X2 ? sizeof(float4) * 4
                                                                : 0;
+    const void *kfn = peaks > 1 ? (const void *)k_greedy_peaks : (const void *)k_greedy;
     cudaFuncAttributes fattr{};
-    if (cudaFuncGetAttributes(&fattr, k_greedy) != cudaSuccess)
+    if (cudaFuncGetAttributes(&fattr, kfn) != cudaSuccess)
         return RBF_E_CUDA;
     const size_t room = dev.smem_optin > fattr.sharedSizeBytes + 1024
                             ? dev.smem_optin - fattr.sharedSizeBytes - 1024 : 0;
     a.smem_cap = per_centre ? (int)std::min<int64_t>(p->nc_max, (int64_t)(room / per_centre)) : 0;
     const size_t smem = per_centre * (size_t)a.smem_cap;
-    if (cudaFuncSetAttribute(k_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)std::max<size_t>(smem, 1)) != cudaSuccess)
         return RBF_E_CUDA;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_greedy, kGThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kGThreads, smem) !=
             cudaSuccess ||
         occ < 1)
         return RBF_E_CUDA;
@@ -1969,7 +2260,7 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
         grid = std::min(p->ctas, dev.sms * std::min(occ, 2));
     grid = std::min(grid, kMaxGrid);
     void *kargs[] = {&a};
-    if (cudaLaunchCooperativeKernel((const void *)k_greedy, grid, kGThreads, kargs, smem, st) !=
+    if (cudaLaunchCooperativeKernel(kfn, grid, kGThreads, kargs, smem, st) !=
         cudaSuccess) {
         cudaGetLastError();
         return RBF_E_CUDA;
@@ -2002,6 +2293,28 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
         h_stats->ctas = grid;
     }
     return (rbf_status)ctl.status;
+}
+
+extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, int64_t nb,
+                                        const rbf_params *p, int32_t *d_sel_idx,
+                                        int64_t *d_sel_iter, double *d_w, double *d_hist,
+                                        int64_t hist_cap, int64_t *h_nc, int64_t *h_n_hist,
+                                        rbf_greedy_stats *h_stats, void *d_ws, size_t ws_bytes,
+                                        void *stream)
+{
+    return greedy_launch(d_xb, d_db, nb, p, d_sel_idx, d_sel_iter, d_w, d_hist, hist_cap, h_nc,
+                         h_n_hist, h_stats, d_ws, ws_bytes, stream, 1, 0.0);
+}
+
+extern "C" rbf_status rbf_greedy_select_peaks(const double *d_xb, const double *d_db, int64_t nb,
+                                              const rbf_params *p, int peaks, double separation,
+                                              int32_t *d_sel_idx, int64_t *d_sel_iter,
+                                              double *d_w, int64_t *h_nc,
+                                              rbf_greedy_stats *h_stats, void *d_ws,
+                                              size_t ws_bytes, void *stream)
+{
+    return greedy_launch(d_xb, d_db, nb, p, d_sel_idx, d_sel_iter, d_w, nullptr, 0, h_nc,
+                         nullptr, h_stats, d_ws, ws_bytes, stream, peaks, separation);
 }
 
 // ---------------------------------------------------------------------------

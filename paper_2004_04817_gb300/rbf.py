@@ -109,6 +109,10 @@ def lib():
         L.rbf_greedy_select.argtypes = [_vp, _vp, C.c_int64, P, _vp, _vp, _vp, _vp, C.c_int64,
                                         C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(GreedyStats), _vp, C.c_size_t, _vp]
+        L.rbf_greedy_select_peaks.restype = C.c_int
+        L.rbf_greedy_select_peaks.argtypes = [_vp, _vp, C.c_int64, P, C.c_int, C.c_double, _vp,
+                                              _vp, _vp, C.POINTER(C.c_int64),
+                                              C.POINTER(GreedyStats), _vp, C.c_size_t, _vp]
         L.rbf_solve_workspace_bytes.restype = C.c_size_t
         L.rbf_solve_workspace_bytes.argtypes = [C.c_int64]
         L.rbf_solve_weights.restype = C.c_int
@@ -293,6 +297,38 @@ def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
                 w=w[:n] if w is not None else None,
                 hist=hist[:min(nh.value, hist_cap)] if hist is not None else None,
                 n_hist=nh.value,
+                stats={f: (list(getattr(stats, f)) if f == "phase_ns" else getattr(stats, f))
+                       for f, _ in GreedyStats._fields_})
+
+
+def greedy_select_peaks(xb, db, *, radius, tol, peaks, separation, tol_mode=1, m=1, seed=1,
+                        nc_max=None, eval_prec=PREC_F64, weights=False, refine_steps=2, ctas=0,
+                        stream=None, workspace=None):
+    """Peak-selection variant of greedy_select: up to ``peaks`` nodes of the
+    active group, at least ``separation`` apart, appended per iteration.
+    Returns a dict like greedy_select (no history)."""
+    L = lib()
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(db, torch.float64, "db", 3)
+    nb = xb.shape[0]
+    nc_max = int(nc_max or min(nb, 4096))
+    p = make_params(radius, tol, tol_mode, eval_prec, m, seed, nc_max, refine_steps, ctas=ctas)
+    need = L.rbf_greedy_workspace_bytes(nb, C.byref(p))
+    if need == 0:
+        raise RBFError(1, "rbf_greedy_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xb.device)
+    idx = torch.empty(nc_max, dtype=torch.int32, device=xb.device)
+    it = torch.empty(nc_max, dtype=torch.int64, device=xb.device)
+    w = torch.empty((nc_max, 3), dtype=torch.float64, device=xb.device) if weights else None
+    nc = C.c_int64(0)
+    stats = GreedyStats()
+    st = L.rbf_greedy_select_peaks(_ptr(xb), _ptr(db), nb, C.byref(p), int(peaks),
+                                   float(separation), _ptr(idx), _ptr(it), _ptr(w), C.byref(nc),
+                                   C.byref(stats), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "rbf_greedy_select_peaks", allow=(E_NC_MAX,))
+    n = nc.value
+    return dict(idx=idx[:n], iter=it[:n], nc=n, status=st, w=w[:n] if w is not None else None,
                 stats={f: (list(getattr(stats, f)) if f == "phase_ns" else getattr(stats, f))
                        for f, _ in GreedyStats._fields_})
 

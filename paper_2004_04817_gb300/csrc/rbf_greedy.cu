@@ -151,6 +151,10 @@ struct GreedyArgs {
                                   // dynamic shared memory (larger sets are read from L2)
     int peaks;                    // peak selection: nodes appended per iteration (<= 1: Alg. 1)
     double sep2;                  // and their squared separation, in units of R
+    double *bmat;                 // block append: B = Phi(S, new), ld x 16, row-major
+    double *lmat;                 // Lambda = Z B, ld x 16
+    double *cmat;                 // Phi(new, new), 16 x 16
+    double *bpart;                // per-CTA partial sums (kPeakGrid x kBlkV)
 };
 
 constexpr int kMaxPeaks = 16;
@@ -158,6 +162,12 @@ constexpr int kMaxPeaks = 16;
 // (no grid barrier); larger groups are split over the grid, one record
 // exchange per round
 constexpr int kPeakBlockPositions = 2048;
+// block append of up to kMaxPeaks nodes: per-CTA partial sums (the K' x K'
+// Gram matrix of Lambda and Lambda^T y, K' = K rounded up to a power of two)
+// and the largest grid of the peak-selection launch
+constexpr int kBlkV = kMaxPeaks * kMaxPeaks + 3 * kMaxPeaks;
+constexpr int kBlkSeg = 8;   // CTA segments of the grid sums
+constexpr int kPeakGrid = 256;
 
 // One candidate of a selection round, and the merge of two: the largest
 // stored error (lowest node on ties) and, for the certification, the two
@@ -858,6 +868,312 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
     return kAppendOk;
 }
 
+
+// ---------------------------------------------------------------------------
+// Block append of K >= 2 nodes (positions pk_pos[0..K), in that order): the
+// same factor as K single appends, in three grid barriers.  With Z = L^-1 of
+// the current n x n factor and y = Z dX_S:
+//   B = Phi(S, new) (n x K),  Lambda = Z B,  M = Phi(new, new) - Lambda^T Lambda,
+//   L22 = chol(M),  Z22 = L22^-1,  y_new = Z22 (dX_new - Lambda^T y),
+//   w_new = Z22^T y_new,  U = Z^T Lambda,
+//   Z gains the rows [-Z22 U^T, Z22],  W_S -= U w_new.
+// The pivots of M are the d^2 of the single appends; at the first one <=
+// kPivotMin the nodes before it are appended and kAppendNotSpd is returned.
+// Lanes of a warp split as (jl, kl) = (lane / K', lane % K'): a warp's row
+// product reads each Z entry once for all K columns.  The K x K work (one
+// warp) and the grid sums are done by every CTA in the same order, so every
+// CTA holds the same bits.  `nc` grows by the number appended.
+// ---------------------------------------------------------------------------
+__device__ int chol_append_block(const GreedyArgs &a, int &nc, double &min_piv, int K,
+                                 const int *pk_pos, const int *pk_node, long long kiter,
+                                 unsigned int &epoch)
+{
+    GreedyCtl *ctl = a.ctl;
+    const int G = g_vg;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gtid = g_vb * kGThreads + tid, gthreads = G * kGThreads;
+    const int gwarp = g_vb * kGWarps + warp, gwarps = G * kGWarps;
+    const int n = nc;
+    const int KP = K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : 16;   // K' (power of two)
+    const int lgKP = K <= 2 ? 1 : K <= 4 ? 2 : K <= 8 ? 3 : 4;
+    const int J = 32 / KP;
+    const int kl = lane & (KP - 1), jl = lane >> lgKP;
+    const int V = KP * KP + 3 * KP;
+    __shared__ double s_acc[kBlkV];
+    __shared__ double s_l[kMaxPeaks][kMaxPeaks + 1];   // M, overwritten by L22 below the diagonal
+    __shared__ double s_z[kMaxPeaks][kMaxPeaks + 1];   // Z22
+    __shared__ double s_inv[kMaxPeaks];
+    __shared__ double s_y[kMaxPeaks][3], s_w[kMaxPeaks][3];
+    __shared__ int s_keff;
+
+    // B1: B[j][k] = phi(|r_new_k - r_j| / R) (zero for k >= K) and Phi(new, new)
+    for (int t = gtid; t < n * KP; t += gthreads) {
+        const int j = t >> lgKP, k = t & (KP - 1);
+        double b = 0.0;
+        if (k < K) {
+            const D4 x = ldcg(a.xg64 + pk_pos[k]), c = ldcg(a.c64 + j);
+            const double dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
+            b = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
+        }
+        a.bmat[t] = b;
+    }
+    if (gtid < K * K) {
+        const int k = gtid / K, l = gtid - k * K;
+        const D4 x = ldcg(a.xg64 + pk_pos[k]), c = ldcg(a.xg64 + pk_pos[l]);
+        const double dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
+        a.cmat[gtid] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
+    }
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+        return kAppendTimeout;
+
+    // B2: Lambda = Z B (warp per row), with the partial sums of Lambda^T
+    // Lambda (entry (kl, l), l = jl + t J) and of Lambda^T y (entry (kl, c),
+    // c = jl + t J < 3) kept by the lane that owns them
+    double gacc[kMaxPeaks / 2], yacc[2];
+#pragma unroll
+    for (int t = 0; t < kMaxPeaks / 2; ++t)
+        gacc[t] = 0.0;
+    yacc[0] = yacc[1] = 0.0;
+    for (int i = gwarp; i < n; i += gwarps) {
+        const double *zr = a.z + (size_t)i * a.ld;
+        double s = 0.0;
+        for (int j = jl; j <= i; j += J)
+            s = fma(ldcg(zr + j), ldcg(a.bmat + (size_t)j * KP + kl), s);
+        for (int o = KP; o < 32; o <<= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (jl == 0)
+            a.lmat[(size_t)i * KP + kl] = s;
+        const D4 y = ldcg(a.y64 + i);
+#pragma unroll
+        for (int t = 0; t < kMaxPeaks / 2; ++t) {
+            if (t * J >= KP)
+                break;
+            const int l = jl + t * J;
+            const double sl = __shfl_sync(0xffffffffu, s, l < KP ? l : 0);
+            if (l < KP)
+                gacc[t] = fma(s, sl, gacc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int c = jl + t * J;
+            if (c < 3)
+                yacc[t] = fma(s, c == 0 ? y.x : c == 1 ? y.y : y.z, yacc[t]);
+        }
+    }
+    for (int v = tid; v < V; v += kGThreads)
+        s_acc[v] = 0.0;
+    __syncthreads();
+    for (int w = 0; w < kGWarps; ++w) {   // warps in order: the same sums in every run
+        if (warp == w) {
+#pragma unroll
+            for (int t = 0; t < kMaxPeaks / 2; ++t) {
+                const int l = jl + t * J;
+                if (t * J < KP && l < KP)
+                    s_acc[kl * KP + l] += gacc[t];
+            }
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int c = jl + t * J;
+                if (c < 3)
+                    s_acc[KP * KP + 3 * kl + c] += yacc[t];
+            }
+        }
+        __syncthreads();
+    }
+    for (int v = tid; v < V; v += kGThreads)
+        a.bpart[(size_t)g_vb * kBlkV + v] = s_acc[v];
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+        return kAppendTimeout;
+    // grid sums: the CTAs split into nseg fixed segments; thread (seg, v)
+    // adds its segment's partials of value v (independent loads), then each
+    // value's segment sums are added in segment order (the same bits in every
+    // CTA)
+    {
+        __shared__ double s_seg[kBlkV];   // nseg * V <= kBlkV for every K'
+        const int nseg = min(kBlkSeg, max(1, kGThreads / V));
+        const int per = (G + nseg - 1) / nseg;
+        for (int t = tid; t < nseg * V; t += kGThreads) {
+            const int seg = t / V, v = t - seg * V;
+            const int b0 = seg * per, b1 = min(G, b0 + per);
+            double s0 = 0.0, s1 = 0.0;
+            int b = b0;
+#pragma unroll 4
+            for (; b + 1 < b1; b += 2) {
+                s0 += ldcg(a.bpart + (size_t)b * kBlkV + v);
+                s1 += ldcg(a.bpart + (size_t)(b + 1) * kBlkV + v);
+            }
+            if (b < b1)
+                s0 += ldcg(a.bpart + (size_t)b * kBlkV + v);
+            s_seg[t] = s0 + s1;
+        }
+        __syncthreads();
+        for (int v = tid; v < V; v += kGThreads) {
+            double t = 0.0;
+            for (int seg = 0; seg < nseg; ++seg)
+                t += s_seg[seg * V + v];
+            s_acc[v] = t;
+        }
+        __syncthreads();
+    }
+
+    // B3 (warp 0): L22 = chol(M) row by row, Z22, y_new, w_new
+    if (warp == 0) {
+        for (int t = lane; t < K * K; t += 32) {
+            const int k = t / K, l = t - k * K;
+            if (l <= k)
+                s_l[k][l] = ldcg(a.cmat + t) - s_acc[k * KP + l];
+        }
+        if (lane < K) {   // dX_new - Lambda^T y, row `lane`
+            const D4 dn = ldcg(a.dg64 + pk_pos[lane]);
+            const double *ly = s_acc + KP * KP + 3 * lane;
+            s_y[lane][0] = dn.x - ly[0];
+            s_y[lane][1] = dn.y - ly[1];
+            s_y[lane][2] = dn.z - ly[2];
+        }
+        __syncwarp();
+        int keff = K;
+        for (int k = 0; k < K; ++k) {
+            const double d2 = s_l[k][k];
+            if (!(d2 > kPivotMin)) {
+                keff = k;
+                break;
+            }
+            if (lane == 0) {
+                s_inv[k] = rsqrt_f64_newton(d2);
+                min_piv = fmin(min_piv, d2);
+            }
+            __syncwarp();
+            const double inv = s_inv[k];
+            if (lane > k && lane < K)
+                s_l[lane][k] *= inv;
+            __syncwarp();
+            if (lane > k && lane < K) {
+                const double lk = s_l[lane][k];
+                for (int j = k + 1; j <= lane; ++j)
+                    s_l[lane][j] = fma(-lk, s_l[j][k], s_l[lane][j]);
+            }
+            __syncwarp();
+        }
+        if (lane < keff) {   // column `lane` of Z22 by forward substitution
+            const int j = lane;
+            s_z[j][j] = s_inv[j];
+            for (int i = j + 1; i < keff; ++i) {
+                double t = 0.0;
+                for (int m = j; m < i; ++m)
+                    t = fma(s_l[i][m], s_z[m][j], t);
+                s_z[i][j] = -t * s_inv[i];
+            }
+        }
+        __syncwarp();
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+        if (lane < keff) {   // y_new = Z22 (dX_new - Lambda^T y), row `lane`
+            const int i = lane;
+            for (int m = 0; m <= i; ++m) {
+                r0 = fma(s_z[i][m], s_y[m][0], r0);
+                r1 = fma(s_z[i][m], s_y[m][1], r1);
+                r2 = fma(s_z[i][m], s_y[m][2], r2);
+            }
+        }
+        __syncwarp();
+        if (lane < keff) {
+            s_y[lane][0] = r0;
+            s_y[lane][1] = r1;
+            s_y[lane][2] = r2;
+        }
+        __syncwarp();
+        if (lane < keff) {   // w_new = Z22^T y_new, row `lane`
+            const int k = lane;
+            double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+            for (int i = k; i < keff; ++i) {
+                w0 = fma(s_z[i][k], s_y[i][0], w0);
+                w1 = fma(s_z[i][k], s_y[i][1], w1);
+                w2 = fma(s_z[i][k], s_y[i][2], w2);
+            }
+            s_w[k][0] = w0;
+            s_w[k][1] = w1;
+            s_w[k][2] = w2;
+        }
+        if (lane == 0)
+            s_keff = keff;
+    }
+    __syncthreads();
+    const int keff = s_keff;
+    if (keff == 0) {
+        if (g_vb == 0 && tid == 0)
+            ctl->status = RBF_E_NOT_SPD;
+        return kAppendNotSpd;
+    }
+
+    // B4: U = Z^T Lambda (warp per row j of Z^T), the new rows' entries
+    // -Z22 U^T in column j, and W_j -= U_j w_new
+    for (int j = gwarp; j < n; j += gwarps) {
+        const double *ztr = a.zt + (size_t)j * a.ld;
+        double s = 0.0;
+        for (int i = j + jl; i < n; i += J)
+            s = fma(ldcg(ztr + i), ldcg(a.lmat + (size_t)i * KP + kl), s);
+        for (int o = KP; o < 32; o <<= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+        double z21 = 0.0;
+        for (int l = 0; l < KP; ++l) {
+            const double ul = __shfl_sync(0xffffffffu, s, l);
+            if (l <= kl && kl < keff)
+                z21 = fma(s_z[kl][l], ul, z21);
+        }
+        double px = 0.0, py = 0.0, pz = 0.0;
+        if (kl < keff) {
+            px = s * s_w[kl][0];
+            py = s * s_w[kl][1];
+            pz = s * s_w[kl][2];
+        }
+        for (int o = 1; o < KP; o <<= 1) {
+            px += __shfl_xor_sync(0xffffffffu, px, o);
+            py += __shfl_xor_sync(0xffffffffu, py, o);
+            pz += __shfl_xor_sync(0xffffffffu, pz, o);
+        }
+        if (jl == 0 && kl < keff) {
+            a.z[(size_t)(n + kl) * a.ld + j] = -z21;
+            a.zt[(size_t)j * a.ld + n + kl] = -z21;
+        }
+        if (lane == 0) {
+            D4 w = ldcg(a.w64 + j);
+            w.x -= px;
+            w.y -= py;
+            w.z -= pz;
+            a.w64[j] = w;
+            put_weight(a, j, w);
+        }
+    }
+    // the new nodes' own entries: the last warp of the grid, lane k for node k
+    if (gwarp == gwarps - 1 && lane < keff) {
+        const int k = lane;
+        for (int l = 0; l <= k; ++l) {
+            a.z[(size_t)(n + k) * a.ld + n + l] = s_z[k][l];
+            a.zt[(size_t)(n + l) * a.ld + n + k] = s_z[k][l];
+        }
+        a.y64[n + k] = mk4(s_y[k][0], s_y[k][1], s_y[k][2], 0.0);
+        const D4 wn = mk4(s_w[k][0], s_w[k][1], s_w[k][2], 0.0);
+        a.w64[n + k] = wn;
+        const int pn = pk_pos[k];
+        const D4 xc = ldcg(a.xg64 + pn);
+        a.c64[n + k] = xc;
+        put_centre(a, n + k, xc);
+        put_weight(a, n + k, wn);
+        a.spos[n + k] = pn;
+        a.in_s[pn] = 1;
+        a.sel_idx[n + k] = pk_node[k];
+        if (a.sel_iter)
+            a.sel_iter[n + k] = kiter;
+    }
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+        return kAppendTimeout;
+    nc = n + keff;
+    if (keff < K) {
+        if (g_vb == 0 && tid == 0)
+            ctl->status = RBF_E_NOT_SPD;
+        return kAppendNotSpd;
+    }
+    return kAppendOk;
+}
 
 // ---------------------------------------------------------------------------
 // FP64 iterative refinement of the support weights (Sec. 2: Phi_SS is SPD,
@@ -1666,7 +1982,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         __shared__ D4 s_pk_x[kMaxPeaks];
         __shared__ float4 s_pk_h[kMaxPeaks], s_pk_l[kMaxPeaks];
         int n_add = add_node >= 0 ? 1 : 0;
-        if (kPeaks && a.peaks > 1) {
+        // (an iteration whose certified maximum is <= E* has no candidate)
+        if (kPeaks && a.peaks > 1 && add_node >= 0) {
             const bool screened = a.prec != RBF_PREC_F64;
             int c = select_peaks(a, g0, g1, estar, !screened, xscale, use, epoch, s_pk_pos,
                                  s_pk_node, s_pk_x, s_pk_h, s_pk_l);
@@ -1709,23 +2026,39 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         const long long nc_before = nc;
         if (add_node >= 0) {
             bool failed = false;
-            for (int r = 0; r < n_add; ++r) {
-                if (nc >= a.nc_max) {
-                    status = RBF_E_NC_MAX;
-                    failed = true;
-                    break;
-                }
+            if (kPeaks && a.peaks > 1 && n_add > 1 && a.nc_max - nc >= 2) {
+                // several peaks: one block append
+                const int kb = min(n_add, a.nc_max - nc);
                 phase(3);
-                const int ar = kPeaks && a.peaks > 1
-                                   ? chol_append(a, red, nc, use, min_piv, s_pk_pos[r],
-                                                 s_pk_node[r], k, epoch)
-                                   : chol_append(a, red, nc, use, min_piv, add_pos, add_node, k,
+                const int ar = chol_append_block(a, nc, min_piv, kb, s_pk_pos, s_pk_node, k,
                                                  epoch);
                 phase(5);
                 if (ar != kAppendOk) {
                     status = RBF_E_NOT_SPD;   // or the latched timeout, which wins
                     failed = true;
-                    break;
+                } else if (kb < n_add) {
+                    status = RBF_E_NC_MAX;
+                    failed = true;
+                }
+            } else {
+                for (int r = 0; r < n_add; ++r) {
+                    if (nc >= a.nc_max) {
+                        status = RBF_E_NC_MAX;
+                        failed = true;
+                        break;
+                    }
+                    phase(3);
+                    const int ar = kPeaks && a.peaks > 1
+                                       ? chol_append(a, red, nc, use, min_piv, s_pk_pos[r],
+                                                     s_pk_node[r], k, epoch)
+                                       : chol_append(a, red, nc, use, min_piv, add_pos, add_node,
+                                                     k, epoch);
+                    phase(5);
+                    if (ar != kAppendOk) {
+                        status = RBF_E_NOT_SPD;   // or the latched timeout, which wins
+                        failed = true;
+                        break;
+                    }
                 }
             }
             if (failed)
@@ -2055,7 +2388,8 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
 struct GreedyWs {
     size_t ctl, part, parti, perm, node_of_pos, pos_of_node, xg64, dg64, xg32, xgl, dgh, dgl,
         in_s, u32, e64,
-        spos, c64, w64, cw32, cwff, y64, z, zt, bvec, lvec, rvec, tvec, rec, total;
+        spos, c64, w64, cw32, cwff, y64, z, zt, bvec, lvec, rvec, tvec, rec, bmat, lmat, cmat,
+        bpart, total;
 };
 
 static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
@@ -2095,6 +2429,10 @@ static GreedyWs greedy_ws_layout(int64_t nb, int64_t ncm)
     L.rvec = take(sizeof(D4) * ncm);
     L.tvec = take(sizeof(D4) * ncm);
     L.rec = take(sizeof(EvalRec) * 2 * kMaxGrid);
+    L.bmat = take(sizeof(double) * kMaxPeaks * ncm);
+    L.lmat = take(sizeof(double) * kMaxPeaks * ncm);
+    L.cmat = take(sizeof(double) * kMaxPeaks * kMaxPeaks);
+    L.bpart = take(sizeof(double) * kPeakGrid * kBlkV);
     L.total = o;
     return L;
 }
@@ -2164,6 +2502,10 @@ static void fill_args(GreedyArgs &a, char *ws, const GreedyWs &L)
     a.rvec = (D4 *)(ws + L.rvec);
     a.tvec = (D4 *)(ws + L.tvec);
     a.rec = (EvalRec *)(ws + L.rec);
+    a.bmat = (double *)(ws + L.bmat);
+    a.lmat = (double *)(ws + L.lmat);
+    a.cmat = (double *)(ws + L.cmat);
+    a.bpart = (double *)(ws + L.bpart);
 }
 }  // namespace rbf
 
@@ -2258,7 +2600,7 @@ static rbf_status greedy_launch(const double *d_xb, const double *d_db, int64_t 
     int grid = (int)std::min<int64_t>(want, (int64_t)dev.sms);
     if (p->ctas > 0)
         grid = std::min(p->ctas, dev.sms * std::min(occ, 2));
-    grid = std::min(grid, kMaxGrid);
+    grid = std::min(grid, peaks > 1 ? kPeakGrid : kMaxGrid);
     void *kargs[] = {&a};
     if (cudaLaunchCooperativeKernel(kfn, grid, kGThreads, kargs, smem, st) !=
         cudaSuccess) {

@@ -2,18 +2,24 @@
 //
 // Where k displacement fields (modes) share one support set, Eq. 6 for all
 // of them is one product D = Phi_vc W with W of size N_c x n_out (n_out = 3 k
-// columns).  Each CTA owns 128 volume points (one M = 128 tile) and walks the
-// centres in K-tiles of 64:
-//   - the four warps evaluate phi (FP32) for their rows of the K-tile and
-//     store it as BF16 in shared memory in the canonical K-major layout
-//     (8 x 16-byte core matrices, no swizzle);
+// columns).  Each CTA owns 128 volume points at a time (one M = 128 tile) and
+// walks the centres in K-tiles of 64:
+//   - sixteen warps evaluate phi (FP32): thread t takes row t % 128 and 16
+//     of the K-tile's 64 centres, and stores phi as BF16 in shared memory in
+//     the canonical K-major layout (8 x 16-byte core matrices, no swizzle).
+//     phi generation on the FP32 pipe is the bound of this kernel (about 20
+//     instructions per pair against 192 MMA flops), so the CTA carries 16
+//     warps to hide the latency of each pair's dependent chain;
 //   - the matching K-tile of W (pre-packed in the same layout) arrives by a
 //     bulk (TMA) copy completed on an mbarrier;
 //   - one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) with
 //     the accumulator in tensor memory and commits to an mbarrier; two
-//     buffers let phi generation of tile t+1 overlap the MMAs of tile t;
+//     buffers let phi generation of tile t+1 overlap the MMAs of tile t, and
+//     one block barrier per K-tile hands the finished A tile to the MMA
+//     thread;
 //   - the epilogue reads the 128 x n_out FP32 accumulator with tcgen05.ld
-//     and stores it.
+//     (warp w: TMEM lanes 32 (w mod 4) .. +31, column groups w / 4, w / 4 + 4,
+//     ...) and stores it.
 // Precision modes: BF16 (one product) and BF16x3, where phi and W are split
 // into three BF16 parts (x = x0 + x1 + x2, parts of order 1, 2^-9, 2^-18) and
 // the six products down to order 2^-18 are accumulated (about FP32 accuracy).
@@ -29,7 +35,7 @@ namespace rbf {
 
 constexpr int kMM = 128;          // points per tile (MMA M)
 constexpr int kMK = 64;           // centres per K-tile
-constexpr int kMThreads = 128;    // four warps: warp w owns TMEM lanes 32w..32w+31
+constexpr int kMThreads = 512;    // sixteen warps; warp w reads TMEM lanes 32 (w mod 4) ..
 constexpr int kModalMaxOut = 256; // MMA N limit
 constexpr int kModalMaxCentres = 4096;
 
@@ -192,32 +198,34 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
     bool ok = true;
 
     const int64_t ntiles = (nv + kMM - 1) / kMM;
+    const int row = tid & (kMM - 1), kgrp = tid >> 7;   // kgrp: centres 16 kgrp .. +15
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        int64_t v = tile * kMM + tid;
+        int64_t v = tile * kMM + row;
         const bool live = v < nv;
         v = live ? v : nv - 1;
         const float4 q = xq[v];
-        for (int kt = 0; kt < sh.nkt && ok; ++kt) {
+        for (int kt = 0; kt < sh.nkt; ++kt) {
             const int buf = kt & 1;
+            bool mine = true;
             // the MMAs that last read this buffer pair must be done
             if (pending[buf]) {
-                if (!mbar_wait(&bars[2 + buf], mphase[buf], limit_ns)) {
-                    ok = false;
-                    break;
+                mine = mbar_wait(&bars[2 + buf], mphase[buf], limit_ns);
+                if (mine) {   // else the exit path waits again for the MMAs in flight
+                    mphase[buf] ^= 1u;
+                    pending[buf] = false;
                 }
-                mphase[buf] ^= 1u;
-                pending[buf] = false;
             }
             // W K-tile (all splits) by one bulk copy
-            if (tid == 0) {
+            if (tid == 0 && mine) {
                 const size_t bytes = sh.splits * sh.w_bytes;
                 bulk_g2s(s_w + buf * sh.splits * sh.w_bytes, wpack + (size_t)kt * bytes,
                          (unsigned)bytes, &bars[buf]);
             }
-            // phi for this thread's row and the 64 centres of the K-tile
+            // phi for this thread's row and its 16 centres of the K-tile
             uint8_t *a0 = s_a + buf * sh.splits * sh.a_bytes;
-#pragma unroll 2
-            for (int k8 = 0; k8 < kMK; k8 += 8) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k8 = kgrp * 16 + h * 8;
                 __nv_bfloat16 p0[8], p1[8], p2[8];
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk) {
@@ -230,7 +238,7 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
                         split3(ph, p0[kk], p1[kk], p2[kk]);
                     }
                 }
-                const int off = kmajor_off(tid, k8);
+                const int off = kmajor_off(row, k8);
                 *(uint4 *)(a0 + off) = pack8(p0);
                 if (sh.splits == 3) {
                     *(uint4 *)(a0 + sh.a_bytes + off) = pack8(p1);
@@ -240,7 +248,12 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
             // generic-proxy stores -> visible to the tensor core (async proxy)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
+            // one barrier: the A tile is complete, and every thread learns
+            // whether a wait anywhere in the CTA gave up
+            if (__syncthreads_or(!mine || *(volatile int *)status == (int)RBF_E_TIMEOUT)) {
+                ok = false;
+                break;
+            }
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 bool got = mbar_wait(&bars[buf], wphase[buf], limit_ns);
@@ -267,46 +280,49 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
                 }
             }
             pending[buf] = true;
-            __syncthreads();
-            if (*(volatile int *)status == (int)RBF_E_TIMEOUT)
-                ok = false;
         }
         // accumulator complete once the last commit has landed
-        for (int b = 0; b < 2 && ok; ++b) {
+        bool mine = ok;
+        for (int b = 0; b < 2 && mine; ++b) {
             if (pending[b]) {
-                if (!mbar_wait(&bars[2 + b], mphase[b], limit_ns)) {
-                    ok = false;
-                    break;
+                mine = mbar_wait(&bars[2 + b], mphase[b], limit_ns);
+                if (mine) {
+                    mphase[b] ^= 1u;
+                    pending[b] = false;
                 }
-                mphase[b] ^= 1u;
-                pending[b] = false;
             }
         }
-        if (!ok)
+        if (__syncthreads_or(!mine || !ok || *(volatile int *)status == (int)RBF_E_TIMEOUT)) {
+            ok = false;
             break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: warp w reads TMEM lanes 32w.. (its own 32 rows)
-        float *orow = out + (size_t)v * sh.n_out;
-        const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
-        int c0 = 0;
-        for (; c0 + 32 <= sh.n_out; c0 += 32) {
-            float vals[32];
-            tmem_ld32(lane_base + (unsigned)c0, vals);
-            if (live) {
-#pragma unroll
-                for (int i = 0; i < 32; i += 4)
-                    *(float4 *)(orow + c0 + i) = make_float4(vals[i], vals[i + 1], vals[i + 2],
-                                                             vals[i + 3]);
-            }
         }
-        if (c0 < sh.n_out) {   // n_out % 32 == 16: one 16-column tail
-            float vals[16];
-            tmem_ld16(lane_base + (unsigned)c0, vals);
-            if (live) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +31 (rows of the
+        // tile) and the 32-column groups w / 4, w / 4 + 4, ...
+        const int quarter = warp & 3;
+        const int erow = quarter * 32 + (tid & 31);
+        const int64_t ev = tile * kMM + erow;
+        float *orow = out + (size_t)(ev < nv ? ev : 0) * sh.n_out;
+        const unsigned lane_base = tmem + ((unsigned)(quarter * 32) << 16);
+        for (int c0 = (warp >> 2) * 32; c0 < sh.n_out; c0 += 128) {
+            if (c0 + 32 <= sh.n_out) {
+                float vals[32];
+                tmem_ld32(lane_base + (unsigned)c0, vals);
+                if (ev < nv) {
 #pragma unroll
-                for (int i = 0; i < 16; i += 4)
-                    *(float4 *)(orow + c0 + i) = make_float4(vals[i], vals[i + 1], vals[i + 2],
-                                                             vals[i + 3]);
+                    for (int i = 0; i < 32; i += 4)
+                        *(float4 *)(orow + c0 + i) =
+                            make_float4(vals[i], vals[i + 1], vals[i + 2], vals[i + 3]);
+                }
+            } else {   // n_out % 32 == 16: one 16-column tail
+                float vals[16];
+                tmem_ld16(lane_base + (unsigned)c0, vals);
+                if (ev < nv) {
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *(float4 *)(orow + c0 + i) =
+                            make_float4(vals[i], vals[i + 1], vals[i + 2], vals[i + 3]);
+                }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -4,6 +4,7 @@
   python -m paper_2004_04817_gb300.profile_case greedy [--m M] [--prec 32|64]
   python -m paper_2004_04817_gb300.profile_case solve
   python -m paper_2004_04817_gb300.profile_case cull [--nv N] [--vprec 32|48] [--radius R]
+  python -m paper_2004_04817_gb300.profile_case modal [--nv N] [--modal-mode 1|3] [--n-out K]
 
 Each case builds the GCB wing workload (N_b = 50,000), runs the calls once
 untimed, then `--reps` more times, and exits 0.
@@ -21,15 +22,18 @@ from paper_2004_04817_gb300 import synth
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["volume", "greedy", "solve", "cull"])
+    ap.add_argument("case", choices=["volume", "greedy", "solve", "cull", "modal"])
     ap.add_argument("--nv", type=int, default=1_000_000)
     ap.add_argument("--m", type=int, default=241)
     ap.add_argument("--prec", type=int, default=48)
     ap.add_argument("--vprec", type=int, default=32)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--radius", type=float, default=0.25, help="cull: support radius")
+    ap.add_argument("--modal-mode", type=int, default=3, choices=[1, 3],
+                    help="modal: 1 BF16, 3 BF16x3")
+    ap.add_argument("--n-out", type=int, default=96, help="modal: columns of W")
     a = ap.parse_args()
-    c = synth.wing_gcb(n_vol=a.nv if a.case in ("volume", "cull") else 0)
+    c = synth.wing_gcb(n_vol=a.nv if a.case in ("volume", "cull", "modal") else 0)
     dev = lambda x, t=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=t,
                                                       device="cuda")
     xb, db = dev(c["xb"]), dev(c["db"])
@@ -46,6 +50,14 @@ def main():
                                 nc_max=g["nc"])
             plan.run(xb, g["idx"], w)
             del plan
+            continue
+        if a.case == "modal":
+            # random modal weights (N_c x n_out): the timing does not depend
+            # on their values
+            W = torch.randn((g["nc"], a.n_out), dtype=torch.float64, device="cuda",
+                            generator=torch.Generator("cuda").manual_seed(1))
+            P.deform_modal(dev(c["xv"]), xb, g["idx"], W, radius=c["radius"],
+                           mode=a.modal_mode)
             continue
         w, _ = P.solve_weights(xb, db, g["idx"], radius=c["radius"])
         if a.case == "volume":

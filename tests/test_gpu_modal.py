@@ -39,6 +39,39 @@ def test_modal_small_against_fp64(n_out, mode, scale):
     assert np.all(err <= scale * bnd + 1e-6), (err / (scale * bnd + 1e-30)).max()
 
 
+@pytest.mark.parametrize("mode,scale,n_out", [(P.MODAL_BF16, 2.0 ** -7, 48),
+                                               (P.MODAL_BF16, 2.0 ** -7, 256),
+                                               (P.MODAL_BF16X3, 2.0 ** -18, 48),
+                                               (P.MODAL_BF16X3, 2.0 ** -18, 160)])
+def test_modal_many_tiles_and_wide_outputs(mode, scale, n_out):
+    # 40,000 points: 313 M tiles, two or three per CTA; n_out = 48 ends in a
+    # 16-column tail of the second column group, 160 and 256 wrap the column
+    # groups (BF16x3 buffers for 256 columns exceed shared memory: below)
+    rng = np.random.default_rng(5)
+    xb = rng.random((300, 3))
+    S = np.sort(rng.choice(300, 150, replace=False)).astype(np.int32)   # 3 K-tiles, padded
+    W = rng.standard_normal((150, n_out))
+    xv = rng.random((40_000, 3)) * 1.2 - 0.1
+    R = 0.6
+    ref, bnd = _ref(xv, xb[S], W, R)
+    d = P.deform_modal(cuda(xv), cuda(xb), cuda(S, torch.int32), cuda(W), radius=R, mode=mode)
+    err = np.abs(d.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(np.isfinite(err))
+    assert np.all(err <= scale * bnd + 1e-6), (err / (scale * bnd + 1e-30)).max()
+
+
+def test_modal_rejects_buffers_beyond_shared_memory():
+    # BF16x3 with 256 columns: two A and two W buffers of three splits each
+    # (96 KB + 192 KB) do not fit in one CTA's shared memory
+    rng = np.random.default_rng(6)
+    xb = rng.random((300, 3))
+    S = np.arange(150, dtype=np.int32)
+    with pytest.raises(P.RBFError) as e:
+        P.deform_modal(cuda(rng.random((100, 3))), cuda(xb), cuda(S, torch.int32),
+                       cuda(rng.standard_normal((150, 256))), radius=0.6, mode=P.MODAL_BF16X3)
+    assert e.value.status == 1
+
+
 def test_modal_sinusoidal_modes_full_support():
     """32 sinusoidal bending modes dz_q = 0.05 sin((2q-1) pi y / (2b)) on the
     GCB support set of the N_b = 50,000 wing; W (N_c x 96) from the FP64

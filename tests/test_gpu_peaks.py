@@ -91,3 +91,39 @@ def test_peaks_grid_split(prec, m, ctas):
     assert r["stats"]["iterations"] == o["iterations"]
     if ctas:
         assert r["stats"]["ctas"] == ctas
+
+
+@pytest.mark.parametrize("prec", [P.PREC_F64, P.PREC_F32X2])
+def test_peaks_capacity_truncates_the_last_block(prec):
+    # 3 seeds + blocks of 4: the capacity 10 cuts the second block to 3 nodes
+    c = synth.tiny_wing(n_span=5, n_chord=24, radius=1.0)
+    estar = oracle.tolerance(c["db"], 1e-5)
+    r = P.greedy_select_peaks(_cuda(c["xb"]), _cuda(c["db"]), radius=c["radius"], tol=estar,
+                              tol_mode=0, m=1, peaks=4, separation=0.1, nc_max=10,
+                              eval_prec=prec)
+    o = oracle.greedy_peaks(c["xb"], c["db"], c["radius"], estar, m=1, ncmax=10, peaks=4,
+                            sep=0.1)
+    assert r["status"] == P.rbf.E_NC_MAX and o["status"] == oracle.E_NC_MAX
+    assert r["idx"].cpu().numpy().tolist() == o["idx"].tolist()
+    assert r["iter"].cpu().numpy().tolist() == o["iter"].tolist()
+
+
+@pytest.mark.parametrize("case", ["in_s", "same_block"])
+def test_peaks_coincident_nodes_not_spd(case):
+    # in_s: node 7 is appended first and its twin 49 later (the block's first
+    # pivot fails); same_block: both twins are peaks of one iteration, so the
+    # block's pivot fails after its first node
+    rng = np.random.default_rng(1 if case == "in_s" else 4)
+    xb = rng.random((50, 3))
+    xb[49] = xb[7]                       # a coincident pair with different displacements
+    db = rng.standard_normal((50, 3)) * 0.1
+    if case == "same_block":
+        db[7], db[49], db[0] = (0.6, 0, 0), (-0.6, 0, 0), (2.0, 0, 0)
+    o = oracle.greedy_peaks(xb, db, 1.5, 1e-9, m=1, peaks=8, sep=0.0)
+    idx, it = o["idx"].tolist(), o["iter"].tolist()
+    assert o["status"] == oracle.E_NOT_SPD
+    assert (it[idx.index(7)] == it[idx.index(49)]) == (case == "same_block")
+    with pytest.raises(P.RBFError) as e:
+        P.greedy_select_peaks(_cuda(xb), _cuda(db), radius=1.5, tol=1e-9, tol_mode=0, m=1,
+                              peaks=8, separation=0.0, eval_prec=P.PREC_F64)
+    assert e.value.status == 2

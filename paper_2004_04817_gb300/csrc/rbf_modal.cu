@@ -4,22 +4,27 @@
 // of them is one product D = Phi_vc W with W of size N_c x n_out (n_out = 3 k
 // columns).  Each CTA owns 128 volume points at a time (one M = 128 tile) and
 // walks the centres in K-tiles of 64:
-//   - sixteen warps evaluate phi (FP32): thread t takes row t % 128 and 16
-//     of the K-tile's 64 centres, and stores phi as BF16 in shared memory in
-//     the canonical K-major layout (8 x 16-byte core matrices, no swizzle).
+//   - sixteen warps evaluate phi (FP32): a thread takes two rows (points)
+//     and one 8-centre chunk of the K-tile, and stores phi as BF16 in shared
+//     memory in a K-major layout of 8 x 16-byte core matrices (no swizzle).
 //     phi generation on the FP32 pipe is the bound of this kernel (about 20
 //     instructions per pair against 192 MMA flops), so the CTA carries 16
-//     warps to hide the latency of each pair's dependent chain;
-//   - the matching K-tile of W (pre-packed in the same layout) arrives by a
-//     bulk (TMA) copy completed on an mbarrier;
-//   - one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) with
-//     the accumulator in tensor memory and commits to an mbarrier; two
-//     buffers let phi generation of tile t+1 overlap the MMAs of tile t, and
-//     one block barrier per K-tile hands the finished A tile to the MMA
-//     thread;
-//   - the epilogue reads the 128 x n_out FP32 accumulator with tcgen05.ld
-//     (warp w: TMEM lanes 32 (w mod 4) .. +31, column groups w / 4, w / 4 + 4,
-//     ...) and stores it.
+//     warps, each thread with two independent chains, to hide the latency
+//     of a pair's dependent chain;
+//   - the matching K-tile of W (pre-packed in the same layout by an earlier
+//     kernel) arrives by a bulk (TMA) copy completed on an mbarrier, started
+//     one K-tile ahead; W buffers are touched only by the async proxy, so the
+//     copies need no proxy fences;
+//   - a seventeenth warp issues tcgen05.mma (kind::f16, BF16 x BF16 ->
+//     FP32) with the accumulator in tensor memory.  The phi warps hand it
+//     each finished A tile through an mbarrier (one arrival per warp), and it
+//     commits each K-tile's MMAs to a second mbarrier that releases the
+//     buffer; with two buffers, phi generation of tile t+1 overlaps the MMAs
+//     of tile t and no block-wide barrier sits in the loop;
+//   - four more warps (one per TMEM lane quarter) read the 128 x n_out FP32
+//     accumulator with tcgen05.ld and store it; two accumulators in TMEM let
+//     them drain tile t while the MMAs of tile t+1 run, so phi generation
+//     never stops for the epilogue.
 // Precision modes: BF16 (one product) and BF16x3, where phi and W are split
 // into three BF16 parts (x = x0 + x1 + x2, parts of order 1, 2^-9, 2^-18) and
 // the six products down to order 2^-18 are accumulated (about FP32 accuracy).
@@ -35,16 +40,30 @@ namespace rbf {
 
 constexpr int kMM = 128;          // points per tile (MMA M)
 constexpr int kMK = 64;           // centres per K-tile
-constexpr int kMThreads = 512;    // sixteen warps; warp w reads TMEM lanes 32 (w mod 4) ..
+constexpr int kMProducers = 16;   // phi warps 0 .. 15
+constexpr int kMEpilogue = 4;     // epilogue warps 17 .. 20 (TMEM lanes 32 (w mod 4) ..)
+constexpr int kMThreads = 32 * (kMProducers + 1 + kMEpilogue);   // + warp 16: MMAs
 constexpr int kModalMaxOut = 256; // MMA N limit
 constexpr int kModalMaxCentres = 4096;
 
 // byte offset of element (row, k) in a K-major no-swizzle tile of 8x8 core
 // matrices (rows of 16 bytes), K extent kMK: core (row/8, k/8) at
-// ((row/8) * (kMK/8) + k/8) * 128, then (row%8) * 16 + (k%8) * 2
+// ((row/8) * (kMK/8) + k/8) * 128, then (row%8) * 16 + (k%8) * 2.  Used for
+// W: descriptor LBO 128 (next core along K), SBO kMK/8 * 128 (next 8 rows).
 __host__ __device__ __forceinline__ int kmajor_off(int row, int k)
 {
     return ((row >> 3) * (kMK / 8) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// The A (phi) tile: the same core matrices with the 8-row groups adjacent,
+// core (row/8, k/8) at (k/8) * kMM/8 * 128 + (row/8) * 128, i.e. each
+// 8-centre chunk is a plane of kMM rows of 16 bytes.  Descriptor LBO
+// kMM/8 * 128 = 2048 (next core along K), SBO 128 (next 8 rows).  A warp
+// writing 32 consecutive rows of one chunk fills 512 contiguous bytes.
+constexpr int kAPlane = kMM / 8 * 128;
+__device__ __forceinline__ int a_off(int row, int k)
+{
+    return (k >> 3) * kAPlane + row * 16 + (k & 7) * 2;
 }
 
 // Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits 0-13,
@@ -125,14 +144,42 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v)
         v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint4 pack8(const __nv_bfloat16 *b)
+__device__ __forceinline__ unsigned bf2_bits(__nv_bfloat162 v)
+{
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
+// Eight FP32 values to BF16 (round to nearest even), two per conversion.
+__device__ __forceinline__ uint4 pack8_f(const float *x)
 {
     uint4 r;
-    r.x = (uint32_t)__bfloat16_as_ushort(b[0]) | ((uint32_t)__bfloat16_as_ushort(b[1]) << 16);
-    r.y = (uint32_t)__bfloat16_as_ushort(b[2]) | ((uint32_t)__bfloat16_as_ushort(b[3]) << 16);
-    r.z = (uint32_t)__bfloat16_as_ushort(b[4]) | ((uint32_t)__bfloat16_as_ushort(b[5]) << 16);
-    r.w = (uint32_t)__bfloat16_as_ushort(b[6]) | ((uint32_t)__bfloat16_as_ushort(b[7]) << 16);
+    r.x = bf2_bits(__floats2bfloat162_rn(x[0], x[1]));
+    r.y = bf2_bits(__floats2bfloat162_rn(x[2], x[3]));
+    r.z = bf2_bits(__floats2bfloat162_rn(x[4], x[5]));
+    r.w = bf2_bits(__floats2bfloat162_rn(x[6], x[7]));
     return r;
+}
+
+// Three-way split of eight values, two per conversion: x = b0 + b1 + b2
+// element by element, the same parts as split3.
+__device__ __forceinline__ void split3_pack8(const float *x, uint4 &q0, uint4 &q1, uint4 &q2)
+{
+    unsigned o0[4], o1[4], o2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 b0 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+        const float2 f0 = __bfloat1622float2(b0);
+        const float r0 = x[2 * i] - f0.x, r1 = x[2 * i + 1] - f0.y;
+        const __nv_bfloat162 b1 = __floats2bfloat162_rn(r0, r1);
+        const float2 f1 = __bfloat1622float2(b1);
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(r0 - f1.x, r1 - f1.y);
+        o0[i] = bf2_bits(b0);
+        o1[i] = bf2_bits(b1);
+        o2[i] = bf2_bits(b2);
+    }
+    q0 = make_uint4(o0[0], o0[1], o0[2], o0[3]);
+    q1 = make_uint4(o1[0], o1[1], o1[2], o1[3]);
+    q2 = make_uint4(o2[0], o2[1], o2[2], o2[3]);
 }
 
 // Three-way BF16 split: x = b0 + b1 + b2 (each the nearest BF16 of what is
@@ -153,38 +200,89 @@ struct ModalShape {
     int tmem_cols;   // allocated TMEM columns (power of 2 >= n_out)
     size_t a_bytes;  // one A tile (one split)
     size_t w_bytes;  // one W K-tile (one split)
+    int nw;          // W K-tile buffers: 3 where shared memory allows, else 2
 };
 
-// A product list for the split mode: (phi part, W part) pairs.
-__constant__ int c_prod_a[6] = {0, 0, 1, 0, 1, 2};
-__constant__ int c_prod_w[6] = {0, 1, 0, 2, 1, 0};
+// Bounded wait on an mbarrier phase that also gives up once another thread
+// of the CTA has raised the shared failure flag.
+__device__ __forceinline__ bool mbar_wait_or_fail(unsigned long long *bar, unsigned parity,
+                                                  uint64_t limit_ns, volatile int *fail)
+{
+    const unsigned a = smem_addr(bar);
+    uint64_t t0 = 0;
+    for (int it = 0;; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done)
+            return true;
+        if (*fail)
+            return false;
+        if (it == 0) {
+            t0 = globaltimer_ns();
+        } else if (globaltimer_ns() - t0 > limit_ns) {
+            *fail = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 
 // Shared memory: [centres float4 x nc_pad][A buf0 x splits][A buf1 x splits]
-//                [W buf0 x splits][W buf1 x splits][mbarriers][tmem slot]
+//                [W buf0 .. buf nw-1, x splits each][11 mbarriers][tmem slot][fail flag]
+// K-tiles are counted across the CTA's M tiles (g = 0, 1, ...); K-tile g uses
+// A buffer g & 1 and W buffer g mod nw.  The CTA's i-th M tile accumulates in
+// TMEM accumulator i & 1, which the epilogue warps drain while the MMAs of
+// tile i + 1 fill the other.  Every mbarrier completes once per use of its
+// buffer or accumulator, so use u waits for phase parity u & 1; no barrier
+// can run two phases ahead of a waiter, because its next completion needs
+// that waiter's own next step.
+template <int SPLITS>
 __global__ void __launch_bounds__(kMThreads, 1)
 k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ centres,
         int nc_pad, const uint8_t *__restrict__ wpack, ModalShape sh, float *__restrict__ out,
         int *status, uint64_t limit_ns)
 {
+    constexpr int kProd = SPLITS == 1 ? 1 : 6;   // (phi part, W part) products
     extern __shared__ __align__(1024) uint8_t smem[];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float4 *s_c = (float4 *)smem;
     uint8_t *s_a = smem + ((sizeof(float4) * (size_t)nc_pad + 1023) & ~(size_t)1023);
     uint8_t *s_w = s_a + 2 * sh.splits * sh.a_bytes;
-    unsigned long long *bars = (unsigned long long *)(s_w + 2 * sh.splits * sh.w_bytes);
-    // bars[0..1]: W tile loaded (per buffer); bars[2..3]: MMAs of buffer done
-    unsigned *s_tmem = (unsigned *)(bars + 4);
+    unsigned long long *bars = (unsigned long long *)(s_w + sh.nw * sh.splits * sh.w_bytes);
+    // per W buffer: K-tile loaded; per A buffer: MMAs done, A tile written
+    // (16 warps); per accumulator: tile's MMAs done, epilogue done (4 warps)
+    unsigned long long *wfull = bars, *mdone = bars + 3, *afull = bars + 5;
+    unsigned long long *accfull = bars + 7, *accfree = bars + 9;
+    unsigned *s_tmem = (unsigned *)(bars + 11);
+    volatile int *fail = (volatile int *)(s_tmem + 1);   // a wait gave up
 
     for (int j = tid; j < nc_pad; j += kMThreads)
         s_c[j] = centres[j];
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i)
-            mbar_init(&bars[i], 1);
+        *fail = 0;
+        for (int i = 0; i < 3; ++i)
+            mbar_init(&wfull[i], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&mdone[i], 1);
+            mbar_init(&afull[i], kMProducers);
+            mbar_init(&accfull[i], 1);
+            mbar_init(&accfree[i], kMEpilogue);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_addr(s_tmem)),
-                     "r"(sh.tmem_cols)
+                     "r"(2 * sh.tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -192,156 +290,229 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *s_tmem;
-    const uint32_t idesc = idesc_bf16(kMM, sh.n_out);
-    unsigned wphase[2] = {0, 0}, mphase[2] = {0, 0};
-    bool pending[2] = {false, false};
-    bool ok = true;
-
     const int64_t ntiles = (nv + kMM - 1) / kMM;
-    const int row = tid & (kMM - 1), kgrp = tid >> 7;   // kgrp: centres 16 kgrp .. +15
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        int64_t v = tile * kMM + row;
-        const bool live = v < nv;
-        v = live ? v : nv - 1;
-        const float4 q = xq[v];
-        for (int kt = 0; kt < sh.nkt; ++kt) {
-            const int buf = kt & 1;
-            bool mine = true;
-            // the MMAs that last read this buffer pair must be done
-            if (pending[buf]) {
-                mine = mbar_wait(&bars[2 + buf], mphase[buf], limit_ns);
-                if (mine) {   // else the exit path waits again for the MMAs in flight
-                    mphase[buf] ^= 1u;
-                    pending[buf] = false;
+
+    if (warp == kMProducers) {
+        // ---------------- MMA warp (lane 0) ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(kMM, sh.n_out);
+            const size_t wbytes = SPLITS * sh.w_bytes;
+            // this CTA's K-tiles: its M tiles times nkt
+            const long long gtot =
+                (long long)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x) * sh.nkt;
+            // descriptors of buffer pair 0; pair 1 and the parts of a split
+            // are fixed address offsets (the start-address field holds
+            // address / 16 and no sum leaves shared memory)
+            const uint64_t ad0 = smem_desc(smem_addr(s_a), kAPlane, 128);
+            const uint64_t wd0 = smem_desc(smem_addr(s_w), 128, (kMK / 8) * 128);
+            const uint64_t a_buf = (uint64_t)(SPLITS * sh.a_bytes) >> 4;
+            const uint64_t a_part = (uint64_t)sh.a_bytes >> 4;
+            const uint64_t w_buf = (uint64_t)wbytes >> 4, w_part = (uint64_t)sh.w_bytes >> 4;
+            long long g = 0;
+            int i = 0;   // M tiles of this CTA
+            int last_acc = -1;   // tile of the last accumulator commit
+            bool ok = true;
+            // W ring: K-tile j in buffer j mod nw.  Copies run ahead: with
+            // three buffers W(g + 1) starts before K-tile g's MMAs (its
+            // buffer was last read by the MMAs of g - 2); with two, after
+            // them (its buffer was last read by those of g - 1).
+            long long w_issued = 0;   // copies started: W(0) .. W(w_issued - 1)
+            int wb = 0;               // buffer of K-tile g
+            unsigned wpar = 0;        // bit b: parity of buffer b's next completion
+            auto w_start = [&](long long j, int kt_j) {
+                const int b = (int)(j % sh.nw);
+                bulk_g2s_static(s_w + b * wbytes, wpack + (size_t)kt_j * wbytes, (unsigned)wbytes,
+                                &wfull[b]);
+                w_issued = j + 1;
+            };
+            if (gtot > 0)
+                w_start(0, 0);
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++i) {
+                const int ab = i & 1;
+                // accumulator ab: free once tile i - 2's epilogue is done
+                if (i >= 2 &&
+                    !mbar_wait_or_fail(&accfree[ab], (unsigned)((i >> 1) - 1) & 1u, limit_ns,
+                                       fail)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned dacc = tmem + (unsigned)(ab * sh.tmem_cols);
+                for (int kt = 0; kt < sh.nkt; ++kt, ++g) {
+                    const int buf = (int)(g & 1);
+                    const unsigned par = (unsigned)(g >> 1) & 1u;
+                    const int kt_next = kt + 1 == sh.nkt ? 0 : kt + 1;
+                    if (sh.nw == 3 && g + 1 < gtot) {
+                        if (g >= 2 && !mbar_wait_or_fail(&mdone[buf], par ^ 1u, limit_ns, fail)) {
+                            ok = false;
+                            break;
+                        }
+                        w_start(g + 1, kt_next);
+                    }
+                    if (!mbar_wait_or_fail(&wfull[wb], (wpar >> wb) & 1u, limit_ns, fail)) {
+                        ok = false;
+                        break;
+                    }
+                    wpar ^= 1u << wb;
+                    if (!mbar_wait_or_fail(&afull[buf], par, limit_ns, fail)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t ab_d = ad0 + (buf ? a_buf : 0), wb_d = wd0 + wb * w_buf;
+#pragma unroll
+                    for (int pr = 0; pr < kProd; ++pr) {
+                        // products x0 w0, x0 w1, x1 w0, x0 w2, x1 w1, x2 w0
+                        const int ia = SPLITS == 1 ? 0 : (pr == 2 || pr == 4) ? 1 : pr == 5 ? 2 : 0;
+                        const int iw = SPLITS == 1 ? 0 : pr == 1 || pr == 4 ? 1 : pr == 3 ? 2 : 0;
+#pragma unroll
+                        for (int ks = 0; ks < kMK / 16; ++ks) {
+                            // K step of 16 = two core matrices along K: A at
+                            // 2 x kAPlane bytes, W at 256 bytes
+                            const uint64_t ad = ab_d + ia * a_part + (uint64_t)(ks * 2 * kAPlane / 16);
+                            const uint64_t bd = wb_d + iw * w_part + (uint64_t)(ks * 256 / 16);
+                            mma_bf16(dacc, ad, bd, idesc, (kt | pr | ks) != 0);
+                        }
+                    }
+                    mma_commit(&mdone[buf]);
+                    if (sh.nw == 2 && g + 1 < gtot) {
+                        if (g >= 1 && !mbar_wait_or_fail(&mdone[buf ^ 1],
+                                                         (unsigned)((g - 1) >> 1) & 1u, limit_ns,
+                                                         fail)) {
+                            ok = false;
+                            break;
+                        }
+                        w_start(g + 1, kt_next);
+                    }
+                    wb = wb + 1 == sh.nw ? 0 : wb + 1;
+                }
+                if (ok) {
+                    mma_commit(&accfull[ab]);
+                    last_acc = i;
                 }
             }
-            // W K-tile (all splits) by one bulk copy
-            if (tid == 0 && mine) {
-                const size_t bytes = sh.splits * sh.w_bytes;
-                bulk_g2s(s_w + buf * sh.splits * sh.w_bytes, wpack + (size_t)kt * bytes,
-                         (unsigned)bytes, &bars[buf]);
+            // nothing of this thread in flight at exit: the W copies started
+            // but not waited for (W(g) .. W(w_issued - 1); K-tile g's own wait
+            // may have given up), and the arrivals of the last commits
+            for (long long j = g; j < w_issued; ++j)
+                mbar_wait(&wfull[j % sh.nw], (unsigned)(j / sh.nw) & 1u, limit_ns);
+            if (g >= 1)
+                mbar_wait(&mdone[(g - 1) & 1], (unsigned)((g - 1) >> 1) & 1u, limit_ns);
+            if (last_acc >= 0)
+                mbar_wait(&accfull[last_acc & 1], (unsigned)(last_acc >> 1) & 1u, limit_ns);
+        }
+    } else if (warp < kMProducers) {
+        // ---------------- phi warps ----------------
+        // rows 64 (warp mod 2) + lane and + 32 + lane of the tile, 8-centre
+        // chunk warp / 2 of each K-tile: every lane of a warp reads the same
+        // centre (a broadcast) for two independent phi chains, and a warp's
+        // stores fill 512 contiguous bytes per row set
+        const int row0 = (warp & 1) * 64 + lane, row1 = row0 + 32;
+        const int chunk = warp >> 1;
+        long long g = 0;
+        bool ok = true;
+        auto point = [&](int64_t t, int row) {
+            int64_t v = t * kMM + row;
+            v = v < nv ? v : nv - 1;
+            return xq[v];
+        };
+        float4 q0n = point(blockIdx.x, row0), q1n = point(blockIdx.x, row1);
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const float4 q0 = q0n, q1 = q1n;
+            if (tile + gridDim.x < ntiles) {   // in flight during this tile
+                q0n = point(tile + gridDim.x, row0);
+                q1n = point(tile + gridDim.x, row1);
             }
-            // phi for this thread's row and its 16 centres of the K-tile
-            uint8_t *a0 = s_a + buf * sh.splits * sh.a_bytes;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k8 = kgrp * 16 + h * 8;
-                __nv_bfloat16 p0[8], p1[8], p2[8];
+            for (int kt = 0; kt < sh.nkt; ++kt, ++g) {
+                const int buf = (int)(g & 1);
+                const unsigned par = (unsigned)(g >> 1) & 1u;
+                // the A buffer: free once the MMAs of use g - 2 are done
+                if (g >= 2 && !mbar_wait_or_fail(&mdone[buf], par ^ 1u, limit_ns, fail)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *a0 = s_a + buf * SPLITS * sh.a_bytes;
+                const int k8 = 8 * chunk;
+                float ph0[8], ph1[8];
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk) {
                     const float4 c = s_c[kt * kMK + k8 + kk];
-                    const float dx = q.x - c.x, dy = q.y - c.y, dz = q.z - c.z;
-                    const float ph = phi_f32_s(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-                    if (sh.splits == 1) {
-                        p0[kk] = __float2bfloat16_rn(ph);
-                    } else {
-                        split3(ph, p0[kk], p1[kk], p2[kk]);
-                    }
+                    const float ax = q0.x - c.x, ay = q0.y - c.y, az = q0.z - c.z;
+                    const float bx = q1.x - c.x, by = q1.y - c.y, bz = q1.z - c.z;
+                    ph0[kk] = phi_f32_s(fmaf(az, az, fmaf(ay, ay, ax * ax)));
+                    ph1[kk] = phi_f32_s(fmaf(bz, bz, fmaf(by, by, bx * bx)));
                 }
-                const int off = kmajor_off(row, k8);
-                *(uint4 *)(a0 + off) = pack8(p0);
-                if (sh.splits == 3) {
-                    *(uint4 *)(a0 + sh.a_bytes + off) = pack8(p1);
-                    *(uint4 *)(a0 + 2 * sh.a_bytes + off) = pack8(p2);
-                }
-            }
-            // generic-proxy stores -> visible to the tensor core (async proxy)
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            // one barrier: the A tile is complete, and every thread learns
-            // whether a wait anywhere in the CTA gave up
-            if (__syncthreads_or(!mine || *(volatile int *)status == (int)RBF_E_TIMEOUT)) {
-                ok = false;
-                break;
-            }
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                bool got = mbar_wait(&bars[buf], wphase[buf], limit_ns);
-                wphase[buf] ^= 1u;
-                if (!got) {
-                    atomicExch(status, (int)RBF_E_TIMEOUT);
+                const int off0 = a_off(row0, k8), off1 = a_off(row1, k8);
+                if (SPLITS == 1) {
+                    *(uint4 *)(a0 + off0) = pack8_f(ph0);
+                    *(uint4 *)(a0 + off1) = pack8_f(ph1);
                 } else {
-                    const uint8_t *w0 = s_w + buf * sh.splits * sh.w_bytes;
-                    const int nprod = sh.splits == 1 ? 1 : 6;
-                    for (int pr = 0; pr < nprod; ++pr) {
-                        const int ia = sh.splits == 1 ? 0 : c_prod_a[pr];
-                        const int iw = sh.splits == 1 ? 0 : c_prod_w[pr];
-                        const unsigned abase = smem_addr(a0 + ia * sh.a_bytes);
-                        const unsigned wbase = smem_addr(w0 + iw * sh.w_bytes);
-#pragma unroll
-                        for (int ks = 0; ks < kMK / 16; ++ks) {
-                            // K step of 16 = two core matrices along K (256 bytes)
-                            const uint64_t ad = smem_desc(abase + ks * 256, 128, (kMK / 8) * 128);
-                            const uint64_t bd = smem_desc(wbase + ks * 256, 128, (kMK / 8) * 128);
-                            mma_bf16(tmem, ad, bd, idesc, (kt | pr | ks) != 0);
-                        }
-                    }
-                    mma_commit(&bars[2 + buf]);
+                    uint4 u0, u1, u2;
+                    split3_pack8(ph0, u0, u1, u2);
+                    *(uint4 *)(a0 + off0) = u0;
+                    *(uint4 *)(a0 + sh.a_bytes + off0) = u1;
+                    *(uint4 *)(a0 + 2 * sh.a_bytes + off0) = u2;
+                    split3_pack8(ph1, u0, u1, u2);
+                    *(uint4 *)(a0 + off1) = u0;
+                    *(uint4 *)(a0 + sh.a_bytes + off1) = u1;
+                    *(uint4 *)(a0 + 2 * sh.a_bytes + off1) = u2;
                 }
-            }
-            pending[buf] = true;
-        }
-        // accumulator complete once the last commit has landed
-        bool mine = ok;
-        for (int b = 0; b < 2 && mine; ++b) {
-            if (pending[b]) {
-                mine = mbar_wait(&bars[2 + b], mphase[b], limit_ns);
-                if (mine) {
-                    mphase[b] ^= 1u;
-                    pending[b] = false;
-                }
+                // generic-proxy stores -> visible to the tensor core (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&afull[buf]);
             }
         }
-        if (__syncthreads_or(!mine || !ok || *(volatile int *)status == (int)RBF_E_TIMEOUT)) {
-            ok = false;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +31 (rows of the
-        // tile) and the 32-column groups w / 4, w / 4 + 4, ...
+    } else {
+        // ---------------- epilogue warps ----------------
+        // the CTA's tile i: accumulator i & 1, TMEM lanes 32 (warp mod 4) ..
+        // +31 (rows of the tile), every 32-column group
         const int quarter = warp & 3;
-        const int erow = quarter * 32 + (tid & 31);
-        const int64_t ev = tile * kMM + erow;
-        float *orow = out + (size_t)(ev < nv ? ev : 0) * sh.n_out;
-        const unsigned lane_base = tmem + ((unsigned)(quarter * 32) << 16);
-        for (int c0 = (warp >> 2) * 32; c0 < sh.n_out; c0 += 128) {
-            if (c0 + 32 <= sh.n_out) {
-                float vals[32];
-                tmem_ld32(lane_base + (unsigned)c0, vals);
-                if (ev < nv) {
+        int i = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            if (!mbar_wait_or_fail(&accfull[i & 1], (unsigned)(i >> 1) & 1u, limit_ns, fail))
+                break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int64_t ev = tile * kMM + quarter * 32 + lane;
+            float *orow = out + (size_t)(ev < nv ? ev : 0) * sh.n_out;
+            const unsigned lane_base =
+                tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((i & 1) * sh.tmem_cols);
+            for (int c0 = 0; c0 < sh.n_out; c0 += 32) {
+                if (c0 + 32 <= sh.n_out) {
+                    float vals[32];
+                    tmem_ld32(lane_base + (unsigned)c0, vals);
+                    if (ev < nv) {
 #pragma unroll
-                    for (int i = 0; i < 32; i += 4)
-                        *(float4 *)(orow + c0 + i) =
-                            make_float4(vals[i], vals[i + 1], vals[i + 2], vals[i + 3]);
-                }
-            } else {   // n_out % 32 == 16: one 16-column tail
-                float vals[16];
-                tmem_ld16(lane_base + (unsigned)c0, vals);
-                if (ev < nv) {
+                        for (int e = 0; e < 32; e += 4)
+                            *(float4 *)(orow + c0 + e) =
+                                make_float4(vals[e], vals[e + 1], vals[e + 2], vals[e + 3]);
+                    }
+                } else {   // n_out % 32 == 16: one 16-column tail
+                    float vals[16];
+                    tmem_ld16(lane_base + (unsigned)c0, vals);
+                    if (ev < nv) {
 #pragma unroll
-                    for (int i = 0; i < 16; i += 4)
-                        *(float4 *)(orow + c0 + i) =
-                            make_float4(vals[i], vals[i + 1], vals[i + 2], vals[i + 3]);
+                        for (int e = 0; e < 16; e += 4)
+                            *(float4 *)(orow + c0 + e) =
+                                make_float4(vals[e], vals[e + 1], vals[e + 2], vals[e + 3]);
+                    }
                 }
             }
+            // the TMEM reads are done before the accumulator is handed back
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&accfree[i & 1]);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-    }
-    if (!ok) {
-        // leave nothing in flight: bounded waits for outstanding work
-        for (int b = 0; b < 2; ++b) {
-            if (pending[b])
-                mbar_wait(&bars[2 + b], mphase[b], limit_ns);
-        }
-        if (tid == 0)
-            atomicExch(status, (int)RBF_E_TIMEOUT);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (*fail && tid == 0)
+        atomicExch(status, (int)RBF_E_TIMEOUT);
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(sh.tmem_cols)
+                     "r"(2 * sh.tmem_cols)
                      : "memory");
 }
 
@@ -410,6 +581,7 @@ static ModalShape modal_shape(int64_t nc, int n_out, int splits)
         s.tmem_cols *= 2;
     s.a_bytes = (size_t)kMM * kMK * 2;
     s.w_bytes = (size_t)n_out * kMK * 2;
+    s.nw = 2;
     return s;
 }
 
@@ -417,7 +589,7 @@ static size_t modal_smem(const ModalShape &s)
 {
     const size_t nc_pad = (size_t)s.nkt * kMK;
     return align_up(sizeof(float4) * nc_pad, 1024) + 2 * s.splits * s.a_bytes +
-           2 * s.splits * s.w_bytes + 4 * 8 + 16;
+           (size_t)s.nw * s.splits * s.w_bytes + 11 * 8 + 16;
 }
 
 struct ModalWs {
@@ -466,16 +638,24 @@ extern "C" rbf_status rbf_deform_modal(const double *d_xv, int64_t nv, const dou
         return RBF_OK;
     if (!d_xv || !d_xb || !d_sel_idx || !d_w || !d_out || ((uintptr_t)d_out & 15) != 0)
         return RBF_E_ARG;
-    const ModalShape sh = modal_shape(nc, n_out, mode == RBF_MODAL_BF16 ? 1 : 3);
+    ModalShape sh = modal_shape(nc, n_out, mode == RBF_MODAL_BF16 ? 1 : 3);
     const ModalWs L = modal_ws(nv, sh);
     if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
         return RBF_E_WORKSPACE;
-    const size_t smem = modal_smem(sh);
     DeviceInfo dev;
     if (!device_info(&dev))
         return RBF_E_CUDA;
-    if (smem > dev.smem_optin)
-        return RBF_E_ARG;   // too many centres for the resident centre table
+    cudaFuncAttributes fattr{};
+    const void *kfn = sh.splits == 1 ? (const void *)k_modal<1> : (const void *)k_modal<3>;
+    if (cudaFuncGetAttributes(&fattr, kfn) != cudaSuccess)
+        return RBF_E_CUDA;
+    ModalShape sh3 = sh;
+    sh3.nw = 3;
+    if (modal_smem(sh3) + fattr.sharedSizeBytes <= dev.smem_optin)
+        sh = sh3;   // a third W buffer lets each copy start one K-tile earlier
+    const size_t smem = modal_smem(sh);
+    if (smem + fattr.sharedSizeBytes > dev.smem_optin)
+        return RBF_E_ARG;   // too many centres or columns for the shared buffers
     cudaStream_t st = (cudaStream_t)stream;
     char *ws = (char *)d_ws;
     float4 *xq = (float4 *)(ws + L.xq);
@@ -493,13 +673,17 @@ extern "C" rbf_status rbf_deform_modal(const double *d_xv, int64_t nv, const dou
     const int64_t wtot = (int64_t)nc_pad * n_out;
     k_modal_pack_w<<<(int)std::min<int64_t>((wtot + 255) / 256, dev.sms * 8), 256, 0, st>>>(
         d_w, (int)nc, n_out, sh.nkt, sh.splits, sh.w_bytes, wp);
-    if (cudaFuncSetAttribute(k_modal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return RBF_E_CUDA;
     const int64_t ntiles = (nv + kMM - 1) / kMM;
     const int grid = (int)std::min<int64_t>(ntiles, dev.sms);
-    k_modal<<<grid, kMThreads, smem, st>>>(xq, nv, c, nc_pad, wp, sh, d_out, status,
-                                           kBarrierLimitNs);
+    if (sh.splits == 1)
+        k_modal<1><<<grid, kMThreads, smem, st>>>(xq, nv, c, nc_pad, wp, sh, d_out, status,
+                                                  kBarrierLimitNs);
+    else
+        k_modal<3><<<grid, kMThreads, smem, st>>>(xq, nv, c, nc_pad, wp, sh, d_out, status,
+                                                  kBarrierLimitNs);
     if (cudaGetLastError() != cudaSuccess)
         return RBF_E_CUDA;
     return RBF_OK;

@@ -138,6 +138,18 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def max_over_ranks(values, world, device):
+    """Whole-job timing over N replica ranks: every rank contributes its own
+    times and gets the largest of each (one all-reduce, MAX).  With N = 1 the
+    values come back unchanged."""
+    if world <= 1:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
 def kernel_traffic(name):
     """DRAM bytes per launch of a kernel from a committed ncu capture, or None
     when the kernel's sources changed since the capture (hash mismatch)."""
@@ -349,12 +361,7 @@ def run_ours(args, rank, world):
     d2h = hout.numel() * 8 + nc * 4
 
     # max over ranks
-    if world > 1:
-        t = torch.tensor([ms_per_step, statistics.mean(e2e_ms)], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_per_step, e2e_mean = t.tolist()
-    else:
-        e2e_mean = statistics.mean(e2e_ms)
+    ms_per_step, e2e_mean = max_over_ranks([ms_per_step, statistics.mean(e2e_ms)], world, dev)
 
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -716,7 +723,7 @@ def run_modal(args, rank, world):
         "roofline": {"bound": "tensor", "kernel": "k_modal (BF16x3)",
                      "achieved": 6 * mma_flops / t16x3 / 1e12, "peak": bf16_peak / 1e12,
                      "unit": "TFLOP/s", "frac": 6 * mma_flops / t16x3 / bf16_peak,
-                     "traffic": None,
+                     "traffic": kernel_traffic("k_modal"),
                      "phi_generation_alu_frac": nv * nc * FLOPS_PER_PAIR / t16x3 / fp32_peak,
                      "bf16_single": {"achieved": mma_flops / t16 / 1e12,
                                      "frac": mma_flops / t16 / bf16_peak}},

@@ -474,22 +474,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
-// bulk_g2s without the proxy fences, for a source written before the kernel
-// started (the launch boundary orders it) into shared memory that only the
-// async proxy touches (bulk copies write it, tcgen05.mma reads it).
-__device__ __forceinline__ void bulk_g2s_static(void *dst, const void *src, unsigned bytes,
-                                                unsigned long long *bar)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
 // One thread: one arrival that expects `bytes` in total from the copies
 // started next with bulk_copy_g2s (fences as in bulk_g2s).
 __device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)

@@ -197,11 +197,30 @@ struct ModalShape {
     int n_out;       // columns (multiple of 16, <= 256)
     int nkt;         // K-tiles
     int splits;      // 1 (BF16) or 3 (BF16x3)
-    int tmem_cols;   // allocated TMEM columns (power of 2 >= n_out)
+    int tmem_cols;   // TMEM columns per accumulator (power of 2 >= its width)
+    int pair;        // BF16x3 with n_out <= 128: products x0 [w0|w1] and x1 [w0|w1]
+                     // as N = 2 n_out MMAs into a 2 n_out accumulator whose
+                     // halves the epilogue adds (4 MMAs per K step, not 6)
     size_t a_bytes;  // one A tile (one split)
     size_t w_bytes;  // one W K-tile (one split)
     int nw;          // W K-tile buffers: 3 where shared memory allows, else 2
 };
+
+// bulk_g2s without the proxy fences, for a source written before the kernel
+// started (the launch boundary orders it) into shared memory that only the
+// async proxy touches (bulk copies write it, tcgen05.mma reads it).
+__device__ __forceinline__ void bulk_g2s_static(void *dst, const void *src, unsigned bytes,
+                                                unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
 
 // Bounded wait on an mbarrier phase that also gives up once another thread
 // of the CTA has raised the shared failure flag.
@@ -296,6 +315,7 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
         // ---------------- MMA warp (lane 0) ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(kMM, sh.n_out);
+            const uint32_t idesc2 = idesc_bf16(kMM, 2 * sh.n_out);   // pair mode
             const size_t wbytes = SPLITS * sh.w_bytes;
             // this CTA's K-tiles: its M tiles times nkt
             const long long gtot =
@@ -360,18 +380,35 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint64_t ab_d = ad0 + (buf ? a_buf : 0), wb_d = wd0 + wb * w_buf;
-#pragma unroll
-                    for (int pr = 0; pr < kProd; ++pr) {
-                        // products x0 w0, x0 w1, x1 w0, x0 w2, x1 w1, x2 w0
-                        const int ia = SPLITS == 1 ? 0 : (pr == 2 || pr == 4) ? 1 : pr == 5 ? 2 : 0;
-                        const int iw = SPLITS == 1 ? 0 : pr == 1 || pr == 4 ? 1 : pr == 3 ? 2 : 0;
+                    if (SPLITS == 3 && sh.pair) {
+                        // x0 [w0|w1] and x1 [w0|w1] (N = 2 n_out; the W parts
+                        // are adjacent along N), x0 w2 and x2 w0 (N = n_out)
 #pragma unroll
                         for (int ks = 0; ks < kMK / 16; ++ks) {
-                            // K step of 16 = two core matrices along K: A at
-                            // 2 x kAPlane bytes, W at 256 bytes
-                            const uint64_t ad = ab_d + ia * a_part + (uint64_t)(ks * 2 * kAPlane / 16);
-                            const uint64_t bd = wb_d + iw * w_part + (uint64_t)(ks * 256 / 16);
-                            mma_bf16(dacc, ad, bd, idesc, (kt | pr | ks) != 0);
+                            const uint64_t ao = (uint64_t)(ks * 2 * kAPlane / 16);
+                            const uint64_t wo = (uint64_t)(ks * 256 / 16);
+                            mma_bf16(dacc, ab_d + ao, wb_d + wo, idesc2, (kt | ks) != 0);
+                            mma_bf16(dacc, ab_d + a_part + ao, wb_d + wo, idesc2, 1);
+                            mma_bf16(dacc, ab_d + ao, wb_d + 2 * w_part + wo, idesc, 1);
+                            mma_bf16(dacc + (unsigned)sh.n_out, ab_d + 2 * a_part + ao, wb_d + wo,
+                                     idesc, 1);
+                        }
+                    } else {
+#pragma unroll
+                        for (int pr = 0; pr < kProd; ++pr) {
+                            // products x0 w0, x0 w1, x1 w0, x0 w2, x1 w1, x2 w0
+                            const int ia =
+                                SPLITS == 1 ? 0 : (pr == 2 || pr == 4) ? 1 : pr == 5 ? 2 : 0;
+                            const int iw = SPLITS == 1 ? 0 : pr == 1 || pr == 4 ? 1 : pr == 3 ? 2 : 0;
+#pragma unroll
+                            for (int ks = 0; ks < kMK / 16; ++ks) {
+                                // K step of 16 = two core matrices along K: A at
+                                // 2 x kAPlane bytes, W at 256 bytes
+                                const uint64_t ad =
+                                    ab_d + ia * a_part + (uint64_t)(ks * 2 * kAPlane / 16);
+                                const uint64_t bd = wb_d + iw * w_part + (uint64_t)(ks * 256 / 16);
+                                mma_bf16(dacc, ad, bd, idesc, (kt | pr | ks) != 0);
+                            }
                         }
                     }
                     mma_commit(&mdone[buf]);
@@ -478,24 +515,40 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
             float *orow = out + (size_t)(ev < nv ? ev : 0) * sh.n_out;
             const unsigned lane_base =
                 tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((i & 1) * sh.tmem_cols);
-            for (int c0 = 0; c0 < sh.n_out; c0 += 32) {
-                if (c0 + 32 <= sh.n_out) {
-                    float vals[32];
-                    tmem_ld32(lane_base + (unsigned)c0, vals);
-                    if (ev < nv) {
-#pragma unroll
-                        for (int e = 0; e < 32; e += 4)
-                            *(float4 *)(orow + c0 + e) =
-                                make_float4(vals[e], vals[e + 1], vals[e + 2], vals[e + 3]);
-                    }
-                } else {   // n_out % 32 == 16: one 16-column tail
-                    float vals[16];
-                    tmem_ld16(lane_base + (unsigned)c0, vals);
+            if (sh.pair) {
+                // the two halves of the accumulator, 16 columns at a time
+                for (int c0 = 0; c0 < sh.n_out; c0 += 16) {
+                    float lo[16], hi[16];
+                    tmem_ld16(lane_base + (unsigned)c0, lo);
+                    tmem_ld16(lane_base + (unsigned)(c0 + sh.n_out), hi);
                     if (ev < nv) {
 #pragma unroll
                         for (int e = 0; e < 16; e += 4)
                             *(float4 *)(orow + c0 + e) =
-                                make_float4(vals[e], vals[e + 1], vals[e + 2], vals[e + 3]);
+                                make_float4(lo[e] + hi[e], lo[e + 1] + hi[e + 1],
+                                            lo[e + 2] + hi[e + 2], lo[e + 3] + hi[e + 3]);
+                    }
+                }
+            } else {
+                for (int c0 = 0; c0 < sh.n_out; c0 += 32) {
+                    if (c0 + 32 <= sh.n_out) {
+                        float vals[32];
+                        tmem_ld32(lane_base + (unsigned)c0, vals);
+                        if (ev < nv) {
+#pragma unroll
+                            for (int e = 0; e < 32; e += 4)
+                                *(float4 *)(orow + c0 + e) =
+                                    make_float4(vals[e], vals[e + 1], vals[e + 2], vals[e + 3]);
+                        }
+                    } else {   // n_out % 32 == 16: one 16-column tail
+                        float vals[16];
+                        tmem_ld16(lane_base + (unsigned)c0, vals);
+                        if (ev < nv) {
+#pragma unroll
+                            for (int e = 0; e < 16; e += 4)
+                                *(float4 *)(orow + c0 + e) =
+                                    make_float4(vals[e], vals[e + 1], vals[e + 2], vals[e + 3]);
+                        }
                     }
                 }
             }
@@ -576,8 +629,9 @@ static ModalShape modal_shape(int64_t nc, int n_out, int splits)
     s.n_out = n_out;
     s.nkt = (int)((nc + kMK - 1) / kMK);
     s.splits = splits;
+    s.pair = splits == 3 && n_out <= 128;
     s.tmem_cols = 32;
-    while (s.tmem_cols < n_out)
+    while (s.tmem_cols < (s.pair ? 2 : 1) * n_out)
         s.tmem_cols *= 2;
     s.a_bytes = (size_t)kMM * kMK * 2;
     s.w_bytes = (size_t)n_out * kMK * 2;

@@ -122,6 +122,18 @@ def test_newer_entry_points_reject_bad_arguments_before_touching_a_device():
     pa = rbf.make_params(2.0, eval_prec=48)
     assert L.rbf_deform_volume_adjoint_factored(fake, 10, fake, None, C.byref(pa), fake,
                                                 C.byref(res), fake, 1 << 20, None) == E_ARG
+    # peak selection: peaks in 1..16, separation finite and >= 0, then the
+    # usual greedy checks (all before any device work)
+    pg = rbf.make_params(2.0, tol=1e-3, m=4, nc_max=50)
+    nc_out = C.c_int64(0)
+    for peaks, sep in ((0, 0.1), (17, 0.1), (4, -0.5), (4, float("nan")), (4, float("inf"))):
+        assert L.rbf_greedy_select_peaks(fake, fake, 1000, C.byref(pg), peaks, sep, fake, None,
+                                         None, C.byref(nc_out), None, fake, 1 << 30,
+                                         None) == E_ARG
+    assert L.rbf_greedy_select_peaks(None, fake, 1000, C.byref(pg), 4, 0.1, fake, None, None,
+                                     C.byref(nc_out), None, fake, 1 << 30, None) == E_ARG
+    assert L.rbf_greedy_select_peaks(fake, fake, 1000, C.byref(pg), 4, 0.1, fake, None, None,
+                                     C.byref(nc_out), None, None, 0, None) == E_WS
     # latency microbenchmarks
     assert L.rbf_measure_latency(99, 0, C.byref(res), None) == E_ARG
     assert L.rbf_measure_latency(1, 64, None, None) == E_ARG

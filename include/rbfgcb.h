@@ -307,6 +307,15 @@ rbf_status rbf_deform_volume(const double *d_xv, int64_t nv,
  *                           (orders 1, 2^-9, 2^-18); the six products down
  *                           to order 2^-18 are accumulated (about FP32
  *                           accuracy).
+ *   mode RBF_MODAL_F16X2  : phi and W split into two FP16 parts each (orders
+ *                           1 and 2^-11; each column of W is first scaled by
+ *                           a power of two into [-1, 1), undone on output);
+ *                           the three products down to order 2^-11 x 2^-11
+ *                           are accumulated.  Errors: about 2^-20 sum_j
+ *                           |w_j phi_vj| plus 2^-24 sum_j |w_j| (phi below
+ *                           the FP16 normal range, 6.1e-5, keeps an absolute
+ *                           precision of 2^-25), with half the products of
+ *                           BF16X3.
  * Errors against FP64 scale with sum_j |w_j phi_vj|, not with |D|: weights
  * of ill-conditioned support sets (large R) cancel heavily.
  *
@@ -318,6 +327,7 @@ rbf_status rbf_deform_volume(const double *d_xv, int64_t nv,
  * (RBF_E_TIMEOUT if a bounded wait ran out).
  * ------------------------------------------------------------------------ */
 #define RBF_MODAL_BF16 1
+#define RBF_MODAL_F16X2 2
 #define RBF_MODAL_BF16X3 3
 
 size_t rbf_modal_workspace_bytes(int64_t nv, int64_t nc, int n_out, int mode);

@@ -22,6 +22,7 @@ from .rbf import (  # noqa: F401
     deform_modal,
     MODAL_BF16,
     MODAL_BF16X3,
+    MODAL_F16X2,
     RBFDeform,
     GreedyBatch,
     VolumeBatch,

@@ -25,12 +25,17 @@
 //     accumulator with tcgen05.ld and store it; two accumulators in TMEM let
 //     them drain tile t while the MMAs of tile t+1 run, so phi generation
 //     never stops for the epilogue.
-// Precision modes: BF16 (one product) and BF16x3, where phi and W are split
+// Precision modes: BF16 (one product); BF16x3, where phi and W are split
 // into three BF16 parts (x = x0 + x1 + x2, parts of order 1, 2^-9, 2^-18) and
-// the six products down to order 2^-18 are accumulated (about FP32 accuracy).
+// the six products down to order 2^-18 are accumulated (about FP32 accuracy);
+// and FP16x2, where phi and the column-scaled W are split into two FP16
+// parts (orders 1, 2^-11) and the three products x0 w0, x0 w1, x1 w0 are
+// accumulated (FP16's 11-bit significand makes two parts as precise as three
+// BF16 ones, at half the products).
 #include <algorithm>
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "rbf_device.cuh"
@@ -80,12 +85,13 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned saddr, unsigned lbo, unsi
     return d;
 }
 
-// Instruction descriptor, kind::f16: D format F32 (bit 4), A and B BF16
-// (bits 7-9 and 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in
-// bits 24-28.
-__host__ __device__ __forceinline__ uint32_t idesc_bf16(int m, int n)
+// Instruction descriptor, kind::f16: D format F32 (bit 4), A and B of ONE
+// type (bits 7-9 and 10-12: 1 = BF16, 0 = FP16, always set together), both
+// K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ __forceinline__ uint32_t idesc_f16kind(int m, int n, bool fp16)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+    const uint32_t fmt = fp16 ? 0u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) |
            ((uint32_t)(m >> 4) << 24);
 }
 
@@ -182,6 +188,28 @@ __device__ __forceinline__ void split3_pack8(const float *x, uint4 &q0, uint4 &q
     q2 = make_uint4(o2[0], o2[1], o2[2], o2[3]);
 }
 
+__device__ __forceinline__ unsigned h2_bits(__half2 v)
+{
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
+// Two-way FP16 split of eight values in [0, 1], two per conversion:
+// x = h0 + h1 element by element (h1 the nearest FP16 of x - h0).
+__device__ __forceinline__ void split2_pack8_f16(const float *x, uint4 &q0, uint4 &q1)
+{
+    unsigned o0[4], o1[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __half2 h0 = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
+        const float2 f0 = __half22float2(h0);
+        const __half2 h1 = __floats2half2_rn(x[2 * i] - f0.x, x[2 * i + 1] - f0.y);
+        o0[i] = h2_bits(h0);
+        o1[i] = h2_bits(h1);
+    }
+    q0 = make_uint4(o0[0], o0[1], o0[2], o0[3]);
+    q1 = make_uint4(o1[0], o1[1], o1[2], o1[3]);
+}
+
 // Three-way BF16 split: x = b0 + b1 + b2 (each the nearest BF16 of what is
 // left), about 24 significant bits in all.
 __device__ __forceinline__ void split3(float x, __nv_bfloat16 &b0, __nv_bfloat16 &b1,
@@ -198,9 +226,10 @@ struct ModalShape {
     int nkt;         // K-tiles
     int splits;      // 1 (BF16) or 3 (BF16x3)
     int tmem_cols;   // TMEM columns per accumulator (power of 2 >= its width)
-    int pair;        // BF16x3 with n_out <= 128: products x0 [w0|w1] and x1 [w0|w1]
-                     // as N = 2 n_out MMAs into a 2 n_out accumulator whose
-                     // halves the epilogue adds (4 MMAs per K step, not 6)
+    int pair;        // split modes with n_out <= 128: products x0 [w0|w1] (and, for
+                     // BF16x3, x1 [w0|w1]) as N = 2 n_out MMAs into a 2 n_out
+                     // accumulator whose halves the epilogue adds (BF16x3: 4
+                     // MMAs per K step, not 6; FP16x2: 2, not 3)
     size_t a_bytes;  // one A tile (one split)
     size_t w_bytes;  // one W K-tile (one split)
     int nw;          // W K-tile buffers: 3 where shared memory allows, else 2
@@ -268,9 +297,10 @@ template <int SPLITS>
 __global__ void __launch_bounds__(kMThreads, 1)
 k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ centres,
         int nc_pad, const uint8_t *__restrict__ wpack, ModalShape sh, float *__restrict__ out,
-        int *status, uint64_t limit_ns)
+        const float *__restrict__ wscale, int *status, uint64_t limit_ns)
 {
-    constexpr int kProd = SPLITS == 1 ? 1 : 6;   // (phi part, W part) products
+    constexpr int kProd = SPLITS == 1 ? 1 : SPLITS == 2 ? 3 : 6;   // (phi part, W part) products
+    constexpr bool kF16 = SPLITS == 2;   // FP16 parts (both operands), else BF16
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float4 *s_c = (float4 *)smem;
@@ -314,8 +344,8 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
     if (warp == kMProducers) {
         // ---------------- MMA warp (lane 0) ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(kMM, sh.n_out);
-            const uint32_t idesc2 = idesc_bf16(kMM, 2 * sh.n_out);   // pair mode
+            const uint32_t idesc = idesc_f16kind(kMM, sh.n_out, kF16);
+            const uint32_t idesc2 = idesc_f16kind(kMM, 2 * sh.n_out, kF16);   // pair mode
             const size_t wbytes = SPLITS * sh.w_bytes;
             // this CTA's K-tiles: its M tiles times nkt
             const long long gtot =
@@ -380,7 +410,16 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint64_t ab_d = ad0 + (buf ? a_buf : 0), wb_d = wd0 + wb * w_buf;
-                    if (SPLITS == 3 && sh.pair) {
+                    if (SPLITS == 2 && sh.pair) {
+                        // x0 [w0|w1] (N = 2 n_out) and x1 w0 (N = n_out)
+#pragma unroll
+                        for (int ks = 0; ks < kMK / 16; ++ks) {
+                            const uint64_t ao = (uint64_t)(ks * 2 * kAPlane / 16);
+                            const uint64_t wo = (uint64_t)(ks * 256 / 16);
+                            mma_bf16(dacc, ab_d + ao, wb_d + wo, idesc2, (kt | ks) != 0);
+                            mma_bf16(dacc, ab_d + a_part + ao, wb_d + wo, idesc, 1);
+                        }
+                    } else if (SPLITS == 3 && sh.pair) {
                         // x0 [w0|w1] and x1 [w0|w1] (N = 2 n_out; the W parts
                         // are adjacent along N), x0 w2 and x2 w0 (N = n_out)
 #pragma unroll
@@ -397,6 +436,7 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
 #pragma unroll
                         for (int pr = 0; pr < kProd; ++pr) {
                             // products x0 w0, x0 w1, x1 w0, x0 w2, x1 w1, x2 w0
+                            // (FP16x2: the first three)
                             const int ia =
                                 SPLITS == 1 ? 0 : (pr == 2 || pr == 4) ? 1 : pr == 5 ? 2 : 0;
                             const int iw = SPLITS == 1 ? 0 : pr == 1 || pr == 4 ? 1 : pr == 3 ? 2 : 0;
@@ -483,6 +523,14 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
                 if (SPLITS == 1) {
                     *(uint4 *)(a0 + off0) = pack8_f(ph0);
                     *(uint4 *)(a0 + off1) = pack8_f(ph1);
+                } else if (SPLITS == 2) {
+                    uint4 u0, u1;
+                    split2_pack8_f16(ph0, u0, u1);
+                    *(uint4 *)(a0 + off0) = u0;
+                    *(uint4 *)(a0 + sh.a_bytes + off0) = u1;
+                    split2_pack8_f16(ph1, u0, u1);
+                    *(uint4 *)(a0 + off1) = u0;
+                    *(uint4 *)(a0 + sh.a_bytes + off1) = u1;
                 } else {
                     uint4 u0, u1, u2;
                     split3_pack8(ph0, u0, u1, u2);
@@ -515,6 +563,8 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
             float *orow = out + (size_t)(ev < nv ? ev : 0) * sh.n_out;
             const unsigned lane_base =
                 tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)((i & 1) * sh.tmem_cols);
+            // FP16x2: each column's power-of-two scale of W, undone here
+            auto scl = [&](int col) { return SPLITS == 2 ? __ldg(wscale + col) : 1.0f; };
             if (sh.pair) {
                 // the two halves of the accumulator, 16 columns at a time
                 for (int c0 = 0; c0 < sh.n_out; c0 += 16) {
@@ -525,8 +575,10 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
 #pragma unroll
                         for (int e = 0; e < 16; e += 4)
                             *(float4 *)(orow + c0 + e) =
-                                make_float4(lo[e] + hi[e], lo[e + 1] + hi[e + 1],
-                                            lo[e + 2] + hi[e + 2], lo[e + 3] + hi[e + 3]);
+                                make_float4((lo[e] + hi[e]) * scl(c0 + e),
+                                            (lo[e + 1] + hi[e + 1]) * scl(c0 + e + 1),
+                                            (lo[e + 2] + hi[e + 2]) * scl(c0 + e + 2),
+                                            (lo[e + 3] + hi[e + 3]) * scl(c0 + e + 3));
                     }
                 }
             } else {
@@ -537,8 +589,9 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
                         if (ev < nv) {
 #pragma unroll
                             for (int e = 0; e < 32; e += 4)
-                                *(float4 *)(orow + c0 + e) =
-                                    make_float4(vals[e], vals[e + 1], vals[e + 2], vals[e + 3]);
+                                *(float4 *)(orow + c0 + e) = make_float4(
+                                    vals[e] * scl(c0 + e), vals[e + 1] * scl(c0 + e + 1),
+                                    vals[e + 2] * scl(c0 + e + 2), vals[e + 3] * scl(c0 + e + 3));
                         }
                     } else {   // n_out % 32 == 16: one 16-column tail
                         float vals[16];
@@ -546,8 +599,9 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
                         if (ev < nv) {
 #pragma unroll
                             for (int e = 0; e < 16; e += 4)
-                                *(float4 *)(orow + c0 + e) =
-                                    make_float4(vals[e], vals[e + 1], vals[e + 2], vals[e + 3]);
+                                *(float4 *)(orow + c0 + e) = make_float4(
+                                    vals[e] * scl(c0 + e), vals[e + 1] * scl(c0 + e + 1),
+                                    vals[e + 2] * scl(c0 + e + 2), vals[e + 3] * scl(c0 + e + 3));
                         }
                     }
                 }
@@ -587,8 +641,24 @@ __global__ void k_modal_pack_centres(const double *__restrict__ xb,
     }
 }
 
+// FP16x2: per column c of W, the power of two 2^(e+1) with max_j |W_jc| <
+// 2^(e+1), so that W / scale lies in (-1, 1) (1 for an all-zero column).
+// One thread per column (n_out <= 256).
+__global__ void k_modal_col_scale(const double *__restrict__ W, int nc, int n_out,
+                                  float *__restrict__ scale)
+{
+    const int c = threadIdx.x;
+    if (c >= n_out)
+        return;
+    double m = 0.0;
+    for (int j = 0; j < nc; ++j)
+        m = fmax(m, fabs(W[(size_t)j * n_out + c]));
+    scale[c] = m > 0.0 ? (float)ldexp(1.0, ilogb(m) + 1) : 1.0f;
+}
+
 __global__ void k_modal_pack_w(const double *__restrict__ W, int nc, int n_out, int nkt,
-                               int splits, size_t w_bytes, uint8_t *__restrict__ wpack)
+                               int splits, size_t w_bytes, const float *__restrict__ scale,
+                               uint8_t *__restrict__ wpack)
 {
     const int64_t total = (int64_t)nkt * kMK * n_out;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -596,6 +666,16 @@ __global__ void k_modal_pack_w(const double *__restrict__ W, int nc, int n_out, 
         const int n = (int)(t % n_out);
         const int64_t kg = t / n_out;          // global centre index
         const int kt = (int)(kg / kMK), k = (int)(kg % kMK);
+        uint8_t *base = wpack + (size_t)kt * splits * w_bytes;
+        const int off = kmajor_off(n, k);
+        if (splits == 2) {   // FP16 parts of W / scale (power of two: exact)
+            const float x = kg < nc ? (float)(W[kg * n_out + n] / (double)scale[n]) : 0.0f;
+            const __half h0 = __float2half_rn(x);
+            const __half h1 = __float2half_rn(x - __half2float(h0));
+            *(__half *)(base + off) = h0;
+            *(__half *)(base + w_bytes + off) = h1;
+            continue;
+        }
         const float x = kg < nc ? (float)W[kg * n_out + n] : 0.0f;
         __nv_bfloat16 b0, b1, b2;
         if (splits == 1) {
@@ -604,8 +684,6 @@ __global__ void k_modal_pack_w(const double *__restrict__ W, int nc, int n_out, 
         } else {
             split3(x, b0, b1, b2);
         }
-        uint8_t *base = wpack + (size_t)kt * splits * w_bytes;
-        const int off = kmajor_off(n, k);
         *(__nv_bfloat16 *)(base + off) = b0;
         if (splits == 3) {
             *(__nv_bfloat16 *)(base + w_bytes + off) = b1;
@@ -629,7 +707,7 @@ static ModalShape modal_shape(int64_t nc, int n_out, int splits)
     s.n_out = n_out;
     s.nkt = (int)((nc + kMK - 1) / kMK);
     s.splits = splits;
-    s.pair = splits == 3 && n_out <= 128;
+    s.pair = splits > 1 && n_out <= 128;
     s.tmem_cols = 32;
     while (s.tmem_cols < (s.pair ? 2 : 1) * n_out)
         s.tmem_cols *= 2;
@@ -647,7 +725,7 @@ static size_t modal_smem(const ModalShape &s)
 }
 
 struct ModalWs {
-    size_t status, xq, c, w, total;
+    size_t status, xq, c, w, scale, total;
 };
 
 static ModalWs modal_ws(int64_t nv, const ModalShape &s)
@@ -663,6 +741,7 @@ static ModalWs modal_ws(int64_t nv, const ModalShape &s)
     L.xq = take(sizeof(float4) * (size_t)nv);
     L.c = take(sizeof(float4) * (size_t)s.nkt * kMK);
     L.w = take((size_t)s.nkt * s.splits * s.w_bytes);
+    L.scale = take(sizeof(float) * kModalMaxOut);
     L.total = o;
     return L;
 }
@@ -674,9 +753,10 @@ using namespace rbf;
 extern "C" size_t rbf_modal_workspace_bytes(int64_t nv, int64_t nc, int n_out, int mode)
 {
     if (nv < 0 || nc < 1 || nc > kModalMaxCentres || n_out < 16 || n_out > kModalMaxOut ||
-        n_out % 16 != 0 || (mode != RBF_MODAL_BF16 && mode != RBF_MODAL_BF16X3))
+        n_out % 16 != 0 ||
+        (mode != RBF_MODAL_BF16 && mode != RBF_MODAL_F16X2 && mode != RBF_MODAL_BF16X3))
         return 0;
-    return modal_ws(nv, modal_shape(nc, n_out, mode == RBF_MODAL_BF16 ? 1 : 3)).total;
+    return modal_ws(nv, modal_shape(nc, n_out, mode)).total;
 }
 
 extern "C" rbf_status rbf_deform_modal(const double *d_xv, int64_t nv, const double *d_xb,
@@ -686,13 +766,13 @@ extern "C" rbf_status rbf_deform_modal(const double *d_xv, int64_t nv, const dou
 {
     if (!p || !(p->radius > 0.0) || nv < 0 || nc < 1 || nc > kModalMaxCentres || n_out < 16 ||
         n_out > kModalMaxOut || n_out % 16 != 0 ||
-        (mode != RBF_MODAL_BF16 && mode != RBF_MODAL_BF16X3))
+        (mode != RBF_MODAL_BF16 && mode != RBF_MODAL_F16X2 && mode != RBF_MODAL_BF16X3))
         return RBF_E_ARG;
     if (nv == 0)
         return RBF_OK;
     if (!d_xv || !d_xb || !d_sel_idx || !d_w || !d_out || ((uintptr_t)d_out & 15) != 0)
         return RBF_E_ARG;
-    ModalShape sh = modal_shape(nc, n_out, mode == RBF_MODAL_BF16 ? 1 : 3);
+    ModalShape sh = modal_shape(nc, n_out, mode);   // mode = number of parts
     const ModalWs L = modal_ws(nv, sh);
     if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
         return RBF_E_WORKSPACE;
@@ -700,7 +780,9 @@ extern "C" rbf_status rbf_deform_modal(const double *d_xv, int64_t nv, const dou
     if (!device_info(&dev))
         return RBF_E_CUDA;
     cudaFuncAttributes fattr{};
-    const void *kfn = sh.splits == 1 ? (const void *)k_modal<1> : (const void *)k_modal<3>;
+    const void *kfn = sh.splits == 1   ? (const void *)k_modal<1>
+                      : sh.splits == 2 ? (const void *)k_modal<2>
+                                       : (const void *)k_modal<3>;
     if (cudaFuncGetAttributes(&fattr, kfn) != cudaSuccess)
         return RBF_E_CUDA;
     ModalShape sh3 = sh;
@@ -715,6 +797,7 @@ extern "C" rbf_status rbf_deform_modal(const double *d_xv, int64_t nv, const dou
     float4 *xq = (float4 *)(ws + L.xq);
     float4 *c = (float4 *)(ws + L.c);
     uint8_t *wp = (uint8_t *)(ws + L.w);
+    float *wscale = (float *)(ws + L.scale);
     int *status = (int *)(ws + L.status);
     const double inv_r = 1.0 / p->radius;
     const int nc_pad = sh.nkt * kMK;
@@ -725,19 +808,24 @@ extern "C" rbf_status rbf_deform_modal(const double *d_xv, int64_t nv, const dou
     k_modal_pack_centres<<<(nc_pad + 127) / 128, 128, 0, st>>>(d_xb, d_sel_idx, (int)nc, nc_pad,
                                                               inv_r, c);
     const int64_t wtot = (int64_t)nc_pad * n_out;
+    if (sh.splits == 2)
+        k_modal_col_scale<<<1, kModalMaxOut, 0, st>>>(d_w, (int)nc, n_out, wscale);
     k_modal_pack_w<<<(int)std::min<int64_t>((wtot + 255) / 256, dev.sms * 8), 256, 0, st>>>(
-        d_w, (int)nc, n_out, sh.nkt, sh.splits, sh.w_bytes, wp);
+        d_w, (int)nc, n_out, sh.nkt, sh.splits, sh.w_bytes, wscale, wp);
     if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return RBF_E_CUDA;
     const int64_t ntiles = (nv + kMM - 1) / kMM;
     const int grid = (int)std::min<int64_t>(ntiles, dev.sms);
     if (sh.splits == 1)
-        k_modal<1><<<grid, kMThreads, smem, st>>>(xq, nv, c, nc_pad, wp, sh, d_out, status,
-                                                  kBarrierLimitNs);
+        k_modal<1><<<grid, kMThreads, smem, st>>>(xq, nv, c, nc_pad, wp, sh, d_out, wscale,
+                                                  status, kBarrierLimitNs);
+    else if (sh.splits == 2)
+        k_modal<2><<<grid, kMThreads, smem, st>>>(xq, nv, c, nc_pad, wp, sh, d_out, wscale,
+                                                  status, kBarrierLimitNs);
     else
-        k_modal<3><<<grid, kMThreads, smem, st>>>(xq, nv, c, nc_pad, wp, sh, d_out, status,
-                                                  kBarrierLimitNs);
+        k_modal<3><<<grid, kMThreads, smem, st>>>(xq, nv, c, nc_pad, wp, sh, d_out, wscale,
+                                                  status, kBarrierLimitNs);
     if (cudaGetLastError() != cudaSuccess)
         return RBF_E_CUDA;
     return RBF_OK;

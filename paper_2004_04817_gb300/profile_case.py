@@ -4,7 +4,7 @@
   python -m paper_2004_04817_gb300.profile_case greedy [--m M] [--prec 32|64]
   python -m paper_2004_04817_gb300.profile_case solve
   python -m paper_2004_04817_gb300.profile_case cull [--nv N] [--vprec 32|48] [--radius R]
-  python -m paper_2004_04817_gb300.profile_case modal [--nv N] [--modal-mode 1|3] [--n-out K]
+  python -m paper_2004_04817_gb300.profile_case modal [--nv N] [--modal-mode 1|2|3] [--n-out K]
 
 Each case builds the GCB wing workload (N_b = 50,000), runs the calls once
 untimed, then `--reps` more times, and exits 0.
@@ -29,8 +29,8 @@ def main():
     ap.add_argument("--vprec", type=int, default=32)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--radius", type=float, default=0.25, help="cull: support radius")
-    ap.add_argument("--modal-mode", type=int, default=3, choices=[1, 3],
-                    help="modal: 1 BF16, 3 BF16x3")
+    ap.add_argument("--modal-mode", type=int, default=3, choices=[1, 2, 3],
+                    help="modal: 1 BF16, 2 FP16x2, 3 BF16x3")
     ap.add_argument("--n-out", type=int, default=96, help="modal: columns of W")
     a = ap.parse_args()
     c = synth.wing_gcb(n_vol=a.nv if a.case in ("volume", "cull", "modal") else 0)

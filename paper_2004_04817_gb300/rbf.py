@@ -530,6 +530,7 @@ def group_of(nb, m, seed):
 
 
 MODAL_BF16 = 1
+MODAL_F16X2 = 2
 MODAL_BF16X3 = 3
 
 

@@ -1,7 +1,8 @@
-"""GPU parity of the tensor-core modal path D = Phi_vc W (tcgen05, BF16
-inputs, FP32 accumulation) against FP64, at the error bounds its input
-rounding allows: BF16 |err| <= 2^-7 (Phi |W|), BF16x3 |err| <= 2^-18 (Phi |W|)
-elementwise."""
+"""GPU parity of the tensor-core modal path D = Phi_vc W (tcgen05, BF16 or
+FP16 inputs, FP32 accumulation) against FP64, at the error bounds its input
+rounding allows: BF16 |err| <= 2^-7 (Phi |W|), BF16x3 |err| <= 2^-18 (Phi |W|),
+FP16x2 |err| <= 2^-20 (Phi |W|) + 2^-24 sum_j |W_j| (phi below the FP16 normal
+range keeps an absolute precision of 2^-25) elementwise."""
 import numpy as np
 import pytest
 import torch
@@ -23,8 +24,15 @@ def _ref(xv, xc, W, R):
     return Phi @ W, Phi @ np.abs(W)
 
 
+def _bound(mode, scale, bnd, W):
+    if mode == P.MODAL_F16X2:
+        return 2.0 ** -20 * bnd + 2.0 ** -24 * np.abs(W).sum(axis=0)[None, :] + 1e-6
+    return scale * bnd + 1e-6
+
+
 @pytest.mark.parametrize("n_out", [16, 96])
-@pytest.mark.parametrize("mode,scale", [(P.MODAL_BF16, 2.0 ** -7), (P.MODAL_BF16X3, 2.0 ** -18)])
+@pytest.mark.parametrize("mode,scale", [(P.MODAL_BF16, 2.0 ** -7), (P.MODAL_BF16X3, 2.0 ** -18),
+                                        (P.MODAL_F16X2, None)])
 def test_modal_small_against_fp64(n_out, mode, scale):
     rng = np.random.default_rng(3)
     xb = rng.random((200, 3))
@@ -36,13 +44,34 @@ def test_modal_small_against_fp64(n_out, mode, scale):
     d = P.deform_modal(cuda(xv), cuda(xb), cuda(S, torch.int32), cuda(W), radius=R, mode=mode)
     err = np.abs(d.cpu().numpy().astype(np.float64) - ref)
     assert np.all(np.isfinite(err))
-    assert np.all(err <= scale * bnd + 1e-6), (err / (scale * bnd + 1e-30)).max()
+    lim = _bound(mode, scale, bnd, W)
+    assert np.all(err <= lim), (err / lim).max()
+
+
+@pytest.mark.parametrize("wmag", [1e-3, 1.0, 1e5])
+def test_modal_f16x2_column_scaling(wmag):
+    # weights far outside the FP16 range (1e5 x N(0, 1)) and far below it:
+    # each column is scaled by a power of two before the FP16 split
+    rng = np.random.default_rng(9)
+    xb = rng.random((200, 3))
+    S = np.sort(rng.choice(200, 70, replace=False)).astype(np.int32)
+    W = rng.standard_normal((70, 48)) * wmag * np.logspace(0, 3, 48)[None, :]
+    xv = rng.random((3000, 3)) * 1.2 - 0.1
+    ref, bnd = _ref(xv, xb[S], W, 0.8)
+    d = P.deform_modal(cuda(xv), cuda(xb), cuda(S, torch.int32), cuda(W), radius=0.8,
+                       mode=P.MODAL_F16X2)
+    err = np.abs(d.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(np.isfinite(err))
+    lim = 2.0 ** -20 * bnd + 2.0 ** -24 * np.abs(W).sum(axis=0)[None, :] + 1e-30
+    assert np.all(err <= lim), (err / lim).max()
 
 
 @pytest.mark.parametrize("mode,scale,n_out", [(P.MODAL_BF16, 2.0 ** -7, 48),
                                                (P.MODAL_BF16, 2.0 ** -7, 256),
                                                (P.MODAL_BF16X3, 2.0 ** -18, 48),
-                                               (P.MODAL_BF16X3, 2.0 ** -18, 160)])
+                                               (P.MODAL_BF16X3, 2.0 ** -18, 160),
+                                               (P.MODAL_F16X2, None, 48),
+                                               (P.MODAL_F16X2, None, 256)])
 def test_modal_many_tiles_and_wide_outputs(mode, scale, n_out):
     # 40,000 points: 313 M tiles, two or three per CTA; n_out = 48 ends in a
     # 16-column tail of the second column group, 160 and 256 wrap the column
@@ -57,7 +86,8 @@ def test_modal_many_tiles_and_wide_outputs(mode, scale, n_out):
     d = P.deform_modal(cuda(xv), cuda(xb), cuda(S, torch.int32), cuda(W), radius=R, mode=mode)
     err = np.abs(d.cpu().numpy().astype(np.float64) - ref)
     assert np.all(np.isfinite(err))
-    assert np.all(err <= scale * bnd + 1e-6), (err / (scale * bnd + 1e-30)).max()
+    lim = _bound(mode, scale, bnd, W)
+    assert np.all(err <= lim), (err / lim).max()
 
 
 def test_modal_rejects_buffers_beyond_shared_memory():
@@ -93,8 +123,10 @@ def test_modal_sinusoidal_modes_full_support():
     xv = c["xv"]
     sample = np.random.default_rng(8).choice(len(xv), 2000, replace=False)
     ref, bnd = _ref(xv[sample], c["xb"][S], W, 2.0)
-    for mode, scale in ((P.MODAL_BF16, 2.0 ** -7), (P.MODAL_BF16X3, 2.0 ** -18)):
+    for mode, scale in ((P.MODAL_BF16, 2.0 ** -7), (P.MODAL_BF16X3, 2.0 ** -18),
+                        (P.MODAL_F16X2, None)):
         d = P.deform_modal(cuda(xv), xb, r["idx"], cuda(W), radius=2.0, mode=mode)
         got = d.cpu().numpy()[sample].astype(np.float64)
         err = np.abs(got - ref)
-        assert np.all(err <= scale * bnd + 1e-6), (mode, (err / (scale * bnd)).max())
+        lim = _bound(mode, scale, bnd, W)
+        assert np.all(err <= lim), (mode, (err / lim).max())

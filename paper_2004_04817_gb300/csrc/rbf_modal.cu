@@ -496,6 +496,8 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
         float4 q0n = point(blockIdx.x, row0), q1n = point(blockIdx.x, row1);
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const float4 q0 = q0n, q1 = q1n;
+            const f2 qx2 = f2_pack(q0.x, q1.x), qy2 = f2_pack(q0.y, q1.y),
+                     qz2 = f2_pack(q0.z, q1.z);
             if (tile + gridDim.x < ntiles) {   // in flight during this tile
                 q0n = point(tile + gridDim.x, row0);
                 q1n = point(tile + gridDim.x, row1);
@@ -510,14 +512,16 @@ k_modal(const float4 *__restrict__ xq, int64_t nv, const float4 *__restrict__ ce
                 }
                 uint8_t *a0 = s_a + buf * SPLITS * sh.a_bytes;
                 const int k8 = 8 * chunk;
+                // both rows at once on the paired FP32 pipe (same operations
+                // and rounding as the scalar path, one instruction for two)
                 float ph0[8], ph1[8];
 #pragma unroll
                 for (int kk = 0; kk < 8; ++kk) {
                     const float4 c = s_c[kt * kMK + k8 + kk];
-                    const float ax = q0.x - c.x, ay = q0.y - c.y, az = q0.z - c.z;
-                    const float bx = q1.x - c.x, by = q1.y - c.y, bz = q1.z - c.z;
-                    ph0[kk] = phi_f32_s(fmaf(az, az, fmaf(ay, ay, ax * ax)));
-                    ph1[kk] = phi_f32_s(fmaf(bz, bz, fmaf(by, by, bx * bx)));
+                    const f2 dx = f2_sub(qx2, f2_bcast(c.x)), dy = f2_sub(qy2, f2_bcast(c.y)),
+                             dz = f2_sub(qz2, f2_bcast(c.z));
+                    const f2 ph = phi_f32x2_s(f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx))));
+                    f2_unpack(ph, ph0[kk], ph1[kk]);
                 }
                 const int off0 = a_off(row0, k8), off1 = a_off(row1, k8);
                 if (SPLITS == 1) {

@@ -1413,6 +1413,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
 
     int nc = 0;
     double min_piv = INFINITY;
+    int staged_nc = -1;   // nc of the centre table last staged in shared memory
 
     for (int s = 0; s < 3; ++s) {
         const int pn = ldcg(a.pos_of_node + seeds[s]);
@@ -1520,7 +1521,10 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
             // plane stride: nc in shared memory, ld in global memory
             const int planes = use_ff ? 4 : 2, wplane = use_ff ? 2 : 1;
             const int pst = smem ? nc : a.ld;
-            if (smem) {
+            // the table (and |w|_1) changes only with an append, which grows
+            // nc: after idle iterations the staged copy is still current
+            const bool fresh = nc != staged_nc;
+            if (smem && fresh) {
                 const float4 *src = use_ff ? a.cwff : a.cw32;
                 const unsigned pbytes = (unsigned)(sizeof(float4) * nc);
                 __syncthreads();   // previous readers of the table are done
@@ -1539,17 +1543,20 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 }
                 mbar_phase ^= 1u;
             }
-            if (tid < 32) {
-                float t = 0.0f;
-                for (int j = tid; j < nc; j += 32)
-                    // .w of the weight plane (plane 2 double-float, 1 FP32) = |w|_1
-                    t += smem ? s_cw[(size_t)wplane * nc + j].w
-                              : ldcg((use_ff ? a.cwff : a.cw32) + (size_t)wplane * a.ld + j).w;
-                t = team_sum(t, 32);
-                if (tid == 0)
-                    s_wabs = t;
+            if (fresh) {
+                if (tid < 32) {
+                    float t = 0.0f;
+                    for (int j = tid; j < nc; j += 32)
+                        // .w of the weight plane (plane 2 double-float, 1 FP32) = |w|_1
+                        t += smem ? s_cw[(size_t)wplane * nc + j].w
+                                  : ldcg((use_ff ? a.cwff : a.cw32) + (size_t)wplane * a.ld + j).w;
+                    t = team_sum(t, 32);
+                    if (tid == 0)
+                        s_wabs = t;
+                }
+                staged_nc = nc;
+                __syncthreads();
             }
-            __syncthreads();
             phase(look >= 0 ? 11 : 8);
             if (!use_ff) {
                 const float4 *cw = smem ? s_cw : a.cw32;

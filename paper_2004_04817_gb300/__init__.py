@@ -34,6 +34,7 @@ from .rbf import (  # noqa: F401
     group_of,
     status_string,
     STATUS,
+    E_NC_MAX,
     PREC_F32,
     PREC_F32X2,
     PREC_F64,

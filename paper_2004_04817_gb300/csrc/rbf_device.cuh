@@ -356,12 +356,12 @@ __device__ __forceinline__ void ff_fma_acc2(ff2 &acc, f2 wh, f2 wl, ff2 ph)
 }
 
 // ----------------------------------------------------------------------------
-// Argmax keys.  Larger key = larger error; among equal errors the lowest node
-// index wins.  Key 0 means "no candidate".
-//  - FP64 errors: the top 40 bits of the (non-negative) double's bit pattern,
-//    then 24 bits of (0xFFFFFF - node).  Truncation keeps the order of errors
-//    that differ by more than 2^-28 relative; the exact FP64 value of the
-//    winner is read back from the per-node error buffer.
+// Argmax keys: a container for an argmax candidate's node and the "no
+// candidate" marker (key 0).
+//  - The top 40 bits of the (non-negative) FP64 error's bit pattern, then 24
+//    bits of (0xFFFFFF - node), so a key is never 0.  Candidates are ranked by
+//    their exact error carried beside the key, then by the lower node index;
+//    the truncated value in the key is not used for ranking.
 // ----------------------------------------------------------------------------
 constexpr uint64_t kIdxBits = 24;
 constexpr uint64_t kIdxMask = (1ull << kIdxBits) - 1;
@@ -376,16 +376,6 @@ __device__ __forceinline__ uint64_t key_f64(double e, int node)
 __device__ __forceinline__ int key_node(uint64_t key)
 {
     return (int)(kIdxMask - (key & kIdxMask));
-}
-
-__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
 }
 
 __device__ __forceinline__ double warp_sum_f64(double v)

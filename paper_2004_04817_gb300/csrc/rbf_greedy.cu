@@ -65,7 +65,6 @@ struct GreedyCtl {
     GridBar bar;
     int status;
     int pad0;
-    unsigned long long slot[3];   // argmax keys (ring, indexed by evaluation count)
     unsigned long long tslot[3];  // screen thresholds (bits of a non-negative double, ring)
     double estar;
     long long nc;
@@ -400,7 +399,6 @@ struct Red {
     double v[kGWarps];
     long long i[kGWarps];
     double s[kGWarps][4];
-    unsigned long long key[kGWarps];
 };
 
 // Block-level argmax of (v, i); thread 0 returns the result.
@@ -446,19 +444,6 @@ __device__ void block_sum4(Red &r, double a[4])
         }
 }
 
-__device__ void block_max_key(Red &r, unsigned long long &key)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    key = warp_max_u64(key);
-    __syncthreads();
-    if (lane == 0)
-        r.key[w] = key;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int k = 1; k < kGWarps; ++k)
-            key = r.key[k] > key ? r.key[k] : key;
-}
-
 // Grid-wide (value, index) argmax through per-CTA partials: every CTA reads
 // the G partials after the barrier and reduces them in the same order.
 __device__ void grid_pick_reduce(const double *pv, const long long *pi, int G, double &v,
@@ -486,6 +471,21 @@ __device__ void grid_pick_reduce(const double *pv, const long long *pi, int G, d
     v = s_v;
     i = s_i;
     __syncthreads();
+}
+
+// The better of two argmax candidates: the larger exact value (errors are
+// non-negative doubles, compared as bit patterns), the lower node index
+// among equal values (Alg. 1).  A candidate is a key, which carries the node
+// (key_node) and is 0 for "none", and its exact value.
+__device__ __forceinline__ bool lead_better(unsigned long long k2, double e2,
+                                            unsigned long long k, double e)
+{
+    if (k2 == 0)
+        return false;
+    if (k == 0)
+        return true;
+    const unsigned long long b2 = dbits(e2), b = dbits(e);
+    return b2 > b || (b2 == b && key_node(k2) < key_node(k));
 }
 
 // Grid-wide reductions of the per-CTA partials (4 values per CTA).  Warp 0
@@ -1429,7 +1429,6 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     phase(5);
     // ---------------- error evaluation over a position range ---------------
     int ev = 0;                      // evaluation counter
-    int p2uses = 0;                  // FP64 re-score passes (key ring index)
     long long pairs32 = 0, pairs64 = 0, pairsff = 0;
     unsigned long long rescored_local = 0;
     // Evaluates E at positions [p0, p1) with the current weights.  With
@@ -1500,7 +1499,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         first = min(first, (long long)((q - look + nb) % nb));
                     if (argmax) {
                         const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
-                        if (k2 > key) {
+                        if (lead_better(k2, e, key, e_lead)) {
                             key = k2;
                             e_lead = e;
                             b_lead = 0.0;
@@ -1600,7 +1599,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         lsq = fmaf(e, e, lsq);
                         if (argmax) {
                             const unsigned long long k2 = key_f64((double)e, ldcg(a.node_of_pos + q));
-                            if (k2 > key) {
+                            if (lead_better(k2, (double)e, key, e_lead)) {
                                 key = k2;
                                 e_lead = (double)e;
                                 b_lead = (double)beta;
@@ -1721,7 +1720,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         lsq = fmaf(ef.h, ef.h, lsq);
                         if (argmax) {
                             const unsigned long long k2 = key_f64(e, qnode);
-                            if (k2 > key) {
+                            if (lead_better(k2, e, key, e_lead)) {
                                 key = k2;
                                 e_lead = e;
                                 b_lead = (double)bf;
@@ -1756,7 +1755,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                             unsigned long long ov1, unsigned long long ov2, long long om1,
                             unsigned long long omx, float osq, long long ofr) {
                 fr = min(fr, ofr);
-                if (ok_ > k) {
+                if (lead_better(ok_, oel, k, el)) {
                     k = ok_;
                     el = oel;
                     bl = obl;
@@ -1824,7 +1823,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 unsigned long long k = 0;
                 const EvalRec *rb = a.rec + (size_t)(use & 1) * kMaxGrid;
                 auto merge = [](unsigned long long &k, EvalRec &t, const EvalRec &o) {
-                    if ((unsigned long long)o.key > k) {
+                    if (lead_better((unsigned long long)o.key, o.e_lead, k, t.e_lead)) {
                         k = (unsigned long long)o.key;
                         t.e_lead = o.e_lead;
                         t.b_lead = o.b_lead;
@@ -1913,8 +1912,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 // ---- pass 2 (rare): FP64 re-score of every node whose upper
                 // bound reaches the leader's lower bound
                 phase(2);
-                const int r2 = p2uses % 3;   // key ring of the FP64 passes
-                unsigned long long key2 = 0;
+                double bv = -1.0;   // exact (value, node) argmax of the re-scored nodes
+                long long bi = -1;
                 const double thr = lower;   // the maximum is >= the leader's lower bound
                 for (int it = 0; it < rounds; ++it) {
                     const int q = p0 + team + it * nteams;
@@ -1929,28 +1928,29 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         ++rescored_local;
                         a.e64[q] = e;
                         a.u32[q] = 0.0f;
-                        const unsigned long long k2 = key_f64(e, ldcg(a.node_of_pos + q));
-                        key2 = k2 > key2 ? k2 : key2;
+                        pick(bv, bi, e, (long long)ldcg(a.node_of_pos + q));
                     }
                 }
-                block_max_key(red, key2);
-                if (tid == 0 && key2)
-                    atomicMax(&ctl->slot[r2], key2);
-                GSYNC_B();
-                const unsigned long long k64 = ldcg(&ctl->slot[r2]);
-                if (k64) {
-                    out.key = k64;
-                    out.p_lead = ldcg(a.pos_of_node + key_node(k64));
-                    out.e_lead = ldcg(a.e64 + out.p_lead);
-                    out.b_lead = 0.0;
+                block_pick(red, bv, bi);
+                if (tid == 0) {
+                    part(use)[g_vb] = bv;
+                    parti(use)[g_vb] = bi;
                 }
-                if (g_vb == 0 && tid == 0)
-                    ctl->slot[(r2 + 2) % 3] = 0ull;
-                ++p2uses;
-                // every node left out has E < thr <= the leader's E, so the
-                // largest FP64 value among the re-scored nodes is the maximum
-                if (k64)
-                    out.gmax = ldcg(a.e64 + ldcg(a.pos_of_node + key_node(k64)));
+                GSYNC_B();
+                double gv;
+                long long gi;
+                grid_pick_reduce(part(use), parti(use), G, gv, gi);
+                ++use;
+                if (gi >= 0) {
+                    out.key = key_f64(gv, (int)gi);
+                    out.p_lead = ldcg(a.pos_of_node + gi);
+                    out.e_lead = gv;
+                    out.b_lead = 0.0;
+                    // every node left out has E < thr <= the leader's E, so
+                    // the largest FP64 value among the re-scored nodes is the
+                    // maximum
+                    out.gmax = gv;
+                }
             }
         }
         phase(5);

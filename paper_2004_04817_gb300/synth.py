@@ -418,3 +418,22 @@ def random_field(n, seed, sigma=1.0):
     """i.i.d. Gaussian (n, 3) field with standard deviation sigma."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return sigma * rng.standard_normal((n, 3))
+
+
+def line_near_tie(n=64, big=10, near=50, rel=2.0 ** -35):
+    """Nodes at (i, 0, 0), i = 0..n-1, all displaced by t = 2^-4 along x,
+    except node ``big`` (2t, the largest displacement) and node ``near``
+    (t (1 + rel)).  With support radius 1.5 the seed nodes are ``big``, n-1
+    and the node farthest from both, and every node more than one step from a
+    seed keeps its own displacement as its error.  So the next pick is decided
+    by a relative difference ``rel`` (exactly representable, far above FP64
+    rounding, below 2^-28), and the picks after it by exact ties."""
+    t = 2.0 ** -4
+    xb = np.zeros((n, 3))
+    xb[:, 0] = np.arange(n, dtype=np.float64)
+    db = np.zeros((n, 3))
+    db[:, 0] = t
+    db[big, 0] = 2.0 * t
+    db[near, 0] = t * (1.0 + rel)
+    return dict(xb=xb, db=db, radius=1.5, t=t, big=big, near=near,
+                name=f"line{n}-near-tie")

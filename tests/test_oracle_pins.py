@@ -444,3 +444,19 @@ def test_peaks_one_is_algorithm_1():
         assert a["idx"].tolist() == b["idx"].tolist()
         assert a["iter"].tolist() == b["iter"].tolist()
         assert a["stats"]["iterations"] == b["iterations"]
+
+
+def test_argmax_resolves_a_difference_of_2_pow_35_and_exact_ties_by_index():
+    """Alg. 1 picks the node of largest error, the lowest index among equal
+    errors.  On the near-tie line the fourth pick is the node whose error is
+    t (1 + 2^-35) (every other free node far from the seeds has exactly t);
+    the picks after it are exact ties, taken in ascending index, skipping the
+    neighbours of each pick (their error drops below t)."""
+    c = synth.line_near_tie()
+    r = oracle.greedy(c["xb"], c["db"], c["radius"], 0.5 * c["t"], m=1, seed=1, ncmax=8)
+    n = len(c["xb"])
+    # seeds: largest displacement; farthest from it; farthest from both
+    # (nodes 36 and 37 are 26 from the nearer seed: the lower index wins)
+    assert r["idx"][:3].tolist() == [c["big"], n - 1, 36]
+    assert r["idx"][3] == c["near"]
+    assert r["idx"][4:8].tolist() == [0, 2, 4, 6]

@@ -145,8 +145,8 @@ typedef struct {
  * Sec. 3).  Seed nodes: n0 = argmax |dr_j|, n1 = the node farthest from n0,
  * n2 = the node farthest from {n0, n1} (lowest index on ties).  Iteration k
  * (from 3) evaluates E_q for q in G_(k mod m) minus S with the current
- * weights, takes the largest (lowest index on ties) and appends it to S when
- * E > E* (strict).  The Cholesky factor of Phi_SS grows by one row per
+ * weights, takes the largest FP64 E_q (the lowest index only among exactly
+ * equal values) and appends it to S when E > E* (strict).  The Cholesky factor of Phi_SS grows by one row per
  * appended node (recurrence Cholesky, Sec. 1), in FP64.  The run stops after
  * m consecutive iterations without an append: those m groups cover every
  * node (Sec. 3) and share one set of weights, so max_q E_q <= E* is then

@@ -633,23 +633,25 @@ __device__ __forceinline__ D4 team_resid_f64(const GreedyArgs &a, int q, int nc,
 
 // Dot product of row `row` (length n, L2-coherent loads) with vector v,
 // spread over the 32 lanes of a warp with four independent accumulators.
+// kVShared: v lies in this CTA's shared memory (plain loads).
+template <bool kVShared = false>
 __device__ __forceinline__ double warp_dot(const double *row, const double *v, int p0, int n)
 {
     const int lane = threadIdx.x & 31;
+    auto ldv = [&](int k) { return kVShared ? v[k] : ldcg(v + k); };
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int p = p0 + lane;
     for (; p + 96 < n; p += 128) {
         const double z0 = ldcg(row + p), z1 = ldcg(row + p + 32), z2 = ldcg(row + p + 64),
                      z3 = ldcg(row + p + 96);
-        const double b0 = ldcg(v + p), b1 = ldcg(v + p + 32), b2 = ldcg(v + p + 64),
-                     b3 = ldcg(v + p + 96);
+        const double b0 = ldv(p), b1 = ldv(p + 32), b2 = ldv(p + 64), b3 = ldv(p + 96);
         s0 = fma(z0, b0, s0);
         s1 = fma(z1, b1, s1);
         s2 = fma(z2, b2, s2);
         s3 = fma(z3, b3, s3);
     }
     for (; p < n; p += 32)
-        s0 = fma(ldcg(row + p), ldcg(v + p), s0);
+        s0 = fma(ldcg(row + p), ldv(p), s0);
     return warp_sum_f64((s0 + s1) + (s2 + s3));
 }
 
@@ -749,7 +751,8 @@ __device__ __forceinline__ void put_centre(const GreedyArgs &a, int j, const D4 
 }
 
 __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, double &min_piv,
-                           int pn, int node, long long kiter, unsigned int &epoch)
+                           int pn, int node, long long kiter, unsigned int &epoch,
+                           double *s_b = nullptr)
 {
     GreedyCtl *ctl = a.ctl;
     const int G = g_vg;
@@ -758,20 +761,48 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
     // FP64 instructions cost a warp ~30 FP32 ones on this GPU, so scalar
     // FP64 work runs once per CTA (warp 0) and sums are split across warps.
     __shared__ double s_sc[8];
-    // A1: b_j = phi(|r_n - r_j| / R), centre j on CTA j mod G (FP64 work
-    // spread over every SM)
-    const D4 xn = ldcg(a.xg64 + pn);
-    for (int j = g_vb + G * tid; j < nc; j += G * kGThreads) {
-        const D4 c = ldcg(a.c64 + j);
-        const double dx = xn.x - c.x, dy = xn.y - c.y, dz = xn.z - c.z;
-        a.bvec[j] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
+    // A1: b_j = phi(|r_n - r_j| / R).
+    //  - s_b given (double-float evaluation; s_b is scratch shared memory of
+    //    at least nc doubles): every CTA computes, in double-float on the FP32
+    //    pipe, the entries its own rows of Z need (j <= its last row), so
+    //    no grid barrier separates A1 from A2.  The entries carry the
+    //    double-float phi's accuracy (about 2^-44 relative), the order of the
+    //    FP64 factorisation's own backward error at a few hundred centres.
+    //  - otherwise: FP64, centre j on CTA j mod G (FP64 work spread over every
+    //    SM), then a grid barrier.
+    if (s_b) {
+        const int base = g_vb * kGWarps;
+        int need = 0;
+        if (nc > base) {
+            const int last = base + ((nc - 1 - base) / gwarps) * gwarps + kGWarps - 1;
+            need = min(nc, last + 1);
+        }
+        const float4 xh = ldcg(a.xg32 + pn), xl = ldcg(a.xgl + pn);
+        for (int j = tid; j < need; j += kGThreads) {
+            const float4 ch = ldcg(a.cwff + j), cl = ldcg(a.cwff + (size_t)a.ld + j);
+            const ff ph = phi_ff_s(dist2_ff(xh.x, xl.x, xh.y, xl.y, xh.z, xl.z, ch.x, cl.x,
+                                            ch.y, cl.y, ch.z, cl.z));
+            s_b[j] = (double)ph.h + (double)ph.l;
+        }
+        // the table's next staging overwrites s_b with bulk (async-proxy)
+        // copies: order these generic writes before them
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    } else {
+        const D4 xn = ldcg(a.xg64 + pn);
+        for (int j = g_vb + G * tid; j < nc; j += G * kGThreads) {
+            const D4 c = ldcg(a.c64 + j);
+            const double dx = xn.x - c.x, dy = xn.y - c.y, dz = xn.z - c.z;
+            a.bvec[j] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
+        }
+        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
     }
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
     // A2: l = Z b (warp per row) and the partial sums of l.l and l.y (lane 0
     // of each warp accumulates its rows)
     double acc4[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = gwarp; i < nc; i += gwarps) {
-        const double s = warp_dot(a.z + (size_t)i * a.ld, a.bvec, 0, i + 1);
+        const double s = s_b ? warp_dot<true>(a.z + (size_t)i * a.ld, s_b, 0, i + 1)
+                             : warp_dot(a.z + (size_t)i * a.ld, a.bvec, 0, i + 1);
         if (lane == 0) {
             a.lvec[i] = s;
             const D4 y = ldcg(a.y64 + i);
@@ -1414,10 +1445,21 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     int nc = 0;
     double min_piv = INFINITY;
     int staged_nc = -1;   // nc of the centre table last staged in shared memory
+    // Scratch for the append's phi row: the shared-memory centre table (64
+    // bytes per centre in double-float mode, so room for 8 doubles per
+    // staged centre).  An append changes nc, after which the table is staged
+    // again; staged_nc is reset after every append that used the scratch, so
+    // a failed one cannot leave a clobbered table marked current.
+    auto bscratch = [&]() -> double * {
+        return a.prec == RBF_PREC_F32X2 && nc <= 8 * a.smem_cap
+                   ? reinterpret_cast<double *>(s_cw) : nullptr;
+    };
 
     for (int s = 0; s < 3; ++s) {
         const int pn = ldcg(a.pos_of_node + seeds[s]);
-        if (chol_append(a, red, nc, use, min_piv, pn, seeds[s], -1, epoch) != kAppendOk) {
+        const int ar = chol_append(a, red, nc, use, min_piv, pn, seeds[s], -1, epoch, bscratch());
+        staged_nc = -1;
+        if (ar != kAppendOk) {
             if (g_vb == 0 && tid == 0) {
                 ctl->nc = nc;
                 ctl->min_pivot = min_piv;
@@ -2057,9 +2099,10 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     phase(3);
                     const int ar = kPeaks && a.peaks > 1
                                        ? chol_append(a, red, nc, use, min_piv, s_pk_pos[r],
-                                                     s_pk_node[r], k, epoch)
+                                                     s_pk_node[r], k, epoch, bscratch())
                                        : chol_append(a, red, nc, use, min_piv, add_pos, add_node,
-                                                     k, epoch);
+                                                     k, epoch, bscratch());
+                    staged_nc = -1;
                     phase(5);
                     if (ar != kAppendOk) {
                         status = RBF_E_NOT_SPD;   // or the latched timeout, which wins

@@ -38,10 +38,17 @@ namespace rbf {
 // problem a contiguous range of CTAs.  Set by each kernel on entry.
 __shared__ int g_vb;
 __shared__ int g_vg;
+// The grid barrier in use: the control block's own, or the candidate that
+// the greedy's start-up calibration found fastest.
+__shared__ GridBar *g_bar;
 
 constexpr int kGThreads = 256;
 constexpr int kGWarps = kGThreads / kWarp;
 constexpr int kMaxGrid = 4096;
+constexpr int kBarCand = 8;            // candidate barrier locations
+constexpr int kBarCandWords = 1088;    // flags per candidate (4,352-byte stride)
+constexpr int kBarCalRounds = 4;       // timed barriers per candidate
+constexpr int kBarCalMinCtas = 8;      // smaller grids keep the control block's barrier
 constexpr int kSmemCentresF32 = 2048;      // FP32 centres staged in shared memory by the
 constexpr int kSmemCentresFF = 1024;       // batched launch (64 KB, two CTAs per SM); the
                                            // single-problem launch (one CTA per SM) stages
@@ -81,7 +88,17 @@ struct GreedyCtl {
     long long n_hist;
     unsigned long long phase_ns[12];  // CTA 0's time per phase (see rbf_greedy_stats)
     long long barriers;               // grid barriers passed
+    // Candidate locations of the grid barrier's flags.  How long a barrier
+    // takes depends on where its flags live (the same launch measured 1.1
+    // and 2.6 us per barrier at workspace offsets a few KB apart), so the
+    // greedy times a few barriers on each candidate and keeps the fastest.
+    // The stride (4 KB + 256 B) varies the address bits above the line.
+    int bar_pick;
+    int pad1;
+    unsigned int bar_cand[kBarCand][kBarCandWords];
 };
+// The host reads back the statistics only (everything before the candidates).
+constexpr size_t kCtlStatBytes = offsetof(GreedyCtl, bar_pick);
 
 // Per-CTA record of an evaluation (see evaluate).
 // mx, u1, u2: bit patterns of non-negative doubles (0 = none); sq: FP32.
@@ -334,7 +351,7 @@ __device__ __forceinline__ int select_peaks(const GreedyArgs &a, int p0, int p1,
             }
         }
         if (gmode) {
-            if (!grid_barrier(&a.ctl->bar, &a.ctl->status, (unsigned)G, a.barrier_ns, epoch,
+            if (!grid_barrier(g_bar, &a.ctl->status, (unsigned)G, a.barrier_ns, epoch,
                               (unsigned)g_vb))
                 return -2;
             if (warp == 0) {
@@ -701,7 +718,8 @@ struct EvalOut {
 //   l = Z b,  d^2 = phi(0) - l.l,  y_new = (dr_n - l.y) / d,
 //   Z gains the row [-(Z^T l)^T / d, 1 / d],
 //   W_j += -(Z^T l)_j / d * y_new (j < nc),  w_new = y_new / d.
-// All CTAs call it; three grid barriers.  Returns kAppendOk, kAppendNotSpd
+// All CTAs call it; two grid barriers with s_b (double-float mode), three
+// without.  Returns kAppendOk, kAppendNotSpd
 // (d^2 <= kPivotMin, status latched) or kAppendTimeout.
 // ---------------------------------------------------------------------------
 constexpr int kAppendOk = 0, kAppendTimeout = 1, kAppendNotSpd = 2;
@@ -795,7 +813,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
             const double dx = xn.x - c.x, dy = xn.y - c.y, dz = xn.z - c.z;
             a.bvec[j] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
         }
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
+        if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
     }
     // A2: l = Z b (warp per row) and the partial sums of l.l and l.y (lane 0
     // of each warp accumulates its rows)
@@ -823,7 +841,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
             t += red.s[k][warp];
         (a.part + (size_t)(use & 1) * kMaxGrid * 4)[4 * g_vb + warp] = t;
     }
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
+    if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
     {
         // grid sums: warp c adds component c of the G partials (fixed order,
         // the same bits in every CTA)
@@ -894,7 +912,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
         if (a.sel_iter)
             a.sel_iter[nc] = kiter;
     }
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
+    if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
     ++nc;
     return kAppendOk;
 }
@@ -954,7 +972,7 @@ __device__ int chol_append_block(const GreedyArgs &a, int &nc, double &min_piv, 
         const double dx = x.x - c.x, dy = x.y - c.y, dz = x.z - c.z;
         a.cmat[gtid] = phi_f64_s(fma(dz, dz, fma(dy, dy, dx * dx)));
     }
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+    if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
         return kAppendTimeout;
 
     // B2: Lambda = Z B (warp per row), with the partial sums of Lambda^T
@@ -1013,7 +1031,7 @@ __device__ int chol_append_block(const GreedyArgs &a, int &nc, double &min_piv, 
     }
     for (int v = tid; v < V; v += kGThreads)
         a.bpart[(size_t)g_vb * kBlkV + v] = s_acc[v];
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+    if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
         return kAppendTimeout;
     // grid sums: the CTAs split into nseg fixed segments; thread (seg, v)
     // adds its segment's partials of value v (independent loads), then each
@@ -1195,7 +1213,7 @@ __device__ int chol_append_block(const GreedyArgs &a, int &nc, double &min_piv, 
         if (a.sel_iter)
             a.sel_iter[n + k] = kiter;
     }
-    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+    if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
         return kAppendTimeout;
     nc = n + keff;
     if (keff < K) {
@@ -1251,7 +1269,7 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
                 lmax = fmax(lmax, red.v[k]);
             pp[4 * g_vb] = lmax;
         }
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+        if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
             return false;
         {
             double g4[4];
@@ -1268,7 +1286,7 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
             if (lane == 0)
                 tvec[i] = mk4(sx, sy, sz, 0.0);
         }
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+        if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
             return false;
         // W += Z^T t
         for (int j = gwarp; j < nc; j += gwarps) {
@@ -1282,7 +1300,7 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
                 a.w64[j] = w;
             }
         }
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+        if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
             return false;
     }
     return true;
@@ -1303,6 +1321,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     if (threadIdx.x == 0) {
         mbar_init(&s_mbar, 1);
         g_bar_wait_ns = 0;
+        g_bar = &a.ctl->bar;
     }
     __syncthreads();
     GreedyCtl *ctl = a.ctl;
@@ -1330,12 +1349,12 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     auto parti = [&](int u) { return a.parti + (size_t)(u & 1) * kMaxGrid; };
 #define GSYNC()                                                                   \
     do {                                                                          \
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) \
+        if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) \
             return;                                                               \
     } while (0)
 #define GSYNC_B()                                                                 \
     do {                                                                          \
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) \
+        if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) \
             return false;                                                         \
     } while (0)
 
@@ -1343,6 +1362,39 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     // CTAs' bounded waits run out and the launch returns RBF_E_TIMEOUT.
     if ((a.flags & RBF_FLAG_TEST_BARRIER_TIMEOUT) && g_vb == 0)
         return;
+
+    // ---------------- barrier placement ------------------------------------
+    // Thread 0 of CTA 0 times kBarCalRounds grid barriers on each candidate
+    // flag array; the fastest is published through the control block's own
+    // barrier and serves the rest of the launch.  Every candidate's flags
+    // start at 0 (the host clears the control block), so each has its own
+    // epoch; the chosen one continues from kBarCalRounds.
+    long long bar_extra = 0;   // barriers passed that `epoch` does not count
+    if (G >= kBarCalMinCtas && G <= kBarCandWords) {
+        unsigned long long best = ~0ull;
+        int pick = 0;
+        for (int k = 0; k < kBarCand; ++k) {
+            GridBar *cb = reinterpret_cast<GridBar *>(ctl->bar_cand[k]);
+            unsigned int ek = 0;
+            const unsigned long long t0 = clock64();
+            for (int r = 0; r < kBarCalRounds; ++r)
+                if (!grid_barrier(cb, &ctl->status, (unsigned)G, a.barrier_ns, ek, (unsigned)g_vb))
+                    return;
+            const unsigned long long dt = clock64() - t0;
+            if (dt < best) {
+                best = dt;
+                pick = k;
+            }
+        }
+        if (g_vb == 0 && tid == 0)
+            ctl->bar_pick = pick;
+        GSYNC();   // control block's barrier: publishes bar_pick
+        if (tid == 0)
+            g_bar = reinterpret_cast<GridBar *>(ctl->bar_cand[ldcg(&ctl->bar_pick)]);
+        __syncthreads();
+        bar_extra = (long long)epoch + (long long)(kBarCand - 1) * kBarCalRounds;
+        epoch = kBarCalRounds;
+    }
 
     // ---------------- prologue: group-ordered packing ----------------------
     double dmax = 0.0, xmax = 0.0;
@@ -2251,7 +2303,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         if (status != RBF_OK)
             atomicCAS(&ctl->status, (int)RBF_OK, status);
         ctl->max_resid = maxres;
-        ctl->barriers = (long long)epoch;
+        ctl->barriers = (long long)epoch + bar_extra;
         ctl->estar = estar;
         ctl->nc = nc;
         ctl->iterations = k - 3 + 1;
@@ -2331,6 +2383,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
     if (threadIdx.x == 0) {
         g_vb = blockIdx.x;
         g_vg = gridDim.x;
+        g_bar = &a.ctl->bar;
     }
     __syncthreads();
     GreedyCtl *ctl = a.ctl;
@@ -2343,7 +2396,7 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
     auto part = [&](int u) { return a.part + (size_t)(u & 1) * kMaxGrid * 4; };
 #define GSYNC()                                                                   \
     do {                                                                          \
-        if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) \
+        if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) \
             return;                                                               \
     } while (0)
 
@@ -2658,7 +2711,7 @@ static rbf_status greedy_launch(const double *d_xb, const double *d_db, int64_t 
         return RBF_E_CUDA;
     }
     GreedyCtl ctl;
-    if (cudaMemcpyAsync(&ctl, ws + L.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(&ctl, ws + L.ctl, kCtlStatBytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return RBF_E_CUDA;
@@ -2773,7 +2826,7 @@ static rbf_status solve_launch(const double *d_xb, const double *d_db, int64_t n
         return RBF_E_CUDA;
     }
     GreedyCtl ctl;
-    if (cudaMemcpyAsync(&ctl, ws + L.g.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st) !=
+    if (cudaMemcpyAsync(&ctl, ws + L.g.ctl, kCtlStatBytes, cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
@@ -3077,7 +3130,7 @@ extern "C" rbf_status rbf_greedy_batch_results(rbf_greedy_batch *b, int32_t *h_s
     rbf_status worst = RBF_OK;
     for (int i = 0; i < b->B; ++i) {
         GreedyCtl ctl;
-        if (cudaMemcpy(&ctl, b->ws + b->ctl_off[i], sizeof(ctl), cudaMemcpyDeviceToHost) !=
+        if (cudaMemcpy(&ctl, b->ws + b->ctl_off[i], kCtlStatBytes, cudaMemcpyDeviceToHost) !=
             cudaSuccess)
             return RBF_E_CUDA;
         if (h_status)

@@ -1307,6 +1307,48 @@ __device__ bool refine_weights(const GreedyArgs &a, Red &red, int nc, int &use,
 }
 
 // ---------------------------------------------------------------------------
+// Barrier placement.  Thread 0 of CTA 0 times kBarCalRounds grid barriers on
+// each candidate flag array of the control block; the fastest is published
+// through the control block's own barrier and serves the rest of the launch
+// (g_bar).  Every candidate's flags start at 0 (the host clears the control
+// block), so each has its own epoch; `epoch` continues from the chosen one's
+// kBarCalRounds and `extra` counts the other barriers passed.  Grids outside
+// [kBarCalMinCtas, kBarCandWords] keep the control block's barrier.  All
+// CTAs call it before their first grid barrier; false on a barrier timeout.
+// ---------------------------------------------------------------------------
+__device__ bool place_barrier(const GreedyArgs &a, int G, unsigned int &epoch, long long &extra)
+{
+    GreedyCtl *ctl = a.ctl;
+    if (G < kBarCalMinCtas || G > kBarCandWords)
+        return true;
+    unsigned long long best = ~0ull;
+    int pick = 0;
+    for (int k = 0; k < kBarCand; ++k) {
+        GridBar *cb = reinterpret_cast<GridBar *>(ctl->bar_cand[k]);
+        unsigned int ek = 0;
+        const unsigned long long t0 = clock64();
+        for (int r = 0; r < kBarCalRounds; ++r)
+            if (!grid_barrier(cb, &ctl->status, (unsigned)G, a.barrier_ns, ek, (unsigned)g_vb))
+                return false;
+        const unsigned long long dt = clock64() - t0;
+        if (dt < best) {
+            best = dt;
+            pick = k;
+        }
+    }
+    if (g_vb == 0 && threadIdx.x == 0)
+        ctl->bar_pick = pick;
+    if (!grid_barrier(&ctl->bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb))
+        return false;   // the control block's barrier publishes bar_pick
+    if (threadIdx.x == 0)
+        g_bar = reinterpret_cast<GridBar *>(ctl->bar_cand[ldcg(&ctl->bar_pick)]);
+    __syncthreads();
+    extra += (long long)epoch + (long long)(kBarCand - 1) * kBarCalRounds;
+    epoch = kBarCalRounds;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // The persistent greedy: one problem on the CTAs g_vb = 0 .. g_vg - 1.
 // kPeaks: the peak-selection variant (a.peaks > 1) is compiled in.
 // ---------------------------------------------------------------------------
@@ -1364,37 +1406,9 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
         return;
 
     // ---------------- barrier placement ------------------------------------
-    // Thread 0 of CTA 0 times kBarCalRounds grid barriers on each candidate
-    // flag array; the fastest is published through the control block's own
-    // barrier and serves the rest of the launch.  Every candidate's flags
-    // start at 0 (the host clears the control block), so each has its own
-    // epoch; the chosen one continues from kBarCalRounds.
     long long bar_extra = 0;   // barriers passed that `epoch` does not count
-    if (G >= kBarCalMinCtas && G <= kBarCandWords) {
-        unsigned long long best = ~0ull;
-        int pick = 0;
-        for (int k = 0; k < kBarCand; ++k) {
-            GridBar *cb = reinterpret_cast<GridBar *>(ctl->bar_cand[k]);
-            unsigned int ek = 0;
-            const unsigned long long t0 = clock64();
-            for (int r = 0; r < kBarCalRounds; ++r)
-                if (!grid_barrier(cb, &ctl->status, (unsigned)G, a.barrier_ns, ek, (unsigned)g_vb))
-                    return;
-            const unsigned long long dt = clock64() - t0;
-            if (dt < best) {
-                best = dt;
-                pick = k;
-            }
-        }
-        if (g_vb == 0 && tid == 0)
-            ctl->bar_pick = pick;
-        GSYNC();   // control block's barrier: publishes bar_pick
-        if (tid == 0)
-            g_bar = reinterpret_cast<GridBar *>(ctl->bar_cand[ldcg(&ctl->bar_pick)]);
-        __syncthreads();
-        bar_extra = (long long)epoch + (long long)(kBarCand - 1) * kBarCalRounds;
-        epoch = kBarCalRounds;
-    }
+    if (!place_barrier(a, G, epoch, bar_extra))
+        return;
 
     // ---------------- prologue: group-ordered packing ----------------------
     double dmax = 0.0, xmax = 0.0;
@@ -2400,6 +2414,12 @@ k_solve(GreedyArgs a, const int32_t *__restrict__ sel, int nc_total, int steps,
             return;                                                               \
     } while (0)
 
+    // a fresh factorisation passes three barriers per support node: place
+    // the barrier first (a reused factor only refines, and keeps the
+    // control block's barrier)
+    long long bar_extra = 0;
+    if (!reuse && !place_barrier(a, G, epoch, bar_extra))
+        return;
     double bad = 0.0;
     for (int j = gtid; j < nc_total; j += gthreads) {
         const int node = sel[j];

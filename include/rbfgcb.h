@@ -385,11 +385,15 @@ void rbf_volume_batch_destroy(rbf_volume_batch *b);
  * eval_prec = RBF_PREC_F32, reading the volume points in place.
  *
  * Its scratch is a fixed array of RBF_NOALLOC_MAX_CENTRES (centre, weight)
- * entries (256 KiB) in device global memory, reserved on every GPU that
- * loads the library and held until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress, with
- * the device current); make the first call on each device before any stream
- * capture.  Every call shares the array and overwrites the entries it reads,
+ * entries (256 KiB) in device global memory, held on every device that has
+ * used it until the process exits.  Under CUDA's default lazy module loading
+ * the array is reserved when the driver loads the library's module on a
+ * device, which happens inside the first call on that device: that call
+ * looks up the array's device address (cudaGetSymbolAddress, with the device
+ * current) and may synchronise the device.  Make the first call on each
+ * device -- a call with nv = 0 counts, and does only this set-up -- outside
+ * time-critical loops and before any stream capture.  Every call shares the
+ * array and overwrites the entries it reads,
  * so results never depend on an earlier call, but calls whose GPU work
  * overlaps (different streams, or host threads) race on it: serialise them.
  * No cudaMalloc, cudaFree or other allocating routine is called.

@@ -298,7 +298,10 @@ typedef struct {
     double min_pivot;     /* smallest Cholesky pivot seen (SPD check)       */
     int64_t n_div;        /* follow mode: accepted divergences              */
     int64_t n_fail;       /* follow mode: rejected steps                    */
-    double worst_rel_gap; /* follow mode: max (E_oracle - E_follow)/E_oracle */
+    double worst_rel_gap; /* follow mode: largest relative gap of any checked
+                           * decision: (max E - E_follow)/max E for an append,
+                           * (E* - E_follow)/E* for an append at or below E*,
+                           * (max E - E*)/E* for "no add" above E*           */
 } orc_greedy_stats;
 
 /*
@@ -308,8 +311,14 @@ typedef struct {
  * every iteration it checks that decision against its own FP64 errors:
  *   - an added node must lie in G_i, not be in S, have E > E*(1 - tie) and
  *     E >= (1 - tie) * max_G_i E; it counts as a divergence when it is not
- *     the oracle's own argmax;
- *   - "no add" is accepted when max_G_i E <= E*(1 + tie).
+ *     the oracle's own argmax or when its E is not above E* (the literal
+ *     algorithm would not have appended it);
+ *   - "no add" is accepted when max_G_i E <= E*(1 + tie), and counts as a
+ *     divergence when max_G_i E > E*.
+ * The 1e-6 band of the comparison is relative: both the argmax and the
+ * E > E* test may go the other way only where the two values compared agree
+ * to tie_rel; each such step is counted in n_div and its gap in
+ * worst_rel_gap.
  * follow_n < 0 runs the literal algorithm.
  */
 int orc_greedy(const double *xb, const double *db, int64_t nb, double R, double Estar,
@@ -410,9 +419,13 @@ int orc_greedy(const double *xb, const double *db, int64_t nb, double R, double 
                     ok = Ef > Estar * (1.0 - tie_rel) && Ef >= (1.0 - tie_rel) * Eloc;
                 }
                 if (!ok) stats->n_fail++;
-                else if (nf != nloc) stats->n_div++;
+                else if (nf != nloc || !(Ef > Estar)) stats->n_div++;
                 if (Eloc > 0.0 && Ef >= 0.0) {
                     double gap = (Eloc - Ef) / Eloc;
+                    if (gap > stats->worst_rel_gap) stats->worst_rel_gap = gap;
+                }
+                if (Estar > 0.0 && Ef >= 0.0 && !(Ef > Estar)) {
+                    double gap = (Estar - Ef) / Estar;
                     if (gap > stats->worst_rel_gap) stats->worst_rel_gap = gap;
                 }
                 add = nf;
@@ -427,6 +440,10 @@ int orc_greedy(const double *xb, const double *db, int64_t nb, double R, double 
                 }
                 if (nloc >= 0 && Eloc > Estar * (1.0 + tie_rel)) stats->n_fail++;
                 else if (nloc >= 0 && Eloc > Estar) stats->n_div++;
+                if (nloc >= 0 && Estar > 0.0 && Eloc > Estar) {
+                    double gap = (Eloc - Estar) / Estar;
+                    if (gap > stats->worst_rel_gap) stats->worst_rel_gap = gap;
+                }
             }
         }
         if (add >= 0) {

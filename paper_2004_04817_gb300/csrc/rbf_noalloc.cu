@@ -9,7 +9,11 @@
 // callers can still pass inputs and outputs, but cannot provide the
 // workspace that rbf_deform_volume needs.  rbf_deform_volume_noalloc keeps
 // its only scratch -- the packed (centre, weight) table -- in a fixed-size
-// array in device global memory that the library reserves when it is loaded.
+// array in device global memory that belongs to this library's module.
+// Under CUDA's default lazy module loading the driver loads the module, and
+// so reserves the array, during the first call on each device (at the
+// cudaGetSymbolAddress of the set-up); that call may synchronise the device
+// and must stay outside time-critical loops and stream captures.
 //
 // The FP32 arithmetic is the same as rbf_deform_volume with RBF_PREC_F32;
 // volume points are read straight from the caller's FP64 array instead of a
@@ -164,16 +168,18 @@ extern "C" rbf_status rbf_deform_volume_noalloc(const double *d_xv, int64_t nv, 
     if (!p || nv < 0 || nc < 0 || nc > RBF_NOALLOC_MAX_CENTRES || !(p->radius > 0.0) ||
         p->eval_prec != RBF_PREC_F32 || nv > (int64_t)1 << 40)
         return RBF_E_ARG;
-    if (nv == 0)
-        return RBF_OK;
-    if (!d_xv || !d_dv || (nc > 0 && (!d_xb || !d_sel_idx || !d_w)))
+    if (nv > 0 && (!d_xv || !d_dv || (nc > 0 && (!d_xb || !d_sel_idx || !d_w))))
         return RBF_E_ARG;
+    // The per-device set-up runs before the empty-input shortcut, so that a
+    // call with nv = 0 prepares the device like any other first call.
     DeviceInfo dev;
     if (!device_info(&dev))
         return RBF_E_CUDA;
     NoAllocDev nd;
     if (!noalloc_setup(dev.device, &nd))
         return RBF_E_CUDA;
+    if (nv == 0)
+        return RBF_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (nc == 0) {
         if (cudaMemsetAsync(d_dv, 0, sizeof(double) * 3 * (size_t)nv, st) != cudaSuccess)

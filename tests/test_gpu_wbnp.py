@@ -25,6 +25,7 @@ import torch
 import oracle
 import paper_2004_04817_gb300 as P
 from paper_2004_04817_gb300 import synth
+from _follow import check_follow
 
 pytestmark = pytest.mark.gpu
 TIE = 1e-6
@@ -69,6 +70,7 @@ def _check_sampled_decisions(c, r, m, n_appends=6, n_idle=4):
     grp = oracle.groups(len(c["xb"]), m, 1)
     rng = np.random.default_rng(11)
     picks = sorted(set([3, nc - 1] + list(rng.integers(4, nc - 1, n_appends - 2))))
+    gaps = []
     for t in picks:
         S = idx[:t]
         members = np.flatnonzero(grp == it[t] % m)
@@ -77,9 +79,12 @@ def _check_sampled_decisions(c, r, m, n_appends=6, n_idle=4):
         e_gpu = e[np.flatnonzero(members == idx[t])[0]]
         assert e_gpu > c["estar"], (t, e_gpu)
         assert e_gpu >= (1.0 - TIE) * e.max(), (t, e_gpu, e.max())
+        gaps.append((e.max() - e_gpu) / e.max())
     # idle iterations: between appends t-1 and t the set is idx[:t]
-    gaps = [t for t in range(4, nc) if it[t] - it[t - 1] > 1]
-    for t in sorted(set(rng.choice(gaps, min(n_idle, len(gaps)), replace=False))) if gaps else []:
+    print(f"\nsampled appends {picks}: worst relative gap to the group maximum "
+          f"{max(gaps):.3e}")
+    idle = [t for t in range(4, nc) if it[t] - it[t - 1] > 1]
+    for t in sorted(set(rng.choice(idle, min(n_idle, len(idle)), replace=False))) if idle else []:
         k = int(rng.integers(it[t - 1] + 1, it[t]))
         S = idx[:t]
         members = np.flatnonzero(grp == k % m)
@@ -155,3 +160,38 @@ def test_gcb_wbnp_weights_and_volume(case):
     err32 = np.abs(dv32 - ref_w).max(axis=1)
     assert np.all(err32 <= bound), (err32 / bound).max()
     print(f"\nWBNP volume: FP32 max error {err32.max():.3e} ({err32.max() / dmax:.2e} of max|dr|)")
+
+
+@pytest.fixture(scope="module")
+def reduced():
+    """The same assembly at 1 % of the point density (3,000 boundary nodes),
+    R = 6 and tolerance 1e-4 of the largest displacement: small enough for
+    the oracle to replay every decision of the run."""
+    c = synth.wbnp_case(n_vol=0, density=0.01)
+    c["d_xb"] = torch.as_tensor(c["xb"], dtype=torch.float64, device="cuda")
+    c["d_db"] = torch.as_tensor(c["db"], dtype=torch.float64, device="cuda")
+    c["estar"] = oracle.tolerance(c["db"], c["tol_rel"])
+    return c
+
+
+@pytest.mark.parametrize("prec", [P.PREC_F32X2, P.PREC_F32])
+def test_wbnp_reduced_whole_selection_follows_oracle(reduced, prec):
+    """Plain greedy, then GCB with m = 1.5 N_b / N_c: the oracle's follow mode
+    checks every append and every idle iteration of both runs in FP64."""
+    c = reduced
+    plain = P.greedy_select(c["d_xb"], c["d_db"], radius=c["radius"], tol=c["estar"],
+                            tol_mode=0, m=1, seed=1, eval_prec=prec)
+    assert plain["status"] == 0
+    m = int(round(1.5 * len(c["xb"]) / plain["nc"]))
+    for mm, r in ((1, plain), (m, None)):
+        if r is None:
+            r = P.greedy_select(c["d_xb"], c["d_db"], radius=c["radius"], tol=c["estar"],
+                                tol_mode=0, m=mm, seed=1, eval_prec=prec)
+            assert r["status"] == 0
+        f = oracle.greedy(c["xb"], c["db"], c["radius"], c["estar"], m=mm, seed=1,
+                          follow=(r["idx"].cpu().numpy(), r["iter"].cpu().numpy()),
+                          tie_rel=TIE, history=False)
+        check_follow(f, f"assembly at 1 % density, prec {prec}, m={mm}, N_c {r['nc']}")
+        assert f["nc"] == r["nc"]
+        assert f["stats"]["iterations"] == r["stats"]["iterations"]
+        assert r["stats"]["final_max"] <= c["estar"]

@@ -137,3 +137,39 @@ def test_newer_entry_points_reject_bad_arguments_before_touching_a_device():
     # latency microbenchmarks
     assert L.rbf_measure_latency(99, 0, C.byref(res), None) == E_ARG
     assert L.rbf_measure_latency(1, 64, None, None) == E_ARG
+
+
+def test_noalloc_entry_point_rejects_bad_arguments_before_touching_a_device():
+    """rbf_deform_volume_noalloc checks its arguments before any CUDA call, so
+    every rejection below runs without a GPU (the dummy addresses are never
+    dereferenced)."""
+    L = P.lib()
+    f = L.rbf_deform_volume_noalloc
+    f.restype = C.c_int
+    f.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                  C.POINTER(rbf.Params), C.c_void_p, C.c_void_p]
+    E_ARG = 1
+    fake = C.c_void_p(256)
+    ok = rbf.make_params(2.0, eval_prec=P.PREC_F32)
+    cap = 8192                                   # RBF_NOALLOC_MAX_CENTRES
+    assert f"#define RBF_NOALLOC_MAX_CENTRES {cap}" in open(HEADER).read()
+    # more centres than the fixed scratch array holds
+    assert f(fake, 10, fake, fake, cap + 1, fake, C.byref(ok), fake, None) == E_ARG
+    # only the FP32 sum is offered
+    for prec in (P.PREC_F64, P.PREC_F32X2, 16):
+        bad = rbf.make_params(2.0, eval_prec=prec)
+        assert f(fake, 10, fake, fake, 5, fake, C.byref(bad), fake, None) == E_ARG
+    # radius must be positive and finite
+    for r in (0.0, -1.0, float("nan")):
+        bad = rbf.make_params(r, eval_prec=P.PREC_F32)
+        assert f(fake, 10, fake, fake, 5, fake, C.byref(bad), fake, None) == E_ARG
+    # null parameters and null arrays
+    assert f(fake, 10, fake, fake, 5, fake, None, fake, None) == E_ARG
+    assert f(None, 10, fake, fake, 5, fake, C.byref(ok), fake, None) == E_ARG
+    assert f(fake, 10, None, fake, 5, fake, C.byref(ok), fake, None) == E_ARG
+    assert f(fake, 10, fake, None, 5, fake, C.byref(ok), fake, None) == E_ARG
+    assert f(fake, 10, fake, fake, 5, None, C.byref(ok), fake, None) == E_ARG
+    assert f(fake, 10, fake, fake, 5, fake, C.byref(ok), None, None) == E_ARG
+    # negative sizes
+    assert f(fake, -1, fake, fake, 5, fake, C.byref(ok), fake, None) == E_ARG
+    assert f(fake, 10, fake, fake, -1, fake, C.byref(ok), fake, None) == E_ARG

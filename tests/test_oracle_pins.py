@@ -460,3 +460,78 @@ def test_argmax_resolves_a_difference_of_2_pow_35_and_exact_ties_by_index():
     assert r["idx"][:3].tolist() == [c["big"], n - 1, 36]
     assert r["idx"][3] == c["near"]
     assert r["idx"][4:8].tolist() == [0, 2, 4, 6]
+
+
+# The follow mode's acceptance band.  The comparison rule lets the GPU's
+# sequence leave the oracle's only where the two values that decide a step
+# (the two largest errors of the active group for the argmax, or the group
+# maximum and E* for the E > E* test of Alg. 1) agree to 1e-6 relative, and
+# every such step is logged.  On the near-tie line every free node far from
+# the seeds keeps exactly its own displacement as its error, so the deciding
+# gaps below are set by the displacements alone.  A band read 1000x too wide,
+# or too narrow, or with the wrong sign, fails one side of each pair.
+BAND = 1e-6
+
+
+@pytest.mark.parametrize("gap,accepted", [(0.5e-6, True), (0.9e-6, True),
+                                          (1.1e-6, False), (2e-6, False)])
+def test_follow_band_on_the_argmax(gap, accepted):
+    """The followed run appends node 0 (error t) while node `near` has the
+    group's largest error t (1 + gap), then `near`, then the exact ties."""
+    c = synth.line_near_tie(rel=gap)
+    estar = 0.5 * c["t"]
+    r = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1, ncmax=8)
+    assert r["idx"].tolist() == [c["big"], 63, 36, c["near"], 0, 2, 4, 6]
+    seq = np.array([c["big"], 63, 36, 0, c["near"], 2, 4, 6], dtype=np.int32)
+    f = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1, ncmax=8,
+                      follow=(seq, r["iter"]), tie_rel=BAND)
+    s = f["stats"]
+    assert f["idx"].tolist() == seq.tolist()
+    assert s["worst_rel_gap"] == pytest.approx(gap / (1.0 + gap), rel=1e-9)
+    if accepted:
+        assert (s["n_fail"], s["n_div"]) == (0, 1)
+    else:
+        assert (s["n_fail"], s["n_div"]) == (1, 0)
+
+
+@pytest.mark.parametrize("gap,accepted", [(0.5e-6, True), (0.9e-6, True),
+                                          (1.1e-6, False), (2e-6, False)])
+def test_follow_band_on_a_missing_append(gap, accepted):
+    """E* = t (1 - gap): the literal run keeps appending nodes of error t;
+    the followed run stops after its fourth node although the group's
+    maximum t lies above E* by the relative gap."""
+    c = synth.line_near_tie()
+    estar = c["t"] * (1.0 - gap)
+    r = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1)
+    assert r["nc"] > 8
+    f = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1,
+                      follow=(r["idx"][:4], r["iter"][:4]), tie_rel=BAND)
+    s = f["stats"]
+    assert f["nc"] == 4
+    assert s["worst_rel_gap"] == pytest.approx((c["t"] - estar) / estar, rel=1e-6)
+    if accepted:
+        assert (s["n_fail"], s["n_div"]) == (0, 1)
+    else:
+        assert (s["n_fail"], s["n_div"]) == (1, 0)
+
+
+@pytest.mark.parametrize("gap,accepted", [(0.5e-6, True), (0.9e-6, True),
+                                          (1.1e-6, False), (2e-6, False)])
+def test_follow_band_on_an_append_at_or_below_estar(gap, accepted):
+    """E* = t (1 + gap): the literal run appends nothing after the seeds; the
+    followed run appends `near` (error t (1 + 2^-35), the group's maximum),
+    which lies below E* by about the relative gap."""
+    c = synth.line_near_tie()
+    estar = c["t"] * (1.0 + gap)
+    lit = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1)
+    assert lit["nc"] == 3
+    seq = np.array([c["big"], 63, 36, c["near"]], dtype=np.int32)
+    f = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1,
+                      follow=(seq, np.array([-1, -1, -1, 3])), tie_rel=BAND)
+    s = f["stats"]
+    e_near = c["db"][c["near"], 0]
+    assert s["worst_rel_gap"] == pytest.approx((estar - e_near) / estar, rel=1e-6)
+    if accepted:
+        assert (s["n_fail"], s["n_div"]) == (0, 1)
+    else:
+        assert (s["n_fail"], s["n_div"]) == (1, 0)

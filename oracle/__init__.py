@@ -77,6 +77,11 @@ def lib():
                                        C.c_uint64, C.c_int64, C.c_int64, C.c_double, ip,
                                        C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                        C.POINTER(C.c_int64), C.c_int]
+        L.orc_greedy_rc.restype = C.c_int
+        L.orc_greedy_rc.argtypes = [dp, dp, C.c_int64, C.c_double, C.c_double, C.c_int64,
+                                    C.c_uint64, C.c_int64, ip, C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_double), dp, C.c_int]
         L.orc_support_kl.restype = C.c_int
         L.orc_support_kl.argtypes = [dp, C.c_int64, ip, C.c_int64, ip, C.c_int64,
                                      C.POINTER(C.c_double), C.c_int]
@@ -244,6 +249,31 @@ def greedy_peaks(xb, db, R, Estar, m=1, seed=1, ncmax=None, peaks=1, sep=0.0, th
     n = nc.value
     return dict(status=st, idx=out_idx[:n].copy(), iter=out_it[:n].copy(), nc=n,
                 iterations=its.value)
+
+
+def greedy_rc(xb, db, R, Estar, m=1, seed=1, ncmax=None, threads=None):
+    """Algorithm 1 with the recurrence-Cholesky append of Sec. 1 (the paper's
+    own CPU procedure; the fair CPU baseline).  Returns dict(status, idx,
+    iter, nc, iterations, final_max, w) with w the final weights (nc x 3)."""
+    L = lib()
+    xb, px = _d(xb)
+    db, pd = _d(db)
+    nb = len(xb)
+    ncmax = int(ncmax or nb)
+    out_idx = np.zeros(ncmax, dtype=np.int32)
+    out_it = np.zeros(ncmax, dtype=np.int64)
+    nc = C.c_int64(0)
+    its = C.c_int64(0)
+    fmax = C.c_double(0.0)
+    w = np.zeros((ncmax, 3))
+    st = L.orc_greedy_rc(px, pd, nb, float(R), float(Estar), int(m), int(seed), ncmax,
+                         out_idx.ctypes.data_as(C.POINTER(C.c_int32)),
+                         out_it.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(nc),
+                         C.byref(its), C.byref(fmax), w.ctypes.data_as(C.POINTER(C.c_double)),
+                         threads or default_threads())
+    n = nc.value
+    return dict(status=st, idx=out_idx[:n].copy(), iter=out_it[:n].copy(), nc=n,
+                iterations=its.value, final_max=fmax.value, w=w[:n].copy())
 
 
 def nearest_support(xb, S, threads=None):

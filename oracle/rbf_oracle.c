@@ -711,3 +711,145 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* cpu_rc: Algorithm 1 with the recurrence Cholesky (RC) decomposition of   */
+/* Sec. 1 and Table 1 instead of a dense re-solve -- the paper's own CPU     */
+/* procedure, kept as the fair CPU baseline of the timings.  Appending node  */
+/* n to S grows the lower Cholesky factor L of Phi_SS by one row:            */
+/*   b_j = phi(|r_n - r_j| / R) (j in S),  L l = b (forward substitution),   */
+/*   d = sqrt(phi(0) - l.l),  new row [l^T, d],                              */
+/* and the forward vector y (L y = dX_S) by y_n = (dr_n - l.y) / d; the      */
+/* weights then follow from L^T W = y (back substitution).  FP64 throughout; */
+/* the group errors are evaluated in parallel over nodes.  out_w (nullable, */
+/* ncmax x 3) receives the final weights.  Partition, seed                   */
+/* nodes, argmax, E > E* and termination are those of orc_greedy, so the two */
+/* select the same sequence unless rounding separates two near-equal errors. */
+/* A squared pivot d^2 <= 1e-13 (of phi(0) = 1) is singular (ORC_E_NOT_SPD). */
+/* ------------------------------------------------------------------------ */
+int orc_greedy_rc(const double *xb, const double *db, int64_t nb, double R, double Estar,
+                  int64_t m, uint64_t seed, int64_t ncmax,
+                  int32_t *out_idx, int64_t *out_iter, int64_t *out_nc,
+                  int64_t *out_iterations, double *final_max, double *out_w, int nthreads)
+{
+    if (nb < 3 || m < 1 || m > nb || ncmax < 3 || !(R > 0.0) || !(Estar >= 0.0))
+        return ORC_E_ARG;
+    int32_t *group_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    int32_t *members = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    int64_t *goff = (int64_t *)calloc((size_t)m + 1, sizeof(int64_t));
+    char *inS = (char *)calloc((size_t)nb, 1);
+    double *E = (double *)malloc(sizeof(double) * (size_t)nb);
+    double *W = (double *)malloc(sizeof(double) * 3 * (size_t)ncmax);
+    double *Y = (double *)malloc(sizeof(double) * 3 * (size_t)ncmax);
+    double *L = (double *)malloc(sizeof(double) * (size_t)ncmax * (size_t)ncmax);
+    double *l = (double *)malloc(sizeof(double) * (size_t)ncmax);
+    if (!group_of || !members || !goff || !inS || !E || !W || !Y || !L || !l) {
+        free(group_of); free(members); free(goff); free(inS); free(E); free(W); free(Y);
+        free(L); free(l);
+        return ORC_E_NOMEM;
+    }
+    orc_groups(nb, m, seed, group_of);
+    for (int64_t j = 0; j < nb; ++j)
+        goff[group_of[j] + 1]++;
+    for (int64_t g = 0; g < m; ++g)
+        goff[g + 1] += goff[g];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+        for (int64_t g = 0; g < m; ++g)
+            fill[g] = goff[g];
+        for (int64_t j = 0; j < nb; ++j)
+            members[fill[group_of[j]]++] = (int32_t)j;
+        free(fill);
+    }
+    int status = ORC_OK;
+    int64_t nc = 0;
+    /* RC append of node n as row nc of L (row-major, leading dimension ncmax) */
+#define RC_APPEND(n_, it_)                                                       \
+    do {                                                                         \
+        const int32_t nn = (n_);                                                 \
+        double ll = 0.0, ly0 = 0.0, ly1 = 0.0, ly2 = 0.0;                        \
+        for (int64_t i = 0; i < nc; ++i) {                                       \
+            double t = orc_phi(dist3(xb + 3 * nn, xb + 3 * out_idx[i]) / R);     \
+            for (int64_t p = 0; p < i; ++p)                                      \
+                t -= L[i * ncmax + p] * l[p];                                    \
+            l[i] = t / L[i * ncmax + i];                                         \
+            ll += l[i] * l[i];                                                   \
+            ly0 += l[i] * Y[3 * i + 0];                                          \
+            ly1 += l[i] * Y[3 * i + 1];                                          \
+            ly2 += l[i] * Y[3 * i + 2];                                          \
+        }                                                                        \
+        const double d2 = orc_phi(0.0) - ll;                                     \
+        if (!(d2 > ORC_PIVOT_REL)) { status = ORC_E_NOT_SPD; break; }            \
+        const double d = sqrt(d2);                                               \
+        for (int64_t p = 0; p < nc; ++p)                                         \
+            L[nc * ncmax + p] = l[p];                                            \
+        L[nc * ncmax + nc] = d;                                                  \
+        Y[3 * nc + 0] = (db[3 * nn + 0] - ly0) / d;                              \
+        Y[3 * nc + 1] = (db[3 * nn + 1] - ly1) / d;                              \
+        Y[3 * nc + 2] = (db[3 * nn + 2] - ly2) / d;                              \
+        out_idx[nc] = nn;                                                        \
+        out_iter[nc] = (it_);                                                    \
+        inS[nn] = 1;                                                             \
+        ++nc;                                                                    \
+    } while (0)
+
+    int32_t seeds[3];
+    orc_seed_nodes(xb, db, nb, seeds);
+    for (int s = 0; s < 3 && status == ORC_OK; ++s)
+        RC_APPEND(seeds[s], -1);
+    int64_t idle = 0, k = 3;
+    double run_max = 0.0;
+    int stale = 1;   /* W must be recomputed from L and y */
+    for (; status == ORC_OK; ++k) {
+        if (stale) {
+            /* back substitution L^T W = y */
+            for (int64_t i = nc - 1; i >= 0; --i)
+                for (int c = 0; c < 3; ++c) {
+                    double t = Y[3 * i + c];
+                    for (int64_t p = i + 1; p < nc; ++p)
+                        t -= L[p * ncmax + i] * W[3 * p + c];
+                    W[3 * i + c] = t / L[i * ncmax + i];
+                }
+            stale = 0;
+        }
+        int64_t gi = k % m;
+        int64_t g0 = goff[gi], gn = goff[gi + 1] - goff[gi];
+        node_errors(xb, db, members + g0, gn, out_idx, nc, W, R, E, nthreads);
+        double Eloc = -1.0;
+        int64_t nloc = -1;
+        for (int64_t t = 0; t < gn; ++t) {
+            int32_t q = members[g0 + t];
+            if (inS[q]) continue;
+            if (E[t] > Eloc) { Eloc = E[t]; nloc = q; }
+        }
+        if (nloc >= 0 && Eloc > Estar) {
+            if (nc >= ncmax) { status = ORC_E_NC_MAX; break; }
+            RC_APPEND((int32_t)nloc, k);
+            stale = 1;
+            idle = 0;
+            run_max = 0.0;
+        } else {
+            for (int64_t t = 0; t < gn; ++t)
+                if (E[t] > run_max) run_max = E[t];
+            if (++idle >= m)
+                break;
+        }
+    }
+#undef RC_APPEND
+    if (out_w && status == ORC_OK) {
+        /* final weights of the selected set: L^T W = y */
+        for (int64_t i = nc - 1; i >= 0; --i)
+            for (int c = 0; c < 3; ++c) {
+                double t = Y[3 * i + c];
+                for (int64_t p = i + 1; p < nc; ++p)
+                    t -= L[p * ncmax + i] * out_w[3 * p + c];
+                out_w[3 * i + c] = t / L[i * ncmax + i];
+            }
+    }
+    *out_nc = nc;
+    *out_iterations = k - 3 + 1;
+    *final_max = run_max;
+    free(group_of); free(members); free(goff); free(inS); free(E); free(W); free(Y);
+    free(L); free(l);
+    return status;
+}

@@ -535,3 +535,38 @@ def test_follow_band_on_an_append_at_or_below_estar(gap, accepted):
         assert (s["n_fail"], s["n_div"]) == (0, 1)
     else:
         assert (s["n_fail"], s["n_div"]) == (1, 0)
+
+
+@pytest.mark.parametrize("m", [1, 5])
+def test_recurrence_cholesky_greedy_selects_the_literal_sequence(m):
+    """The fair CPU baseline (Alg. 1 with the recurrence-Cholesky append of
+    Sec. 1) must select exactly the nodes, at exactly the iterations, of the
+    literal oracle (dense re-solve every iteration), stop at the same
+    iteration with the same final maximum to rounding, and give weights that
+    reproduce the displacements at the support nodes."""
+    for c in (synth.tiny_wing(n_span=6, n_chord=30, radius=1.0),
+              synth.tiny_wing(n_span=8, n_chord=25, radius=2.0)):
+        estar = oracle.tolerance(c["db"], 2e-3)
+        a = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=3, history=False)
+        b = oracle.greedy_rc(c["xb"], c["db"], c["radius"], estar, m=m, seed=3)
+        assert a["status"] == b["status"] == 0
+        assert b["idx"].tolist() == a["idx"].tolist()
+        assert b["iter"].tolist() == a["iter"].tolist()
+        assert b["iterations"] == a["stats"]["iterations"]
+        assert abs(b["final_max"] - a["stats"]["final_max"]) <= 1e-12
+        assert b["final_max"] <= estar
+        W, st, _ = oracle.solve_weights(c["xb"], c["db"], a["idx"], c["radius"])
+        assert np.abs(b["w"] - W).max() <= 1e-9 * np.abs(W).max()
+        F = oracle.rbf_sum(c["xb"][b["idx"]], c["xb"], b["idx"], b["w"], c["radius"])
+        assert np.abs(F - c["db"][b["idx"]]).max() <= 1e-10 * np.abs(c["db"]).max()
+
+
+def test_recurrence_cholesky_greedy_reports_a_singular_append():
+    """Two coincident boundary nodes make Phi_SS singular (Sec. 2): with
+    tolerance 0 the greedy must eventually try to append the duplicate, and
+    the RC pivot d^2 = phi(0) - l.l vanishes there."""
+    c = synth.tiny_wing(n_span=4, n_chord=12, radius=1.0)
+    xb = np.vstack([c["xb"], c["xb"][5:6]])
+    db = np.vstack([c["db"], c["db"][5:6] + 1e-3])
+    b = oracle.greedy_rc(xb, db, 1.0, 0.0, m=1, seed=1)
+    assert b["status"] == oracle.E_NOT_SPD

@@ -41,6 +41,24 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--launcher-check", action="store_true",
+                    help="start the ranks (gloo, no GPU work) and report the rank count and "
+                         "the max-over-ranks step time; tests the multi-rank host path")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["volume", "greedy", "solve", "cull", "modal", "adjoint", "batched"],
+                    help="run one kernel's calls on the GCB wing (a few launches, no timing) "
+                         "for an ncu capture; see profiles/")
+    ap.add_argument("--reps", type=int, default=2, help="--profile-case: repetitions")
+    ap.add_argument("--m", type=int, default=241, help="--profile-case greedy: groups")
+    ap.add_argument("--radius", type=float, default=0.25, help="--profile-case cull: radius")
+    ap.add_argument("--modal-mode", type=int, default=3, choices=[1, 2, 3],
+                    help="--profile-case modal: 1 BF16, 2 FP16x2, 3 BF16x3")
+    ap.add_argument("--n-out", type=int, default=96, help="--profile-case modal: columns of W")
+    ap.add_argument("--record-traffic", nargs="+", default=None,
+                    metavar=("REPORT", "KERNEL"),
+                    help="REPORT KERNEL LAUNCH SRC...: write profiles/traffic_KERNEL.json "
+                         "(DRAM bytes of one captured launch, hash of its sources) from an "
+                         "ncu report")
     ap.add_argument("--nv", type=int, default=2_000_000)
     ap.add_argument("--prec", type=int, default=48, choices=[32, 48, 64],
                     help="greedy pair arithmetic: FP32, double-float (48) or FP64")
@@ -286,6 +304,29 @@ def run_ours(args, rank, world):
         pt.append(a.elapsed_time(b))
     plain_ms = statistics.median(pt)
 
+    # configuration 2's m sweep at the same tolerance: time to tolerance
+    # (greedy with refined weights) for m = N_b/N_c, 1.5 N_b/N_c, 2 N_b/N_c
+    sweep = {}
+    for fac_m in (1.0, 1.5, 2.0):
+        mm = max(1, int(round(fac_m * nb / nc_plain)))
+        ts_, gs = [], None
+        for _ in range(3):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record()
+            gs = P.greedy_select(xb, db, radius=R, tol=tol, tol_mode=1, m=mm, seed=1,
+                                 eval_prec=args.prec, weights=True, refine_steps=2,
+                                 workspace=gws if mm == m else None)
+            b.record()
+            torch.cuda.synchronize()
+            ts_.append(a.elapsed_time(b))
+        t_ = statistics.median(ts_)
+        sweep[f"{fac_m:g} N_b/N_c"] = {
+            "m": mm, "time_to_tol_s": t_ / 1e3, "nc": gs["nc"],
+            "iterations": gs["stats"]["iterations"],
+            "us_per_iteration": t_ * 1e3 / max(gs["stats"]["iterations"], 1),
+            "speedup_vs_plain": plain_ms / t_, "final_max": gs["stats"]["final_max"]}
+
     # rbf_solve_weights alone (refactorises the selected set from scratch)
     sw = []
     for _ in range(3):
@@ -342,6 +383,30 @@ def run_ours(args, rank, world):
                                "plan": plan.info()}
         del plan
 
+    # the adjoint of the volume deformation on the selected set (configuration
+    # 5: J = sum_v |d_v - t_v|^2 / 2, t_v Gaussian with sigma 0.01, seed 5):
+    # factor once per support set, then each gradient = transposed pair sums
+    # (double-float) + FP64 reduction and refined solve
+    from paper_2004_04817_gb300 import synth
+    fac = P.Factor(xb, g_last["idx"], radius=R)
+    P.deform_volume(xv, xb, g_last["idx"], recs[-1][3], radius=R, eval_prec=48, out=dv)
+    gv = (dv - tod(synth.random_field(nv, seed=5, sigma=0.01))).contiguous()
+    adj = {}
+    for vp in (48, 32):
+        P.adjoint_factored(xv, gv, fac, eval_prec=vp)
+        ts_ = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record()
+            P.adjoint_factored(xv, gv, fac, eval_prec=vp)
+            b.record()
+            torch.cuda.synchronize()
+            ts_.append(a.elapsed_time(b))
+        t_ = statistics.median(ts_)
+        adj[PREC_NAME[vp]] = {"ms": t_, "pairs_per_s": nv * nc / (t_ * 1e-3)}
+    del fac, gv
+
     # e2e through the public API with host buffers (pinned), copies timed
     hx = torch.from_numpy(np.ascontiguousarray(c["xb"])).pin_memory()
     hd = torch.from_numpy(np.ascontiguousarray(c["db"])).pin_memory()
@@ -395,6 +460,21 @@ def run_ours(args, rank, world):
          "pairs_per_s": vol_pairs / (v_ms * 1e-3),
          "achieved_tflops": vol_achieved / 1e12, "frac": vol_achieved / fp32_peak},
     ]
+    for k_ in adj.values():
+        k_["useful_flops_frac_fp32_peak"] = k_["pairs_per_s"] * FLOPS_PER_PAIR / fp32_peak
+    # the recurrence-Cholesky appends against HBM (Table 1's RC row): each
+    # append at support size k reads the lower triangles of Z = L^-1 and Z^T
+    # (8 k (k + 1) bytes) and writes the new row of each (16 (k + 1) bytes);
+    # the appends run at k = 3 .. N_c - 1
+    app_bytes = sum(8 * k_ * (k_ + 1) + 16 * (k_ + 1) for k_ in range(3, nc))
+    app_s = st["phase_ns"][3] * 1e-9
+    appends = {"appends": nc - 3, "bytes_total": app_bytes, "ms_total": app_s * 1e3,
+               "us_per_append": app_s * 1e6 / max(nc - 3, 1),
+               "bytes_per_s": app_bytes / max(app_s, 1e-12),
+               "frac_of_hbm": app_bytes / max(app_s, 1e-12) / (float(pk.get("hbm_gbs", 0.0)) * 1e9)
+               if pk.get("hbm_gbs") else None,
+               "hbm_peak_source": "measured copy bandwidth (hbm_gbs)",
+               "note": "Z and Z^T are L2-resident at this N_c; the append is latency-bound"}
     tot = g_ms + s_ms + v_ms
     for k in kernels:
         k["share"] = k["ms"] / tot
@@ -452,6 +532,9 @@ def run_ours(args, rank, world):
                                                 vol_pairs * FLOPS_PER_PAIR / (t * 1e-3) / fp32_peak}
                              for k, t in vol_alone.items()},
                    "cull_sensitivity": cull},
+        "m_sweep": sweep,
+        "adjoint": adj,
+        "appends": appends,
         "weights_max_resid": res_last,
         "kernels": kernels,
         "roofline": roof,
@@ -469,63 +552,222 @@ def run_ours(args, rank, world):
 
 
 # --------------------------------------------------------------------------
-def oracle_step(c, m, nv_sample):
-    """One pass of the oracle over the workload with a volume sample; returns
-    (seconds for the full workload, seconds spent, details)."""
+def profile_case(args):
+    """Small launches of one kernel for an ncu capture: builds the GCB wing
+    (N_b = 50,000, ``--nv`` volume points), runs the calls once, then
+    ``--reps`` more times, and exits 0.  No timing: numbers printed under a
+    profiler are not benchmark values."""
+    import torch
+    import paper_2004_04817_gb300 as P
+    from paper_2004_04817_gb300 import synth
+
+    case = args.profile_case
+    if case == "batched":
+        cases = batched_problems(n_inst=8, nv=args.nv // 8)
+        tod = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64,
+                                        device="cuda")
+        base = [dict(xb=tod(c["xb"]), db=tod(c["db"]), radius=2.0, tol=c["tol_rel"], tol_mode=1,
+                     seed=c["seed"], nc_max=1024) for c in cases]
+        cal = P.GreedyBatch([dict(q, m=1) for q in base])
+        cal.run()
+        ms_ = [max(1, int(round(1.5 * len(c["xb"]) / r["nc"])))
+               for c, r in zip(cases, cal.results())]
+        gb = P.GreedyBatch([dict(q, m=m) for q, m in zip(base, ms_)])
+        gb.run()
+        vb = P.VolumeBatch([dict(xv=tod(c["xv"]), xb=q["xb"], idx=gb.idx[i], w=gb.w[i],
+                                 nc_ptr=gb.nc_ptr + 8 * i, radius=2.0)
+                            for i, (c, q) in enumerate(zip(cases, base))])
+        for _ in range(1 + args.reps):
+            gb.run()
+            vb.run()
+        torch.cuda.synchronize()
+        print("profile case done", case, [r["nc"] for r in gb.results()])
+        return 0
+    nv = args.nv if case in ("volume", "cull", "modal", "adjoint") else 0
+    c = synth.wing_gcb(n_vol=nv)
+    dev = lambda x, t=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=t,
+                                                      device="cuda")
+    xb, db = dev(c["xb"]), dev(c["db"])
+    xv = dev(c["xv"]) if nv else None
+    R = c["radius"]
+    g = P.greedy_select(xb, db, radius=R, tol=c["tol_rel"], tol_mode=1,
+                        m=args.m if case == "greedy" else 241, seed=1, eval_prec=args.prec,
+                        weights=True)
+    fac = P.Factor(xb, g["idx"], radius=R) if case == "adjoint" else None
+    gv = None
+    if case == "adjoint":
+        dv = P.deform_volume(xv, xb, g["idx"], g["w"], radius=R, eval_prec=P.PREC_F32X2)
+        gv = (dv - dev(synth.random_field(nv, seed=5, sigma=0.01))).contiguous()
+    for _ in range(1 + args.reps):
+        if case == "greedy":
+            g = P.greedy_select(xb, db, radius=R, tol=c["tol_rel"], tol_mode=1, m=args.m,
+                                seed=1, eval_prec=args.prec)
+        elif case == "solve":
+            P.solve_weights(xb, db, g["idx"], radius=R)
+        elif case == "volume":
+            P.deform_volume(xv, xb, g["idx"], g["w"], radius=R, eval_prec=args.vol_prec)
+        elif case == "cull":
+            w, _ = P.solve_weights(xb, db, g["idx"], radius=args.radius)
+            plan = P.VolumePlan(xv, radius=args.radius, eval_prec=args.vol_prec,
+                                nc_max=g["nc"])
+            plan.run(xb, g["idx"], w)
+            del plan
+        elif case == "modal":
+            # random modal weights (N_c x n_out): the timing does not depend on them
+            W = torch.randn((g["nc"], args.n_out), dtype=torch.float64, device="cuda",
+                            generator=torch.Generator("cuda").manual_seed(1))
+            P.deform_modal(xv, xb, g["idx"], W, radius=R, mode=args.modal_mode)
+        elif case == "adjoint":
+            P.adjoint_factored(xv, gv, fac, eval_prec=args.vol_prec)
+    torch.cuda.synchronize()
+    print("profile case done", case, g["nc"])
+    return 0
+
+
+def record_traffic(rep, kernel, launch, *srcs):
+    """Write profiles/traffic_<kernel>.json from an ncu report: DRAM bytes of
+    one launch (dram__bytes_read.sum + dram__bytes_write.sum) and a hash of the
+    kernel's sources, so the benchmark reports the figure only while the
+    kernel is unchanged (see kernel_traffic)."""
+    import csv
+    import hashlib
+    import io
+    out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True,
+                         text=True, check=True).stdout
+    rows = list(csv.reader(io.StringIO(out)))
+    hdr, units, data = rows[0], rows[1], rows[2:]
+    d = dict(zip(hdr, data[int(launch)]))
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    tot = 0.0
+    for name in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        tot += float(d[name]) * scale[units[hdr.index(name)]]
+    h = hashlib.sha1()
+    for src in srcs:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    rec = {"kernel": kernel, "report": os.path.basename(rep), "launch": int(launch),
+           "dram_bytes_per_launch": tot, "sources": list(srcs), "sources_sha1": h.hexdigest(),
+           "duration": d.get("gpu__time_duration.sum")}
+    with open(os.path.join(ROOT, "profiles", f"traffic_{kernel}.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
+    return 0
+
+
+# --------------------------------------------------------------------------
+def cpu_model():
+    """The host CPU's model name (x86 "model name", else the Arm part numbers)."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return None
+    for key in ("model name", "Model name"):
+        for line in txt.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    parts = sorted({line.split(":", 1)[1].strip() for line in txt.splitlines()
+                    if line.startswith("CPU part")})
+    impl = sorted({line.split(":", 1)[1].strip() for line in txt.splitlines()
+                   if line.startswith("CPU implementer")})
+    return f"implementer {','.join(impl)} part {','.join(parts)}" if parts else None
+
+
+def oracle_step(c, m, threads, kind="oracle", nv_sample=None):
+    """One pass of the CPU code over the workload: GCB greedy to tolerance,
+    final weights and the volume sum (on the first ``nv_sample`` points,
+    scaled by the point count, when given).  ``kind`` "oracle" is the literal
+    oracle (dense Cholesky re-solve every iteration, then a dense solve);
+    "cpu_rc" is Algorithm 1 with the recurrence-Cholesky append of Sec. 1 (the
+    paper's own procedure, weights by back substitution).  Returns (seconds
+    for the whole workload, seconds spent, details)."""
     import oracle
+    nv_s = len(c["xv"]) if nv_sample is None else min(nv_sample, len(c["xv"]))
     t0 = time.perf_counter()
     estar = oracle.tolerance(c["db"], c["tol_rel"])
-    g = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1, history=False)
-    t1 = time.perf_counter()
-    W, st, _ = oracle.solve_weights(c["xb"], c["db"], g["idx"], c["radius"])
+    if kind == "oracle":
+        g = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=m, seed=1, history=False,
+                          threads=threads)
+        t1 = time.perf_counter()
+        W, st, _ = oracle.solve_weights(c["xb"], c["db"], g["idx"], c["radius"])
+    else:
+        g = oracle.greedy_rc(c["xb"], c["db"], c["radius"], estar, m=m, seed=1,
+                             threads=threads)
+        t1 = time.perf_counter()
+        W = g["w"]
     t2 = time.perf_counter()
-    oracle.rbf_sum(c["xv"][:nv_sample], c["xb"], g["idx"], W, c["radius"])
+    oracle.rbf_sum(c["xv"][:nv_s], c["xb"], g["idx"], W, c["radius"], threads=threads)
     t3 = time.perf_counter()
-    scale = len(c["xv"]) / nv_sample
+    scale = len(c["xv"]) / nv_s
     full = (t1 - t0) + (t2 - t1) + (t3 - t2) * scale
-    return full, t3 - t0, {"nc": g["nc"], "greedy_s": t1 - t0, "solve_s": t2 - t1,
-                           "volume_sample_s": t3 - t2}
+    return full, t3 - t0, {"nc": g["nc"], "greedy_s": t1 - t0, "weights_s": t2 - t1,
+                           "volume_s": (t3 - t2) * scale, "volume_points_run": nv_s}
 
 
-def cpu_baseline(c, m, nv_sample=100_000):
+def cpu_baseline(c, m):
+    """The CPU code timed on this host's cores: the literal oracle (the value)
+    and the paper's recurrence-Cholesky procedure (the fair baseline), each on
+    one thread and on every core.  On every core the whole workload runs; on
+    one thread the volume sum runs on 100,000 of the points and is scaled."""
     import oracle
-    full, spent, det = oracle_step(c, m, nv_sample)
-    return {"value": full, "unit": "s", "cores": oracle.default_threads(), "kind": "oracle",
-            "sample": f"full GCB greedy (m={m}) and weights; volume sum on {nv_sample} of "
-                      f"{len(c['xv'])} points, scaled by the point count",
-            "spent_s": spent, **det}
+    allc = oracle.default_threads()
+    variants = []
+    spent_total = 0.0
+    for kind in ("oracle", "cpu_rc"):
+        for threads in (allc, 1):
+            sample = None if threads == allc else 100_000
+            full, spent, det = oracle_step(c, m, threads, kind, sample)
+            spent_total += spent
+            variants.append({"kind": kind, "threads": threads, "value": full, "unit": "s",
+                             "spent_s": spent, **det})
+    lit = variants[0]
+    return {"value": lit["value"], "unit": "s", "cores": allc, "kind": "oracle",
+            "sample": f"whole workload on {allc} threads: GCB greedy (m={m}) to tolerance, "
+                      f"weights, volume sum over all {len(c['xv'])} points; the one-thread "
+                      f"runs sum 100,000 points and scale by the point count",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(), "variants": variants,
+            "fair_baseline": {"kind": "cpu_rc", "threads": allc,
+                              "value": variants[2]["value"],
+                              "what": "Algorithm 1 with the recurrence-Cholesky append (Sec. 1)"},
+            "spent_s": spent_total}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on this host's
+    cores, on the whole GCB wing workload (greedy, weights, all volume points)
+    in every step."""
     import oracle
     c = workload(args.nv)
     nb = len(c["xb"])
     estar = oracle.tolerance(c["db"], c["tol_rel"])
+    threads = oracle.default_threads()
     # m from the oracle's own plain-greedy N_c (untimed calibration)
     g1 = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1, history=False)
     m = max(1, int(round(1.5 * nb / g1["nc"])))
-    nv_sample = 50_000
     for _ in range(args.warmup):
-        oracle_step(c, m, nv_sample)
+        oracle_step(c, m, threads)
     vals, spent = [], 0.0
     for _ in range(args.steps):
-        v, s, det = oracle_step(c, m, nv_sample)
+        v, s_, det = oracle_step(c, m, threads)
         vals.append(v)
-        spent += s
+        spent += s_
     v = statistics.mean(vals)
-    base = {"kind": "oracle", "cores": oracle.default_threads(),
-            "sample": f"full GCB greedy (m={m}) and weights; volume sum on {nv_sample} of "
-                      f"{len(c['xv'])} points, scaled by the point count", "value": v,
-            "unit": "s"}
+    sample = (f"whole workload every step: GCB greedy (m={m}) with a dense re-solve per "
+              f"iteration, weights, volume sum over all {len(c['xv'])} points")
+    base = {"kind": "oracle", "cores": threads, "sample": sample, "value": v, "unit": "s",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+    cfg = workload_desc(c, m, g1["nc"], 64, 64)
+    cfg["eval"] = "FP64 pairs (oracle)"
+    cfg["solve"] = "FP64 dense Cholesky re-solve every iteration, then a dense solve"
+    cfg["volume_eval"] = "FP64"
     return {
         "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded wing generator, paper_2004_04817_gb300/synth.py)",
-        "config": workload_desc(c, m, g1["nc"], args.prec, args.vol_prec), "impl": "reference",
+        "config": cfg, "impl": "reference",
         "cpu_baseline": base,
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "gpu_launches": 0, "spent_s": spent,
+        "gpu_launches": 0, "spent_s": spent, "details_last_step": det,
     }
 
 
@@ -987,10 +1229,56 @@ def run_peaks(args, rank, world):
     }
 
 
+def free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def launch_ranks(n, argv):
+    """``--gpus N`` without a launcher: start N ranks of this script (one per
+    GPU) through torch.distributed.run on this node and return its exit
+    status; rank 0 prints the JSON line."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={n}", "--master-addr=127.0.0.1", f"--master-port={free_port()}",
+           os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
+
+
+def run_launcher_check(args, rank, world):
+    """The multi-rank host path without GPU work: every rank reports made-up
+    step times (rank r: 10 + r ms), the ranks meet at barriers and agree on
+    the largest (gloo on CPU)."""
+    import torch
+    torch.distributed.barrier()
+    ms = max_over_ranks([10.0 + rank], world, torch.device("cpu"))[0]
+    torch.distributed.barrier()
+    return {"launcher_check": True, "n_gpus": world, "ranks": world, "ms_max_over_ranks": ms}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", 1))
     rank = int(os.environ.get("RANK", 0))
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1 and args.impl != "reference":
+        return launch_ranks(args.gpus, sys.argv[1:])
+    if args.launcher_check:
+        if world > 1:
+            import torch
+            torch.distributed.init_process_group("gloo")
+        out = run_launcher_check(args, rank, world) if world > 1 else \
+            {"launcher_check": True, "n_gpus": 1, "ranks": 1, "ms_max_over_ranks": 10.0}
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return 0
+    if args.profile_case:
+        return profile_case(args)
+    if args.record_traffic:
+        return record_traffic(*args.record_traffic)
     if args.impl == "reference":
         if rank != 0:
             return 0

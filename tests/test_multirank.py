@@ -52,3 +52,23 @@ def test_one_rank_is_unchanged():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks([3.0, 4.0], 1, torch.device("cpu")) == [3.0, 4.0]
+
+
+def test_bench_starts_its_own_ranks_for_gpus_n():
+    """`bench.py --gpus 2` started without a launcher must start two ranks
+    itself (torch.distributed.run on this node) and report n_gpus = 2; the
+    launcher check runs that host path with gloo ranks and no GPU work."""
+    import json
+    import subprocess
+    env = dict(os.environ)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2",
+                        "--launcher-check"], capture_output=True, text=True, env=env,
+                       timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    out = json.loads(lines[0])
+    assert out["n_gpus"] == 2 and out["ranks"] == 2
+    assert out["ms_max_over_ranks"] == 11.0

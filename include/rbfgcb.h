@@ -181,6 +181,24 @@ rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, int64_t nb,
                              void *d_ws, size_t ws_bytes, void *stream);
 
 /* --------------------------------------------------------------------------
+ * Certified screening record of a finished greedy run (FP32 and double-float
+ * modes; Alg. 1's argmax and E > E* test decide on these values).  After
+ * rbf_greedy_select returned RBF_OK on workspace d_ws (same nb and p), every
+ * boundary node outside S was last evaluated with the final weights of the
+ * evaluation table; for each node n this gives that screened error E~_n
+ * (d_err[n], FP64) and its bound beta_n (d_bound[n], FP32) with
+ * |E~_n - E_n| <= beta_n, E_n the exact error with those weights (beta_n = 0
+ * where an FP64 re-score replaced the screened value).  d_w_eval (nc x 3
+ * FP64, nc = the run's N_c) receives the table's weights: the FP32 values
+ * (FP32 mode) or the double-float sums h + l (double-float mode).  Entries
+ * of nodes in S are stale.  The bounds are derived in the library's sources
+ * (constants at the screened evaluation).  ASYNC.
+ * ------------------------------------------------------------------------ */
+rbf_status rbf_greedy_screen_errors(const void *d_ws, size_t ws_bytes, int64_t nb,
+                                    const rbf_params *p, int64_t nc, double *d_err,
+                                    float *d_bound, double *d_w_eval, void *stream);
+
+/* --------------------------------------------------------------------------
  * Peak-selection variant of the greedy (the prior art the paper cites in
  * Sec. 1: several error-peak nodes added at a time).  In each iteration the
  * nodes of the active group outside S with E > E* are taken in decreasing E
@@ -571,6 +589,21 @@ rbf_status rbf_measure_fma_peak(int prec, double *h_flops, void *stream);
 #define RBF_LAT_FP64_WARP 2
 #define RBF_LAT_FP32_WARP 3
 rbf_status rbf_measure_latency(int what, int param, double *h_ns, void *stream);
+
+/* --------------------------------------------------------------------------
+ * Largest relative error of a hardware approximation over every normal
+ * float x in [2^-126, 4), against the FP64 square root:
+ *   RBF_APPROX_SQRT:  sqrt.approx.f32(x), used by the FP32 pair path;
+ *   RBF_APPROX_RSQRT: rsqrtf(x) as compiled in this library, the start of
+ *                     every double-float square root.
+ * The certified error bounds of the screened evaluation (FP32 and
+ * double-float modes of the greedy) assume at most 2^-22 for both; this
+ * probe measures it on the device at hand.  h_max_rel: host.  No caller
+ * memory is used (one library word in device memory).  SYNCHRONOUS.
+ * ------------------------------------------------------------------------ */
+#define RBF_APPROX_SQRT 1
+#define RBF_APPROX_RSQRT 2
+rbf_status rbf_measure_approx_error(int which, double *h_max_rel, void *stream);
 
 /* Status latched by the last ASYNC call's device work on this device
  * (RBF_OK if none failed); reading it synchronises the device. */

@@ -27,6 +27,7 @@ from .rbf import (  # noqa: F401
     GreedyBatch,
     VolumeBatch,
     VolumePlan,
+    measure_approx_error,
     measure_fma_peak,
     measure_latency,
     nearest_support,

@@ -61,12 +61,27 @@ constexpr int kLookChunk = 16;             // groups per look-ahead evaluation
 // iteration), by precision; a look-ahead runs only when scanning one group
 // costs at most half an idle iteration (see the main loop).
 constexpr double kLookPairsFF = 8000.0, kLookPairsF32 = 40000.0, kLookPairsF64 = 400.0;
-constexpr float kU32 = 5.9604645e-8f;      // 2^-24, unit roundoff of FP32
-constexpr float kBetaPhi = 16.0f;          // error-bound factors (see screen_bound)
-constexpr float kBetaCoord = 8.0f;
-constexpr float kUFFf = 5.684341886080802e-14f;  // 2^-44: double-float accuracy used in the
-constexpr float kBetaFF = 72.0f;                  // bound of the ff errors: 64 for the pair
-                                                  // sums, 8 for the team sum and |dr - F|
+constexpr float kU32 = 5.9604645e-8f;      // u = 2^-24, unit roundoff of FP32
+constexpr float kU32Sq = 3.5527137e-15f;   // u^2 = 2^-48, the double-float error unit
+constexpr int kFFRenorm = 8;               // double-float accumulators renormalised every
+                                           // kFFRenorm terms (bounds the low-part growth)
+// Certified error bounds of the screened evaluation.  For a node q with
+// sums over nc centres split over a team of ts lanes (n_l = ceil(nc / ts)
+// terms per lane, log2(ts) levels of the team sum), X = max |x / R| over the
+// boundary, W1 = sum_j |w_j|_1, sb = sum_j |w_j|_1 phi_qj (both as computed),
+// |dr|_1 and the computed error E~, the derivation (phi Lipschitz with
+// constant 2.109375 and |phi'(eta) eta| <= 0.6912 on [0, 1]; sqrt.approx.f32
+// and rsqrtf within 2^-22 relative, which rbf_measure_approx_error checks)
+// gives, with u = 2^-24:
+//   FP32:         |E~ - E| <= u   ((n_l + log2 ts + 10) sb + |dr|_1
+//                                  + (7.32 X + 4.5) W1 + 4.24 E~)
+//   double-float: |E~ - E| <= u^2 ((9.5 n_ch + 3 log2 ts + 43) sb + 4 |dr|_1
+//                                  + (7.32 X + 41.5) W1 + 50 E~)
+// (n_ch = ceil(n_l / 2) + 1 terms per accumulator chain, renormalised every
+// kFFRenorm terms), each times 1 + (2 n_l + 2 log2 ts + nc / 32 + 40) u for
+// the second-order terms, the FP32 sums sb and W1 and the FP32 evaluation of
+// the bound itself.  E is the exact error of q with the weights as held in
+// the evaluation table.
 
 struct GreedyCtl {
     GridBar bar;
@@ -1665,9 +1680,16 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 __syncthreads();
             }
             phase(look >= 0 ? 11 : 8);
+            // terms per lane, team levels and the rounding-up factor of the
+            // bounds (see the derivation at kU32)
+            const int n_l = (nc + ts - 1) / ts;
+            const float lg_ts = (float)(31 - __clz(ts));
+            const float b_up =
+                1.0f + (2.0f * (float)n_l + 2.0f * lg_ts + (float)nc * (1.0f / 32.0f) + 40.0f) * kU32;
             if (!use_ff) {
                 const float4 *cw = smem ? s_cw : a.cw32;
-                const float coord_term = kBetaCoord * xscale * s_wabs * 1.001f;
+                const float c_sb = (float)n_l + lg_ts + 10.0f;
+                const float coord_term = (7.32f * xscale + 4.5f) * s_wabs;
                 for (int it = 0; it < rounds; ++it) {
                     const int q = p0 + team + it * nteams;
                     const bool act = q < p1;
@@ -1697,7 +1719,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         // (proportional to sum |w| phi), of the coordinates
                         // (max|x|/R * sum |w|), of the displacement and of E
                         const float beta =
-                            kU32 * (kBetaPhi * (sb + dabs) + coord_term + 4.0f * e) + 1e-30f;
+                            kU32 * (c_sb * sb + dabs + coord_term + 4.24f * e) * b_up + 1e-30f;
                         a.u32[q] = beta;
                         a.e64[q] = (double)e;
                         const unsigned long long upb = dbits((double)e + (double)beta);
@@ -1727,7 +1749,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     pairs32 += (long long)nq * nc;
             } else {
                 const float4 *cw = smem ? s_cw : a.cwff;
-                const float coord_term = (16.0f * xscale + 4.0f) * s_wabs;
+                const float c_sb = 9.5f * (float)((n_l + 1) / 2 + 1) + 3.0f * lg_ts + 43.0f;
+                const float coord_term = (7.32f * xscale + 41.5f) * s_wabs;
                 for (int it = 0; it < rounds; ++it) {
                     const int q = p0 + team + it * nteams;
                     const bool act = q < p1;
@@ -1744,7 +1767,16 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     const f2 bxh = f2_bcast(qxh), bxl = f2_bcast(qxl), byh = f2_bcast(qyh),
                              byl = f2_bcast(qyl), bzh = f2_bcast(qzh), bzl = f2_bcast(qzl);
                     int j = sub;
+                    int nren = 0;
                     for (; j + ts < nc; j += 2 * ts) {
+                        if (++nren == kFFRenorm) {
+                            // error-free renormalisation: the low parts restart
+                            // below one ulp of the high parts
+                            nren = 0;
+                            gx = two_sum2(gx.h, gx.l);
+                            gy = two_sum2(gy.h, gy.l);
+                            gz = two_sum2(gz.h, gz.l);
+                        }
                         const int j2 = j + ts;
                         const float4 ch0 = smem ? cw[j] : ldcg(cw + j);
                         const float4 cl0 = smem ? cw[pst + j] : ldcg(cw + pst + j);
@@ -1816,8 +1848,8 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         // square root; the FP32 evaluation of the bound is
                         // rounded up by the factor
                         const float bf =
-                            fmaxf(kUFFf * (kBetaFF * (sb + dabs) + coord_term + 4.0f * ef.h) *
-                                      1.000002f,
+                            fmaxf(kU32Sq * (c_sb * sb + 4.0f * dabs + coord_term + 50.0f * ef.h) *
+                                      b_up,
                                   1e-18f);
                         a.u32[q] = bf;
                         a.e64[q] = e;
@@ -2769,6 +2801,68 @@ extern "C" rbf_status rbf_greedy_select(const double *d_xb, const double *d_db, 
 {
     return greedy_launch(d_xb, d_db, nb, p, d_sel_idx, d_sel_iter, d_w, d_hist, hist_cap, h_nc,
                          h_n_hist, h_stats, d_ws, ws_bytes, stream, 1, 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// The last stored screened errors and bounds of a greedy workspace, in node
+// order, and the weights of the evaluation table (the certified bounds are
+// stated for those weights).
+// ---------------------------------------------------------------------------
+__global__ void k_screen_gather(const int32_t *__restrict__ pos_of_node,
+                                const double *__restrict__ e64, const float *__restrict__ u32,
+                                int nb, double *__restrict__ e_out, float *__restrict__ b_out)
+{
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nb; n += gridDim.x * blockDim.x) {
+        const int pos = pos_of_node[n];
+        e_out[n] = e64[pos];
+        b_out[n] = u32[pos];
+    }
+}
+
+__global__ void k_table_weights(const float4 *__restrict__ cw32, const float4 *__restrict__ cwff,
+                                int prec, int ld, int nc, double *__restrict__ w_out)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nc; j += gridDim.x * blockDim.x) {
+        double w[3];
+        if (prec == RBF_PREC_F32X2) {
+            const float4 h = cwff[2 * (size_t)ld + j], l = cwff[3 * (size_t)ld + j];
+            w[0] = (double)h.x + (double)l.x;
+            w[1] = (double)h.y + (double)l.y;
+            w[2] = (double)h.z + (double)l.z;
+        } else {
+            const float4 h = cw32[(size_t)ld + j];
+            w[0] = h.x;
+            w[1] = h.y;
+            w[2] = h.z;
+        }
+        for (int c = 0; c < 3; ++c)
+            w_out[3 * j + c] = w[c];
+    }
+}
+
+extern "C" rbf_status rbf_greedy_screen_errors(const void *d_ws, size_t ws_bytes, int64_t nb,
+                                               const rbf_params *p, int64_t nc, double *d_err,
+                                               float *d_bound, double *d_w_eval, void *stream)
+{
+    if (!greedy_args_ok(nb, p) || !d_ws || !d_err || !d_bound ||
+        (p->eval_prec != RBF_PREC_F32 && p->eval_prec != RBF_PREC_F32X2) || nc < 0 ||
+        nc > p->nc_max || (nc > 0 && !d_w_eval))
+        return RBF_E_ARG;
+    const GreedyWs L = greedy_ws_layout(nb, p->nc_max);
+    if (ws_bytes < L.total)
+        return RBF_E_WORKSPACE;
+    const char *ws = (const char *)d_ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_screen_gather<<<(int)std::min<int64_t>((nb + 255) / 256, 1024), 256, 0, st>>>(
+        (const int32_t *)(ws + L.pos_of_node), (const double *)(ws + L.e64),
+        (const float *)(ws + L.u32), (int)nb, d_err, d_bound);
+    if (nc > 0)
+        k_table_weights<<<(int)((nc + 255) / 256), 256, 0, st>>>(
+            (const float4 *)(ws + L.cw32), (const float4 *)(ws + L.cwff), p->eval_prec,
+            (int)p->nc_max, (int)nc, d_w_eval);
+    if (cudaGetLastError() != cudaSuccess)
+        return RBF_E_CUDA;
+    return RBF_OK;
 }
 
 extern "C" rbf_status rbf_greedy_select_peaks(const double *d_xb, const double *d_db, int64_t nb,

@@ -1,5 +1,6 @@
 // rbf_host.cu -- host helpers, status strings and the FMA-peak microbenchmark.
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -233,6 +234,64 @@ extern "C" rbf_status rbf_measure_latency(int what, int param, double *h_ns, voi
             best = per;
     }
     *h_ns = best;
+    return RBF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Accuracy of the two hardware approximations the evaluation bounds rely on:
+// sqrt.approx.f32 (the FP32 pair path) and rsqrtf (the start of the
+// double-float square roots), checked against the FP64 square root on every
+// normal float in [2^-126, 4).  The largest relative error goes to a
+// file-scope word as the bit pattern of a non-negative double, merged with an
+// integer atomicMax (order-preserving for such bit patterns).
+// ---------------------------------------------------------------------------
+static __device__ unsigned long long g_approx_max;
+
+__global__ void __launch_bounds__(256) k_approx_error(int which, unsigned lo, unsigned n)
+{
+    double mx = 0.0;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float x = __uint_as_float(lo + i);
+        const double ex = sqrt((double)x);
+        double rel;
+        if (which == RBF_APPROX_SQRT)
+            rel = fabs((double)sqrt_approx(x) - ex) / ex;
+        else
+            rel = fabs((double)rsqrtf(x) * ex - 1.0);
+        mx = fmax(mx, rel);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(&g_approx_max, (unsigned long long)__double_as_longlong(mx));
+}
+
+extern "C" rbf_status rbf_measure_approx_error(int which, double *h_max_rel, void *stream)
+{
+    if (!h_max_rel || (which != RBF_APPROX_SQRT && which != RBF_APPROX_RSQRT))
+        return RBF_E_ARG;
+    DeviceInfo dev;
+    if (!device_info(&dev))
+        return RBF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *word = nullptr;
+    if (cudaGetSymbolAddress(&word, g_approx_max) != cudaSuccess ||
+        cudaMemsetAsync(word, 0, sizeof(unsigned long long), st) != cudaSuccess) {
+        cudaGetLastError();
+        return RBF_E_CUDA;
+    }
+    const unsigned lo = 0x00800000u;            // 2^-126, the smallest normal float
+    const unsigned n = 0x40800000u - lo;        // up to 4.0 (exclusive)
+    k_approx_error<<<dev.sms * 8, 256, 0, st>>>(which, lo, n);
+    unsigned long long bits = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess ||
+        cudaMemcpyFromSymbol(&bits, g_approx_max, sizeof(bits)) != cudaSuccess) {
+        cudaGetLastError();
+        return RBF_E_CUDA;
+    }
+    double v;
+    memcpy(&v, &bits, sizeof(v));
+    *h_max_rel = v;
     return RBF_OK;
 }
 

@@ -192,6 +192,11 @@ def lib():
         L.rbf_support_kl.restype = C.c_int
         L.rbf_support_kl.argtypes = [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int64,
                                      C.POINTER(C.c_double), _vp, C.c_size_t, _vp]
+        L.rbf_greedy_screen_errors.restype = C.c_int
+        L.rbf_greedy_screen_errors.argtypes = [_vp, C.c_size_t, C.c_int64, P, C.c_int64, _vp,
+                                               _vp, _vp, _vp]
+        L.rbf_measure_approx_error.restype = C.c_int
+        L.rbf_measure_approx_error.argtypes = [C.c_int, C.POINTER(C.c_double), _vp]
         L.rbf_measure_latency.restype = C.c_int
         L.rbf_measure_latency.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), _vp]
         L.rbf_factor_workspace_bytes.restype = C.c_size_t
@@ -259,13 +264,16 @@ def make_params(radius, tol=0.0, tol_mode=1, eval_prec=PREC_F64, m=1, seed=1, nc
 
 def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
                   eval_prec=PREC_F64, hist_cap=0, history_full=False, weights=False,
-                  refine_steps=2, ctas=0, stream=None, workspace=None):
+                  refine_steps=2, ctas=0, stream=None, workspace=None, screen=False):
     """GCB greedy (m = 1: plain greedy).  Returns a dict with ``idx`` (int32
     CUDA tensor, selection order), ``iter`` (int64), ``nc``, ``hist`` (CUDA
     (n, 6) or None), ``stats`` (dict) and ``status`` (0 or RBF_E_NC_MAX).
     ``history_full`` adds FP64 all-node maxima to the history after every
     m-th iteration (diagnostic).  ``weights`` also returns ``w``, the refined
-    FP64 weights of the selected set."""
+    FP64 weights of the selected set.  ``screen`` (FP32 and double-float
+    modes) also returns ``screen``: the final screened error and certified
+    bound of every node (``err``, ``bound``, node order) and the evaluation
+    table's weights ``w_eval`` (rbf_greedy_screen_errors)."""
     L = lib()
     _dev(xb, torch.float64, "xb", 3)
     _dev(db, torch.float64, "db", 3)
@@ -293,7 +301,16 @@ def greedy_select(xb, db, *, radius, tol, tol_mode=1, m=1, seed=1, nc_max=None,
                              C.byref(stats), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "rbf_greedy_select", allow=(E_NC_MAX,))
     n = nc.value
-    return dict(idx=idx[:n], iter=it[:n], nc=n, status=st,
+    scr = None
+    if screen and st == 0:
+        err = torch.empty(nb, dtype=torch.float64, device=xb.device)
+        bnd = torch.empty(nb, dtype=torch.float32, device=xb.device)
+        wev = torch.empty((max(n, 1), 3), dtype=torch.float64, device=xb.device)
+        _check(L.rbf_greedy_screen_errors(_ptr(ws), ws.numel(), nb, C.byref(p), n, _ptr(err),
+                                          _ptr(bnd), _ptr(wev), _stream(stream)),
+               "rbf_greedy_screen_errors")
+        scr = dict(err=err, bound=bnd, w_eval=wev[:n])
+    return dict(idx=idx[:n], iter=it[:n], nc=n, status=st, screen=scr,
                 w=w[:n] if w is not None else None,
                 hist=hist[:min(nh.value, hist_cap)] if hist is not None else None,
                 n_hist=nh.value,
@@ -599,6 +616,18 @@ def measure_latency(what, param=0, stream=None):
     _check(lib().rbf_measure_latency(int(what), int(param), C.byref(ns), _stream(stream)),
            "rbf_measure_latency")
     return ns.value
+
+
+APPROX_SQRT, APPROX_RSQRT = 1, 2
+
+
+def measure_approx_error(which, stream=None):
+    """Largest relative error of sqrt.approx.f32 (APPROX_SQRT) or rsqrtf
+    (APPROX_RSQRT) over every normal float in [2^-126, 4)."""
+    r = C.c_double(0.0)
+    _check(lib().rbf_measure_approx_error(int(which), C.byref(r), _stream(stream)),
+           "rbf_measure_approx_error")
+    return r.value
 
 
 def measure_fma_peak(prec=32, stream=None):

@@ -313,6 +313,25 @@ rbf_status rbf_deform_volume(const double *d_xv, int64_t nv,
                              void *d_ws, size_t ws_bytes, void *stream);
 
 /* --------------------------------------------------------------------------
+ * Many displacement fields on one support set in double-float (Eq. 6 for
+ * every column of W): D = Phi_vc W, W nc x n_out FP64 (row-major, support
+ * order), e.g. n_out = 96 for 32 modes of 3 components.  phi is computed once
+ * per (point, centre) pair in double-float and shared by all columns; the
+ * products and sums are double-float on the FP32 pipe, so the result carries
+ * FP64-level accuracy (about 2^-44 sum_j |w_j phi_vj| per column), unlike the
+ * tensor-core path, whose FP32 accumulation limits it to about 2^-24 sum_j
+ * |w_j phi_vj| -- too coarse when the weights of a support set cancel
+ * heavily (large radius, high modes).
+ * p: radius; eval_prec must be RBF_PREC_F32X2.  1 <= n_out <= 192.
+ * d_out : device FP64 nv x n_out (row-major).  ASYNC.
+ * ------------------------------------------------------------------------ */
+size_t rbf_volume_fields_workspace_bytes(int64_t nv, int64_t nc, int n_out);
+rbf_status rbf_deform_volume_fields(const double *d_xv, int64_t nv, const double *d_xb,
+                                    const int32_t *d_sel_idx, int64_t nc, const double *d_w,
+                                    int n_out, const rbf_params *p, double *d_out, void *d_ws,
+                                    size_t ws_bytes, void *stream);
+
+/* --------------------------------------------------------------------------
  * Modal volume deformation on the tensor cores: for k displacement fields
  * (modes) that share one support set, Eq. 6 for all of them is the product
  * D = Phi_vc W with W of size nc x n_out (n_out = 3 k, e.g. 96 for 32

@@ -14,6 +14,7 @@ from .rbf import (  # noqa: F401
     greedy_select_peaks,
     solve_weights,
     deform_volume,
+    deform_volume_fields,
     solve_system,
     adjoint,
     adjoint_factored,

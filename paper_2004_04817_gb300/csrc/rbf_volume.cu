@@ -455,6 +455,240 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
     return RBF_OK;
 }
 
+namespace rbf {
+
+// ---------------------------------------------------------------------------
+// Many displacement fields on one support set (Eq. 6 for every column of
+// W, nc x n_out): D = Phi_vc W in double-float on the FP32 pipe.  Phi is
+// computed once per (point, centre) pair into shared memory and shared by
+// all n_out columns, so a pair costs one double-float phi plus n_out
+// double-float multiply-adds instead of n_out / 3 separate volume sums.
+//   CTA: 256 threads = PP point pairs x FG column groups of kFieldsF columns;
+//   a warp shares its column group (weights read as broadcasts) and covers
+//   32 consecutive point pairs (phi entries read conflict-free).
+//   Per centre tile of kFieldsK centres: stage the weights (w_hi, w_hi,
+//   w_lo, w_lo per column, so one 16-byte load gives both paired operands),
+//   compute the tile's phi (each thread kFieldsK / FG centres of its point
+//   pair), then accumulate.  Accumulators are renormalised (error-free
+//   two_sum) every kFieldsRenorm centres, which bounds the growth of their low
+//   parts.
+// ---------------------------------------------------------------------------
+constexpr int kFieldsF = 24;          // columns per thread
+constexpr int kFieldsK = 32;          // centres per shared-memory tile
+constexpr int kFieldsThreads = 256;
+constexpr int kFieldsMaxOut = 192;    // 8 column groups
+constexpr int kFieldsRenorm = 8;
+
+static int fields_pad(int n_out)
+{
+    int np = kFieldsF;
+    while (np < n_out)
+        np *= 2;
+    return np;   // 24, 48, 96 or 192: FG = np / 24 divides 8
+}
+
+__global__ void k_pack_fields_w(const double *__restrict__ w, int nc, int n_out, int n_pad,
+                                float4 *__restrict__ wp)
+{
+    const int64_t tot = (int64_t)nc * n_pad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / n_pad;
+        const int f = (int)(i - j * n_pad);
+        float h = 0.0f, l = 0.0f;
+        if (f < n_out)
+            split_f64(w[j * n_out + f], h, l);
+        wp[i] = make_float4(h, h, l, l);
+    }
+}
+
+// double-float centres: (c_hi, c_lo) per centre
+__global__ void k_pack_centres_hl(const double *__restrict__ xb, const int32_t *__restrict__ sel,
+                                  int64_t nc, double inv_r, float4 *__restrict__ c)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = sel[j];
+        float h0, l0, h1, l1, h2, l2;
+        split_f64(xb[3 * n] * inv_r, h0, l0);
+        split_f64(xb[3 * n + 1] * inv_r, h1, l1);
+        split_f64(xb[3 * n + 2] * inv_r, h2, l2);
+        c[2 * j] = make_float4(h0, h1, h2, 0.0f);
+        c[2 * j + 1] = make_float4(l0, l1, l2, 0.0f);
+    }
+}
+
+template <int FG>
+__global__ void __launch_bounds__(kFieldsThreads, 1)
+k_fields_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_t nv,
+            const float4 *__restrict__ c, int nc, const float4 *__restrict__ wp, int n_out,
+            double *__restrict__ out)
+{
+    constexpr int PP = kFieldsThreads / FG;      // point pairs per CTA
+    constexpr int NP = FG * kFieldsF;            // padded columns
+    static_assert(PP % 32 == 0, "a warp must share one column group");
+    extern __shared__ float4 s_f[];
+    float4 *s_w = s_f;                           // [kFieldsK][NP]
+    float4 *s_phi = s_f + kFieldsK * NP;         // [kFieldsK][PP]: (h0, h1, l0, l1)
+    const int tid = threadIdx.x;
+    const int pp = tid % PP, fg = tid / PP;
+    const int64_t per_block = 2 * (int64_t)PP;
+    for (int64_t base = blockIdx.x * per_block; base < nv; base += (int64_t)gridDim.x * per_block) {
+        int64_t v0 = base + pp, v1 = base + PP + pp;
+        const int64_t r0 = v0 < nv ? v0 : nv - 1, r1 = v1 < nv ? v1 : nv - 1;
+        const float4 h0 = xh[r0], h1 = xh[r1], l0 = xl[r0], l1 = xl[r1];
+        const f2 qxh = f2_pack(h0.x, h1.x), qyh = f2_pack(h0.y, h1.y), qzh = f2_pack(h0.z, h1.z);
+        const f2 qxl = f2_pack(l0.x, l1.x), qyl = f2_pack(l0.y, l1.y), qzl = f2_pack(l0.z, l1.z);
+        const f2 z = f2_pack(0.0f, 0.0f);
+        ff2 acc[kFieldsF];
+#pragma unroll
+        for (int f = 0; f < kFieldsF; ++f)
+            acc[f] = ff2{z, z};
+        int nren = 0;
+        for (int t0 = 0; t0 < nc; t0 += kFieldsK) {
+            const int nt = min(kFieldsK, nc - t0);
+            __syncthreads();   // the previous tile's readers are done
+            for (int i = tid; i < nt * NP; i += kFieldsThreads)
+                s_w[i] = wp[(int64_t)t0 * NP + i];
+            for (int k = fg; k < nt; k += FG) {
+                const float4 ch = __ldg(c + 2 * (t0 + k)), cl = __ldg(c + 2 * (t0 + k) + 1);
+                const ff2 s2 = dist2_ff2(qxh, qxl, qyh, qyl, qzh, qzl, f2_bcast(ch.x),
+                                         f2_bcast(cl.x), f2_bcast(ch.y), f2_bcast(cl.y),
+                                         f2_bcast(ch.z), f2_bcast(cl.z));
+                const ff2 ph = phi_ff2_s(s2);
+                float a0, a1, b0, b1;
+                f2_unpack(ph.h, a0, a1);
+                f2_unpack(ph.l, b0, b1);
+                s_phi[k * PP + pp] = make_float4(a0, a1, b0, b1);
+            }
+            __syncthreads();
+            for (int k = 0; k < nt; ++k) {
+                if (++nren == kFieldsRenorm) {
+                    nren = 0;
+#pragma unroll
+                    for (int f = 0; f < kFieldsF; ++f)
+                        acc[f] = two_sum2(acc[f].h, acc[f].l);
+                }
+                const float4 pv = s_phi[k * PP + pp];
+                const ff2 ph{f2_pack(pv.x, pv.y), f2_pack(pv.z, pv.w)};
+                const float4 *wk = s_w + k * NP + fg * kFieldsF;
+#pragma unroll
+                for (int f = 0; f < kFieldsF; ++f) {
+                    const float4 w = wk[f];
+                    ff_fma_acc2(acc[f], f2_pack(w.x, w.y), f2_pack(w.z, w.w), ph);
+                }
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < kFieldsF; ++f) {
+            const int col = fg * kFieldsF + f;
+            if (col < n_out) {
+                float hh0, hh1, ll0, ll1;
+                f2_unpack(acc[f].h, hh0, hh1);
+                f2_unpack(acc[f].l, ll0, ll1);
+                if (v0 < nv)
+                    out[v0 * n_out + col] = (double)hh0 + (double)ll0;
+                if (v1 < nv)
+                    out[v1 * n_out + col] = (double)hh1 + (double)ll1;
+            }
+        }
+    }
+}
+
+struct FieldsWs {
+    size_t xh, xl, c, w, total;
+};
+
+static FieldsWs fields_ws(int64_t nv, int64_t nc, int n_out)
+{
+    FieldsWs L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    L.xh = take(sizeof(float4) * (size_t)nv);
+    L.xl = take(sizeof(float4) * (size_t)nv);
+    L.c = take(sizeof(float4) * 2 * (size_t)std::max<int64_t>(nc, 1));
+    L.w = take(sizeof(float4) * (size_t)std::max<int64_t>(nc, 1) * fields_pad(n_out));
+    L.total = o;
+    return L;
+}
+
+}  // namespace rbf
+
+extern "C" size_t rbf_volume_fields_workspace_bytes(int64_t nv, int64_t nc, int n_out)
+{
+    using namespace rbf;
+    if (nv < 0 || nc < 0 || n_out < 1 || n_out > kFieldsMaxOut)
+        return 0;
+    return fields_ws(nv, nc, n_out).total;
+}
+
+extern "C" rbf_status rbf_deform_volume_fields(const double *d_xv, int64_t nv, const double *d_xb,
+                                               const int32_t *d_sel_idx, int64_t nc,
+                                               const double *d_w, int n_out, const rbf_params *p,
+                                               double *d_out, void *d_ws, size_t ws_bytes,
+                                               void *stream)
+{
+    using namespace rbf;
+    if (!p || !(p->radius > 0.0) || !std::isfinite(p->radius) || p->eval_prec != RBF_PREC_F32X2 ||
+        nv < 0 || nc < 0 || nc > INT32_MAX / kFieldsMaxOut || n_out < 1 || n_out > kFieldsMaxOut)
+        return RBF_E_ARG;
+    if (nv == 0)
+        return RBF_OK;
+    if (!d_xv || !d_out || (nc > 0 && (!d_xb || !d_sel_idx || !d_w)))
+        return RBF_E_ARG;
+    const FieldsWs L = fields_ws(nv, nc, n_out);
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255) != 0)
+        return RBF_E_WORKSPACE;
+    DeviceInfo dev;
+    if (!device_info(&dev))
+        return RBF_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nc == 0) {
+        if (cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)nv * n_out, st) != cudaSuccess)
+            return RBF_E_CUDA;
+        return RBF_OK;
+    }
+    char *ws = (char *)d_ws;
+    float4 *xh = (float4 *)(ws + L.xh), *xl = (float4 *)(ws + L.xl);
+    float4 *c = (float4 *)(ws + L.c), *wp = (float4 *)(ws + L.w);
+    const double inv_r = 1.0 / p->radius;
+    const int n_pad = fields_pad(n_out);
+    const int fg = n_pad / kFieldsF;
+    k_pack_points_ff<<<(int)std::min<int64_t>((nv + 255) / 256, (int64_t)dev.sms * 8), 256, 0, st>>>(
+        d_xv, nv, inv_r, xh, xl);
+    k_pack_centres_hl<<<(int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4), 256, 0,
+                        st>>>(d_xb, d_sel_idx, nc, inv_r, c);
+    const int64_t wtot = nc * n_pad;
+    k_pack_fields_w<<<(int)std::min<int64_t>((wtot + 255) / 256, (int64_t)dev.sms * 8), 256, 0,
+                      st>>>(d_w, (int)nc, n_out, n_pad, wp);
+    const int pp = kFieldsThreads / fg;
+    const size_t smem = sizeof(float4) * (size_t)kFieldsK * (n_pad + pp);
+    const int64_t tiles = (nv + 2 * pp - 1) / (2 * pp);
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)dev.sms);
+    const void *kfn = fg == 1   ? (const void *)k_fields_ff<1>
+                      : fg == 2 ? (const void *)k_fields_ff<2>
+                      : fg == 4 ? (const void *)k_fields_ff<4>
+                                : (const void *)k_fields_ff<8>;
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return RBF_E_CUDA;
+    if (fg == 1)
+        k_fields_ff<1><<<grid, kFieldsThreads, smem, st>>>(xh, xl, nv, c, (int)nc, wp, n_out, d_out);
+    else if (fg == 2)
+        k_fields_ff<2><<<grid, kFieldsThreads, smem, st>>>(xh, xl, nv, c, (int)nc, wp, n_out, d_out);
+    else if (fg == 4)
+        k_fields_ff<4><<<grid, kFieldsThreads, smem, st>>>(xh, xl, nv, c, (int)nc, wp, n_out, d_out);
+    else
+        k_fields_ff<8><<<grid, kFieldsThreads, smem, st>>>(xh, xl, nv, c, (int)nc, wp, n_out, d_out);
+    if (cudaGetLastError() != cudaSuccess)
+        return RBF_E_CUDA;
+    return RBF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Batched volume sums: many problems (each its own points, support set and
 // weights) in one launch of the double-float kernel.  Work items are tiles of

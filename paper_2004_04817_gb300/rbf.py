@@ -192,6 +192,11 @@ def lib():
         L.rbf_support_kl.restype = C.c_int
         L.rbf_support_kl.argtypes = [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int64,
                                      C.POINTER(C.c_double), _vp, C.c_size_t, _vp]
+        L.rbf_volume_fields_workspace_bytes.restype = C.c_size_t
+        L.rbf_volume_fields_workspace_bytes.argtypes = [C.c_int64, C.c_int64, C.c_int]
+        L.rbf_deform_volume_fields.restype = C.c_int
+        L.rbf_deform_volume_fields.argtypes = [_vp, C.c_int64, _vp, _vp, C.c_int64, _vp, C.c_int,
+                                               P, _vp, _vp, C.c_size_t, _vp]
         L.rbf_greedy_screen_errors.restype = C.c_int
         L.rbf_greedy_screen_errors.argtypes = [_vp, C.c_size_t, C.c_int64, P, C.c_int64, _vp,
                                                _vp, _vp, _vp]
@@ -535,6 +540,31 @@ def deform_volume(xv, xb, sel_idx, w, *, radius, eval_prec=PREC_F32, stream=None
                              _ptr(dv), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "rbf_deform_volume")
     return dv
+
+
+def deform_volume_fields(xv, xb, sel_idx, w, *, radius, stream=None, workspace=None, out=None):
+    """Eq. 6 for every column of ``w`` (nc x n_out FP64) on one support set,
+    double-float (FP64-level accuracy): (nv, n_out) FP64."""
+    L = lib()
+    _dev(xv, torch.float64, "xv", 3)
+    _dev(xb, torch.float64, "xb", 3)
+    _dev(sel_idx, torch.int32, "sel_idx")
+    if w.device.type != "cuda" or w.dtype != torch.float64 or w.dim() != 2 or \
+            not w.is_contiguous() or w.shape[0] != sel_idx.numel():
+        raise ValueError("w must be a contiguous CUDA float64 (nc, n_out) tensor")
+    nv, nc, n_out = xv.shape[0], sel_idx.numel(), w.shape[1]
+    need = L.rbf_volume_fields_workspace_bytes(nv, nc, n_out)
+    if need == 0:
+        raise RBFError(1, "rbf_volume_fields_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= need else \
+        _workspace(need, xv.device)
+    d = out if out is not None else torch.empty((nv, n_out), dtype=torch.float64,
+                                                device=xv.device)
+    p = make_params(radius, eval_prec=PREC_F32X2)
+    st = L.rbf_deform_volume_fields(_ptr(xv), nv, _ptr(xb), _ptr(sel_idx), nc, _ptr(w), n_out,
+                                    C.byref(p), _ptr(d), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "rbf_deform_volume_fields")
+    return d
 
 
 def group_of(nb, m, seed):

@@ -65,5 +65,8 @@ def test_screened_errors_within_certified_bounds(prec, m, ctas):
     print(f"\nprec {prec}, m {m}, ctas {ctas}: N_c {r['nc']}, {screened.sum()} screened "
           f"nodes, {(~screened).sum()} re-scored in FP64, largest |E~ - E| / beta "
           f"{ratio:.3e}, median beta / E* {np.median(b[screened]) / r['stats']['estar']:.2e}")
-    # the certified final maximum is an upper bound of the exact one
-    assert r["stats"]["final_max"] >= E.max() - slack.max()
+    # the certified final maximum bounds every screened node's exact error
+    # (re-scored nodes were evaluated in FP64 with the FP64 weights, not with
+    # the table's rounded ones)
+    if screened.any():
+        assert r["stats"]["final_max"] >= (E - slack)[screened].max()

@@ -130,3 +130,58 @@ def test_modal_sinusoidal_modes_full_support():
         err = np.abs(got - ref)
         lim = _bound(mode, scale, bnd, W)
         assert np.all(err <= lim), (mode, (err / lim).max())
+
+
+# ---- many fields in double-float (the accurate path for heavily cancelling
+# weights): FP64-level results, bound 2^-40 sum_j |w_j phi_vj| (the derived
+# double-float error is about 2^-44 of that sum) ----
+@pytest.mark.parametrize("n_out", [3, 24, 96, 150])
+def test_volume_fields_against_fp64(n_out):
+    rng = np.random.default_rng(5)
+    xb = rng.random((3000, 3))
+    S = np.sort(rng.choice(3000, 1100, replace=False)).astype(np.int32)   # 35 tiles, ragged
+    W = rng.standard_normal((1100, n_out)) * np.logspace(0, 4, n_out)[None, :]
+    xv = rng.random((1500, 3)) * 1.2 - 0.1                               # ragged point tile
+    R = 0.8
+    ref, bnd = _ref(xv, xb[S], W, R)
+    d = P.deform_volume_fields(cuda(xv), cuda(xb), cuda(S, torch.int32), cuda(W), radius=R)
+    err = np.abs(d.cpu().numpy() - ref)
+    lim = 2.0 ** -40 * bnd + 1e-300
+    assert np.all(err <= lim), (err / lim).max()
+    # each column agrees with the 3-column double-float volume sum
+    if n_out >= 3:
+        dv = P.deform_volume(cuda(xv), cuda(xb), cuda(S, torch.int32),
+                             cuda(np.ascontiguousarray(W[:, :3])), radius=R,
+                             eval_prec=P.PREC_F32X2).cpu().numpy()
+        assert np.abs(dv - d.cpu().numpy()[:, :3]).max() <= 2.0 ** -39 * bnd[:, :3].max()
+
+
+def test_volume_fields_sinusoidal_modes_full_support():
+    """Configuration 4b with an accurate result: the 32 sinusoidal bending
+    modes on the GCB support set of the N_b = 50,000 wing, where every
+    FP32-accumulating path (tensor cores, FP32 sums) misses.  The
+    double-float fields must match FP64 to 1e-5 of the largest modal
+    displacement (and in fact to the double-float bound)."""
+    c = synth.wing_gcb(n_vol=200_000)
+    xb, db = cuda(c["xb"]), cuda(c["db"])
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    r = P.greedy_select(xb, db, radius=2.0, tol=estar, tol_mode=0, m=241, seed=1,
+                        eval_prec=P.PREC_F32X2)
+    S = r["idx"].cpu().numpy()
+    y = c["xb"][S, 1]
+    modes = np.zeros((len(S), 96))
+    for q in range(1, 33):
+        modes[:, 3 * (q - 1) + 2] = 0.05 * np.sin((2 * q - 1) * np.pi * y / 2.0)
+    W = np.zeros_like(modes)
+    for q in range(32):
+        x, res = P.solve_system(xb, r["idx"], cuda(modes[:, 3 * q:3 * q + 3]), radius=2.0)
+        W[:, 3 * q:3 * q + 3] = x.cpu().numpy()
+    xv = c["xv"]
+    sample = np.random.default_rng(8).choice(len(xv), 2000, replace=False)
+    ref, bnd = _ref(xv[sample], c["xb"][S], W, 2.0)
+    d = P.deform_volume_fields(cuda(xv), xb, r["idx"], cuda(W), radius=2.0)
+    err = np.abs(d.cpu().numpy()[sample] - ref)
+    assert err.max() <= 1e-5 * 0.05, err.max()
+    assert np.all(err <= 2.0 ** -40 * bnd + 1e-300), (err / (2.0 ** -40 * bnd)).max()
+    print(f"\n32 modes, double-float fields: max error {err.max():.3e} "
+          f"(largest sum |w phi| {bnd.max():.3e})")

@@ -45,7 +45,8 @@ def parse():
                     help="start the ranks (gloo, no GPU work) and report the rank count and "
                          "the max-over-ranks step time; tests the multi-rank host path")
     ap.add_argument("--profile-case", default=None,
-                    choices=["volume", "greedy", "solve", "cull", "modal", "adjoint", "batched"],
+                    choices=["volume", "greedy", "solve", "cull", "modal", "fields", "adjoint",
+                             "batched"],
                     help="run one kernel's calls on the GCB wing (a few launches, no timing) "
                          "for an ncu capture; see profiles/")
     ap.add_argument("--reps", type=int, default=2, help="--profile-case: repetitions")
@@ -583,7 +584,7 @@ def profile_case(args):
         torch.cuda.synchronize()
         print("profile case done", case, [r["nc"] for r in gb.results()])
         return 0
-    nv = args.nv if case in ("volume", "cull", "modal", "adjoint") else 0
+    nv = args.nv if case in ("volume", "cull", "modal", "fields", "adjoint") else 0
     c = synth.wing_gcb(n_vol=nv)
     dev = lambda x, t=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=t,
                                                       device="cuda")
@@ -617,6 +618,11 @@ def profile_case(args):
             W = torch.randn((g["nc"], args.n_out), dtype=torch.float64, device="cuda",
                             generator=torch.Generator("cuda").manual_seed(1))
             P.deform_modal(xv, xb, g["idx"], W, radius=R, mode=args.modal_mode)
+        elif case == "fields":
+            # random weights (N_c x n_out): the timing does not depend on them
+            W = torch.randn((g["nc"], args.n_out), dtype=torch.float64, device="cuda",
+                            generator=torch.Generator("cuda").manual_seed(1))
+            P.deform_volume_fields(xv, xb, g["idx"], W, radius=R)
         elif case == "adjoint":
             P.adjoint_factored(xv, gv, fac, eval_prec=args.vol_prec)
     torch.cuda.synchronize()

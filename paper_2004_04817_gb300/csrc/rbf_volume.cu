@@ -463,7 +463,8 @@ namespace rbf {
 // computed once per (point, centre) pair into shared memory and shared by
 // all n_out columns, so a pair costs one double-float phi plus n_out
 // double-float multiply-adds instead of n_out / 3 separate volume sums.
-//   CTA: 256 threads = PP point pairs x FG column groups of kFieldsF columns;
+//   CTA: 256 threads = PP point pairs x FG column groups of F columns (12
+//   when n_out <= 96: two CTAs per SM; else 24);
 //   a warp shares its column group (weights read as broadcasts) and covers
 //   32 consecutive point pairs (phi entries read conflict-free).
 //   Per centre tile of kFieldsK centres: stage the weights (w_hi, w_hi,
@@ -473,18 +474,21 @@ namespace rbf {
 //   two_sum) every kFieldsRenorm centres, which bounds the growth of their low
 //   parts.
 // ---------------------------------------------------------------------------
-constexpr int kFieldsF = 24;          // columns per thread
+constexpr int kFieldsFMax = 24;       // columns per thread (12 or 24)
 constexpr int kFieldsK = 32;          // centres per shared-memory tile
 constexpr int kFieldsThreads = 256;
 constexpr int kFieldsMaxOut = 192;    // 8 column groups
 constexpr int kFieldsRenorm = 8;
 
+static int fields_cols(int n_out) { return n_out <= 96 ? 12 : kFieldsFMax; }
+
 static int fields_pad(int n_out)
 {
-    int np = kFieldsF;
+    const int f = fields_cols(n_out);
+    int np = f;
     while (np < n_out)
         np *= 2;
-    return np;   // 24, 48, 96 or 192: FG = np / 24 divides 8
+    return np;   // f, 2f, 4f or 8f: FG = np / f divides 8
 }
 
 __global__ void k_pack_fields_w(const double *__restrict__ w, int nc, int n_out, int n_pad,
@@ -518,14 +522,14 @@ __global__ void k_pack_centres_hl(const double *__restrict__ xb, const int32_t *
     }
 }
 
-template <int FG>
-__global__ void __launch_bounds__(kFieldsThreads, 1)
+template <int FG, int F>
+__global__ void __launch_bounds__(kFieldsThreads, F <= 12 ? 2 : 1)
 k_fields_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_t nv,
             const float4 *__restrict__ c, int nc, const float4 *__restrict__ wp, int n_out,
             double *__restrict__ out)
 {
     constexpr int PP = kFieldsThreads / FG;      // point pairs per CTA
-    constexpr int NP = FG * kFieldsF;            // padded columns
+    constexpr int NP = FG * F;                   // padded columns
     static_assert(PP % 32 == 0, "a warp must share one column group");
     extern __shared__ float4 s_f[];
     float4 *s_w = s_f;                           // [kFieldsK][NP]
@@ -540,9 +544,9 @@ k_fields_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_
         const f2 qxh = f2_pack(h0.x, h1.x), qyh = f2_pack(h0.y, h1.y), qzh = f2_pack(h0.z, h1.z);
         const f2 qxl = f2_pack(l0.x, l1.x), qyl = f2_pack(l0.y, l1.y), qzl = f2_pack(l0.z, l1.z);
         const f2 z = f2_pack(0.0f, 0.0f);
-        ff2 acc[kFieldsF];
+        ff2 acc[F];
 #pragma unroll
-        for (int f = 0; f < kFieldsF; ++f)
+        for (int f = 0; f < F; ++f)
             acc[f] = ff2{z, z};
         int nren = 0;
         for (int t0 = 0; t0 < nc; t0 += kFieldsK) {
@@ -566,22 +570,22 @@ k_fields_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_
                 if (++nren == kFieldsRenorm) {
                     nren = 0;
 #pragma unroll
-                    for (int f = 0; f < kFieldsF; ++f)
+                    for (int f = 0; f < F; ++f)
                         acc[f] = two_sum2(acc[f].h, acc[f].l);
                 }
                 const float4 pv = s_phi[k * PP + pp];
                 const ff2 ph{f2_pack(pv.x, pv.y), f2_pack(pv.z, pv.w)};
-                const float4 *wk = s_w + k * NP + fg * kFieldsF;
+                const float4 *wk = s_w + k * NP + fg * F;
 #pragma unroll
-                for (int f = 0; f < kFieldsF; ++f) {
+                for (int f = 0; f < F; ++f) {
                     const float4 w = wk[f];
                     ff_fma_acc2(acc[f], f2_pack(w.x, w.y), f2_pack(w.z, w.w), ph);
                 }
             }
         }
 #pragma unroll
-        for (int f = 0; f < kFieldsF; ++f) {
-            const int col = fg * kFieldsF + f;
+        for (int f = 0; f < F; ++f) {
+            const int col = fg * F + f;
             if (col < n_out) {
                 float hh0, hh1, ll0, ll1;
                 f2_unpack(acc[f].h, hh0, hh1);
@@ -657,7 +661,8 @@ extern "C" rbf_status rbf_deform_volume_fields(const double *d_xv, int64_t nv, c
     float4 *c = (float4 *)(ws + L.c), *wp = (float4 *)(ws + L.w);
     const double inv_r = 1.0 / p->radius;
     const int n_pad = fields_pad(n_out);
-    const int fg = n_pad / kFieldsF;
+    const int fcols = fields_cols(n_out);
+    const int fg = n_pad / fcols;
     k_pack_points_ff<<<(int)std::min<int64_t>((nv + 255) / 256, (int64_t)dev.sms * 8), 256, 0, st>>>(
         d_xv, nv, inv_r, xh, xl);
     k_pack_centres_hl<<<(int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4), 256, 0,
@@ -668,22 +673,34 @@ extern "C" rbf_status rbf_deform_volume_fields(const double *d_xv, int64_t nv, c
     const int pp = kFieldsThreads / fg;
     const size_t smem = sizeof(float4) * (size_t)kFieldsK * (n_pad + pp);
     const int64_t tiles = (nv + 2 * pp - 1) / (2 * pp);
-    const int grid = (int)std::min<int64_t>(tiles, (int64_t)dev.sms);
-    const void *kfn = fg == 1   ? (const void *)k_fields_ff<1>
-                      : fg == 2 ? (const void *)k_fields_ff<2>
-                      : fg == 4 ? (const void *)k_fields_ff<4>
-                                : (const void *)k_fields_ff<8>;
-    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return RBF_E_CUDA;
-    if (fg == 1)
-        k_fields_ff<1><<<grid, kFieldsThreads, smem, st>>>(xh, xl, nv, c, (int)nc, wp, n_out, d_out);
-    else if (fg == 2)
-        k_fields_ff<2><<<grid, kFieldsThreads, smem, st>>>(xh, xl, nv, c, (int)nc, wp, n_out, d_out);
-    else if (fg == 4)
-        k_fields_ff<4><<<grid, kFieldsThreads, smem, st>>>(xh, xl, nv, c, (int)nc, wp, n_out, d_out);
-    else
-        k_fields_ff<8><<<grid, kFieldsThreads, smem, st>>>(xh, xl, nv, c, (int)nc, wp, n_out, d_out);
+#define RBF_FIELDS_LAUNCH(FGV, FV)                                                            \
+    do {                                                                                      \
+        if (cudaFuncSetAttribute(k_fields_ff<FGV, FV>,                                        \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=   \
+            cudaSuccess)                                                                      \
+            return RBF_E_CUDA;                                                                \
+        int occ = 1;                                                                          \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fields_ff<FGV, FV>,         \
+                                                          kFieldsThreads, smem) != cudaSuccess || \
+            occ < 1)                                                                          \
+            occ = 1;                                                                          \
+        const int grid = (int)std::min<int64_t>(tiles, (int64_t)dev.sms * occ);               \
+        k_fields_ff<FGV, FV><<<grid, kFieldsThreads, smem, st>>>(xh, xl, nv, c, (int)nc, wp,  \
+                                                                 n_out, d_out);               \
+    } while (0)
+    if (fcols == 12) {
+        if (fg == 1)
+            RBF_FIELDS_LAUNCH(1, 12);
+        else if (fg == 2)
+            RBF_FIELDS_LAUNCH(2, 12);
+        else if (fg == 4)
+            RBF_FIELDS_LAUNCH(4, 12);
+        else
+            RBF_FIELDS_LAUNCH(8, 12);
+    } else {
+        RBF_FIELDS_LAUNCH(8, 24);
+    }
+#undef RBF_FIELDS_LAUNCH
     if (cudaGetLastError() != cudaSuccess)
         return RBF_E_CUDA;
     return RBF_OK;

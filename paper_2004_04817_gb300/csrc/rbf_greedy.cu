@@ -1749,10 +1749,24 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     pairs32 += (long long)nq * nc;
             } else {
                 const float4 *cw = smem ? s_cw : a.cwff;
-                const float c_sb = 9.5f * (float)((n_l + 1) / 2 + 1) + 3.0f * lg_ts + 43.0f;
+                // wide teams: two warps per node when the group leaves room
+                // (at most one node per warp pair of the grid), which halves
+                // each lane's chain of pairs -- the pass is latency-bound
+                const bool wide = (int64_t)nq * 64 <= (int64_t)gthreads;
+                const int tsw = wide ? 64 : ts;
+                const int subw = wide ? (tid & 63) : sub;
+                const int teamw = wide ? (gtid >> 6) : team;
+                const int nteamsw = wide ? (gthreads >> 6) : nteams;
+                const int roundsw = (nq + nteamsw - 1) / nteamsw;
+                const int n_lw = (nc + tsw - 1) / tsw;
+                const float lg_w = (float)(31 - __clz(tsw));
+                const float b_upw =
+                    1.0f + (2.0f * (float)n_lw + 2.0f * lg_w + (float)nc * (1.0f / 32.0f) + 40.0f) * kU32;
+                const float c_sb = 9.5f * (float)((n_lw + 1) / 2 + 1) + 3.0f * lg_w + 43.0f;
                 const float coord_term = (7.32f * xscale + 41.5f) * s_wabs;
-                for (int it = 0; it < rounds; ++it) {
-                    const int q = p0 + team + it * nteams;
+                __shared__ float s_pair[2][kGWarps / 2][8];
+                for (int it = 0; it < roundsw; ++it) {
+                    const int q = p0 + teamw + it * nteamsw;
                     const bool act = q < p1;
                     const int qq = act ? q : p0;
                     // the node's coordinates: high part = the FP32 copy, low part
@@ -1766,9 +1780,9 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     ff2 gx{z2, z2}, gy{z2, z2}, gz{z2, z2};
                     const f2 bxh = f2_bcast(qxh), bxl = f2_bcast(qxl), byh = f2_bcast(qyh),
                              byl = f2_bcast(qyl), bzh = f2_bcast(qzh), bzl = f2_bcast(qzl);
-                    int j = sub;
+                    int j = subw;
                     int nren = 0;
-                    for (; j + ts < nc; j += 2 * ts) {
+                    for (; j + tsw < nc; j += 2 * tsw) {
                         if (++nren == kFFRenorm) {
                             // error-free renormalisation: the low parts restart
                             // below one ulp of the high parts
@@ -1777,7 +1791,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                             gy = two_sum2(gy.h, gy.l);
                             gz = two_sum2(gz.h, gz.l);
                         }
-                        const int j2 = j + ts;
+                        const int j2 = j + tsw;
                         const float4 ch0 = smem ? cw[j] : ldcg(cw + j);
                         const float4 cl0 = smem ? cw[pst + j] : ldcg(cw + pst + j);
                         const float4 wh0 = smem ? cw[2 * pst + j] : ldcg(cw + 2 * pst + j);
@@ -1821,7 +1835,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         return ff_add(ff_add(two_sum(h0, l0), two_sum(h1, l1)), two_sum(f.h, f.l));
                     };
                     ff sx = lane_sum(gx, fx), sy = lane_sum(gy, fy), sz = lane_sum(gz, fz);
-                    for (int o = 1; o < ts; o <<= 1) {
+                    for (int o = 1; o < min(tsw, 32); o <<= 1) {
                         sx = ff_add(sx, ff{__shfl_xor_sync(0xffffffffu, sx.h, o),
                                            __shfl_xor_sync(0xffffffffu, sx.l, o)});
                         sy = ff_add(sy, ff{__shfl_xor_sync(0xffffffffu, sy.h, o),
@@ -1829,8 +1843,30 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         sz = ff_add(sz, ff{__shfl_xor_sync(0xffffffffu, sz.h, o),
                                            __shfl_xor_sync(0xffffffffu, sz.l, o)});
                     }
-                    sb = team_sum(sb, ts);
-                    if (act && sub == 0 && !ldcg(a.in_s + q)) {
+                    sb = team_sum(sb, min(tsw, 32));
+                    if (wide) {
+                        // the odd warp of the pair hands its sums to the even
+                        // one (one more team level); buffers alternate by
+                        // round, so one 64-thread barrier per round suffices
+                        float *sp = s_pair[it & 1][warp >> 1];
+                        if ((warp & 1) && lane == 0) {
+                            sp[0] = sx.h;
+                            sp[1] = sx.l;
+                            sp[2] = sy.h;
+                            sp[3] = sy.l;
+                            sp[4] = sz.h;
+                            sp[5] = sz.l;
+                            sp[6] = sb;
+                        }
+                        asm volatile("bar.sync %0, 64;" ::"r"(1 + (warp >> 1)) : "memory");
+                        if (!(warp & 1) && lane == 0) {
+                            sx = ff_add(sx, ff{sp[0], sp[1]});
+                            sy = ff_add(sy, ff{sp[2], sp[3]});
+                            sz = ff_add(sz, ff{sp[4], sp[5]});
+                            sb += sp[6];
+                        }
+                    }
+                    if (act && subw == 0 && !ldcg(a.in_s + q)) {
                         const float4 dh = ldcg(a.dgh + q), dl = ldcg(a.dgl + q);
                         const int qnode = ldcg(a.node_of_pos + q);
                         // E = |dr - F| in double-float; FP64 only converts the
@@ -1849,7 +1885,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         // rounded up by the factor
                         const float bf =
                             fmaxf(kU32Sq * (c_sb * sb + 4.0f * dabs + coord_term + 50.0f * ef.h) *
-                                      b_up,
+                                      b_upw,
                                   1e-18f);
                         a.u32[q] = bf;
                         a.e64[q] = e;

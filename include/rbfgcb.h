@@ -244,6 +244,9 @@ typedef struct {
     rbf_params params;
     int32_t *d_sel_idx;   /* device int32[params.nc_max] (output) */
     double *d_w;          /* device FP64 params.nc_max x 3 or NULL (output) */
+    int64_t *d_sel_iter;  /* device int64[params.nc_max] or NULL (output): the
+                             iteration k of Alg. 1 that appended each node
+                             (-1 for the seed nodes), as rbf_greedy_select */
 } rbf_greedy_problem;
 
 typedef struct rbf_greedy_batch rbf_greedy_batch;

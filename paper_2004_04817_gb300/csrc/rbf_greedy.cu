@@ -3202,7 +3202,7 @@ extern "C" rbf_status rbf_greedy_batch_create(const rbf_greedy_problem *h_probs,
         a.barrier_ns = kBarrierLimitNs;
         a.ld = (int)q.params.nc_max;
         a.sel_idx = q.d_sel_idx;
-        a.sel_iter = nullptr;
+        a.sel_iter = q.d_sel_iter;
         a.hist = nullptr;
         a.hist_cap = 0;
         a.w_out = q.d_w;

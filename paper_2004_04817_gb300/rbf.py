@@ -73,6 +73,7 @@ class GreedyProblem(C.Structure):
         ("params", Params),
         ("d_sel_idx", C.c_void_p),
         ("d_w", C.c_void_p),
+        ("d_sel_iter", C.c_void_p),
     ]
 
 
@@ -673,7 +674,8 @@ class GreedyBatch:
 
     ``problems``: list of dicts with ``xb``, ``db`` (CUDA FP64 (n, 3)),
     ``radius``, ``tol``, ``tol_mode``, ``m``, ``seed``, ``nc_max``.  Outputs
-    per problem: ``idx[i]`` (int32, nc_max), ``w[i]`` (FP64 (nc_max, 3)) and
+    per problem: ``idx[i]`` (int32, nc_max), ``iter[i]`` (int64, the iteration that
+    appended each node), ``w[i]`` (FP64 (nc_max, 3)) and
     the device array ``nc`` (int64, B).  ``run()`` only enqueues (it can be
     captured in a CUDA graph); ``results()`` synchronises.
     """
@@ -683,7 +685,7 @@ class GreedyBatch:
         self.B = len(problems)
         dev = problems[0]["xb"].device
         self.problems = problems
-        self.idx, self.w = [], []
+        self.idx, self.w, self.iter = [], [], []
         arr = (GreedyProblem * self.B)()
         for i, q in enumerate(problems):
             _dev(q["xb"], torch.float64, "xb", 3)
@@ -691,6 +693,7 @@ class GreedyBatch:
             ncm = int(q.get("nc_max") or min(q["xb"].shape[0], 4096))
             self.idx.append(torch.empty(ncm, dtype=torch.int32, device=dev))
             self.w.append(torch.empty((ncm, 3), dtype=torch.float64, device=dev))
+            self.iter.append(torch.empty(ncm, dtype=torch.int64, device=dev))
             arr[i].d_xb = q["xb"].data_ptr()
             arr[i].d_db = q["db"].data_ptr()
             arr[i].nb = q["xb"].shape[0]
@@ -698,6 +701,7 @@ class GreedyBatch:
                                         q.get("m", 1), q.get("seed", 1), ncm, refine_steps)
             arr[i].d_sel_idx = self.idx[i].data_ptr()
             arr[i].d_w = self.w[i].data_ptr()
+            arr[i].d_sel_iter = self.iter[i].data_ptr()
         self._arr = arr
         need = L.rbf_greedy_batch_workspace_bytes(arr, self.B)
         if need == 0:

@@ -87,3 +87,63 @@ def test_batched_graph_replay_is_identical(batch):
         nc = res[i]["nc"]
         assert torch.equal(gb.idx[i][:nc], idx_before[i][:nc])
         assert torch.equal(vb.dv[i], before[i])
+
+
+# ---- configuration 4a's problem sizes: the eight smallest of its 64 wings
+# (N_b from PCG64(seed) ~ U[5000, 100000], seeds 100-163, 5.4k-23k nodes),
+# tolerance 1e-4, m = round(1.5 N_b / N_c) from a plain-greedy batch; every
+# decision of every problem replayed by the oracle's follow mode ----
+CONFIG4A_SEEDS = [108, 123, 157, 147, 148, 107, 114, 112]
+
+
+def _config4a_case(seed, nv):
+    import math
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nb = int(rng.integers(5000, 100001))
+    ns = max(2, int(round(math.sqrt(nb / 5))))
+    nch = int(round(nb / ns))
+    return synth.wing_case(ns, nch, nv, vol_seed=seed, vol_kind="box", radius=2.0,
+                           tol_rel=1e-4)
+
+
+def test_batched_config4a_sizes_follow_oracle():
+    from _follow import check_follow
+    cases = [_config4a_case(s, 20_000) for s in CONFIG4A_SEEDS]
+    base = []
+    for s, c in zip(CONFIG4A_SEEDS, cases):
+        c["d_xb"], c["d_db"], c["d_xv"] = cuda(c["xb"]), cuda(c["db"]), cuda(c["xv"])
+        c["estar"] = oracle.tolerance(c["db"], c["tol_rel"])
+        base.append(dict(xb=c["d_xb"], db=c["d_db"], radius=2.0, tol=c["estar"], tol_mode=0,
+                         seed=s, nc_max=1024))
+    cal = P.GreedyBatch([dict(q, m=1) for q in base])
+    cal.run()
+    ms = [max(1, int(round(1.5 * len(c["xb"]) / r["nc"])))
+          for c, r in zip(cases, cal.results())]
+    gb = P.GreedyBatch([dict(q, m=m) for q, m in zip(base, ms)])
+    gb.run()
+    res = gb.results()
+    vb = P.VolumeBatch([dict(xv=c["d_xv"], xb=c["d_xb"], idx=gb.idx[i], w=gb.w[i],
+                             nc_ptr=gb.nc_ptr + 8 * i, radius=2.0)
+                        for i, c in enumerate(cases)])
+    vb.run()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    for i, (s, c, m) in enumerate(zip(CONFIG4A_SEEDS, cases, ms)):
+        r = res[i]
+        assert r["status"] == 0, (s, r["status"])
+        nc = r["nc"]
+        idx = gb.idx[i][:nc].cpu().numpy()
+        it = gb.iter[i][:nc].cpu().numpy()
+        f = oracle.greedy(c["xb"], c["db"], 2.0, c["estar"], m=m, seed=s, follow=(idx, it),
+                          tie_rel=1e-6, history=False)
+        check_follow(f, f"batched wing seed {s}, N_b {len(c['xb'])}, m={m}, N_c {nc}")
+        assert f["nc"] == nc and f["stats"]["iterations"] == r["iterations"]
+        assert r["final_max"] <= c["estar"]
+        dmax = np.abs(c["db"]).max()
+        Wo, st, _ = oracle.solve_weights(c["xb"], c["db"], idx, 2.0)
+        assert st == 0
+        assert np.abs(gb.w[i][:nc].cpu().numpy() - Wo).max() <= 1e-5 * dmax
+        sample = np.sort(rng.choice(len(c["xv"]), 1000, replace=False))
+        ref = oracle.rbf_sum(c["xv"][sample], c["xb"], idx, Wo, 2.0)
+        got = vb.dv[i].cpu().numpy()[sample]
+        assert np.abs(got - ref).max() <= 1e-5 * dmax

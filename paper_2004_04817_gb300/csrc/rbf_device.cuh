@@ -201,7 +201,8 @@ __device__ __forceinline__ ff phi_ff_s(ff s)
     const float e0 = __fmul_rn(s.h, y);
     const float r = __fadd_rn(fmaf(-e0, e0, s.h), s.l);
     const ff eta = fast_two_sum(e0, __fmul_rn(__fmul_rn(r, 0.5f), y));
-    ff t = two_sum(1.0f, -eta.h);
+    // 1 - eta.h by FastTwoSum (exact for eta.h <= 1; beyond, phi is set to 0)
+    ff t = fast_two_sum(1.0f, -eta.h);
     t = fast_two_sum(t.h, __fsub_rn(t.l, eta.l));
     const ff t2 = ff_sqr(t);
     const ff t4 = ff_sqr(t2);
@@ -225,6 +226,57 @@ __device__ __forceinline__ ff dist2_ff(float qxh, float qxl, float qyh, float qy
     ff dz = two_sum(qzh, -czh);
     dz.l = __fadd_rn(dz.l, __fsub_rn(qzl, czl));
     return ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+}
+
+// ----------------------------------------------------------------------------
+// Grid split of coordinates, for exact differences.  With 2^k above every
+// |x| of a computation, G = 2^(k-23) and g = G 2^-24, a coordinate is stored
+// as h = G rint(x / G) and l = g rint((x - h) / g): both are floats (at most
+// 2^23 units of G or g), |x - h - l| <= g / 2 = 2^(k-48), and for two
+// coordinates h1 - h2 and l1 - l2 are exact in FP32 (at most 2^24 units).
+// The squared distance then needs no TwoSum on the differences.
+// ----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double grid_unit(double xmax)
+{
+    int k = 0;
+    frexp(xmax > 1e-30 ? xmax : 1e-30, &k);   // xmax = f 2^k, f in [0.5, 1)
+    return ldexp(1.0, k - 23);
+}
+
+__host__ __device__ __forceinline__ void split_grid(double x, double G, float &h, float &l)
+{
+    const double hd = rint(x / G) * G;
+    const double g = G * 5.9604644775390625e-08;   // G 2^-24
+    h = (float)hd;
+    l = (float)(rint((x - hd) / g) * g);
+}
+
+// Squared distance of two grid-split points.  Per component the exact
+// difference (qh - ch) + (ql - cl) is normalised by FastTwoSum (|qh - ch| is
+// a multiple of G, so it is 0 or at least G >= |ql - cl|) and squared with an
+// error-free product; the three squares are summed by two TwoSums, their low
+// parts in FP32, and the result renormalised.
+__device__ __forceinline__ void gs_square(float qh, float ql, float ch, float cl, float &p,
+                                          float &e)
+{
+    const ff d = fast_two_sum(__fsub_rn(qh, ch), __fsub_rn(ql, cl));
+    p = __fmul_rn(d.h, d.h);
+    e = fmaf(d.h, d.h, -p);
+    e = fmaf(__fadd_rn(d.h, d.h), d.l, e);
+}
+
+__device__ __forceinline__ ff dist2_gs(float qxh, float qxl, float qyh, float qyl, float qzh,
+                                       float qzl, float cxh, float cxl, float cyh, float cyl,
+                                       float czh, float czl)
+{
+    float px, ex, py, ey, pz, ez;
+    gs_square(qxh, qxl, cxh, cxl, px, ex);
+    gs_square(qyh, qyl, cyh, cyl, py, ey);
+    gs_square(qzh, qzl, czh, czl, pz, ez);
+    const ff s1 = two_sum(px, py);
+    const ff s2 = two_sum(s1.h, pz);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), ez), __fadd_rn(s1.l, s2.l));
+    return fast_two_sum(s2.h, lo);
 }
 
 // acc += w * phi with w and phi in ff; acc kept as an unnormalised pair whose
@@ -308,6 +360,29 @@ __device__ __forceinline__ ff2 dist2_ff2(f2 qxh, f2 qxl, f2 qyh, f2 qyl, f2 qzh,
     return ff_add2(ff_add2(ff_sqr2(dx), ff_sqr2(dy)), ff_sqr2(dz));
 }
 
+// Squared distances of two (query, centre) pairs of grid-split points (the
+// method of dist2_gs, lane by lane).
+__device__ __forceinline__ void gs_square2(f2 qh, f2 ql, f2 ch, f2 cl, f2 &p, f2 &e)
+{
+    const ff2 d = fast_two_sum2(f2_sub(qh, ch), f2_sub(ql, cl));
+    p = f2_mul(d.h, d.h);
+    e = f2_fma(d.h, d.h, f2_neg(p));
+    e = f2_fma(f2_add(d.h, d.h), d.l, e);
+}
+
+__device__ __forceinline__ ff2 dist2_gs2(f2 qxh, f2 qxl, f2 qyh, f2 qyl, f2 qzh, f2 qzl, f2 cxh,
+                                         f2 cxl, f2 cyh, f2 cyl, f2 czh, f2 czl)
+{
+    f2 px, ex, py, ey, pz, ez;
+    gs_square2(qxh, qxl, cxh, cxl, px, ex);
+    gs_square2(qyh, qyl, cyh, cyl, py, ey);
+    gs_square2(qzh, qzl, czh, czl, pz, ez);
+    const ff2 s1 = two_sum2(px, py);
+    const ff2 s2 = two_sum2(s1.h, pz);
+    const f2 lo = f2_add(f2_add(f2_add(ex, ey), ez), f2_add(s1.l, s2.l));
+    return fast_two_sum2(s2.h, lo);
+}
+
 // phi for two pairs (same method as phi_ff_s; the reciprocal square roots
 // are scalar MUFU operations).
 __device__ __forceinline__ ff2 phi_ff2_s(ff2 s)
@@ -320,7 +395,7 @@ __device__ __forceinline__ ff2 phi_ff2_s(ff2 s)
     const f2 e0 = f2_mul(s.h, y);
     const f2 r = f2_add(f2_fma(f2_neg(e0), e0, s.h), s.l);
     const ff2 eta = fast_two_sum2(e0, f2_mul(f2_mul(r, f2_bcast(0.5f)), y));
-    ff2 t = two_sum2(f2_bcast(1.0f), f2_neg(eta.h));
+    ff2 t = fast_two_sum2(f2_bcast(1.0f), f2_neg(eta.h));
     t = fast_two_sum2(t.h, f2_sub(t.l, eta.l));
     const ff2 t2 = ff_sqr2(t);
     const ff2 t4 = ff_sqr2(t2);

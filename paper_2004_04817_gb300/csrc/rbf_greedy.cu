@@ -76,7 +76,7 @@ constexpr int kFFRenorm = 8;               // double-float accumulators renormal
 //   FP32:         |E~ - E| <= u   ((n_l + log2 ts + 10) sb + |dr|_1
 //                                  + (7.32 X + 4.5) W1 + 4.24 E~)
 //   double-float: |E~ - E| <= u^2 ((9.5 n_ch + 3 log2 ts + 43) sb + 4 |dr|_1
-//                                  + (7.32 X + 41.5) W1 + 50 E~)
+//                                  + (14.7 X + 44) W1 + 50 E~)
 // (n_ch = ceil(n_l / 2) + 1 terms per accumulator chain, renormalised every
 // kFFRenorm terms), each times 1 + (2 n_l + 2 log2 ts + nc / 32 + 40) u for
 // the second-order terms, the FP32 sums sb and W1 and the FP32 evaluation of
@@ -769,13 +769,17 @@ __device__ __forceinline__ void put_weight(const GreedyArgs &a, int j, const D4 
     }
 }
 
+// Grid unit of the grid split (split_grid) of this launch's boundary, set by
+// every CTA in the prologue (double-float mode).
+__shared__ double s_gunit;
+
 __device__ __forceinline__ void put_centre(const GreedyArgs &a, int j, const D4 &c)
 {
     if (a.prec == RBF_PREC_F32X2) {
         float h0, l0, h1, l1, h2, l2;
-        split_f64(c.x, h0, l0);
-        split_f64(c.y, h1, l1);
-        split_f64(c.z, h2, l2);
+        split_grid(c.x, s_gunit, h0, l0);
+        split_grid(c.y, s_gunit, h1, l1);
+        split_grid(c.z, s_gunit, h2, l2);
         a.cwff[j] = make_float4(h0, h1, h2, 0.0f);
         a.cwff[(size_t)a.ld + j] = make_float4(l0, l1, l2, 0.0f);
     } else if (a.prec == RBF_PREC_F32) {
@@ -813,7 +817,7 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
         const float4 xh = ldcg(a.xg32 + pn), xl = ldcg(a.xgl + pn);
         for (int j = tid; j < need; j += kGThreads) {
             const float4 ch = ldcg(a.cwff + j), cl = ldcg(a.cwff + (size_t)a.ld + j);
-            const ff ph = phi_ff_s(dist2_ff(xh.x, xl.x, xh.y, xl.y, xh.z, xl.z, ch.x, cl.x,
+            const ff ph = phi_ff_s(dist2_gs(xh.x, xl.x, xh.y, xl.y, xh.z, xl.z, ch.x, cl.x,
                                             ch.y, cl.y, ch.z, cl.z));
             s_b[j] = (double)ph.h + (double)ph.l;
         }
@@ -1437,13 +1441,17 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                      z = a.xb[3 * node + 2] * a.inv_r;
         const double d0 = a.db[3 * node], d1 = a.db[3 * node + 1], d2 = a.db[3 * node + 2];
         a.xg64[pos] = mk4(x, y, z, 0.0);
-        a.xg32[pos] = make_float4((float)x, (float)y, (float)z, 0.0f);
         {
             float h0, l0, h1, l1, h2, l2;
-            split_f64(x, h0, l0);
-            split_f64(y, h1, l1);
-            split_f64(z, h2, l2);
-            a.xgl[pos] = make_float4(l0, l1, l2, 0.0f);
+            if (a.prec != RBF_PREC_F32X2) {
+                // FP32 copy (FP32 mode) and its remainders; double-float mode
+                // writes the grid split once the maximum |x| is known
+                a.xg32[pos] = make_float4((float)x, (float)y, (float)z, 0.0f);
+                split_f64(x, h0, l0);
+                split_f64(y, h1, l1);
+                split_f64(z, h2, l2);
+                a.xgl[pos] = make_float4(l0, l1, l2, 0.0f);
+            }
             split_f64(d0, h0, l0);
             split_f64(d1, h1, l1);
             split_f64(d2, h2, l2);
@@ -1490,6 +1498,23 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
     }
     const double estar = a.tol_mode == 1 ? a.tol * sqrt(g4[0]) : a.tol;
     const float xscale = (float)g4[1];
+    if (a.prec == RBF_PREC_F32X2) {
+        // grid split of the scaled coordinates (exact differences in the
+        // pair distances); visible to every CTA after the seed search's
+        // grid barriers, before the first append reads it
+        if (tid == 0)
+            s_gunit = grid_unit(g4[1]);
+        __syncthreads();
+        for (int p = gtid; p < nb; p += gthreads) {
+            const D4 x = ldcg(a.xg64 + p);
+            float h0, l0, h1, l1, h2, l2;
+            split_grid(x.x, s_gunit, h0, l0);
+            split_grid(x.y, s_gunit, h1, l1);
+            split_grid(x.z, s_gunit, h2, l2);
+            a.xg32[p] = make_float4(h0, h1, h2, 0.0f);
+            a.xgl[p] = make_float4(l0, l1, l2, 0.0f);
+        }
+    }
 
     // ---------------- seed nodes (lowest index on ties) ---------------------
     int seeds[3];
@@ -1763,7 +1788,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 const float b_upw =
                     1.0f + (2.0f * (float)n_lw + 2.0f * lg_w + (float)nc * (1.0f / 32.0f) + 40.0f) * kU32;
                 const float c_sb = 9.5f * (float)((n_lw + 1) / 2 + 1) + 3.0f * lg_w + 43.0f;
-                const float coord_term = (7.32f * xscale + 41.5f) * s_wabs;
+                const float coord_term = (14.7f * xscale + 44.0f) * s_wabs;
                 __shared__ float s_pair[2][kGWarps / 2][8];
                 for (int it = 0; it < roundsw; ++it) {
                     const int q = p0 + teamw + it * nteamsw;
@@ -1800,7 +1825,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         const float4 cl1 = smem ? cw[pst + j2] : ldcg(cw + pst + j2);
                         const float4 wh1 = smem ? cw[2 * pst + j2] : ldcg(cw + 2 * pst + j2);
                         const float4 wl1 = smem ? cw[3 * pst + j2] : ldcg(cw + 3 * pst + j2);
-                        const ff2 s2 = dist2_ff2(bxh, bxl, byh, byl, bzh, bzl,
+                        const ff2 s2 = dist2_gs2(bxh, bxl, byh, byl, bzh, bzl,
                                                  f2_pack(ch0.x, ch1.x), f2_pack(cl0.x, cl1.x),
                                                  f2_pack(ch0.y, ch1.y), f2_pack(cl0.y, cl1.y),
                                                  f2_pack(ch0.z, ch1.z), f2_pack(cl0.z, cl1.z));
@@ -1817,7 +1842,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         const float4 cl = smem ? cw[pst + j] : ldcg(cw + pst + j);
                         const float4 wh = smem ? cw[2 * pst + j] : ldcg(cw + 2 * pst + j);
                         const float4 wl = smem ? cw[3 * pst + j] : ldcg(cw + 3 * pst + j);
-                        const ff s2 = dist2_ff(qxh, qxl, qyh, qyl, qzh, qzl, ch.x, cl.x, ch.y,
+                        const ff s2 = dist2_gs(qxh, qxl, qyh, qyl, qzh, qzl, ch.x, cl.x, ch.y,
                                                cl.y, ch.z, cl.z);
                         const ff ph = phi_ff_s(s2);
                         ff_fma_acc(fx, wh.x, wl.x, ph);

@@ -40,15 +40,46 @@ __global__ void k_pack_points_f32(const double *__restrict__ x, int64_t n, doubl
     }
 }
 
+// Largest |x| / R over the volume points and the selected centres, as the
+// bit pattern of a non-negative double (integer atomicMax keeps the order);
+// it fixes the grid of the grid split (split_grid).
+__global__ void k_grid_max(const double *__restrict__ x, int64_t n, const double *__restrict__ xb,
+                           const int32_t *__restrict__ sel, int64_t nc, double inv_r,
+                           unsigned long long *__restrict__ out)
+{
+    double mx = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        mx = fmax(mx, fabs(x[i] * inv_r));
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = sel[j];
+        mx = fmax(mx, fmax(fabs(xb[3 * q] * inv_r),
+                           fmax(fabs(xb[3 * q + 1] * inv_r), fabs(xb[3 * q + 2] * inv_r))));
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+__device__ __forceinline__ double grid_of(const unsigned long long *gmax)
+{
+    return grid_unit(__longlong_as_double((long long)*gmax));
+}
+
+// grid-split points (x / R) for the double-float kernels
 __global__ void k_pack_points_ff(const double *__restrict__ x, int64_t n, double inv_r,
+                                 const unsigned long long *__restrict__ gmax,
                                  float4 *__restrict__ hi, float4 *__restrict__ lo)
 {
+    const double G = grid_of(gmax);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float h0, l0, h1, l1, h2, l2;
-        split_f64(x[3 * i] * inv_r, h0, l0);
-        split_f64(x[3 * i + 1] * inv_r, h1, l1);
-        split_f64(x[3 * i + 2] * inv_r, h2, l2);
+        split_grid(x[3 * i] * inv_r, G, h0, l0);
+        split_grid(x[3 * i + 1] * inv_r, G, h1, l1);
+        split_grid(x[3 * i + 2] * inv_r, G, h2, l2);
         hi[i] = make_float4(h0, h1, h2, 0.0f);
         lo[i] = make_float4(l0, l1, l2, 0.0f);
     }
@@ -57,15 +88,17 @@ __global__ void k_pack_points_ff(const double *__restrict__ x, int64_t n, double
 // double-float centres and weights: (c_hi, c_lo, w_hi, w_lo) per centre
 __global__ void k_pack_centres_ff(const double *__restrict__ xb, const int32_t *__restrict__ sel,
                                   const double *__restrict__ w, int64_t nc, double inv_r,
+                                  const unsigned long long *__restrict__ gmax,
                                   float4 *__restrict__ cff)
 {
+    const double G = grid_of(gmax);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t n = sel[j];
         float h0, l0, h1, l1, h2, l2;
-        split_f64(xb[3 * n] * inv_r, h0, l0);
-        split_f64(xb[3 * n + 1] * inv_r, h1, l1);
-        split_f64(xb[3 * n + 2] * inv_r, h2, l2);
+        split_grid(xb[3 * n] * inv_r, G, h0, l0);
+        split_grid(xb[3 * n + 1] * inv_r, G, h1, l1);
+        split_grid(xb[3 * n + 2] * inv_r, G, h2, l2);
         cff[4 * j] = make_float4(h0, h1, h2, 0.0f);
         cff[4 * j + 1] = make_float4(l0, l1, l2, 0.0f);
         split_f64(w[3 * j], h0, l0);
@@ -238,7 +271,7 @@ k_volume_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_
                 const float4 wh = s_cwff[4 * j + 2], wl = s_cwff[4 * j + 3];
 #pragma unroll
                 for (int i = 0; i < P; ++i) {
-                    const ff2 s2 = dist2_ff2(qxh[i], qxl[i], qyh[i], qyl[i], qzh[i], qzl[i],
+                    const ff2 s2 = dist2_gs2(qxh[i], qxl[i], qyh[i], qyl[i], qzh[i], qzl[i],
                                              f2_bcast(ch.x), f2_bcast(cl.x), f2_bcast(ch.y),
                                              f2_bcast(cl.y), f2_bcast(ch.z), f2_bcast(cl.z));
                     const ff2 ph = phi_ff2_s(s2);
@@ -317,13 +350,15 @@ k_volume_f64(const double *__restrict__ xv, int64_t nv, double inv_r,
 // Workspace layout.
 // ---------------------------------------------------------------------------
 struct VolumeWs {
-    size_t off_xq32, off_c32, off_c64, off_xh, off_xl, off_cff, total;
+    size_t off_gmax, off_xq32, off_c32, off_c64, off_xh, off_xl, off_cff, total;
 };
 
 static VolumeWs volume_ws_layout(int64_t nv, int64_t nc, int prec)
 {
     VolumeWs L{};
     size_t o = 0;
+    L.off_gmax = o;
+    o = 256;
     L.off_xq32 = o;
     if (prec == RBF_PREC_F32)
         o = align_up(o + sizeof(float4) * (size_t)nv, 256);
@@ -415,10 +450,14 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
     } else if (p->eval_prec == RBF_PREC_F32X2) {
         float4 *xh = (float4 *)(ws + L.off_xh), *xl = (float4 *)(ws + L.off_xl);
         float4 *cff = (float4 *)(ws + L.off_cff);
+        unsigned long long *gmax = (unsigned long long *)(ws + L.off_gmax);
         const int pb = (int)std::min<int64_t>((nv + 255) / 256, (int64_t)dev.sms * 8);
-        k_pack_points_ff<<<pb, 256, 0, st>>>(d_xv, nv, inv_r, xh, xl);
+        if (cudaMemsetAsync(gmax, 0, sizeof(*gmax), st) != cudaSuccess)
+            return RBF_E_CUDA;
+        k_grid_max<<<pb, 256, 0, st>>>(d_xv, nv, d_xb, d_sel_idx, nc, inv_r, gmax);
+        k_pack_points_ff<<<pb, 256, 0, st>>>(d_xv, nv, inv_r, gmax, xh, xl);
         const int cb = (int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4);
-        k_pack_centres_ff<<<cb, 256, 0, st>>>(d_xb, d_sel_idx, d_w, nc, inv_r, cff);
+        k_pack_centres_ff<<<cb, 256, 0, st>>>(d_xb, d_sel_idx, d_w, nc, inv_r, gmax, cff);
         const size_t smem = sizeof(float4) * 4 * (size_t)std::min<int64_t>(nc, kTileFF);
         static bool attr_ff = false;
         if (!attr_ff) {
@@ -508,15 +547,18 @@ __global__ void k_pack_fields_w(const double *__restrict__ w, int nc, int n_out,
 
 // double-float centres: (c_hi, c_lo) per centre
 __global__ void k_pack_centres_hl(const double *__restrict__ xb, const int32_t *__restrict__ sel,
-                                  int64_t nc, double inv_r, float4 *__restrict__ c)
+                                  int64_t nc, double inv_r,
+                                  const unsigned long long *__restrict__ gmax,
+                                  float4 *__restrict__ c)
 {
+    const double G = grid_of(gmax);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t n = sel[j];
         float h0, l0, h1, l1, h2, l2;
-        split_f64(xb[3 * n] * inv_r, h0, l0);
-        split_f64(xb[3 * n + 1] * inv_r, h1, l1);
-        split_f64(xb[3 * n + 2] * inv_r, h2, l2);
+        split_grid(xb[3 * n] * inv_r, G, h0, l0);
+        split_grid(xb[3 * n + 1] * inv_r, G, h1, l1);
+        split_grid(xb[3 * n + 2] * inv_r, G, h2, l2);
         c[2 * j] = make_float4(h0, h1, h2, 0.0f);
         c[2 * j + 1] = make_float4(l0, l1, l2, 0.0f);
     }
@@ -556,7 +598,7 @@ k_fields_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_
                 s_w[i] = wp[(int64_t)t0 * NP + i];
             for (int k = fg; k < nt; k += FG) {
                 const float4 ch = __ldg(c + 2 * (t0 + k)), cl = __ldg(c + 2 * (t0 + k) + 1);
-                const ff2 s2 = dist2_ff2(qxh, qxl, qyh, qyl, qzh, qzl, f2_bcast(ch.x),
+                const ff2 s2 = dist2_gs2(qxh, qxl, qyh, qyl, qzh, qzl, f2_bcast(ch.x),
                                          f2_bcast(cl.x), f2_bcast(ch.y), f2_bcast(cl.y),
                                          f2_bcast(ch.z), f2_bcast(cl.z));
                 const ff2 ph = phi_ff2_s(s2);
@@ -600,7 +642,7 @@ k_fields_ff(const float4 *__restrict__ xh, const float4 *__restrict__ xl, int64_
 }
 
 struct FieldsWs {
-    size_t xh, xl, c, w, total;
+    size_t gmax, xh, xl, c, w, total;
 };
 
 static FieldsWs fields_ws(int64_t nv, int64_t nc, int n_out)
@@ -612,6 +654,7 @@ static FieldsWs fields_ws(int64_t nv, int64_t nc, int n_out)
         o = align_up(o + bytes, 256);
         return at;
     };
+    L.gmax = take(sizeof(unsigned long long));
     L.xh = take(sizeof(float4) * (size_t)nv);
     L.xl = take(sizeof(float4) * (size_t)nv);
     L.c = take(sizeof(float4) * 2 * (size_t)std::max<int64_t>(nc, 1));
@@ -663,10 +706,14 @@ extern "C" rbf_status rbf_deform_volume_fields(const double *d_xv, int64_t nv, c
     const int n_pad = fields_pad(n_out);
     const int fcols = fields_cols(n_out);
     const int fg = n_pad / fcols;
-    k_pack_points_ff<<<(int)std::min<int64_t>((nv + 255) / 256, (int64_t)dev.sms * 8), 256, 0, st>>>(
-        d_xv, nv, inv_r, xh, xl);
+    unsigned long long *gmax = (unsigned long long *)(ws + L.gmax);
+    const int pb = (int)std::min<int64_t>((nv + 255) / 256, (int64_t)dev.sms * 8);
+    if (cudaMemsetAsync(gmax, 0, sizeof(*gmax), st) != cudaSuccess)
+        return RBF_E_CUDA;
+    k_grid_max<<<pb, 256, 0, st>>>(d_xv, nv, d_xb, d_sel_idx, nc, inv_r, gmax);
+    k_pack_points_ff<<<pb, 256, 0, st>>>(d_xv, nv, inv_r, gmax, xh, xl);
     k_pack_centres_hl<<<(int)std::min<int64_t>((nc + 255) / 256, (int64_t)dev.sms * 4), 256, 0,
-                        st>>>(d_xb, d_sel_idx, nc, inv_r, c);
+                        st>>>(d_xb, d_sel_idx, nc, inv_r, gmax, c);
     const int64_t wtot = nc * n_pad;
     k_pack_fields_w<<<(int)std::min<int64_t>((wtot + 255) / 256, (int64_t)dev.sms * 8), 256, 0,
                       st>>>(d_w, (int)nc, n_out, n_pad, wp);

@@ -27,17 +27,29 @@ constexpr int kAdjChunk = 1024;      // volume points per shared-memory chunk
 
 // Packing: scaled volume points and their gradients (hi/lo splits for the
 // double-float path).
-__global__ void k_adjoint_pack(const double *__restrict__ xv, const double *__restrict__ gv,
-                               int64_t nv, double inv_r, float4 *__restrict__ xh,
-                               float4 *__restrict__ xl, float4 *__restrict__ gh,
-                               float4 *__restrict__ gl)
+// Double-float path (gmax given): coordinates grid-split (split_grid) for
+// exact pair differences; FP32 path: the FP32 rounding in the high part.
+__device__ __forceinline__ void adj_split(double x, const unsigned long long *gmax, double G,
+                                          float &h, float &l)
 {
+    if (gmax)
+        split_grid(x, G, h, l);
+    else
+        split_f64(x, h, l);
+}
+
+__global__ void k_adjoint_pack(const double *__restrict__ xv, const double *__restrict__ gv,
+                               int64_t nv, double inv_r, const unsigned long long *gmax,
+                               float4 *__restrict__ xh, float4 *__restrict__ xl,
+                               float4 *__restrict__ gh, float4 *__restrict__ gl)
+{
+    const double G = gmax ? grid_of(gmax) : 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv;
          i += (int64_t)gridDim.x * blockDim.x) {
         float h0, l0, h1, l1, h2, l2;
-        split_f64(xv[3 * i] * inv_r, h0, l0);
-        split_f64(xv[3 * i + 1] * inv_r, h1, l1);
-        split_f64(xv[3 * i + 2] * inv_r, h2, l2);
+        adj_split(xv[3 * i] * inv_r, gmax, G, h0, l0);
+        adj_split(xv[3 * i + 1] * inv_r, gmax, G, h1, l1);
+        adj_split(xv[3 * i + 2] * inv_r, gmax, G, h2, l2);
         xh[i] = make_float4(h0, h1, h2, 0.0f);
         xl[i] = make_float4(l0, l1, l2, 0.0f);
         split_f64(gv[3 * i], h0, l0);
@@ -49,15 +61,16 @@ __global__ void k_adjoint_pack(const double *__restrict__ xv, const double *__re
 }
 
 __global__ void k_adjoint_centres(const double *__restrict__ xb, const int32_t *__restrict__ sel,
-                                  int nc, double inv_r, float4 *__restrict__ ch,
-                                  float4 *__restrict__ cl)
+                                  int nc, double inv_r, const unsigned long long *gmax,
+                                  float4 *__restrict__ ch, float4 *__restrict__ cl)
 {
+    const double G = gmax ? grid_of(gmax) : 0.0;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nc; j += gridDim.x * blockDim.x) {
         const int64_t n = sel[j];
         float h0, l0, h1, l1, h2, l2;
-        split_f64(xb[3 * n] * inv_r, h0, l0);
-        split_f64(xb[3 * n + 1] * inv_r, h1, l1);
-        split_f64(xb[3 * n + 2] * inv_r, h2, l2);
+        adj_split(xb[3 * n] * inv_r, gmax, G, h0, l0);
+        adj_split(xb[3 * n + 1] * inv_r, gmax, G, h1, l1);
+        adj_split(xb[3 * n + 2] * inv_r, gmax, G, h2, l2);
         ch[j] = make_float4(h0, h1, h2, 0.0f);
         cl[j] = make_float4(l0, l1, l2, 0.0f);
     }
@@ -117,7 +130,7 @@ k_adjoint_partial(const float4 *__restrict__ xh, const float4 *__restrict__ xl,
             for (int i = 0; i < nvc; ++i) {
                 const float4 x0 = s_xh[i], x1 = s_xl[i];
                 const float4 g0 = s_gh[i], g1 = s_gl[i];
-                const ff s2 = dist2_ff(x0.x, x1.x, x0.y, x1.y, x0.z, x1.z, qh.x, ql.x, qh.y,
+                const ff s2 = dist2_gs(x0.x, x1.x, x0.y, x1.y, x0.z, x1.z, qh.x, ql.x, qh.y,
                                        ql.y, qh.z, ql.z);
                 const ff ph = phi_ff_s(s2);
                 ff_fma_acc(ax, g0.x, g1.x, ph);
@@ -151,7 +164,7 @@ __global__ void k_adjoint_reduce(const double *__restrict__ partial, int nblocks
 }
 
 struct AdjWs {
-    size_t xh, xl, gh, gl, ch, cl, partial, gc, solve, total;
+    size_t gmax, xh, xl, gh, gl, ch, cl, partial, gc, solve, total;
     int blocks;
 };
 
@@ -164,6 +177,7 @@ static AdjWs adjoint_ws_layout(int64_t nv, int64_t nc, int blocks)
         o = align_up(o + bytes, 256);
         return at;
     };
+    L.gmax = take(sizeof(unsigned long long));
     L.xh = take(sizeof(float4) * nv);
     L.xl = take(sizeof(float4) * nv);
     L.gh = take(sizeof(float4) * nv);
@@ -213,13 +227,19 @@ static rbf_status adjoint_rhs(const double *d_xv, int64_t nv, const double *d_xb
     double *partial = (double *)(ws + L.partial), *gc = (double *)(ws + L.gc);
     const int blocks = (int)std::min<int64_t>(L.blocks, std::max<int64_t>(
                                                             (nv + kAdjChunk - 1) / kAdjChunk, 1));
-    if (nv > 0) {
-        const int pb = (int)std::min<int64_t>((nv + 255) / 256, (int64_t)dev.sms * 8);
-        k_adjoint_pack<<<pb, 256, 0, st>>>(d_xv, d_gv, nv, inv_r, xh, xl, gh, gl);
-    }
-    k_adjoint_centres<<<(int)((nc + 127) / 128), 128, 0, st>>>(d_xb, d_sel_idx, (int)nc, inv_r,
-                                                                ch, cl);
     const bool ffm = eval_prec == RBF_PREC_F32X2;
+    unsigned long long *gmax = ffm ? (unsigned long long *)(ws + L.gmax) : nullptr;
+    const int pb = (int)std::min<int64_t>((std::max<int64_t>(nv, nc) + 255) / 256,
+                                          (int64_t)dev.sms * 8);
+    if (ffm) {
+        if (cudaMemsetAsync(gmax, 0, sizeof(*gmax), st) != cudaSuccess)
+            return RBF_E_CUDA;
+        k_grid_max<<<pb, 256, 0, st>>>(d_xv, nv, d_xb, d_sel_idx, nc, inv_r, gmax);
+    }
+    if (nv > 0)
+        k_adjoint_pack<<<pb, 256, 0, st>>>(d_xv, d_gv, nv, inv_r, gmax, xh, xl, gh, gl);
+    k_adjoint_centres<<<(int)((nc + 127) / 128), 128, 0, st>>>(d_xb, d_sel_idx, (int)nc, inv_r,
+                                                                gmax, ch, cl);
     const size_t smem = sizeof(float4) * 4 * kAdjChunk;
     static bool attr = false;
     if (!attr) {

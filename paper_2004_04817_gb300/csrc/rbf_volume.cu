@@ -40,34 +40,6 @@ __global__ void k_pack_points_f32(const double *__restrict__ x, int64_t n, doubl
     }
 }
 
-// Largest |x| / R over the volume points and the selected centres, as the
-// bit pattern of a non-negative double (integer atomicMax keeps the order);
-// it fixes the grid of the grid split (split_grid).
-__global__ void k_grid_max(const double *__restrict__ x, int64_t n, const double *__restrict__ xb,
-                           const int32_t *__restrict__ sel, int64_t nc, double inv_r,
-                           unsigned long long *__restrict__ out)
-{
-    double mx = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        mx = fmax(mx, fabs(x[i] * inv_r));
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = sel[j];
-        mx = fmax(mx, fmax(fabs(xb[3 * q] * inv_r),
-                           fmax(fabs(xb[3 * q + 1] * inv_r), fabs(xb[3 * q + 2] * inv_r))));
-    }
-    for (int o = 16; o > 0; o >>= 1)
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0)
-        atomicMax(out, (unsigned long long)__double_as_longlong(mx));
-}
-
-__device__ __forceinline__ double grid_of(const unsigned long long *gmax)
-{
-    return grid_unit(__longlong_as_double((long long)*gmax));
-}
-
 // grid-split points (x / R) for the double-float kernels
 __global__ void k_pack_points_ff(const double *__restrict__ x, int64_t n, double inv_r,
                                  const unsigned long long *__restrict__ gmax,

@@ -2,10 +2,12 @@
 pairs farther apart than R skipped (the Wendland C2 basis is zero there,
 Sec. 2).
 
-The culled double-float sum must equal the unculled double-float kernel
-bit for bit (same terms in the same order, zero terms left out); the culled
-FP32 sum may differ from the unculled FP32 kernel only by the phi values the
-latter gives at d >= R (below 1e-28).  Both are compared with the FP64
+The culled double-float sum keeps the standard double-float split of the
+coordinates, the unculled kernel the grid split of its exact-difference
+distances, so the two agree to the double-float rounding (2^-38 sum |w|,
+far inside the FP64 oracle check below); the culled FP32 sum may differ
+from the unculled FP32 kernel only by the phi values the latter gives at
+d >= R (below 1e-28).  Both are compared with the FP64
 oracle on seeded samples, at a radius where culling removes most pairs and
 at one where it removes none.
 """
@@ -46,7 +48,8 @@ def _check(c, plan, S, W, R, prec, sample=3000):
     ref_gpu = P.deform_volume(c["d_xv"], c["d_xb"], d_S, d_W, radius=R, eval_prec=prec)
     dv_h, ref_h = dv.cpu().numpy(), ref_gpu.cpu().numpy()
     if prec == P.PREC_F32X2:
-        assert np.array_equal(dv_h, ref_h), np.abs(dv_h - ref_h).max()
+        assert np.abs(dv_h - ref_h).max() <= 2.0 ** -38 * np.abs(W).sum(), \
+            np.abs(dv_h - ref_h).max()
     else:
         assert np.abs(dv_h - ref_h).max() <= 1e-24 * np.abs(W).sum()
     rng = np.random.default_rng(len(S))

@@ -408,6 +408,11 @@ def run_ours(args, rank, world):
         adj[PREC_NAME[vp]] = {"ms": t_, "pairs_per_s": nv * nc / (t_ * 1e-3)}
     del fac, gv
 
+    # configuration 4b (32 modes on the selected set, double-float fields)
+    # and configuration 4a (the 64-wing batch in one graph replay)
+    fields = fields_summary(P, torch, dev, c, xb, xv, g_last["idx"], R, flush)
+    batched = batched_summary(P, torch, dev, flush)
+
     # e2e through the public API with host buffers (pinned), copies timed
     hx = torch.from_numpy(np.ascontiguousarray(c["xb"])).pin_memory()
     hd = torch.from_numpy(np.ascontiguousarray(c["db"])).pin_memory()
@@ -535,6 +540,8 @@ def run_ours(args, rank, world):
                    "cull_sensitivity": cull},
         "m_sweep": sweep,
         "adjoint": adj,
+        "modal_fields_4b": fields,
+        "batched_4a": batched,
         "appends": appends,
         "weights_max_resid": res_last,
         "kernels": kernels,
@@ -793,27 +800,24 @@ def batched_problems(n_inst=64, nv=200_000):
     return cases
 
 
-def run_batched(args, rank, world):
-    import torch
-    import paper_2004_04817_gb300 as P
-
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    P.lib()
+def batched_setup(P, torch, dev):
+    """Configuration 4a: the 64 wings on the device, m = round(1.5 N_b / N_c)
+    from an untimed plain-greedy batch, the GCB greedy batch and the volume
+    batch (tile autotuned at creation), and CUDA graphs of (greedy + volume)
+    and of the volume batch alone."""
     cases = batched_problems()
     tod = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     for c in cases:
         c["d_xb"], c["d_db"], c["d_xv"] = tod(c["xb"]), tod(c["db"]), tod(c["xv"])
     base = [dict(xb=c["d_xb"], db=c["d_db"], radius=2.0, tol=c["tol_rel"], tol_mode=1,
                  seed=c["seed"], nc_max=1024) for c in cases]
-    # calibration (untimed): N_c of each problem's plain greedy fixes its m
     cal = P.GreedyBatch([dict(q, m=1) for q in base])
     cal.run()
     rc = cal.results()
     ms_ = [max(1, int(round(1.5 * len(c["xb"]) / r["nc"]))) for c, r in zip(cases, rc)]
     gb = P.GreedyBatch([dict(q, m=m) for q, m in zip(base, ms_)])
     gb.run()
-    res = gb.results()
+    gb.results()
     vb = P.VolumeBatch([dict(xv=c["d_xv"], xb=c["d_xb"], idx=gb.idx[i], w=gb.w[i],
                              nc_ptr=gb.nc_ptr + 8 * i, radius=2.0)
                         for i, c in enumerate(cases)])
@@ -823,6 +827,98 @@ def run_batched(args, rank, world):
     with torch.cuda.graph(g, stream=stream):
         gb.run()
         vb.run()
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=stream):
+        vb.run()
+    return cases, gb, vb, g, g2, ms_
+
+
+def fields_summary(P, torch, dev, c, xb, xv, idx, R, flush, reps=3):
+    """Configuration 4b on a selected set: 32 sinusoidal bending modes
+    dz_q = 0.05 sin((2q - 1) pi y / (2b)) (W: N_c x 96 from FP64 solves), all
+    columns in one double-float pass; error against FP64 on 500 points."""
+    import oracle
+    S = idx.cpu().numpy()
+    y = c["xb"][S, 1]
+    modes = np.zeros((len(S), 96))
+    for q in range(1, 33):
+        modes[:, 3 * (q - 1) + 2] = 0.05 * np.sin((2 * q - 1) * np.pi * y / 2.0)
+    tod = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    W = torch.empty((len(S), 96), dtype=torch.float64, device=dev)
+    for q in range(32):
+        x, _ = P.solve_system(xb, idx, tod(modes[:, 3 * q:3 * q + 3]), radius=R)
+        W[:, 3 * q:3 * q + 3] = x
+    out = torch.empty((xv.shape[0], 96), dtype=torch.float64, device=dev)
+    ws = torch.empty(P.lib().rbf_volume_fields_workspace_bytes(xv.shape[0], len(S), 96),
+                     dtype=torch.uint8, device=dev)
+    fn = lambda: P.deform_volume_fields(xv, xb, idx, W, radius=R, out=out, workspace=ws)
+    fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    smp = np.random.default_rng(8).choice(xv.shape[0], 500, replace=False)
+    Phi = oracle.phi(np.linalg.norm(c["xv"][smp][:, None] - c["xb"][S][None], axis=-1) / R)
+    ref = Phi @ W.cpu().numpy()
+    err = float(np.abs(out.cpu().numpy()[smp] - ref).max())
+    t = statistics.median(ts)
+    del out, ws, W
+    torch.cuda.empty_cache()
+    return {"ms": t, "columns": 96, "pairs_per_s": xv.shape[0] * len(S) / (t * 1e-3),
+            "max_abs_err_vs_fp64": err, "err_rel_max_disp": err / 0.05,
+            "sample_points": 500}
+
+
+def batched_summary(P, torch, dev, flush, reps=3, warmup=1):
+    """The 64-wing batch timed as one graph replay (greedy + volume) and the
+    volume batch alone, L2 flushed before each replay."""
+    t0 = time.perf_counter()
+    cases, gb, vb, g, g2, ms_ = batched_setup(P, torch, dev)
+    setup_s = time.perf_counter() - t0
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(graph):
+        for _ in range(warmup):
+            graph.replay()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record()
+            graph.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+    t_all, t_vol = timed(g), timed(g2)
+    res = gb.results()
+    ncs = [r["nc"] for r in res]
+    pairs = sum(len(c["xv"]) * n for c, n in zip(cases, ncs))
+    out = {"instances": len(cases), "ms": t_all, "instances_per_s": len(cases) / (t_all * 1e-3),
+           "greedy_ms": t_all - t_vol, "volume_ms": t_vol,
+           "volume_pairs_per_s": pairs / (t_vol * 1e-3),
+           "n_b_range": [min(len(c["xb"]) for c in cases), max(len(c["xb"]) for c in cases)],
+           "nc_range": [min(ncs), max(ncs)],
+           "statuses": sorted(set(int(r["status"]) for r in res)), "setup_s": setup_s,
+           "volume_tile": vb.info()}
+    del g, g2, gb, vb, cases
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args, rank, world):
+    import torch
+    import paper_2004_04817_gb300 as P
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    P.lib()
+    cases, gb, vb, g, g2, ms_ = batched_setup(P, torch, dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     for _ in range(args.warmup):
@@ -844,9 +940,6 @@ def run_batched(args, rank, world):
     ncs = [r["nc"] for r in res]
     pairs_vol = sum(len(c["xv"]) * n for c, n in zip(cases, ncs))
     # volume alone (graph of the volume batch)
-    g2 = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g2, stream=stream):
-        vb.run()
     tv = []
     for _ in range(3):
         flush.zero_()

@@ -513,6 +513,10 @@ def run_ours(args, rank, world):
         "dtype": {32: "f32", 48: "f32x2", 64: "f64"}[args.prec],
         "data": "synthetic (seeded wing generator, paper_2004_04817_gb300/synth.py)",
         "config": workload_desc(c, m, nc_plain, args.prec, args.vol_prec),
+        "gcb_vs_plain": {"gcb_time_to_tol_s": g_ms / 1e3, "plain_time_to_tol_s": plain_ms / 1e3,
+                         "speedup": plain_ms / g_ms, "m": m, "nc_gcb": nc, "nc_plain": nc_plain,
+                         "volume_pairs_per_s": vol_pairs / (v_ms * 1e-3),
+                         "volume_fp32_peak_frac": vol_achieved / fp32_peak},
         "greedy": {
             "gcb_s": g_ms / 1e3, "plain_s": plain_ms / 1e3,
             "speedup_gcb_vs_plain": plain_ms / g_ms, "m": m,

@@ -300,7 +300,11 @@ rbf_status rbf_solve_system(const double *d_xb, int64_t nb, const int32_t *d_sel
  * Volume displacements, Eq. 6: dv_v = sum_{j in S} w_j phi(|x_v - r_j| / R)
  * for the nv volume points.
  *
- * d_xv : device FP64 nv x 3.   d_dv : device FP64 nv x 3 (output).
+ * d_xv : FP64 nv x 3.   d_dv : FP64 nv x 3 (output).  Both may be device
+ *        memory or pinned host memory that the device reaches at the same
+ *        address (on a GB300 the kernels then read the points and write the
+ *        displacements over NVLink-C2C, each once, with no separate copy);
+ *        any other pointer gives RBF_E_ARG before device work.
  * d_xb, d_sel_idx, nc, d_w : centres r_j = xb[sel_idx[j]] and weights w_j
  *                            (device FP64 nc x 3), as from rbf_solve_weights.
  * p->eval_prec selects the pair arithmetic (FP32, double-float or FP64); only

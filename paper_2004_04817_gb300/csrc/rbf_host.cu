@@ -36,6 +36,18 @@ bool device_info(DeviceInfo *out)
     return true;
 }
 
+bool device_accessible(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return true;
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 void fisher_yates(int64_t n, uint64_t seed, int32_t *perm)
 {
     uint64_t st = seed;

@@ -22,6 +22,10 @@ struct DeviceInfo {
 // Queries (and caches per device) the current device's properties.
 bool device_info(DeviceInfo *out);
 
+// True when the device can read and write p at that address: device or
+// managed memory, or pinned host memory mapped at the same address.
+bool device_accessible(const void *p);
+
 // Grid barrier wait limit for the persistent kernels.
 constexpr uint64_t kBarrierLimitNs = 4000000000ull;   // 4 s
 

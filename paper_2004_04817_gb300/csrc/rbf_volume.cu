@@ -81,6 +81,13 @@ __global__ void k_pack_centres_ff(const double *__restrict__ xb, const int32_t *
     }
 }
 
+__global__ void k_fill_zero(double *__restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = 0.0;
+}
+
 // centres c_j = xb[sel[j]] / R and weights w_j, interleaved (c_j, w_j).
 __global__ void k_pack_centres(const double *__restrict__ xb, const int32_t *__restrict__ sel,
                                const double *__restrict__ w, int64_t nc, double inv_r,
@@ -377,6 +384,10 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
         return RBF_OK;
     if (!d_xv || !d_dv)
         return RBF_E_ARG;
+    // the points and displacements may be pinned host memory the device can
+    // reach (read and written once per point by the kernels)
+    if (!device_accessible(d_xv) || !device_accessible(d_dv))
+        return RBF_E_ARG;
     if (nc > 0 && (!d_xb || !d_sel_idx || !d_w))
         return RBF_E_ARG;
     if (nc > (int64_t)1 << 30 || nv > (int64_t)1 << 40)
@@ -391,9 +402,9 @@ extern "C" rbf_status rbf_deform_volume(const double *d_xv, int64_t nv, const do
     char *ws = (char *)d_ws;
     const double inv_r = 1.0 / p->radius;
     if (nc == 0) {
-        if (cudaMemsetAsync(d_dv, 0, sizeof(double) * 3 * (size_t)nv, st) != cudaSuccess)
-            return RBF_E_CUDA;
-        return RBF_OK;
+        k_fill_zero<<<(int)std::min<int64_t>((3 * nv + 255) / 256, (int64_t)dev.sms * 8), 256, 0,
+                      st>>>(d_dv, 3 * nv);
+        return cudaGetLastError() == cudaSuccess ? RBF_OK : RBF_E_CUDA;
     }
     if (p->eval_prec == RBF_PREC_F32) {
         float4 *xq = (float4 *)(ws + L.off_xq32);

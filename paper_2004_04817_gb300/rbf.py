@@ -234,9 +234,10 @@ def _check(st, where, allow=()):
     return st
 
 
-def _dev(t, dtype, name, shape2=None):
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError(f"{name} must be a CUDA tensor")
+def _dev(t, dtype, name, shape2=None, host_ok=False):
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or (host_ok and t.is_pinned())):
+        raise TypeError(f"{name} must be a CUDA tensor" +
+                        (" or a pinned host tensor" if host_ok else ""))
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -524,9 +525,12 @@ def deform(dc, xv, xb, sel_idx, *, radius, eval_prec=PREC_F32X2, factor=None):
 
 def deform_volume(xv, xb, sel_idx, w, *, radius, eval_prec=PREC_F32, stream=None,
                   workspace=None, out=None):
-    """Volume displacements (nv, 3) FP64 by Eq. 6 in FP32 or FP64 pairs."""
+    """Volume displacements (nv, 3) FP64 by Eq. 6 in FP32, double-float or
+    FP64 pairs.  ``xv`` and ``out`` may be pinned host tensors: the kernels
+    then read the points from, and write the displacements to, host memory
+    directly (each once), with no copy through the copy engines."""
     L = lib()
-    _dev(xv, torch.float64, "xv", 3)
+    _dev(xv, torch.float64, "xv", 3, host_ok=True)
     _dev(xb, torch.float64, "xb", 3)
     _dev(sel_idx, torch.int32, "sel_idx")
     _dev(w, torch.float64, "w", 3)
@@ -534,9 +538,9 @@ def deform_volume(xv, xb, sel_idx, w, *, radius, eval_prec=PREC_F32, stream=None
     p = make_params(radius, eval_prec=eval_prec)
     need = L.rbf_volume_workspace_bytes(nv, nc, C.byref(p))
     ws = workspace if workspace is not None and workspace.numel() >= need else \
-        _workspace(need, xv.device)
-    dv = out if out is not None else torch.empty((nv, 3), dtype=torch.float64, device=xv.device)
-    _dev(dv, torch.float64, "out", 3)
+        _workspace(need, xb.device)
+    dv = out if out is not None else torch.empty((nv, 3), dtype=torch.float64, device=xb.device)
+    _dev(dv, torch.float64, "out", 3, host_ok=True)
     st = L.rbf_deform_volume(_ptr(xv), nv, _ptr(xb), _ptr(sel_idx), nc, _ptr(w), C.byref(p),
                              _ptr(dv), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "rbf_deform_volume")

@@ -773,6 +773,28 @@ __device__ __forceinline__ void put_weight(const GreedyArgs &a, int j, const D4 
 // every CTA in the prologue (double-float mode).
 __shared__ double s_gunit;
 
+// put_weight with the three components held by lanes 0-2 of the warp (all
+// lanes call it): each lane splits its own component, lane 0 writes.
+__device__ __forceinline__ void put_weight_lanes(const GreedyArgs &a, int j, double wc, int lane)
+{
+    if (a.prec == RBF_PREC_F32X2) {
+        float h = 0.0f, l = 0.0f;
+        if (lane < 3)
+            split_f64(wc, h, l);
+        const float h1 = __shfl_sync(0xffffffffu, h, 1), h2 = __shfl_sync(0xffffffffu, h, 2);
+        const float l1 = __shfl_sync(0xffffffffu, l, 1), l2 = __shfl_sync(0xffffffffu, l, 2);
+        if (lane == 0) {
+            a.cwff[2 * (size_t)a.ld + j] = make_float4(h, h1, h2, fabsf(h) + fabsf(h1) + fabsf(h2));
+            a.cwff[3 * (size_t)a.ld + j] = make_float4(l, l1, l2, 0.0f);
+        }
+    } else if (a.prec == RBF_PREC_F32) {
+        const float f = lane < 3 ? (float)wc : 0.0f;
+        const float f1 = __shfl_sync(0xffffffffu, f, 1), f2 = __shfl_sync(0xffffffffu, f, 2);
+        if (lane == 0)
+            a.cw32[(size_t)a.ld + j] = make_float4(f, f1, f2, fabsf(f) + fabsf(f1) + fabsf(f2));
+    }
+}
+
 __device__ __forceinline__ void put_centre(const GreedyArgs &a, int j, const D4 &c)
 {
     if (a.prec == RBF_PREC_F32X2) {
@@ -836,29 +858,31 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
     }
     // A2: l = Z b (warp per row) and the partial sums of l.l and l.y (lane 0
     // of each warp accumulates its rows)
-    double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+    // lane c < 4 of a warp accumulates component c of (l.l, l.y): one FP64
+    // instruction per row instead of four in series
+    double acc = 0.0;
     for (int i = gwarp; i < nc; i += gwarps) {
+        double yc = 0.0;
+        if (lane >= 1 && lane < 4)
+            yc = ldcg(&a.y64[i].x + (lane - 1));
         const double s = s_b ? warp_dot<true>(a.z + (size_t)i * a.ld, s_b, 0, i + 1)
                              : warp_dot(a.z + (size_t)i * a.ld, a.bvec, 0, i + 1);
-        if (lane == 0) {
+        if (lane == 0)
             a.lvec[i] = s;
-            const D4 y = ldcg(a.y64 + i);
-            acc4[0] = fma(s, s, acc4[0]);
-            acc4[1] = fma(s, y.x, acc4[1]);
-            acc4[2] = fma(s, y.y, acc4[2]);
-            acc4[3] = fma(s, y.z, acc4[3]);
-        }
+        if (lane < 4)
+            acc = fma(s, lane == 0 ? s : yc, acc);
     }
-    if (lane == 0)
-        for (int c = 0; c < 4; ++c)
-            red.s[warp][c] = acc4[c];
+    if (lane < 4)
+        red.s[warp][lane] = acc;
     __syncthreads();
-    // component c summed by lane 0 of warp c (four SM sub-partitions)
-    if (lane == 0 && warp < 4) {
-        double t = 0.0;
-        for (int k = 0; k < kGWarps; ++k)
-            t += red.s[k][warp];
-        (a.part + (size_t)(use & 1) * kMaxGrid * 4)[4 * g_vb + warp] = t;
+    // the 8 warps x 4 components summed by warp 0 in a three-level tree
+    if (warp == 0) {
+        double t = red.s[lane >> 2][lane & 3];
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        t += __shfl_xor_sync(0xffffffffu, t, 8);
+        t += __shfl_xor_sync(0xffffffffu, t, 16);
+        if (lane < 4)
+            (a.part + (size_t)(use & 1) * kMaxGrid * 4)[4 * g_vb + lane] = t;
     }
     if (!grid_barrier(g_bar, &ctl->status, (unsigned)G, a.barrier_ns, epoch, (unsigned)g_vb)) return kAppendTimeout;
     {
@@ -901,19 +925,23 @@ __device__ int chol_append(const GreedyArgs &a, Red &red, int &nc, int &use, dou
     // A3: u = Z^T l (warp per row of Z^T); new row of Z; weight update.  The
     // new node's own entries are written by the last warp of the grid, which
     // has the fewest rows.
+    // lanes 0-2 update one component of W_j each (its load issued before
+    // the row product) and lane 0 assembles the table entry
     for (int j = gwarp; j < nc; j += gwarps) {
+        double wc = 0.0;
+        if (lane < 3)
+            wc = ldcg(&a.w64[j].x + lane);
         const double s = warp_dot(a.zt + (size_t)j * a.ld, a.lvec, j, nc);
+        const double zz = -s * inv_d;
         if (lane == 0) {
-            const double zz = -s * inv_d;
             a.z[(size_t)nc * a.ld + j] = zz;
             a.zt[(size_t)j * a.ld + nc] = zz;
-            D4 w = ldcg(a.w64 + j);
-            w.x = fma(zz, yx, w.x);
-            w.y = fma(zz, yy, w.y);
-            w.z = fma(zz, yz, w.z);
-            a.w64[j] = w;
-            put_weight(a, j, w);
         }
+        if (lane < 3) {
+            wc = fma(zz, lane == 0 ? yx : (lane == 1 ? yy : yz), wc);
+            (&a.w64[j].x)[lane] = wc;
+        }
+        put_weight_lanes(a, j, wc, lane);
     }
     if (gwarp == gwarps - 1 && lane == 0) {
         a.z[(size_t)nc * a.ld + nc] = inv_d;

@@ -294,3 +294,31 @@ def test_barrier_timeout_returns_status_and_context_survives():
     r, estar = run_greedy(c, 1, P.PREC_F64, 2e-3)
     o = oracle.greedy(c["xb"], c["db"], c["radius"], estar, m=1, seed=1, history=False)
     assert host(r["idx"]).tolist() == o["idx"].tolist()
+
+
+def test_double_float_far_from_the_origin():
+    """The double-float pair kernels hold coordinates on a grid set by the
+    largest |x| / R (exact differences): a wing translated 1,000 spans away
+    (|x| / R = 500) must give the oracle's selection and volume
+    displacements within the same bars as at the origin."""
+    c = synth.wing_small(n_vol=5_000)
+    off = np.array([1000.0, -700.0, 300.0])
+    xb, xv = c["xb"] + off, c["xv"] + off
+    R = c["radius"]
+    estar = oracle.tolerance(c["db"], c["tol_rel"])
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    r = P.greedy_select(d(xb), d(c["db"]), radius=R, tol=estar, tol_mode=0, m=5, seed=1,
+                        eval_prec=P.PREC_F32X2, weights=True)
+    f = oracle.greedy(xb, c["db"], R, estar, m=5, seed=1,
+                      follow=(host(r["idx"]), host(r["iter"])), tie_rel=TIE, history=False)
+    check_follow(f, "double-float, wing 1,000 spans from the origin")
+    assert r["stats"]["final_max"] <= estar
+    S = host(r["idx"])
+    Wo, st, _ = oracle.solve_weights(xb, c["db"], S, R)
+    assert st == 0
+    dmax = np.abs(c["db"]).max()
+    ref = oracle.rbf_sum(xv, xb, S, Wo, R)
+    dv = P.deform_volume(d(xv), d(xb), r["idx"], d(Wo), radius=R, eval_prec=P.PREC_F32X2)
+    err = np.abs(dv.cpu().numpy() - ref).max()
+    print(f"\nfar from the origin: volume error {err:.2e} ({err / dmax:.1e} of max|dr|)")
+    assert err <= 1e-5 * dmax

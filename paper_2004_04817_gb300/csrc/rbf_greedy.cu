@@ -78,7 +78,9 @@ constexpr int kFFRenorm = 8;               // double-float accumulators renormal
 //   double-float: |E~ - E| <= u^2 ((9.5 n_ch + 3 log2 ts + 43) sb + 4 |dr|_1
 //                                  + (14.7 X + 44) W1 + 50 E~)
 // (n_ch = ceil(n_l / 2) + 1 terms per accumulator chain, renormalised every
-// kFFRenorm terms), each times 1 + (2 n_l + 2 log2 ts + nc / 32 + 40) u for
+// kFFRenorm terms; chains of more than 16 terms are summed in blocks of
+// kFFRenorm, with 3 ceil(n_ch / 8) + 114 in place of 9.5 n_ch + 43), each
+// times 1 + (2 n_l + 2 log2 ts + nc / 32 + 40) u for
 // the second-order terms, the FP32 sums sb and W1 and the FP32 evaluation of
 // the bound itself.  E is the exact error of q with the weights as held in
 // the evaluation table.
@@ -1815,7 +1817,15 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                 const float lg_w = (float)(31 - __clz(tsw));
                 const float b_upw =
                     1.0f + (2.0f * (float)n_lw + 2.0f * lg_w + (float)nc * (1.0f / 32.0f) + 40.0f) * kU32;
-                const float c_sb = 9.5f * (float)((n_lw + 1) / 2 + 1) + 3.0f * lg_w + 43.0f;
+                // long chains (few lanes per node) are summed in blocks: every
+                // kFFRenorm terms the normalised block joins a running total
+                // by an accurate double-float add, so the rounding of the low
+                // parts no longer accumulates along the whole chain
+                const int n_ch = (n_lw + 1) / 2 + 1;
+                const bool blocked = n_ch > 16;
+                const float c_sb = blocked ? 3.0f * (float)((n_ch + kFFRenorm - 1) / kFFRenorm) +
+                                                 3.0f * lg_w + 114.0f
+                                           : 9.5f * (float)n_ch + 3.0f * lg_w + 43.0f;
                 const float coord_term = (14.7f * xscale + 44.0f) * s_wabs;
                 __shared__ float s_pair[2][kGWarps / 2][8];
                 for (int it = 0; it < roundsw; ++it) {
@@ -1831,6 +1841,7 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                     // two centres (j, j + ts) per step in paired registers
                     const f2 z2 = f2_pack(0.0f, 0.0f);
                     ff2 gx{z2, z2}, gy{z2, z2}, gz{z2, z2};
+                    ff2 tx{z2, z2}, ty{z2, z2}, tz{z2, z2};   // block totals (long chains)
                     const f2 bxh = f2_bcast(qxh), bxl = f2_bcast(qxl), byh = f2_bcast(qyh),
                              byl = f2_bcast(qyl), bzh = f2_bcast(qzh), bzl = f2_bcast(qzl);
                     int j = subw;
@@ -1843,6 +1854,14 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                             gx = two_sum2(gx.h, gx.l);
                             gy = two_sum2(gy.h, gy.l);
                             gz = two_sum2(gz.h, gz.l);
+                            if (blocked) {
+                                tx = ff_add2(tx, gx);
+                                ty = ff_add2(ty, gy);
+                                tz = ff_add2(tz, gz);
+                                gx = ff2{z2, z2};
+                                gy = ff2{z2, z2};
+                                gz = ff2{z2, z2};
+                            }
                         }
                         const int j2 = j + tsw;
                         const float4 ch0 = smem ? cw[j] : ldcg(cw + j);
@@ -1887,6 +1906,11 @@ __device__ __forceinline__ void greedy_body(const GreedyArgs &a)
                         f2_unpack(g.l, l0, l1);
                         return ff_add(ff_add(two_sum(h0, l0), two_sum(h1, l1)), two_sum(f.h, f.l));
                     };
+                    if (blocked) {
+                        gx = ff_add2(tx, two_sum2(gx.h, gx.l));
+                        gy = ff_add2(ty, two_sum2(gy.h, gy.l));
+                        gz = ff_add2(tz, two_sum2(gz.h, gz.l));
+                    }
                     ff sx = lane_sum(gx, fx), sy = lane_sum(gy, fy), sz = lane_sum(gz, fz);
                     for (int o = 1; o < min(tsw, 32); o <<= 1) {
                         sx = ff_add(sx, ff{__shfl_xor_sync(0xffffffffu, sx.h, o),

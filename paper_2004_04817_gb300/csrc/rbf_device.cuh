@@ -243,12 +243,29 @@ __host__ __device__ __forceinline__ double grid_unit(double xmax)
     return ldexp(1.0, k - 23);
 }
 
+// x rounded to the nearest multiple of the power of two q, ties to even
+// (the value of q rint(x / q)), for |x| / q < 2^51: x + 1.5 2^52 q has q as
+// its unit in the last place, so the addition rounds x to the grid and the
+// subtraction is exact.  Two FP64 additions replace a division (a long FP64
+// sequence, and FP64 is the slowest pipe of this GPU).  The one difference:
+// x = -0 gives +0.
+__host__ __device__ __forceinline__ double round_to_grid(double x, double q)
+{
+    const double s = 6755399441055744.0 * q;   // 1.5 2^52 q
+#ifdef __CUDA_ARCH__
+    return __dsub_rn(__dadd_rn(x, s), s);
+#else
+    return (x + s) - s;
+#endif
+}
+
 __host__ __device__ __forceinline__ void split_grid(double x, double G, float &h, float &l)
 {
-    const double hd = rint(x / G) * G;
+    // |x| < 2^k: |x| / G < 2^23 and |x - hd| / g <= 2^23
+    const double hd = round_to_grid(x, G);
     const double g = G * 5.9604644775390625e-08;   // G 2^-24
     h = (float)hd;
-    l = (float)(rint((x - hd) / g) * g);
+    l = (float)round_to_grid(x - hd, g);
 }
 
 // Largest |x| / R over the volume points and the selected centres, as the
@@ -258,20 +275,21 @@ static __global__ void k_grid_max(const double *__restrict__ x, int64_t n, const
                            const int32_t *__restrict__ sel, int64_t nc, double inv_r,
                            unsigned long long *__restrict__ out)
 {
+    // max |x| first, one scaling at the end: rounding is monotonic, so
+    // fl(max |x| / R) = max fl(|x| / R)
     double mx = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * n;
          i += (int64_t)gridDim.x * blockDim.x)
-        mx = fmax(mx, fabs(x[i] * inv_r));
+        mx = fmax(mx, fabs(x[i]));
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = sel[j];
-        mx = fmax(mx, fmax(fabs(xb[3 * q] * inv_r),
-                           fmax(fabs(xb[3 * q + 1] * inv_r), fabs(xb[3 * q + 2] * inv_r))));
+        mx = fmax(mx, fmax(fabs(xb[3 * q]), fmax(fabs(xb[3 * q + 1]), fabs(xb[3 * q + 2]))));
     }
     for (int o = 16; o > 0; o >>= 1)
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0)
-        atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+        atomicMax(out, (unsigned long long)__double_as_longlong(mx * inv_r));
 }
 
 __device__ __forceinline__ double grid_of(const unsigned long long *gmax)

@@ -685,12 +685,17 @@ def record_traffic(rep, kernel, launch, *srcs):
     """Write profiles/traffic_<kernel>.json from an ncu report: DRAM bytes of
     one launch (dram__bytes_read.sum + dram__bytes_write.sum) and a hash of the
     kernel's sources, so the benchmark reports the figure only while the
-    kernel is unchanged (see kernel_traffic)."""
+    kernel is unchanged (see kernel_traffic).  REPORT is an .ncu-rep file or
+    its raw page exported as CSV (`ncu -i REPORT --page raw --csv`)."""
     import csv
     import hashlib
     import io
-    out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True,
-                         text=True, check=True).stdout
+    if rep.endswith(".csv"):
+        with open(rep) as f:
+            out = f.read()
+    else:
+        out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True,
+                             text=True, check=True).stdout
     rows = list(csv.reader(io.StringIO(out)))
     hdr, units, data = rows[0], rows[1], rows[2:]
     d = dict(zip(hdr, data[int(launch)]))
@@ -704,7 +709,8 @@ def record_traffic(rep, kernel, launch, *srcs):
             h.update(f.read())
     rec = {"kernel": kernel, "report": os.path.basename(rep), "launch": int(launch),
            "dram_bytes_per_launch": tot, "sources": list(srcs), "sources_sha1": h.hexdigest(),
-           "duration": d.get("gpu__time_duration.sum")}
+           "duration": "%s %s" % (d.get("gpu__time_duration.sum"),
+                                  units[hdr.index("gpu__time_duration.sum")])}
     with open(os.path.join(ROOT, "profiles", f"traffic_{kernel}.json"), "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps(rec))

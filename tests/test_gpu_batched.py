@@ -147,3 +147,64 @@ def test_batched_config4a_sizes_follow_oracle():
         ref = oracle.rbf_sum(c["xv"][sample], c["xb"], idx, Wo, 2.0)
         got = vb.dv[i].cpu().numpy()[sample]
         assert np.abs(got - ref).max() <= 1e-5 * dmax
+
+
+def test_batched_config4a_full_batch_certified():
+    """The whole 64-wing batch at the sizes and settings the benchmark times
+    (N_b 5.4k-99k, 200,000 volume points each, tol 1e-4 relative, m = 1.5
+    N_b / N_c from a plain-greedy batch): every problem ends certified, i.e.
+    the oracle's FP64 error of every boundary node with weights solved on the
+    selected set is at most E* (the stopping rule of Sec. 3); weights and
+    sampled volume displacements match the oracle; the two largest problems'
+    selections are replayed by the oracle's follow mode."""
+    from _follow import check_follow
+    seeds = list(range(100, 164))
+    cases = [_config4a_case(s, 200_000) for s in seeds]
+    base = []
+    for s, c in zip(seeds, cases):
+        c["d_xb"], c["d_db"], c["d_xv"] = cuda(c["xb"]), cuda(c["db"]), cuda(c["xv"])
+        base.append(dict(xb=c["d_xb"], db=c["d_db"], radius=2.0, tol=c["tol_rel"], tol_mode=1,
+                         seed=s, nc_max=1024))
+    cal = P.GreedyBatch([dict(q, m=1) for q in base])
+    cal.run()
+    ms = [max(1, int(round(1.5 * len(c["xb"]) / r["nc"])))
+          for c, r in zip(cases, cal.results())]
+    del cal
+    gb = P.GreedyBatch([dict(q, m=m) for q, m in zip(base, ms)])
+    gb.run()
+    res = gb.results()
+    vb = P.VolumeBatch([dict(xv=c["d_xv"], xb=c["d_xb"], idx=gb.idx[i], w=gb.w[i],
+                             nc_ptr=gb.nc_ptr + 8 * i, radius=2.0)
+                        for i, c in enumerate(cases)])
+    vb.run()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    for i, (s, c) in enumerate(zip(seeds, cases)):
+        r = res[i]
+        assert r["status"] == 0, (s, r["status"])
+        nc = r["nc"]
+        idx = gb.idx[i][:nc].cpu().numpy()
+        assert len(np.unique(idx)) == nc
+        estar = oracle.tolerance(c["db"], c["tol_rel"])
+        assert r["final_max"] <= estar * (1.0 + 1e-12), (s, r["final_max"], estar)
+        dmax = np.abs(c["db"]).max()
+        Wo, st, _ = oracle.solve_weights(c["xb"], c["db"], idx, 2.0)
+        assert st == 0
+        assert np.abs(gb.w[i][:nc].cpu().numpy() - Wo).max() <= 1e-5 * dmax, s
+        # every node within E*: the certificate of the stopping rule
+        E = np.linalg.norm(c["db"] - oracle.rbf_sum(c["xb"], c["xb"], idx, Wo, 2.0), axis=1)
+        assert E.max() <= estar * (1.0 + 1e-6), (s, E.max(), estar)
+        sample = np.sort(rng.choice(len(c["xv"]), 200, replace=False))
+        ref = oracle.rbf_sum(c["xv"][sample], c["xb"], idx, Wo, 2.0)
+        got = vb.dv[i].cpu().numpy()[sample]
+        assert np.abs(got - ref).max() <= 1e-5 * dmax, s
+    for i in sorted(range(len(cases)), key=lambda k: -len(cases[k]["xb"]))[:2]:
+        c, r = cases[i], res[i]
+        nc = r["nc"]
+        idx = gb.idx[i][:nc].cpu().numpy()
+        it = gb.iter[i][:nc].cpu().numpy()
+        estar = oracle.tolerance(c["db"], c["tol_rel"])
+        f = oracle.greedy(c["xb"], c["db"], 2.0, estar, m=ms[i], seed=seeds[i], follow=(idx, it),
+                          tie_rel=1e-6, history=False)
+        check_follow(f, f"64-wing batch, seed {seeds[i]}, N_b {len(c['xb'])}, m={ms[i]}, N_c {nc}")
+        assert f["nc"] == nc and f["stats"]["iterations"] == r["iterations"]

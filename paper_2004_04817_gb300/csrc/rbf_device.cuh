@@ -369,6 +369,19 @@ __device__ __forceinline__ ff2 fast_two_sum2(f2 a, f2 b)
     return ff2{s, f2_sub(b, f2_sub(s, a))};
 }
 
+// TwoSum of two non-negative paired values: FastTwoSum on (max, min) gives
+// the same (s, e), since both compute the rounded sum and its exact error,
+// with three FP32-pipe operations instead of six (and four min/max on the
+// ALU pipe, which the pair kernels leave less busy).
+__device__ __forceinline__ ff2 two_sum2_nn(f2 a, f2 b)
+{
+    float a0, a1, b0, b1;
+    f2_unpack(a, a0, a1);
+    f2_unpack(b, b0, b1);
+    return fast_two_sum2(f2_pack(fmaxf(a0, b0), fmaxf(a1, b1)),
+                         f2_pack(fminf(a0, b0), fminf(a1, b1)));
+}
+
 __device__ __forceinline__ ff2 ff_add2(ff2 a, ff2 b)
 {
     const ff2 s = two_sum2(a.h, b.h);
@@ -423,8 +436,8 @@ __device__ __forceinline__ ff2 dist2_gs2(f2 qxh, f2 qxl, f2 qyh, f2 qyl, f2 qzh,
     gs_square2(qxh, qxl, cxh, cxl, px, ex);
     gs_square2(qyh, qyl, cyh, cyl, py, ey);
     gs_square2(qzh, qzl, czh, czl, pz, ez);
-    const ff2 s1 = two_sum2(px, py);
-    const ff2 s2 = two_sum2(s1.h, pz);
+    const ff2 s1 = two_sum2_nn(px, py);   // squares: non-negative
+    const ff2 s2 = two_sum2_nn(s1.h, pz);
     const f2 lo = f2_add(f2_add(f2_add(ex, ey), ez), f2_add(s1.l, s2.l));
     return fast_two_sum2(s2.h, lo);
 }
@@ -445,7 +458,7 @@ __device__ __forceinline__ ff2 phi_ff2_s(ff2 s)
     t = fast_two_sum2(t.h, f2_sub(t.l, eta.l));
     const ff2 t2 = ff_sqr2(t);
     const ff2 t4 = ff_sqr2(t2);
-    ff2 p = two_sum2(f2_bcast(1.0f), f2_mul(f2_bcast(4.0f), eta.h));
+    ff2 p = two_sum2_nn(f2_bcast(1.0f), f2_mul(f2_bcast(4.0f), eta.h));   // eta >= 0
     p = fast_two_sum2(p.h, f2_fma(f2_bcast(4.0f), eta.l, p.l));
     ff2 ph = ff_mul2(t4, p);
     float e0a, e0b;

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "../../include/rbfgcb.h"
@@ -243,29 +244,61 @@ __host__ __device__ __forceinline__ double grid_unit(double xmax)
     return ldexp(1.0, k - 23);
 }
 
-// x rounded to the nearest multiple of the power of two q, ties to even
-// (the value of q rint(x / q)), for |x| / q < 2^51: x + 1.5 2^52 q has q as
-// its unit in the last place, so the addition rounds x to the grid and the
-// subtraction is exact.  Two FP64 additions replace a division (a long FP64
-// sequence, and FP64 is the slowest pipe of this GPU).  The one difference:
-// x = -0 gives +0.
-__host__ __device__ __forceinline__ double round_to_grid(double x, double q)
+// Magnitude m (an integer) rounded to the nearest multiple of 2^sh, ties to
+// even, returned as the count of 2^sh; sh >= 64 gives 0.
+__host__ __device__ __forceinline__ uint64_t rne_shift(uint64_t m, int sh)
 {
-    const double s = 6755399441055744.0 * q;   // 1.5 2^52 q
-#ifdef __CUDA_ARCH__
-    return __dsub_rn(__dadd_rn(x, s), s);
-#else
-    return (x + s) - s;
-#endif
+    if (sh <= 0)
+        return m << (-sh);
+    if (sh >= 64)
+        return 0;
+    const uint64_t q = m >> sh, rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
 }
 
+// The split with integer operations on the bits of x, which give exactly
+// G rint(x / G) and g rint((x - h) / g) (ties to even): with |x| = M 2^E
+// (M the 53-bit significand), H = M rounded at bit kg - E is the count of
+// G, R = M - H 2^(kg - E) is x - h in units of 2^E (exact), and L = R
+// rounded at bit kg - 24 - E is the count of g.  H and |L| are at most
+// 2^23, so h = +-H G and l = +-L g are floats.  No FP64 arithmetic: FP64 is
+// the slowest pipe of this GPU, and the rounding by FP64 divisions (or by
+// adding and subtracting 1.5 2^52 G) made the packing of the volume points
+// FP64-bound.  Zero and subnormal x (far below g) split into +0, +0, and a
+// zero part is +0, as the FP64 rounding gives.
 __host__ __device__ __forceinline__ void split_grid(double x, double G, float &h, float &l)
 {
-    // |x| < 2^k: |x| / G < 2^23 and |x - hd| / g <= 2^23
-    const double hd = round_to_grid(x, G);
-    const double g = G * 5.9604644775390625e-08;   // G 2^-24
-    h = (float)hd;
-    l = (float)round_to_grid(x - hd, g);
+    uint64_t b, bg;
+#ifdef __CUDA_ARCH__
+    b = (uint64_t)__double_as_longlong(x);
+    bg = (uint64_t)__double_as_longlong(G);
+#else
+    memcpy(&b, &x, 8);
+    memcpy(&bg, &G, 8);
+#endif
+    h = 0.0f;
+    l = 0.0f;
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0)
+        return;
+    const int kg = (int)((bg >> 52) & 0x7ff) - 1023;            // G = 2^kg, kg >= -122
+    const uint64_t M = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const bool neg = (b >> 63) != 0;
+    const int shH = kg - (e - 1075);                            // >= 30 when |x| < 2^(kg + 23)
+    const uint64_t H = shH >= 54 ? 0 : rne_shift(M, shH);
+    const int64_t R = shH >= 54 ? (int64_t)M : (int64_t)M - (int64_t)(H << shH);
+    const bool rneg = R < 0;
+    const uint64_t L = rne_shift(rneg ? (uint64_t)(-R) : (uint64_t)R, shH - 24);
+#ifdef __CUDA_ARCH__
+    const float Gf = __int_as_float((kg + 127) << 23);            // 2^kg, a normal float
+#else
+    const float Gf = ldexpf(1.0f, kg);
+#endif
+    const float gf = Gf * 5.9604644775390625e-08f;              // 2^(kg - 24), exact
+    if (H)
+        h = (neg ? -(float)(uint32_t)H : (float)(uint32_t)H) * Gf;
+    if (L)
+        l = ((neg != rneg) ? -(float)(uint32_t)L : (float)(uint32_t)L) * gf;
 }
 
 // Largest |x| / R over the volume points and the selected centres, as the
